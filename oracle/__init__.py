@@ -1,0 +1,181 @@
+"""Python front end of the FP64 WSR oracle (``wsr_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
+CPU-baseline leg are the only callers.  The CUDA library never imports this
+package and this package never imports the CUDA library; the two share only
+the seeded generators of ``wsr_scenes``.
+
+Every array handed to the C code is float64; scenes made by ``wsr_scenes``
+hold float32 values, which are upcast exactly, so the oracle sees the same
+numbers as the GPU.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "wsr_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libwsr_oracle.so")
+PROJ_STRIDE = 22
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (portable flags, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", _SRC, "-o", tmp, "-lm", "-lpthread"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            dp = ctypes.POINTER(ctypes.c_double)
+            common = [ctypes.c_long, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, dp,
+                      dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp]
+            lib.wsro_project.argtypes = common + [dp]
+            lib.wsro_render.argtypes = common + [ctypes.c_int, dp, dp, dp, ctypes.c_double,
+                                                 ctypes.POINTER(ctypes.c_longlong)]
+            lib.wsro_render_pixels.argtypes = common + [ctypes.c_int, ctypes.c_long,
+                                                        ctypes.POINTER(ctypes.c_int), dp, dp, dp,
+                                                        ctypes.c_double]
+            lib.wsro_grad.argtypes = common + [ctypes.c_int, dp] + [dp] * 8
+            lib.wsro_sh_basis.argtypes = [ctypes.c_long, ctypes.c_int, dp, dp, dp]
+            for f in (lib.wsro_project, lib.wsro_render, lib.wsro_render_pixels, lib.wsro_grad,
+                      lib.wsro_sh_basis):
+                f.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _d(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+class _Args:
+    """Marshalled (scene, camera, weight) argument block."""
+
+    def __init__(self, scene, cam, weight):
+        self.keep = [_d(scene.means), _d(scene.log_scales), _d(scene.quats), _d(scene.sh),
+                     _d(scene.opacity), _d(scene.lc_v)]
+        cam16 = np.concatenate([np.asarray(cam.R, np.float64).reshape(9),
+                                np.asarray(cam.T, np.float64).reshape(3),
+                                [cam.fx, cam.fy, cam.cx, cam.cy]]).astype(np.float64)
+        wpar = np.array([weight.sigma, weight.beta, weight.w_bg, *weight.c_bg], np.float64)
+        self.keep += [cam16, wpar]
+        self.n = scene.n
+        self.K = (scene.sh_degree + 1) ** 2
+        self.vd = bool(scene.view_dependent_opacity)
+        self.args = ([ctypes.c_long(scene.n), ctypes.c_int(scene.sh_degree), ctypes.c_int(int(self.vd))]
+                     + [_ptr(a) for a in self.keep[:6]]
+                     + [_ptr(cam16), ctypes.c_int(cam.width), ctypes.c_int(cam.height),
+                        ctypes.c_double(cam.znear), ctypes.c_int(weight.kind), _ptr(wpar)])
+
+
+def project(scene, cam, weight) -> dict:
+    """Per-Gaussian projection table (Eqs. 3-5, 4, 11, 8-10)."""
+    lib = _load()
+    a = _Args(scene, cam, weight)
+    out = np.zeros((scene.n, PROJ_STRIDE), np.float64)
+    rc = lib.wsro_project(*a.args, _ptr(out))
+    if rc:
+        raise RuntimeError(f"wsro_project failed ({rc})")
+    return dict(visible=out[:, 0] > 0.5, t=out[:, 1:4], mean2d=out[:, 4:6], cov2d=out[:, 6:9],
+                conic=out[:, 9:12], color=out[:, 12:15], u=out[:, 15], w=out[:, 16],
+                depth=out[:, 17], rx=out[:, 18], ry=out[:, 19])
+
+
+def render(scene, cam, weight, *, threads: int | None = None, amb_tau: float | None = None):
+    """Full-image WSR forward (Eq. 7).
+
+    Returns dict(rgb [H, W, 3], den [H, W] = w_B + sum a_i, pairs, amb [H, W]
+    or None).  ``amb`` bounds how far a pixel can move if the pairs within
+    ``amb_tau`` of the q <= 9 cutoff were decided the other way.
+    """
+    lib = _load()
+    a = _Args(scene, cam, weight)
+    H, W = cam.height, cam.width
+    rgb = np.zeros((H, W, 3), np.float64)
+    den = np.zeros((H, W), np.float64)
+    amb = np.zeros((H, W), np.float64) if amb_tau is not None else None
+    pairs = ctypes.c_longlong(0)
+    rc = lib.wsro_render(*a.args, ctypes.c_int(threads or default_threads()), _ptr(rgb), _ptr(den),
+                         _ptr(amb), ctypes.c_double(amb_tau or 0.0), ctypes.byref(pairs))
+    if rc:
+        raise RuntimeError(f"wsro_render failed ({rc})")
+    return dict(rgb=rgb, den=den, pairs=int(pairs.value), amb=amb)
+
+
+def render_pixels(scene, cam, weight, xy, *, threads: int | None = None, amb_tau: float = 0.0):
+    """WSR at the listed pixels (``xy`` [M, 2] int: column, row), each summed
+    over every Gaussian.  Returns dict(rgb [M, 3], den [M], amb [M])."""
+    lib = _load()
+    a = _Args(scene, cam, weight)
+    xy = np.ascontiguousarray(np.asarray(xy, dtype=np.int32))
+    m = xy.shape[0]
+    rgb = np.zeros((m, 3), np.float64)
+    den = np.zeros(m, np.float64)
+    amb = np.zeros(m, np.float64)
+    rc = lib.wsro_render_pixels(*a.args, ctypes.c_int(threads or default_threads()), ctypes.c_long(m),
+                                xy.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _ptr(rgb), _ptr(den),
+                                _ptr(amb), ctypes.c_double(amb_tau))
+    if rc:
+        raise RuntimeError(f"wsro_render_pixels failed ({rc})")
+    return dict(rgb=rgb, den=den, amb=amb)
+
+
+def grad(scene, cam, weight, grad_rgb, *, threads: int | None = None) -> dict:
+    """Analytic gradient of <grad_rgb, C> with respect to every parameter."""
+    lib = _load()
+    a = _Args(scene, cam, weight)
+    n, K = scene.n, a.K
+    G = _d(grad_rgb).reshape(cam.height, cam.width, 3)
+    out = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
+               sh=np.zeros((n, K, 3)), opacity=np.zeros((n, K)) if a.vd else np.zeros(n),
+               lc_v=np.zeros(n), wpar=np.zeros(6), g2d=np.zeros((n, 9)))
+    rc = lib.wsro_grad(*a.args, ctypes.c_int(threads or default_threads()), _ptr(G),
+                       _ptr(out["means"]), _ptr(out["log_scales"]), _ptr(out["quats"]),
+                       _ptr(out["sh"]), _ptr(out["opacity"]), _ptr(out["lc_v"]),
+                       _ptr(out["wpar"]), _ptr(out["g2d"]))
+    if rc:
+        raise RuntimeError(f"wsro_grad failed ({rc})")
+    return out
+
+
+def sh_basis(dirs, deg: int, with_grad: bool = False):
+    """Real SH basis Y[M, K] (and polynomial gradient [M, K, 3]) at unit dirs."""
+    lib = _load()
+    d = _d(dirs).reshape(-1, 3)
+    K = (deg + 1) ** 2
+    Y = np.zeros((d.shape[0], K))
+    dY = np.zeros((d.shape[0], K, 3)) if with_grad else None
+    rc = lib.wsro_sh_basis(ctypes.c_long(d.shape[0]), ctypes.c_int(deg), _ptr(d), _ptr(Y), _ptr(dY))
+    if rc:
+        raise RuntimeError("wsro_sh_basis failed")
+    return (Y, dY) if with_grad else Y
