@@ -36,22 +36,30 @@ def tiny_scene(seed, deg, vd, n=40, box=1.2, ls=-2.2):
                          log_scale_mu=ls, log_scale_sd=0.4)
     K = (deg + 1) ** 2
     extra_means = np.array([[0.1, 0.0, -3.1],    # behind / at the camera (camera at z=-3)
+                            [0.3, -2.2, -0.6],   # above the image: t_y/t_z beyond the clamp
                             [2.6, 0.2, -0.5],    # off to the side: t_x/t_z beyond the clamp
                             [-0.1, 0.1, -2.2]])  # close to the camera: large footprint
-    extra_ls = np.array([[-2.0, -2.0, -2.0], [-0.6, -1.0, -0.8], [-2.5, -2.2, -2.4]])
+    extra_ls = np.array([[-2.0, -2.0, -2.0], [-0.9, -0.6, -0.8], [-0.6, -1.0, -0.8], [-2.5, -2.2, -2.4]])
+    m = extra_means.shape[0]
     rng = np.random.default_rng(seed + 100)
-    q = rng.normal(size=(3, 4))
+    q = rng.normal(size=(m, 4))
     q /= np.linalg.norm(q, axis=1, keepdims=True)
-    sh = rng.normal(0, 0.3, size=(3, K, 3))
-    op = (np.abs(rng.normal(0.5, 0.2, size=(3, K))) if vd else rng.normal(size=3))
+    sh = rng.normal(0, 0.3, size=(m, K, 3))
+    op = (np.abs(rng.normal(0.5, 0.2, size=(m, K))) if vd else rng.normal(size=m))
     return _scene(np.concatenate([sc.means, extra_means]), np.concatenate([sc.log_scales, extra_ls]),
                   np.concatenate([sc.quats, q]), np.concatenate([sc.sh, sh]),
-                  np.concatenate([sc.opacity, op]), np.concatenate([sc.lc_v, rng.uniform(0.05, 0.15, 3)]),
+                  np.concatenate([sc.opacity, op]), np.concatenate([sc.lc_v, rng.uniform(0.05, 0.15, m)]),
                   deg, vd)
 
 
 def tiny_cam(w=40, h=30):
-    return ws.look_at((0.0, 0.0, -3.0), width=w, height=h)
+    """Camera with unequal focal lengths and an off-centre principal point, so
+    that a mix-up of x and y intrinsics changes the result."""
+    c = ws.look_at((0.0, 0.0, -3.0), width=w, height=h)
+    c.fy = c.fx * 1.15
+    c.cx = 0.47 * w
+    c.cy = 0.54 * h
+    return c
 
 
 WEIGHTS = [ws.WeightParams(ws.DIR, 0.0, 0.0, 1.0, (0.0, 0.0, 0.0)),
@@ -359,8 +367,12 @@ def test_gradient_matches_finite_differences(wi, deg, vd):
         assert e < 2e-6, (name, e, worst)
     # the clamped off-screen Gaussian and the culled one are part of the test
     P = oracle.project(sc, cam, WEIGHTS[wi])
-    assert not P["visible"][-3]
-    assert np.abs(an["means"][-2]).max() > 0   # clamped Gaussian contributes
+    assert not P["visible"][-4]
+    lx, ly = 1.3 * 0.5 * cam.width / cam.fx, 1.3 * 0.5 * cam.height / cam.fy
+    t = P["t"]
+    assert abs(t[-3, 1] / t[-3, 2]) > ly and abs(t[-2, 0] / t[-2, 2]) > lx
+    assert np.abs(an["means"][-3]).max() > 0   # both clamped Gaussians contribute
+    assert np.abs(an["means"][-2]).max() > 0
 
 
 def test_gradient_2d_records_match_finite_differences_of_projection_outputs():
