@@ -1,0 +1,273 @@
+/*
+ * wsr.h — C ABI of the GB300 (sm_103a) Weighted Sum Rendering library.
+ *
+ * Weighted Sum Rendering (WSR) renders a 3D Gaussian scene without sorting:
+ * every pixel is the order-independent weighted sum of Eq. 7 of "Sort-free
+ * Gaussian Splatting via Weighted Sum Rendering" (arXiv 2410.18931),
+ *
+ *     C = (c_B w_B + sum_i c_i a_i) / (w_B + sum_i a_i),
+ *     a_i = u_i w(d_i) exp(-q_i / 2),      q_i <= 9 (3-sigma footprint),
+ *
+ * with the depth weights w(d) of Eqs. 8-10 and the view-dependent opacity
+ * u_i of Eq. 11.  The hot path is four calls:
+ *
+ *     wsr_project     per-Gaussian projection (Sec. 3 Eqs. 3-5, Eq. 4, Eq. 11,
+ *                     Eqs. 8-10) into a 48-byte render record per view
+ *     wsr_bin         sort-free tile binning: per-tile count, prefix scan and
+ *                     unordered scatter (Sec. 4.1, Fig. 2 without the sort)
+ *     wsr_render_fwd  per-pixel accumulation of Eq. 7
+ *     wsr_render_bwd  gradient of Eq. 7 and of the projection chain with
+ *                     respect to every stored parameter
+ *
+ * Conventions for every call:
+ *   - All data pointers are DEVICE pointers owned by the caller.  The library
+ *     allocates no memory; scratch comes from a caller-provided workspace
+ *     whose size wsr_workspace_size() returns (256-byte aligned).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy stream).  All
+ *     work is enqueued asynchronously on it; no call synchronises the stream
+ *     except wsr_check() and wsr_bin_total().
+ *   - Every call returns a wsr_status.  Argument errors are found on the host
+ *     before anything is enqueued (WSR_ERR_INVALID_ARG / WSR_ERR_UNSUPPORTED).
+ *     Errors found on the device (tile-list overflow) are recorded in the
+ *     workspace and reported by wsr_check().  Launch failures return
+ *     WSR_ERR_CUDA.  No call aborts, throws or exits.
+ *   - Camera convention: world-to-camera rotation R (row-major) and
+ *     translation T, camera axes x right, y down, z forward; pixel (x, y) has
+ *     its centre at (x + 0.5, y + 0.5).
+ */
+#ifndef WSR_H
+#define WSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WSR_OK = 0,
+    WSR_ERR_INVALID_ARG = 1,  /* null pointer, bad size, bad enum, too-small workspace */
+    WSR_ERR_CAPACITY = 2,     /* the tile list did not fit in list_capacity */
+    WSR_ERR_CUDA = 3,         /* a CUDA launch or runtime call failed */
+    WSR_ERR_TIMEOUT = 4,      /* reserved: no kernel of this library waits on another */
+    WSR_ERR_UNSUPPORTED = 5   /* valid but unsupported combination (e.g. tile shape) */
+} wsr_status;
+
+/* Storage types of Gaussian parameter arrays. */
+enum { WSR_F32 = 0, WSR_F16 = 1, WSR_BF16 = 2 };
+/* Depth-weight functions: Eq. 8 (DIR), Eq. 9 (EXP), Eq. 10 (LC). */
+enum { WSR_WEIGHT_DIR = 0, WSR_WEIGHT_EXP = 1, WSR_WEIGHT_LC = 2 };
+/* Opacity: sigmoid of a logit (Eq. 3's t_i) or view-dependent SH (Eq. 11). */
+enum { WSR_OPACITY_LOGIT = 0, WSR_OPACITY_SH = 1 };
+
+#define WSR_MAX_VIEWS 32
+#define WSR_RECORD_FLOATS 12      /* one render record: 48 bytes */
+#define WSR_GRAD_RECORD_FLOATS 9  /* one 2D gradient record: 36 bytes */
+
+/* Pinhole camera (passed by value through host memory). */
+typedef struct {
+    float R[9];          /* world -> camera rotation, row-major */
+    float T[3];          /* world -> camera translation */
+    float fx, fy;        /* focal lengths, pixels */
+    float cx, cy;        /* principal point, pixels */
+    int32_t width, height;
+    float znear;         /* Gaussians with camera z <= znear are culled (App. C) */
+} wsr_camera;
+
+/*
+ * Gaussian scene 𝒢 = {(p_i, t_i or H^alpha_i, q_i, s_i, H_i)} (Sec. 3).
+ * K = (sh_degree + 1)^2.  All arrays are dense, row-major, device memory.
+ *   means       [n, 3]  float32                    centres p_i
+ *   log_scales  [n, 3]  dtype_scales_quats          log s_i  (s = exp(.))
+ *   quats       [n, 4]  dtype_scales_quats          q_i = (w, x, y, z), any norm
+ *   sh          [n, K, 3] dtype_sh                  colour SH H_i (Eq. 4)
+ *   opacity     [n] logit (WSR_OPACITY_LOGIT) or [n, K] SH (WSR_OPACITY_SH),
+ *               dtype_sh
+ *   lc_v        [n] float32, the per-Gaussian v_i of Eq. 10 (required for LC,
+ *               ignored otherwise, may then be NULL)
+ * Reduced-precision storage: dtype_scales_quats in {WSR_F32, WSR_BF16},
+ * dtype_sh in {WSR_F32, WSR_F16}.  Every array must be 16-byte aligned.
+ */
+typedef struct {
+    int64_t n;
+    int32_t sh_degree;           /* 0..3 */
+    int32_t opacity_mode;        /* WSR_OPACITY_LOGIT or WSR_OPACITY_SH */
+    int32_t dtype_scales_quats;
+    int32_t dtype_sh;
+    const float* means;
+    const void* log_scales;
+    const void* quats;
+    const void* sh;
+    const void* opacity;
+    const float* lc_v;
+} wsr_gaussians;
+
+/*
+ * Depth weight w(d) and background.  `params` points to 6 device floats:
+ * [sigma, beta, w_B, c_B.r, c_B.g, c_B.b].  EXP (Eq. 9) uses sigma and beta,
+ * LC (Eq. 10) uses sigma (and the per-Gaussian v_i), DIR (Eq. 8) neither.
+ * Keeping them on the device lets them change between graph replays.
+ */
+typedef struct {
+    int32_t kind;                /* WSR_WEIGHT_* */
+    const float* params;         /* device [6] */
+} wsr_weight;
+
+/* Tile shape for binning and rendering.  Supported: 16x16, 8x8, 32x8, 16x8. */
+typedef struct {
+    int32_t tile_w, tile_h;
+} wsr_tiles;
+
+/*
+ * Gradient outputs (device float32, OVERWRITTEN by wsr_render_bwd), shaped
+ * like the parameters: means [n,3], log_scales [n,3], quats [n,4],
+ * sh [n,K,3], opacity [n] or [n,K], lc_v [n], weight_params [6] (sigma, beta,
+ * w_B, c_B).  Gradients over several views are summed.  A NULL member skips
+ * writing that output (the others are still computed).
+ */
+typedef struct {
+    float* means;
+    float* log_scales;
+    float* quats;
+    float* sh;
+    float* opacity;
+    float* lc_v;
+    float* weight_params;
+} wsr_grads;
+
+/* Human-readable message of a status code (static string). */
+const char* wsr_status_string(wsr_status s);
+
+/* Library version, as major * 10000 + minor * 100 + patch. */
+int32_t wsr_version(void);
+
+/* Total tiles over all views for the tile shape (0 on invalid arguments). */
+int64_t wsr_num_tiles(const wsr_camera* cams, int32_t n_cams, const wsr_tiles* tiles);
+
+/* Total pixels over all views (the rows of out_rgb / out_den). */
+int64_t wsr_num_pixels(const wsr_camera* cams, int32_t n_cams);
+
+/*
+ * Workspace bytes needed by wsr_bin / wsr_render_fwd / wsr_render_bwd for
+ * these views and tile shape (the same workspace serves all of them; it may
+ * be reused across calls on the same stream).  0 on invalid arguments.
+ */
+size_t wsr_workspace_size(const wsr_camera* cams, int32_t n_cams, const wsr_tiles* tiles);
+
+/*
+ * wsr_project — projection of every Gaussian into every view.
+ * Sec. 3 Eq. 3 (Sigma = R S S^t R^t), Eq. 5 (Sigma_2D = J W Sigma W^t J^t,
+ * plus the 3DGS 0.3-pixel dilation and Jacobian clamp), Eq. 4 (SH colour,
+ * RGB = max(0, Y.H + 0.5)), Eq. 11 / Eq. 3 (opacity), Eqs. 8-10 (weight),
+ * App. C (near-plane culling).
+ *   records  [n_cams, n, 12] float32 output.  Per Gaussian and view:
+ *            {mu_x, mu_y, A', 2B', C', u w, c_r u w, c_g u w, c_b u w,
+ *             rx, ry, depth}, where (A, B, C) is the conic Sigma_2D^{-1},
+ *            primed entries are multiplied by log2(e)/2, and rx, ry are the
+ *            3-sigma half extents in pixels.  rx < 0 marks a culled Gaussian.
+ */
+wsr_status wsr_project(const wsr_gaussians* g, const wsr_camera* cams, int32_t n_cams,
+                       const wsr_weight* w, float* records, void* stream);
+
+/*
+ * wsr_bin — sort-free tile binning (Sec. 4.1: tiles and per-tile replication
+ * as in 3DGS, with the depth sort removed because Eq. 7 is order-independent).
+ *   records        [n_cams, n, 12] from wsr_project
+ *   tile_offsets   [num_tiles + 1] uint32 output: exclusive prefix sum of the
+ *                  per-tile counts; tile t owns tile_list[offsets[t], offsets[t+1])
+ *   tile_list      [list_capacity] uint32 output: record indices (view * n + i),
+ *                  in no particular order within a tile
+ *   list_capacity  entries available in tile_list
+ * The total instance count is tile_offsets[num_tiles].  If it exceeds
+ * list_capacity, nothing is written past the end, every offset is clamped to
+ * list_capacity (so the render calls stay in bounds, with incomplete tiles),
+ * the workspace records WSR_ERR_CAPACITY (see wsr_check) and the true total
+ * (wsr_bin_total); the caller grows the list and runs the frame again.
+ */
+wsr_status wsr_bin(const float* records, int64_t n, const wsr_camera* cams, int32_t n_cams,
+                   const wsr_tiles* tiles, uint32_t* tile_offsets, uint32_t* tile_list,
+                   uint64_t list_capacity, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * wsr_bin_count — first half of wsr_bin (count + scan only), for callers that
+ * size tile_list exactly: read the total with wsr_bin_total afterwards.
+ * tile_offsets is written unclamped.
+ */
+wsr_status wsr_bin_count(const float* records, int64_t n, const wsr_camera* cams, int32_t n_cams,
+                         const wsr_tiles* tiles, uint32_t* tile_offsets, void* workspace,
+                         size_t workspace_bytes, void* stream);
+
+/*
+ * Synchronises `stream` and returns in *total the number of tile instances
+ * (Gaussian-tile pairs) counted by the last wsr_bin / wsr_bin_count that used
+ * this workspace, before any clamping to the list capacity.
+ */
+wsr_status wsr_bin_total(const void* workspace, size_t workspace_bytes, uint64_t* total, void* stream);
+
+/*
+ * wsr_render_fwd — Eq. 7 per pixel, one thread block per tile.
+ *   out_rgb  [num_pixels, 3] float32 output, views concatenated in order, each
+ *            view row-major (y * width + x)
+ *   out_den  [num_pixels] float32 output: the full denominator w_B + sum a_i
+ *            (kept for the backward pass)
+ */
+wsr_status wsr_render_fwd(const float* records, int64_t n, const uint32_t* tile_offsets,
+                          const uint32_t* tile_list, const wsr_camera* cams, int32_t n_cams,
+                          const wsr_tiles* tiles, const wsr_weight* w, float* out_rgb,
+                          float* out_den, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * wsr_render_bwd — gradient of a scalar loss L through Eq. 7 and the
+ * projection, given grad_rgb = dL/dC.  Two stages:
+ *   (1) per tile, recompute every (pixel, Gaussian) term from the records and
+ *       reduce into grad_records [n_cams, n, 9] float32 (overwritten):
+ *       {dL/dmu_x, dL/dmu_y, dL/dA, dL/dB, dL/dC, dL/d(uw) at fixed c uw,
+ *        dL/d(c uw) (3)}; (A, B, C) unscaled conic, B counted once;
+ *       plus the background terms dL/dw_B, dL/dc_B;
+ *   (2) per Gaussian, chain grad_records back to the stored parameters.
+ * `g` must be the scene given to wsr_project; out_rgb / out_den come from
+ * wsr_render_fwd on the same records.
+ */
+wsr_status wsr_render_bwd(const wsr_gaussians* g, const float* records, const uint32_t* tile_offsets,
+                          const uint32_t* tile_list, const wsr_camera* cams, int32_t n_cams,
+                          const wsr_tiles* tiles, const wsr_weight* w, const float* out_rgb,
+                          const float* out_den, const float* grad_rgb, float* grad_records,
+                          const wsr_grads* grads, void* workspace, size_t workspace_bytes,
+                          void* stream);
+
+/*
+ * The two stages of wsr_render_bwd as separate calls (same arguments and
+ * semantics; wsr_render_bwd is exactly wsr_render_bwd_tiles followed by
+ * wsr_project_bwd).  wsr_render_bwd_tiles overwrites grad_records and
+ * accumulates the background terms in the workspace; wsr_project_bwd adds the
+ * sigma/beta terms there and writes grads (weight_params included).
+ */
+wsr_status wsr_render_bwd_tiles(const float* records, int64_t n, const uint32_t* tile_offsets,
+                                const uint32_t* tile_list, const wsr_camera* cams, int32_t n_cams,
+                                const wsr_tiles* tiles, const wsr_weight* w, const float* out_rgb,
+                                const float* out_den, const float* grad_rgb, float* grad_records,
+                                void* workspace, size_t workspace_bytes, void* stream);
+wsr_status wsr_project_bwd(const wsr_gaussians* g, const wsr_camera* cams, int32_t n_cams,
+                           const wsr_weight* w, const float* grad_records, const wsr_grads* grads,
+                           void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * wsr_loss_l1 — mean absolute error against a target and its gradient
+ * (the L1 part of the 3DGS loss of Sec. 4.4, used to drive the backward).
+ *   loss_out [1] float32 (overwritten), grad_rgb [num_pixels * 3] (overwritten)
+ */
+wsr_status wsr_loss_l1(const float* rgb, const float* target, int64_t count, float* loss_out,
+                       float* grad_rgb, void* stream);
+
+/*
+ * wsr_check — synchronises `stream` and returns the first device-side error
+ * recorded in the workspace (WSR_OK if none), then clears it.
+ */
+wsr_status wsr_check(void* workspace, size_t workspace_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WSR_H */

@@ -1,0 +1,136 @@
+"""ctypes binding of ``libwsr.so`` (declarations in ``include/wsr.h``).
+
+Argument marshalling only: every function here forwards to the C ABI of the
+same name, turning torch tensors into device pointers and a torch stream into
+a ``cudaStream_t``.  A missing library is an error (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libwsr.so")
+
+WSR_OK, WSR_ERR_INVALID_ARG, WSR_ERR_CAPACITY, WSR_ERR_CUDA, WSR_ERR_TIMEOUT, WSR_ERR_UNSUPPORTED = range(6)
+WSR_F32, WSR_F16, WSR_BF16 = 0, 1, 2
+WSR_WEIGHT_DIR, WSR_WEIGHT_EXP, WSR_WEIGHT_LC = 0, 1, 2
+WSR_OPACITY_LOGIT, WSR_OPACITY_SH = 0, 1
+WSR_MAX_VIEWS = 32
+WSR_RECORD_FLOATS = 12
+WSR_GRAD_RECORD_FLOATS = 9
+
+_c_void_p = ctypes.c_void_p
+
+
+class wsr_camera(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_float * 9), ("T", ctypes.c_float * 3), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("znear", ctypes.c_float)]
+
+
+class wsr_gaussians(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32), ("opacity_mode", ctypes.c_int32),
+                ("dtype_scales_quats", ctypes.c_int32), ("dtype_sh", ctypes.c_int32),
+                ("means", _c_void_p), ("log_scales", _c_void_p), ("quats", _c_void_p),
+                ("sh", _c_void_p), ("opacity", _c_void_p), ("lc_v", _c_void_p)]
+
+
+class wsr_weight(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("params", _c_void_p)]
+
+
+class wsr_tiles(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32)]
+
+
+class wsr_grads(ctypes.Structure):
+    _fields_ = [("means", _c_void_p), ("log_scales", _c_void_p), ("quats", _c_void_p), ("sh", _c_void_p),
+                ("opacity", _c_void_p), ("lc_v", _c_void_p), ("weight_params", _c_void_p)]
+
+
+# name -> (restype, argtypes)
+_P = ctypes.POINTER
+_SIGS = {
+    "wsr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "wsr_version": (ctypes.c_int32, []),
+    "wsr_num_tiles": (ctypes.c_int64, [_P(wsr_camera), ctypes.c_int32, _P(wsr_tiles)]),
+    "wsr_num_pixels": (ctypes.c_int64, [_P(wsr_camera), ctypes.c_int32]),
+    "wsr_workspace_size": (ctypes.c_size_t, [_P(wsr_camera), ctypes.c_int32, _P(wsr_tiles)]),
+    "wsr_project": (ctypes.c_int, [_P(wsr_gaussians), _P(wsr_camera), ctypes.c_int32, _P(wsr_weight),
+                                   _c_void_p, _c_void_p]),
+    "wsr_bin": (ctypes.c_int, [_c_void_p, ctypes.c_int64, _P(wsr_camera), ctypes.c_int32, _P(wsr_tiles),
+                               _c_void_p, _c_void_p, ctypes.c_uint64, _c_void_p, ctypes.c_size_t, _c_void_p]),
+    "wsr_bin_count": (ctypes.c_int, [_c_void_p, ctypes.c_int64, _P(wsr_camera), ctypes.c_int32,
+                                     _P(wsr_tiles), _c_void_p, _c_void_p, ctypes.c_size_t, _c_void_p]),
+    "wsr_bin_total": (ctypes.c_int, [_c_void_p, ctypes.c_size_t, _P(ctypes.c_uint64), _c_void_p]),
+    "wsr_render_fwd": (ctypes.c_int, [_c_void_p, ctypes.c_int64, _c_void_p, _c_void_p, _P(wsr_camera),
+                                      ctypes.c_int32, _P(wsr_tiles), _P(wsr_weight), _c_void_p, _c_void_p,
+                                      _c_void_p, ctypes.c_size_t, _c_void_p]),
+    "wsr_render_bwd": (ctypes.c_int, [_P(wsr_gaussians), _c_void_p, _c_void_p, _c_void_p, _P(wsr_camera),
+                                      ctypes.c_int32, _P(wsr_tiles), _P(wsr_weight), _c_void_p, _c_void_p,
+                                      _c_void_p, _c_void_p, _P(wsr_grads), _c_void_p, ctypes.c_size_t,
+                                      _c_void_p]),
+    "wsr_render_bwd_tiles": (ctypes.c_int, [_c_void_p, ctypes.c_int64, _c_void_p, _c_void_p, _P(wsr_camera),
+                                            ctypes.c_int32, _P(wsr_tiles), _P(wsr_weight), _c_void_p, _c_void_p,
+                                            _c_void_p, _c_void_p, _c_void_p, ctypes.c_size_t, _c_void_p]),
+    "wsr_project_bwd": (ctypes.c_int, [_P(wsr_gaussians), _P(wsr_camera), ctypes.c_int32, _P(wsr_weight),
+                                       _c_void_p, _P(wsr_grads), _c_void_p, ctypes.c_size_t, _c_void_p]),
+    "wsr_loss_l1": (ctypes.c_int, [_c_void_p, _c_void_p, ctypes.c_int64, _c_void_p, _c_void_p, _c_void_p]),
+    "wsr_check": (ctypes.c_int, [_c_void_p, ctypes.c_size_t, _c_void_p]),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libwsr.so (built by ``paper_2410_18931_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"libwsr.so is not built ({p}); run paper_2410_18931_gb300.build.build()")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> list:
+    return sorted(_SIGS)
+
+
+class WSRError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        lib = load()
+        msg = lib.wsr_status_string(status).decode()
+        super().__init__(f"{fn} failed: {msg} ({status})")
+        self.status = status
+
+
+def check(fn: str, status: int) -> None:
+    if status != WSR_OK:
+        raise WSRError(fn, status)
+
+
+def make_cameras(cams) -> tuple:
+    """(ctypes array of wsr_camera, count) from objects with R, T, fx, fy,
+    cx, cy, width, height and znear attributes."""
+    arr = (wsr_camera * len(cams))()
+    for k, c in enumerate(cams):
+        R = [float(v) for v in __import__("numpy").asarray(c.R, dtype="float64").reshape(9)]
+        T = [float(v) for v in __import__("numpy").asarray(c.T, dtype="float64").reshape(3)]
+        arr[k].R[:] = R
+        arr[k].T[:] = T
+        arr[k].fx, arr[k].fy, arr[k].cx, arr[k].cy = float(c.fx), float(c.fy), float(c.cx), float(c.cy)
+        arr[k].width, arr[k].height = int(c.width), int(c.height)
+        arr[k].znear = float(c.znear)
+    return arr, len(cams)
+
+
+def tiles(tw: int, th: int) -> wsr_tiles:
+    return wsr_tiles(int(tw), int(th))

@@ -1,0 +1,339 @@
+// C ABI of the WSR library: argument checks, view table, workspace layout and
+// dispatch to the kernels.  Nothing here allocates device memory.
+#include <math.h>
+#include <string.h>
+
+#include "wsr_launch.h"
+
+using namespace wsr;
+
+namespace {
+
+constexpr int32_t kVersion = 1 * 10000 + 0 * 100 + 0;
+
+bool tiles_ok(const wsr_tiles* t) {
+    if (!t) return false;
+    return (t->tile_w == 16 && t->tile_h == 16) || (t->tile_w == 8 && t->tile_h == 8) ||
+           (t->tile_w == 32 && t->tile_h == 8) || (t->tile_w == 16 && t->tile_h == 8);
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Builds the per-view constant table.  Returns WSR_OK or the argument error.
+wsr_status make_views(const wsr_camera* cams, int32_t n_cams, const wsr_tiles* tiles, Views* vs) {
+    if (!cams || n_cams < 1 || n_cams > WSR_MAX_VIEWS) return WSR_ERR_INVALID_ARG;
+    int tw = 16, th = 16;
+    if (tiles) {
+        if (!tiles_ok(tiles)) return WSR_ERR_UNSUPPORTED;
+        tw = tiles->tile_w;
+        th = tiles->tile_h;
+    }
+    memset(vs, 0, sizeof(Views));
+    vs->n = n_cams;
+    vs->tile_w = tw;
+    vs->tile_h = th;
+    long long tile_base = 0, pix_base = 0;
+    for (int v = 0; v < n_cams; ++v) {
+        const wsr_camera& c = cams[v];
+        if (c.width <= 0 || c.height <= 0 || c.width > 32768 || c.height > 32768) return WSR_ERR_INVALID_ARG;
+        if (!(c.fx > 0.0f) || !(c.fy > 0.0f) || !(c.znear >= 0.0f) || !isfinite(c.cx) || !isfinite(c.cy))
+            return WSR_ERR_INVALID_ARG;
+        for (int k = 0; k < 9; ++k)
+            if (!isfinite(c.R[k])) return WSR_ERR_INVALID_ARG;
+        for (int k = 0; k < 3; ++k)
+            if (!isfinite(c.T[k])) return WSR_ERR_INVALID_ARG;
+        View& V = vs->v[v];
+        memcpy(V.R, c.R, sizeof V.R);
+        memcpy(V.T, c.T, sizeof V.T);
+        V.fx = c.fx; V.fy = c.fy; V.cx = c.cx; V.cy = c.cy; V.znear = c.znear;
+        for (int k = 0; k < 3; ++k)
+            V.campos[k] = (float)(-((double)c.R[k] * c.T[0] + (double)c.R[3 + k] * c.T[1] +
+                                    (double)c.R[6 + k] * c.T[2]));
+        V.limx = (float)(1.3 * 0.5 * c.width / (double)c.fx);
+        V.limy = (float)(1.3 * 0.5 * c.height / (double)c.fy);
+        V.W = c.width;
+        V.H = c.height;
+        V.tiles_x = (c.width + tw - 1) / tw;
+        V.tiles_y = (c.height + th - 1) / th;
+        V.tile_base = (int)tile_base;
+        V.pix_base = pix_base;
+        tile_base += (long long)V.tiles_x * V.tiles_y;
+        pix_base += (long long)c.width * c.height;
+        if (tile_base > (1ll << 30)) return WSR_ERR_INVALID_ARG;
+    }
+    vs->total_tiles = (int)tile_base;
+    vs->total_pix = pix_base;
+    return WSR_OK;
+}
+
+struct WsLayout {
+    size_t cursor, block_sums, total;
+};
+
+WsLayout ws_layout(const Views& vs) {
+    WsLayout L;
+    const size_t nb = (size_t)(vs.total_tiles + kScanTile - 1) / kScanTile;
+    L.cursor = kWsHeader;
+    L.block_sums = L.cursor + align256(sizeof(unsigned) * ((size_t)vs.total_tiles + 1));
+    L.total = L.block_sums + align256(sizeof(unsigned long long) * (nb + 1));
+    return L;
+}
+
+wsr_status check_ws(const Views& vs, void* ws, size_t bytes) {
+    if (!ws || !aligned16(ws)) return WSR_ERR_INVALID_ARG;
+    if (bytes < ws_layout(vs).total) return WSR_ERR_INVALID_ARG;
+    return WSR_OK;
+}
+
+wsr_status check_gauss(const wsr_gaussians* g, int32_t n_cams, int wkind, GaussPtrs* out) {
+    if (!g || g->n < 0) return WSR_ERR_INVALID_ARG;
+    if (g->sh_degree < 0 || g->sh_degree > 3) return WSR_ERR_INVALID_ARG;
+    if (g->opacity_mode != WSR_OPACITY_LOGIT && g->opacity_mode != WSR_OPACITY_SH) return WSR_ERR_INVALID_ARG;
+    const bool full = g->dtype_scales_quats == WSR_F32 && g->dtype_sh == WSR_F32;
+    const bool red = g->dtype_scales_quats == WSR_BF16 && g->dtype_sh == WSR_F16;
+    if (!full && !red) {
+        const bool known = (g->dtype_scales_quats >= WSR_F32 && g->dtype_scales_quats <= WSR_BF16) &&
+                           (g->dtype_sh >= WSR_F32 && g->dtype_sh <= WSR_BF16);
+        return known ? WSR_ERR_UNSUPPORTED : WSR_ERR_INVALID_ARG;
+    }
+    if ((unsigned long long)g->n * (unsigned long long)n_cams > 0xffffffffull) return WSR_ERR_INVALID_ARG;
+    if (g->n > 0) {
+        if (!g->means || !g->log_scales || !g->quats || !g->sh || !g->opacity) return WSR_ERR_INVALID_ARG;
+        if (wkind == WSR_WEIGHT_LC && !g->lc_v) return WSR_ERR_INVALID_ARG;
+        if (!aligned16(g->means) || !aligned16(g->log_scales) || !aligned16(g->quats) || !aligned16(g->sh) ||
+            !aligned16(g->opacity) || (g->lc_v && !aligned16(g->lc_v)))
+            return WSR_ERR_INVALID_ARG;
+    }
+    out->n = g->n;
+    out->deg = g->sh_degree;
+    out->vd = g->opacity_mode == WSR_OPACITY_SH;
+    out->red = red ? 1 : 0;
+    out->means = g->means;
+    out->log_scales = g->log_scales;
+    out->quats = g->quats;
+    out->sh = g->sh;
+    out->opacity = g->opacity;
+    out->lc_v = g->lc_v;
+    return WSR_OK;
+}
+
+wsr_status check_weight(const wsr_weight* w, WeightDev* out) {
+    if (!w || !w->params) return WSR_ERR_INVALID_ARG;
+    if (w->kind < WSR_WEIGHT_DIR || w->kind > WSR_WEIGHT_LC) return WSR_ERR_INVALID_ARG;
+    out->kind = w->kind;
+    out->params = w->params;
+    return WSR_OK;
+}
+
+wsr_status cuda_status(cudaError_t e) { return e == cudaSuccess ? WSR_OK : WSR_ERR_CUDA; }
+
+#define WSR_TRY(expr)                         \
+    do {                                      \
+        const wsr_status st_ = (expr);        \
+        if (st_ != WSR_OK) return st_;        \
+    } while (0)
+#define WSR_CUDA(expr)                                        \
+    do {                                                      \
+        const cudaError_t ce_ = (expr);                       \
+        if (ce_ != cudaSuccess) return WSR_ERR_CUDA;          \
+    } while (0)
+
+}  // namespace
+
+extern "C" {
+
+const char* wsr_status_string(wsr_status s) {
+    switch (s) {
+        case WSR_OK: return "ok";
+        case WSR_ERR_INVALID_ARG: return "invalid argument";
+        case WSR_ERR_CAPACITY: return "tile list capacity exceeded";
+        case WSR_ERR_CUDA: return "CUDA error";
+        case WSR_ERR_TIMEOUT: return "timeout";
+        case WSR_ERR_UNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+int32_t wsr_version(void) { return kVersion; }
+
+int64_t wsr_num_tiles(const wsr_camera* cams, int32_t n_cams, const wsr_tiles* tiles) {
+    static thread_local Views vs;
+    if (!tiles || make_views(cams, n_cams, tiles, &vs) != WSR_OK) return 0;
+    return vs.total_tiles;
+}
+
+int64_t wsr_num_pixels(const wsr_camera* cams, int32_t n_cams) {
+    static thread_local Views vs;
+    if (make_views(cams, n_cams, nullptr, &vs) != WSR_OK) return 0;
+    return vs.total_pix;
+}
+
+size_t wsr_workspace_size(const wsr_camera* cams, int32_t n_cams, const wsr_tiles* tiles) {
+    static thread_local Views vs;
+    if (!tiles || make_views(cams, n_cams, tiles, &vs) != WSR_OK) return 0;
+    return ws_layout(vs).total;
+}
+
+wsr_status wsr_project(const wsr_gaussians* g, const wsr_camera* cams, int32_t n_cams, const wsr_weight* w,
+                       float* records, void* stream) {
+    static thread_local Views vs;
+    WeightDev wd;
+    GaussPtrs gp;
+    WSR_TRY(check_weight(w, &wd));
+    WSR_TRY(make_views(cams, n_cams, nullptr, &vs));
+    WSR_TRY(check_gauss(g, n_cams, wd.kind, &gp));
+    if (gp.n > 0 && (!records || !aligned16(records))) return WSR_ERR_INVALID_ARG;
+    return cuda_status(launch_project(gp, vs, wd, records, (cudaStream_t)stream));
+}
+
+static wsr_status bin_count_impl(const float* records, int64_t n, const Views& vs, uint32_t* tile_offsets,
+                                 unsigned long long capacity, void* workspace, cudaStream_t s) {
+    const WsLayout L = ws_layout(vs);
+    char* ws = (char*)workspace;
+    WsHeader* hdr = (WsHeader*)ws;
+    unsigned* cursor = (unsigned*)(ws + L.cursor);
+    unsigned* bsum = (unsigned*)(ws + L.block_sums);
+    WSR_CUDA(cudaMemsetAsync(&hdr->err, 0, sizeof(int), s));
+    WSR_CUDA(launch_bin_count(records, n, vs, cursor, s));
+    WSR_CUDA(launch_scan(vs, cursor, bsum, tile_offsets, capacity, hdr, s));
+    return WSR_OK;
+}
+
+wsr_status wsr_bin_count(const float* records, int64_t n, const wsr_camera* cams, int32_t n_cams,
+                         const wsr_tiles* tiles, uint32_t* tile_offsets, void* workspace, size_t workspace_bytes,
+                         void* stream) {
+    static thread_local Views vs;
+    if (!tiles) return WSR_ERR_INVALID_ARG;
+    WSR_TRY(make_views(cams, n_cams, tiles, &vs));
+    WSR_TRY(check_ws(vs, workspace, workspace_bytes));
+    if (n < 0 || (n > 0 && (!records || !aligned16(records))) || !tile_offsets) return WSR_ERR_INVALID_ARG;
+    if ((unsigned long long)n * (unsigned long long)n_cams > 0xffffffffull) return WSR_ERR_INVALID_ARG;
+    return bin_count_impl(records, n, vs, tile_offsets, ~0ull, workspace, (cudaStream_t)stream);
+}
+
+wsr_status wsr_bin(const float* records, int64_t n, const wsr_camera* cams, int32_t n_cams, const wsr_tiles* tiles,
+                   uint32_t* tile_offsets, uint32_t* tile_list, uint64_t list_capacity, void* workspace,
+                   size_t workspace_bytes, void* stream) {
+    static thread_local Views vs;
+    if (!tiles) return WSR_ERR_INVALID_ARG;
+    WSR_TRY(make_views(cams, n_cams, tiles, &vs));
+    WSR_TRY(check_ws(vs, workspace, workspace_bytes));
+    if (n < 0 || (n > 0 && (!records || !aligned16(records))) || !tile_offsets) return WSR_ERR_INVALID_ARG;
+    if (list_capacity > 0 && !tile_list) return WSR_ERR_INVALID_ARG;
+    if ((unsigned long long)n * (unsigned long long)n_cams > 0xffffffffull) return WSR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    WSR_TRY(bin_count_impl(records, n, vs, tile_offsets, list_capacity, workspace, s));
+    const WsLayout L = ws_layout(vs);
+    char* ws = (char*)workspace;
+    WSR_CUDA(launch_bin_scatter(records, n, vs, (unsigned*)(ws + L.cursor), tile_list, list_capacity,
+                                (WsHeader*)ws, s));
+    return WSR_OK;
+}
+
+wsr_status wsr_bin_total(const void* workspace, size_t workspace_bytes, uint64_t* total, void* stream) {
+    if (!workspace || workspace_bytes < kWsHeader || !total) return WSR_ERR_INVALID_ARG;
+    unsigned long long t = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    WSR_CUDA(cudaMemcpyAsync(&t, &((const WsHeader*)workspace)->total, sizeof t, cudaMemcpyDeviceToHost, s));
+    WSR_CUDA(cudaStreamSynchronize(s));
+    *total = t;
+    return WSR_OK;
+}
+
+wsr_status wsr_render_fwd(const float* records, int64_t n, const uint32_t* tile_offsets, const uint32_t* tile_list,
+                          const wsr_camera* cams, int32_t n_cams, const wsr_tiles* tiles, const wsr_weight* w,
+                          float* out_rgb, float* out_den, void* workspace, size_t workspace_bytes, void* stream) {
+    static thread_local Views vs;
+    WeightDev wd;
+    if (!tiles) return WSR_ERR_INVALID_ARG;
+    WSR_TRY(check_weight(w, &wd));
+    WSR_TRY(make_views(cams, n_cams, tiles, &vs));
+    WSR_TRY(check_ws(vs, workspace, workspace_bytes));
+    if (n < 0 || !tile_offsets || !out_rgb || !out_den) return WSR_ERR_INVALID_ARG;
+    if (n > 0 && (!records || !tile_list)) return WSR_ERR_INVALID_ARG;
+    return cuda_status(
+        launch_render_fwd(records, tile_offsets, tile_list, vs, wd, out_rgb, out_den, (cudaStream_t)stream));
+}
+
+wsr_status wsr_render_bwd_tiles(const float* records, int64_t n, const uint32_t* tile_offsets,
+                                const uint32_t* tile_list, const wsr_camera* cams, int32_t n_cams,
+                                const wsr_tiles* tiles, const wsr_weight* w, const float* out_rgb,
+                                const float* out_den, const float* grad_rgb, float* grad_records, void* workspace,
+                                size_t workspace_bytes, void* stream) {
+    static thread_local Views vs;
+    WeightDev wd;
+    if (!tiles) return WSR_ERR_INVALID_ARG;
+    WSR_TRY(check_weight(w, &wd));
+    WSR_TRY(make_views(cams, n_cams, tiles, &vs));
+    WSR_TRY(check_ws(vs, workspace, workspace_bytes));
+    if (n < 0 || !tile_offsets || !out_rgb || !out_den || !grad_rgb) return WSR_ERR_INVALID_ARG;
+    if (n > 0 && (!records || !tile_list || !grad_records)) return WSR_ERR_INVALID_ARG;
+    if ((unsigned long long)n * (unsigned long long)n_cams > 0xffffffffull) return WSR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    WsHeader* hdr = (WsHeader*)workspace;
+    WSR_CUDA(cudaMemsetAsync(hdr->gw, 0, sizeof hdr->gw, s));
+    if (n > 0)
+        WSR_CUDA(cudaMemsetAsync(grad_records, 0, sizeof(float) * WSR_GRAD_RECORD_FLOATS * (size_t)n * n_cams, s));
+    WSR_CUDA(launch_render_bwd(records, tile_offsets, tile_list, vs, wd, out_rgb, out_den, grad_rgb, grad_records,
+                               hdr->gw, s));
+    return WSR_OK;
+}
+
+wsr_status wsr_project_bwd(const wsr_gaussians* g, const wsr_camera* cams, int32_t n_cams, const wsr_weight* w,
+                           const float* grad_records, const wsr_grads* grads, void* workspace,
+                           size_t workspace_bytes, void* stream) {
+    static thread_local Views vs;
+    WeightDev wd;
+    GaussPtrs gp;
+    if (!grads || !workspace || workspace_bytes < kWsHeader || !aligned16(workspace)) return WSR_ERR_INVALID_ARG;
+    WSR_TRY(check_weight(w, &wd));
+    WSR_TRY(make_views(cams, n_cams, nullptr, &vs));
+    WSR_TRY(check_gauss(g, n_cams, wd.kind, &gp));
+    if (gp.n > 0 && !grad_records) return WSR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    WsHeader* hdr = (WsHeader*)workspace;
+    wsr_grads inner = *grads;
+    inner.weight_params = hdr->gw;
+    WSR_CUDA(launch_project_bwd(gp, vs, wd, grad_records, inner, s));
+    if (grads->weight_params)
+        WSR_CUDA(cudaMemcpyAsync(grads->weight_params, hdr->gw, 6 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return WSR_OK;
+}
+
+wsr_status wsr_render_bwd(const wsr_gaussians* g, const float* records, const uint32_t* tile_offsets,
+                          const uint32_t* tile_list, const wsr_camera* cams, int32_t n_cams, const wsr_tiles* tiles,
+                          const wsr_weight* w, const float* out_rgb, const float* out_den, const float* grad_rgb,
+                          float* grad_records, const wsr_grads* grads, void* workspace, size_t workspace_bytes,
+                          void* stream) {
+    if (!g || !grads) return WSR_ERR_INVALID_ARG;
+    {
+        // validate the scene before enqueuing anything
+        static thread_local Views vs;
+        WeightDev wd;
+        GaussPtrs gp;
+        WSR_TRY(check_weight(w, &wd));
+        WSR_TRY(make_views(cams, n_cams, tiles, &vs));
+        WSR_TRY(check_gauss(g, n_cams, wd.kind, &gp));
+    }
+    WSR_TRY(wsr_render_bwd_tiles(records, g->n, tile_offsets, tile_list, cams, n_cams, tiles, w, out_rgb, out_den,
+                                 grad_rgb, grad_records, workspace, workspace_bytes, stream));
+    return wsr_project_bwd(g, cams, n_cams, w, grad_records, grads, workspace, workspace_bytes, stream);
+}
+
+wsr_status wsr_loss_l1(const float* rgb, const float* target, int64_t count, float* loss_out, float* grad_rgb,
+                       void* stream) {
+    if (count < 0 || !loss_out || (count > 0 && (!rgb || !target || !grad_rgb))) return WSR_ERR_INVALID_ARG;
+    return cuda_status(launch_loss_l1(rgb, target, count, loss_out, grad_rgb, (cudaStream_t)stream));
+}
+
+wsr_status wsr_check(void* workspace, size_t workspace_bytes, void* stream) {
+    if (!workspace || workspace_bytes < kWsHeader) return WSR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int err = 0;
+    WSR_CUDA(cudaMemcpyAsync(&err, workspace, sizeof err, cudaMemcpyDeviceToHost, s));
+    WSR_CUDA(cudaStreamSynchronize(s));
+    if (err != 0) WSR_CUDA(cudaMemsetAsync(workspace, 0, sizeof(int), s));
+    return (wsr_status)err;
+}
+
+}  // extern "C"

@@ -1,0 +1,53 @@
+// Host-side launch interface between the C ABI (api.cu) and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "wsr_common.cuh"
+
+namespace wsr {
+
+struct GaussPtrs {
+    long long n;
+    int deg;       // 0..3
+    int vd;        // opacity from SH (Eq. 11) instead of a logit
+    int red;       // reduced-precision storage (bf16 scales/quats, f16 SH/opacity)
+    const float* means;
+    const void* log_scales;
+    const void* quats;
+    const void* sh;
+    const void* opacity;
+    const float* lc_v;
+};
+
+struct WeightDev {
+    int kind;
+    const float* params;   // device [6]: sigma, beta, w_B, c_B
+};
+
+cudaError_t launch_project(const GaussPtrs& g, const Views& vs, WeightDev w, float* records,
+                           cudaStream_t s);
+cudaError_t launch_project_bwd(const GaussPtrs& g, const Views& vs, WeightDev w,
+                               const float* grad_records, const wsr_grads& out, cudaStream_t s);
+
+cudaError_t launch_bin_count(const float* records, long long n, const Views& vs,
+                             unsigned* cursor, cudaStream_t s);
+cudaError_t launch_scan(const Views& vs, unsigned* cursor, unsigned* block_sums,
+                        unsigned* tile_offsets, unsigned long long capacity, WsHeader* hdr,
+                        cudaStream_t s);
+cudaError_t launch_bin_scatter(const float* records, long long n, const Views& vs,
+                               unsigned* cursor, unsigned* tile_list,
+                               unsigned long long capacity, WsHeader* hdr, cudaStream_t s);
+
+cudaError_t launch_render_fwd(const float* records, const unsigned* tile_offsets,
+                              const unsigned* tile_list, const Views& vs, WeightDev w,
+                              float* out_rgb, float* out_den, cudaStream_t s);
+cudaError_t launch_render_bwd(const float* records, const unsigned* tile_offsets,
+                              const unsigned* tile_list, const Views& vs, WeightDev w,
+                              const float* out_rgb, const float* out_den, const float* grad_rgb,
+                              float* grad_records, float* grad_wparams, cudaStream_t s);
+
+cudaError_t launch_loss_l1(const float* rgb, const float* target, long long count,
+                           float* loss, float* grad, cudaStream_t s);
+
+}  // namespace wsr

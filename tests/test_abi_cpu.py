@@ -1,0 +1,113 @@
+"""The C-ABI library on a machine without a GPU: it builds, loads, exports
+every function that ``include/wsr.h`` declares, and rejects bad arguments on
+the host before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "wsr.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2410_18931_gb300 import build
+    build.build()
+    from paper_2410_18931_gb300 import _abi
+    return _abi.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w]+\s*\*?\s*(wsr_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_hot_path():
+    names = declared_functions()
+    for n in ("wsr_project", "wsr_bin", "wsr_render_fwd", "wsr_render_bwd"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2410_18931_gb300 import _abi
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in _abi.exported_symbols(), f"binding lacks {name}"
+
+
+def test_status_strings(lib):
+    assert lib.wsr_status_string(0) == b"ok"
+    assert b"capacity" in lib.wsr_status_string(2)
+    assert lib.wsr_version() >= 10000
+
+
+def _cam(w=1920, h=1080):
+    from paper_2410_18931_gb300 import _abi
+    import wsr_scenes as ws
+    arr, n = _abi.make_cameras([ws.look_at((0, 0, -5), width=w, height=h)])
+    return arr, n
+
+
+def test_tile_and_pixel_counts(lib):
+    from paper_2410_18931_gb300 import _abi
+    cams, n = _cam()
+    t16 = _abi.tiles(16, 16)
+    assert lib.wsr_num_tiles(cams, n, ctypes.byref(t16)) == 120 * 68
+    assert lib.wsr_num_tiles(cams, n, ctypes.byref(_abi.tiles(32, 8))) == 60 * 135
+    assert lib.wsr_num_pixels(cams, n) == 1920 * 1080
+    assert lib.wsr_workspace_size(cams, n, ctypes.byref(t16)) >= 256 + 4 * (8160 + 1)
+    # unsupported tile shape
+    assert lib.wsr_workspace_size(cams, n, ctypes.byref(_abi.tiles(12, 12))) == 0
+    assert lib.wsr_num_tiles(cams, 0, ctypes.byref(t16)) == 0
+
+
+def test_argument_errors_are_returned(lib):
+    from paper_2410_18931_gb300 import _abi as A
+    cams, n = _cam(64, 48)
+    t16 = A.tiles(16, 16)
+    fake = 1 << 20   # never dereferenced: validation fails first
+    w = A.wsr_weight(A.WSR_WEIGHT_EXP, fake)
+    g = A.wsr_gaussians(10, 3, A.WSR_OPACITY_SH, A.WSR_F32, A.WSR_F32, fake, fake, fake, fake, fake, None)
+    # null scene / weight
+    assert lib.wsr_project(None, cams, n, ctypes.byref(w), fake, None) == A.WSR_ERR_INVALID_ARG
+    assert lib.wsr_project(ctypes.byref(g), cams, n, None, fake, None) == A.WSR_ERR_INVALID_ARG
+    # SH degree out of range
+    bad = A.wsr_gaussians(10, 4, 1, 0, 0, fake, fake, fake, fake, fake, None)
+    assert lib.wsr_project(ctypes.byref(bad), cams, n, ctypes.byref(w), fake, None) == A.WSR_ERR_INVALID_ARG
+    # LC needs the per-Gaussian v_i
+    wlc = A.wsr_weight(A.WSR_WEIGHT_LC, fake)
+    assert lib.wsr_project(ctypes.byref(g), cams, n, ctypes.byref(wlc), fake, None) == A.WSR_ERR_INVALID_ARG
+    # unknown weight kind
+    wbad = A.wsr_weight(7, fake)
+    assert lib.wsr_project(ctypes.byref(g), cams, n, ctypes.byref(wbad), fake, None) == A.WSR_ERR_INVALID_ARG
+    # mixed storage types are valid enums but unsupported
+    mix = A.wsr_gaussians(10, 3, 1, A.WSR_BF16, A.WSR_F32, fake, fake, fake, fake, fake, None)
+    assert lib.wsr_project(ctypes.byref(mix), cams, n, ctypes.byref(w), fake, None) == A.WSR_ERR_UNSUPPORTED
+    # misaligned record buffer
+    assert lib.wsr_project(ctypes.byref(g), cams, n, ctypes.byref(w), fake + 4, None) == A.WSR_ERR_INVALID_ARG
+    # too many views
+    many = (A.wsr_camera * 40)(*([cams[0]] * 40))
+    assert lib.wsr_project(ctypes.byref(g), many, 40, ctypes.byref(w), fake, None) == A.WSR_ERR_INVALID_ARG
+    # a zero-size camera
+    zc = (A.wsr_camera * 1)(cams[0])
+    zc[0].width = 0
+    assert lib.wsr_workspace_size(zc, 1, ctypes.byref(t16)) == 0
+    # workspace too small
+    ws = lib.wsr_workspace_size(cams, n, ctypes.byref(t16))
+    assert lib.wsr_bin(fake, 10, cams, n, ctypes.byref(t16), fake, fake, 100, fake, ws - 16,
+                       None) == A.WSR_ERR_INVALID_ARG
+    # unsupported tile shape
+    assert lib.wsr_bin(fake, 10, cams, n, ctypes.byref(A.tiles(24, 24)), fake, fake, 100, fake, ws,
+                       None) == A.WSR_ERR_UNSUPPORTED
+    # null outputs of the renderer
+    assert lib.wsr_render_fwd(fake, 10, fake, fake, cams, n, ctypes.byref(t16), ctypes.byref(w), None, fake,
+                              fake, ws, None) == A.WSR_ERR_INVALID_ARG
+    # backward without gradient outputs
+    assert lib.wsr_render_bwd(ctypes.byref(g), fake, fake, fake, cams, n, ctypes.byref(t16), ctypes.byref(w),
+                              fake, fake, fake, fake, None, fake, ws, None) == A.WSR_ERR_INVALID_ARG
+    # negative counts
+    assert lib.wsr_loss_l1(fake, fake, -1, fake, fake, None) == A.WSR_ERR_INVALID_ARG
+    assert lib.wsr_check(None, 0, None) == A.WSR_ERR_INVALID_ARG

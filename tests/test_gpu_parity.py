@@ -1,0 +1,293 @@
+"""CUDA path against the FP64 oracle, element by element (needs a GPU).
+
+Tolerances: forward max abs pixel error 1e-4 (plus, for pixels that hold a
+Gaussian within |q - 9| <= 0.02 of the cutoff, the oracle's bound on what
+deciding that tie the other way changes); gradients max error / max
+magnitude 1e-3 per tensor.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import wsr_scenes as ws
+from tests.gpu_util import AMB_TAU, FWD_TOL, GRAD_TOL, compare_image, gpu_render, rel_err
+
+pytestmark = pytest.mark.gpu
+
+TILES = [(16, 16), (8, 8), (32, 8), (16, 8)]
+
+
+def _oracle(scene, cam, weight):
+    return oracle.render(scene, cam, weight, amb_tau=AMB_TAU)
+
+
+@pytest.mark.parametrize("tile", TILES)
+def test_workload1_forward_all_tiles(tile):
+    """1k Gaussians, 128x128, EXP, degree 0: full image, every tile shape."""
+    scene, cams, weight, _ = ws.workload(1)
+    cam = cams[0].rounded()
+    (rgb, den), = gpu_render(scene, [cam], weight, tile=tile)
+    ref = _oracle(scene, cam, weight)
+    excess, raw, n_amb = compare_image(rgb, ref)
+    assert excess <= FWD_TOL, (excess, raw, n_amb)
+    assert np.abs(den - ref["den"]).max() <= 1e-3 * max(1.0, np.abs(ref["den"]).max())
+
+
+@pytest.mark.parametrize("kind", [ws.DIR, ws.EXP, ws.LC])
+@pytest.mark.parametrize("deg,vd", [(3, True), (1, False), (2, True), (0, True)])
+def test_ragged_image_each_weight(kind, deg, vd):
+    """20k clustered Gaussians on a 200x120 image (not a multiple of any
+    tile side), SH degree 0-3, both opacity modes, each weight function."""
+    sc = ws.random_scene(20_000, 7 + deg, sh_degree=deg, vd_opacity=vd, clusters=16, box=1.5,
+                         log_scale_mu=-3.5, log_scale_sd=0.6)
+    cam = ws.look_at((0.3, -0.2, -4.0), width=200, height=120).rounded()
+    w = ws.WeightParams(kind, 0.1 if kind == ws.EXP else 4.5, 0.8, 0.7, (0.2, 0.1, 0.3))
+    if kind == ws.DIR:
+        w = ws.WeightParams(kind, 0.0, 0.0, 0.7, (0.2, 0.1, 0.3))
+    ref = _oracle(sc, cam, w)
+    for tile in [(16, 16), (32, 8)]:
+        (rgb, _), = gpu_render(sc, [cam], w, tile=tile)
+        excess, raw, n_amb = compare_image(rgb, ref)
+        assert excess <= FWD_TOL, (tile, excess, raw, n_amb)
+
+
+@pytest.mark.parametrize("kind", [ws.DIR, ws.EXP, ws.LC])
+def test_workload2_full_size_forward(kind):
+    """200k Gaussians, 32 clusters, SH degree 3, view-dependent opacity,
+    1280x720: the whole image against the oracle, each weight function."""
+    scene, cams, weight, _ = ws.workload(2, weight_kind=kind)
+    cam = cams[0].rounded()
+    (rgb, _), = gpu_render(scene, [cam], weight)
+    ref = _oracle(scene, cam, weight)
+    excess, raw, n_amb = compare_image(rgb, ref)
+    assert excess <= FWD_TOL, (excess, raw, n_amb)
+    assert n_amb < 0.01 * cam.width * cam.height
+
+
+def test_workload3_full_size_forward():
+    """1M Gaussians, 64 clusters, SH degree 3, VD opacity, LC, 1920x1080."""
+    scene, cams, weight, _ = ws.workload(3)
+    cam = cams[0].rounded()
+    (rgb, _), = gpu_render(scene, [cam], weight)
+    ref = _oracle(scene, cam, weight)
+    excess, raw, n_amb = compare_image(rgb, ref)
+    assert excess <= FWD_TOL, (excess, raw, n_amb)
+
+
+def test_multiview_uneven_sizes():
+    """Three views of different sizes in one call; each view against the oracle."""
+    sc = ws.random_scene(30_000, 11, sh_degree=3, vd_opacity=True, clusters=8, box=2.0)
+    cams = [c.rounded() for c in ws.sphere_cameras(3, 6.0, [(160, 90), (97, 131), (256, 144)])]
+    w = ws.default_weight(ws.LC)
+    views = gpu_render(sc, cams, w)
+    for cam, (rgb, _) in zip(cams, views):
+        ref = _oracle(sc, cam, w)
+        excess, raw, n_amb = compare_image(rgb, ref)
+        assert excess <= FWD_TOL, (cam.width, cam.height, excess, raw, n_amb)
+
+
+def test_reduced_precision_storage_matches_oracle_on_stored_values():
+    """bf16 scales/quats and f16 SH/opacity: the kernel arithmetic against the
+    oracle run on the stored (rounded) values."""
+    sc = ws.random_scene(20_000, 12, sh_degree=3, vd_opacity=True, clusters=16, box=1.5, log_scale_mu=-3.5)
+    q = ws.quantize_reduced(sc)
+    cam = ws.look_at((0.0, 0.0, -4.0), width=160, height=120).rounded()
+    w = ws.default_weight(ws.LC)
+    (rgb, _), = gpu_render(q, [cam], w, reduced=True)
+    ref = _oracle(q, cam, w)
+    excess, raw, n_amb = compare_image(rgb, ref)
+    assert excess <= FWD_TOL, (excess, raw, n_amb)
+
+
+def _grad_case(scene, cam, weight, tile=(16, 16)):
+    import torch
+    views, (r, g, wpar, st) = gpu_render(scene, [cam], weight, tile=tile, want_state=True)
+    G = np.random.default_rng(5).normal(size=(cam.height, cam.width, 3)).astype(np.float32)
+    out = r.backward(g, weight.kind, wpar, st, torch.tensor(G, device="cuda").reshape(-1, 3))
+    torch.cuda.synchronize()
+    ref = oracle.grad(scene, cam, weight, G.astype(np.float64))
+    return out, ref
+
+
+@pytest.mark.parametrize("kind,deg,vd", [(ws.LC, 3, True), (ws.EXP, 3, True), (ws.DIR, 1, False),
+                                         (ws.EXP, 2, False)])
+def test_gradients_match_oracle(kind, deg, vd):
+    sc = ws.random_scene(3_000, 20 + deg, sh_degree=deg, vd_opacity=vd, clusters=6, box=1.2,
+                         log_scale_mu=-3.2, log_scale_sd=0.5)
+    cam = ws.look_at((0.2, 0.1, -3.5), width=96, height=72).rounded()
+    w = ws.WeightParams(kind, 0.1 if kind == ws.EXP else 4.8, 0.8, 0.6, (0.3, 0.2, 0.1))
+    out, ref = _grad_case(sc, cam, w)
+    for k in ("means", "log_scales", "quats", "sh", "opacity"):
+        e = rel_err(out[k].cpu().numpy(), ref[k])
+        assert e <= GRAD_TOL, (k, e)
+    if kind == ws.LC:
+        assert rel_err(out["lc_v"].cpu().numpy(), ref["lc_v"]) <= GRAD_TOL
+    gw = out["weight_params"].cpu().numpy()
+    for k in range(6):
+        if (kind == ws.DIR and k < 2) or (kind == ws.LC and k == 1):
+            continue
+        assert abs(gw[k] - ref["wpar"][k]) <= GRAD_TOL * max(abs(ref["wpar"][k]), 1e-3), (k, gw[k], ref["wpar"][k])
+
+
+def test_gradient_records_match_oracle():
+    """The per-Gaussian 2D gradient records of the tile kernel alone."""
+    sc = ws.random_scene(2_000, 31, sh_degree=2, vd_opacity=True, clusters=4, box=1.0, log_scale_mu=-3.0)
+    cam = ws.look_at((0.0, 0.0, -3.0), width=80, height=64).rounded()
+    w = ws.WeightParams(ws.EXP, 0.1, 0.8, 0.8, (0.1, 0.2, 0.3))
+    out, ref = _grad_case(sc, cam, w)
+    gr = out["grad_records"].cpu().numpy().reshape(-1, 9).astype(np.float64)
+    P = oracle.project(sc, cam, w)
+    uw = P["u"] * P["w"]
+    col = P["color"]
+    # oracle g2d: dL/dc and dL/d(uw) at fixed c; the kernel: d/d(c uw) and d/d(uw) at fixed c uw
+    conv = gr.copy()
+    conv[:, 6:9] = gr[:, 6:9] * uw[:, None]
+    conv[:, 5] = gr[:, 5] + (gr[:, 6:9] * col).sum(1)
+    for c, name in [((0, 2), "mean"), ((2, 5), "conic"), ((5, 6), "uw"), ((6, 9), "color")]:
+        e = rel_err(conv[:, c[0]:c[1]], ref["g2d"][:, c[0]:c[1]])
+        assert e <= GRAD_TOL, (name, e)
+
+
+def test_workload3_full_size_gradients():
+    """1M Gaussians, 1920x1080, LC, L1 loss against the seeded target:
+    every gradient tensor against the oracle's analytic gradient."""
+    import torch
+    scene, cams, weight, extra = ws.workload(3)
+    cam = cams[0].rounded()
+    views, (r, g, wpar, st) = gpu_render(scene, [cam], weight, want_state=True)
+    target = ws.target_image(extra["target_seed"], cam.height, cam.width)
+    tgt = torch.tensor(target, device="cuda").reshape(-1, 3)
+    loss = torch.empty(1, device="cuda")
+    G = torch.empty_like(st.rgb)
+    r.loss_l1(st.rgb, tgt, loss, G)
+    out = r.backward(g, weight.kind, wpar, st, G)
+    torch.cuda.synchronize()
+    Gn = G.cpu().numpy().astype(np.float64).reshape(cam.height, cam.width, 3)
+    ref = oracle.grad(scene, cam, weight, Gn)
+    for k in ("means", "log_scales", "quats", "sh", "opacity", "lc_v"):
+        e = rel_err(out[k].cpu().numpy(), ref[k])
+        assert e <= GRAD_TOL, (k, e)
+
+
+# --------------------------------------------------------------------------
+# edge cases
+# --------------------------------------------------------------------------
+
+def test_empty_scene_is_background():
+    sc = ws.random_scene(10, 1, sh_degree=1, vd_opacity=True).subset(np.arange(0))
+    cam = ws.look_at((0.0, 0.0, -4.0), width=40, height=24).rounded()
+    w = ws.WeightParams(ws.EXP, 0.1, 0.8, 0.5, (0.25, 0.5, 0.75))
+    (rgb, den), = gpu_render(sc, [cam], w)
+    assert np.abs(rgb - np.array([0.25, 0.5, 0.75])).max() < 1e-7
+    assert np.all(den == np.float32(0.5))
+
+
+def test_all_culled_behind_camera():
+    sc = ws.random_scene(500, 2, sh_degree=0, vd_opacity=False, box=0.5)
+    sc.means[:, 2] -= 10.0                     # camera at z = -4 looking along +z: all behind it
+    cam = ws.look_at((0.0, 0.0, -4.0), width=48, height=32).rounded()
+    w = ws.default_weight(ws.DIR, w_bg=1.0, c_bg=(0.1, 0.2, 0.3))
+    (rgb, _), = gpu_render(sc, [cam], w)
+    assert np.abs(rgb - np.array([0.1, 0.2, 0.3])).max() < 1e-7
+
+
+def test_zero_opacity_gives_background_exactly():
+    sc = ws.random_scene(2000, 3, sh_degree=2, vd_opacity=True, box=1.0, log_scale_mu=-3.0)
+    sc.opacity[:] = 0.0
+    cam = ws.look_at((0.0, 0.0, -3.0), width=64, height=48).rounded()
+    w = ws.WeightParams(ws.LC, 10.0, 0.0, 0.9, (0.3, 0.6, 0.9))
+    (rgb, den), = gpu_render(sc, [cam], w)
+    assert np.abs(rgb - np.float32([0.3, 0.6, 0.9])).max() < 1e-6
+    assert np.all(den == np.float32(0.9))
+
+
+def test_single_gaussian_straddling_the_border():
+    sc = ws.random_scene(1, 4, sh_degree=0, vd_opacity=False, box=0.1)
+    sc.means[:] = [[0.55, -0.4, 0.0]]
+    sc.log_scales[:] = -1.6
+    cam = ws.look_at((0.0, 0.0, -2.0), width=50, height=30).rounded()
+    w = ws.default_weight(ws.EXP)
+    (rgb, _), = gpu_render(sc, [cam], w)
+    ref = _oracle(sc, cam, w)
+    excess, _, _ = compare_image(rgb, ref)
+    assert excess <= FWD_TOL
+    assert (np.abs(rgb - 0.0).max(axis=2) > 1e-3).sum() > 20      # it does reach the image
+
+
+def test_permutation_changes_only_rounding():
+    sc = ws.random_scene(20_000, 5, sh_degree=3, vd_opacity=True, clusters=8, box=1.5)
+    cam = ws.look_at((0.0, 0.0, -4.0), width=128, height=96).rounded()
+    w = ws.default_weight(ws.LC)
+    (a, _), = gpu_render(sc, [cam], w)
+    perm = np.random.default_rng(1).permutation(sc.n)
+    (b, _), = gpu_render(sc.subset(perm), [cam], w)
+    assert np.abs(a - b).max() < 2e-6
+
+
+def test_capacity_overflow_is_reported_and_recovered():
+    import torch
+    from paper_2410_18931_gb300 import Gaussians, Renderer
+    from paper_2410_18931_gb300 import _abi as A
+    sc = ws.random_scene(5000, 6, sh_degree=1, vd_opacity=True, box=1.0, log_scale_mu=-2.5)
+    cam = ws.look_at((0.0, 0.0, -3.0), width=96, height=64).rounded()
+    w = ws.default_weight(ws.EXP)
+    g = Gaussians.from_scene(sc)
+    wpar = torch.tensor(w.as_array(), device="cuda")
+    r = Renderer([cam])
+    st = r.alloc_state(g.n)
+    r.wsr_project(g, w.kind, wpar, st.records)
+    r.wsr_bin_count(st.records, g.n, st.tile_offsets)
+    total = r.wsr_bin_total()
+    assert total > 1000
+    small = torch.zeros(total // 3, dtype=torch.int32, device="cuda")
+    guard = torch.full((4096,), -7, dtype=torch.int32, device="cuda")   # allocated right after
+    r.wsr_bin(st.records, g.n, st.tile_offsets, small)
+    assert r.wsr_check() == A.WSR_ERR_CAPACITY
+    assert r.wsr_bin_total() == total
+    offs = st.tile_offsets.cpu().numpy().astype(np.int64)
+    assert offs.max() <= small.numel() and np.all(np.diff(offs) >= 0)
+    assert (guard.cpu().numpy() == -7).all()
+    assert r.wsr_check() == A.WSR_OK                                    # cleared
+    # the Renderer grows the list and renders the full image
+    r2 = Renderer([cam])
+    r2.capacity = total // 3
+    st2 = r2.forward(g, w.kind, wpar)
+    ref = _oracle(sc, cam, w)
+    excess, _, _ = compare_image(st2.rgb.cpu().numpy().reshape(cam.height, cam.width, 3), ref)
+    assert excess <= FWD_TOL and r2.capacity >= total
+
+
+def test_autograd_function_matches_raw_backward():
+    import torch
+    from paper_2410_18931_gb300 import Gaussians, Renderer, render
+    sc = ws.random_scene(3000, 8, sh_degree=3, vd_opacity=True, clusters=4, box=1.0, log_scale_mu=-3.0)
+    cam = ws.look_at((0.0, 0.0, -3.0), width=64, height=48).rounded()
+    w = ws.default_weight(ws.LC)
+    g = Gaussians.from_scene(sc)
+    params = [t.clone().requires_grad_(True) for t in (g.means, g.log_scales, g.quats, g.sh, g.opacity, g.lc_v)]
+    wpar = torch.tensor(w.as_array(), device="cuda", requires_grad=True)
+    gg = Gaussians(*params, g.sh_degree, g.view_dependent)
+    r = Renderer([cam])
+    img = render(r, w.kind, gg, wpar)
+    R = torch.randn_like(img)
+    (img * R).sum().backward()
+    st = r.forward(g, w.kind, wpar.detach())
+    raw = r.backward(g, w.kind, wpar.detach(), st, R)
+    for p, k in zip(params, ("means", "log_scales", "quats", "sh", "opacity", "lc_v")):
+        assert torch.allclose(p.grad, raw[k], rtol=1e-5, atol=1e-7), k
+    assert torch.allclose(wpar.grad, raw["weight_params"], rtol=1e-4, atol=1e-6)
+
+
+def test_l1_loss_kernel():
+    import torch
+    from paper_2410_18931_gb300 import Renderer
+    cam = ws.look_at((0.0, 0.0, -3.0), width=33, height=17)
+    r = Renderer([cam])
+    a = torch.rand(33 * 17, 3, device="cuda")
+    b = torch.rand(33 * 17, 3, device="cuda")
+    loss = torch.empty(1, device="cuda")
+    g = torch.empty_like(a)
+    r.loss_l1(a, b, loss, g)
+    ref = (a.double() - b.double()).abs().mean()
+    assert abs(loss.item() - ref.item()) < 1e-6
+    assert torch.equal(g, torch.sign(a - b) / a.numel())
