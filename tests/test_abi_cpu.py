@@ -13,8 +13,8 @@ HEADER = os.path.join(ROOT, "include", "wsr.h")
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2410_18931_gb300 import build
-    build.build()
+    import __graft_entry__
+    __graft_entry__._build_module().build()
     from paper_2410_18931_gb300 import _abi
     return _abi.load()
 
