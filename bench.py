@@ -1,0 +1,493 @@
+#!/usr/bin/env python3
+"""Weighted Sum Rendering benchmark: forward and forward+backward Mpix/s.
+
+Workload (default): 1,000,000 Gaussians in 64 clusters, SH degree 3,
+view-dependent opacity, LC weight, one 1920x1080 view on a ring of radius 5,
+16x16 tiles, L1 loss against a seeded random target.  One step is the whole
+hot path: project -> sort-free bin -> render forward -> L1 loss -> render
+backward (tiles) -> projection backward, every stage a C-ABI call.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
+on the launching stream; L2 is flushed (a 512 MB write) between steps outside
+the events.  The K-step region is bracketed by a barrier and
+torch.cuda.synchronize() on both sides; the per-step time is the maximum over
+ranks.  With N GPUs (torchrun) every rank renders its own ring view of the
+same scene (independent problems, weak scaling, no collective on the data
+path).
+
+Printed: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on a band of rows of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# FP32 work per (pixel, Gaussian) pair inside the cutoff, counted from the
+# inner loops of the render kernels (an FMA counts 2): forward 15, backward 45.
+FLOPS_PER_PAIR_FWD = 15
+FLOPS_PER_PAIR_BWD = 45
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+METRIC = "fwd and fwd+bwd Mpix/s at 1M Gaussians 1080p vs plain FP32 path; max err"
+KERNELS_PER_STEP = 10    # project 1, bin 5 (count, 3 scan, scatter), fwd 1, loss 1, bwd tiles 1, project bwd 1
+
+
+# --------------------------------------------------------------------------
+# multi-rank helpers (host logic; covered by the gloo tests)
+# --------------------------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def ring_view_for_rank(rank: int, world: int, width: int, height: int):
+    """Each rank renders its own camera of a ring of ``world`` cameras."""
+    import wsr_scenes as ws
+    return ws.ring_cameras(world, 5.0, width, height)[rank]
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# the measured path
+# --------------------------------------------------------------------------
+
+class Step:
+    """Buffers and the per-step sequence of C-ABI calls for one view."""
+
+    def __init__(self, scene, cam, weight, tile, target):
+        import torch
+
+        from paper_2410_18931_gb300 import Gaussians, Renderer
+        from paper_2410_18931_gb300 import _abi as A
+        self.A = A
+        self.torch = torch
+        self.g = Gaussians.from_scene(scene)
+        self.kind = weight.kind
+        self.wpar = torch.tensor(weight.as_array(), device="cuda")
+        self.r = Renderer([cam], tile=tile)
+        self.cam = cam
+        # size the tile list once (exact count + headroom), then fixed
+        self.st = self.r.forward(self.g, self.kind, self.wpar)
+        self.target = torch.as_tensor(target).reshape(-1, 3).cuda()
+        self.loss = torch.zeros(1, device="cuda")
+        self.grad_rgb = torch.empty_like(self.st.rgb)
+        n, K = self.g.n, (self.g.sh_degree + 1) ** 2
+        dev = "cuda"
+        self.out = dict(means=torch.empty(n, 3, device=dev), log_scales=torch.empty(n, 3, device=dev),
+                        quats=torch.empty(n, 4, device=dev), sh=torch.empty(n, K, 3, device=dev),
+                        opacity=torch.empty((n, K) if self.g.view_dependent else (n,), device=dev),
+                        lc_v=torch.empty(n, device=dev), weight_params=torch.empty(6, device=dev))
+        self.grads = A.wsr_grads(*[self.out[k].data_ptr() for k in
+                                   ("means", "log_scales", "quats", "sh", "opacity", "lc_v", "weight_params")])
+        self.grad_records = torch.empty(n * A.WSR_GRAD_RECORD_FLOATS, device=dev)
+        self.stream = torch.cuda.current_stream()
+        self.stage_names = ["project", "bin", "render_fwd", "loss", "render_bwd_tiles", "project_bwd"]
+
+    def run(self, events=None):
+        r, st, g, k, w = self.r, self.st, self.g, self.kind, self.wpar
+        ev = events or [None] * 7
+
+        def mark(i):
+            if ev[i] is not None:
+                ev[i].record(self.stream)
+        mark(0)
+        r.wsr_project(g, k, w, st.records)
+        mark(1)
+        r.wsr_bin(st.records, g.n, st.tile_offsets, st.tile_list)
+        mark(2)
+        r.wsr_render_fwd(st.records, g.n, st.tile_offsets, st.tile_list, k, w, st.rgb, st.den)
+        mark(3)
+        r.loss_l1(st.rgb, self.target, self.loss, self.grad_rgb)
+        mark(4)
+        r.wsr_render_bwd_tiles(st.records, g.n, st.tile_offsets, st.tile_list, k, w, st.rgb, st.den,
+                               self.grad_rgb, self.grad_records)
+        mark(5)
+        r.wsr_project_bwd(g, k, w, self.grad_records, self.grads)
+        mark(6)
+
+
+def build_workload(args, rank, world):
+    import wsr_scenes as ws
+    scene, cams, weight, extra = ws.workload(args.workload)
+    if world > 1:
+        cam = ring_view_for_rank(rank, world, cams[0].width, cams[0].height).rounded()
+    else:
+        cam = cams[0].rounded()
+    target = ws.target_image(extra.get("target_seed", 3) + rank, cam.height, cam.width)
+    return scene, cam, weight, extra, target
+
+
+def crop_rows(cam, y0, rows):
+    """The same camera restricted to image rows [y0, y0 + rows)."""
+    import copy
+    c = copy.deepcopy(cam)
+    c.cy = cam.cy - y0
+    c.height = rows
+    return c
+
+
+def profile_traffic(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, or None when the
+    kernel source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    d = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    if not m or not d:
+        return None
+    src = os.path.join(ROOT, "paper_2410_18931_gb300", "csrc", "render.cu")
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != d.group(1):
+        return None
+    return float(m.group(1))
+
+
+def cpu_oracle_leg(scene, cam, weight, target, gpu_rgb, budget_s: float):
+    """The FP64 oracle on a band of rows of the same workload (fwd + bwd),
+    sized to about ``budget_s`` seconds; also the max error of the GPU image
+    on that band.  Returns (baseline dict, max_err dict)."""
+    import numpy as np
+
+    import oracle
+    threads = os.cpu_count() or 1
+    y0 = cam.height // 2
+
+    def one(rows):
+        c = crop_rows(cam, y0 - rows // 2, rows)
+        t0 = time.perf_counter()
+        out = oracle.render(scene, c, weight, threads=threads, amb_tau=0.02)
+        tgt = target[y0 - rows // 2: y0 - rows // 2 + rows]
+        G = np.sign(out["rgb"] - tgt) / (3.0 * cam.width * cam.height)
+        oracle.grad(scene, c, weight, G, threads=threads)
+        return time.perf_counter() - t0, out, c
+
+    t8, _, _ = one(8)
+    rows = int(min(cam.height, max(8, 8 * budget_s / max(t8, 1e-3))))
+    rows -= rows % 2
+    t, out, c = one(rows)
+    y = y0 - rows // 2
+    gpu_band = gpu_rgb[y:y + rows]
+    err = np.abs(gpu_band.astype(np.float64) - out["rgb"])
+    excess = err - out["amb"][..., None]
+    base = {"value": round(rows * cam.width / t / 1e6, 4), "unit": "Mpix/s", "cores": threads, "kind": "oracle",
+            "sample": f"fwd+bwd (Eq. 7 and its gradient, FP64) on rows {y}..{y + rows - 1} "
+                      f"({rows}x{cam.width} px) of the same 1M-Gaussian 1080p view, {t:.1f} s"}
+    maxerr = {"max_abs_err": float(err.max()), "max_abs_err_beyond_tie_bound": float(max(excess.max(), 0.0)),
+              "pixels_checked": int(rows * cam.width), "tolerance": 1e-4}
+    return base, maxerr
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle, as it stands, on host cores."""
+    import numpy as np
+
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    scene, cam, weight, extra, target = build_workload(args, 0, 1)
+    threads = os.cpu_count() or 1
+    total_budget = 150.0
+    per_step = total_budget / max(1, args.steps + args.warmup)
+    y0 = cam.height // 2
+
+    def step(rows):
+        c = crop_rows(cam, y0 - rows // 2, rows)
+        out = oracle.render(scene, c, weight, threads=threads)
+        tgt = target[y0 - rows // 2: y0 - rows // 2 + rows]
+        G = np.sign(out["rgb"] - tgt) / (3.0 * cam.width * cam.height)
+        oracle.grad(scene, c, weight, G, threads=threads)
+
+    t0 = time.perf_counter()
+    step(8)
+    t8 = time.perf_counter() - t0
+    rows = int(min(cam.height, max(8, 8 * per_step / max(t8, 1e-3))))
+    for _ in range(args.warmup):
+        step(rows)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(rows)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = rows * cam.width / dt / 1e6
+    line = {"metric": METRIC, "value": round(value, 4), "unit": "Mpix/s",
+            "impl": "reference", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": extra["name"], "rows_per_step": rows, "width": cam.width},
+            "cpu_baseline": {"value": round(value, 4), "unit": "Mpix/s", "cores": threads, "kind": "oracle",
+                             "sample": f"fwd+bwd on a {rows}-row band of the 1920x1080 view per step"},
+            "e2e": {"value": round(value, 4), "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://", world_size=world, rank=rank,
+                                device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev_index = torch.cuda.current_device()
+
+    scene, cam, weight, extra, target = build_workload(args, rank, world)
+    tile = tuple(int(v) for v in args.tile.split("x"))
+    S = Step(scene, cam, weight, tile, target)
+    A = S.A
+    npix = cam.width * cam.height
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    # pair statistics (outside timing): algorithmic pairs and tile instances
+    S.run()
+    torch.cuda.synchronize()
+    pairs = S.r.wsr_count_pairs(S.st)
+    instances = S.r.wsr_bin_total()
+    A.check("wsr_bin", S.r.wsr_check())
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        S.run()
+    torch.cuda.synchronize()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    clocks = ClockSampler(dev_index)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()                      # L2 flush, outside the step's events
+        S.run(evs[k])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier()
+    clk = clocks.stop()
+    status = S.r.wsr_check()               # no list overflow in the timed steps
+    A.check("wsr_bin (timed)", status)
+
+    stage = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(6)] for k in range(args.steps)])
+    step_ms = stage.sum(axis=1)
+    ms = float(step_ms.mean())
+    ms_max = max_over_ranks(ms, device="cuda")
+    stage_ms = stage.mean(axis=0)
+    fwd_ms = float(stage_ms[0] + stage_ms[1] + stage_ms[2])
+    fwd_ms = max_over_ranks(fwd_ms, device="cuda")
+    value = world * npix / (ms_max * 1e-3) / 1e6
+    fwd_value = world * npix / (fwd_ms * 1e-3) / 1e6
+
+    # ---- e2e: same step through the public API with host buffers ---------
+    e2e = None if args.no_e2e else run_e2e(args, S, scene, target, flush)
+
+    # ---- roofline of the dominant kernel ----------------------------------
+    names = S.stage_names
+    dom = int(np.argmax(stage_ms))
+    sms = torch.cuda.get_device_properties(dev_index).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roof = None
+    if names[dom] in ("render_bwd_tiles", "render_fwd"):
+        fl = FLOPS_PER_PAIR_BWD if names[dom] == "render_bwd_tiles" else FLOPS_PER_PAIR_FWD
+        ach = pairs * fl / (stage_ms[dom] * 1e-3) / 1e12
+        kern = "k_render_bwd" if names[dom] == "render_bwd_tiles" else "k_render_fwd"
+        roof = {"bound": "alu", "kernel": kern, "achieved": round(ach, 3), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": profile_traffic(kern),
+                "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 (FMA) x {SM_MAX_MHZ:.0f} MHz",
+                "work": f"{pairs} pairs with q <= 9 x {fl} FP32 flops"}
+    else:
+        roof = {"bound": "hbm", "kernel": names[dom], "achieved": None, "peak": None, "unit": "GB/s",
+                "frac": None, "traffic": None}
+
+    # ---- stage rooflines (context) ----------------------------------------
+    hbm_peak = 6780.0
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm_peak = float(mp.get("hbm_gbs", hbm_peak))
+    except Exception:
+        pass
+    K = (S.g.sh_degree + 1) ** 2
+    param_bytes = S.g.n * (12 + 12 + 16 + K * 12 + (K * 4 if S.g.view_dependent else 4) + 4)
+    stages = {n: round(float(v), 4) for n, v in zip(names, stage_ms)}
+    extra_out = {
+        "fwd_mpix_s": round(fwd_value, 2),
+        "stage_ms": stages,
+        "project_hbm_frac": round((param_bytes + S.g.n * 48) / (stage_ms[0] * 1e-3) / 1e9 / hbm_peak, 4),
+        "project_bwd_hbm_frac": round((2 * param_bytes + S.g.n * 36) / (stage_ms[5] * 1e-3) / 1e9 / hbm_peak, 4),
+        "pairs_in_cutoff": pairs, "tile_instances": instances,
+        "bbox_overhead": round(instances * tile[0] * tile[1] / max(pairs, 1), 3),
+    }
+
+    line = {"metric": METRIC, "value": round(value, 2),
+            "unit": "Mpix/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms_max, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": extra["name"], "gaussians": S.g.n, "width": cam.width, "height": cam.height,
+                       "sh_degree": S.g.sh_degree, "opacity": "view-dependent SH", "weight": "lc",
+                       "tile": args.tile, "views_per_rank": 1,
+                       "l2": "flushed between steps (512 MB write outside the step events)"},
+            "gpu_launches": KERNELS_PER_STEP * args.steps, "roofline": roof, "clocks": clk, "e2e": e2e,
+            "wall_s_timed_region": round(wall, 4)}
+    line.update(extra_out)
+
+    if rank == 0 and not args.no_cpu_baseline:
+        gpu_rgb = S.st.rgb.reshape(cam.height, cam.width, 3).cpu().numpy()
+        base, maxerr = cpu_oracle_leg(scene, cam, weight, target, gpu_rgb, args.cpu_budget)
+        line["cpu_baseline"] = base
+        line["max_err"] = maxerr
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_e2e(args, S, scene, target, flush):
+    """The step through the C ABI with host inputs: every step copies the
+    Gaussian parameters and the target from pinned host memory and reads back
+    the loss and the rendered image."""
+    import numpy as np
+    import torch
+    g = S.g
+    host = {k: getattr(g, k).cpu().pin_memory() for k in ("means", "log_scales", "quats", "sh", "opacity", "lc_v")}
+    tgt_h = S.target.cpu().pin_memory()
+    rgb_h = torch.empty_like(S.st.rgb, device="cpu").pin_memory()
+    loss_h = torch.empty(1).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in host.values()) + tgt_h.numel() * 4
+    d2h = rgb_h.numel() * 4 + 4
+
+    def one():
+        for k, v in host.items():
+            getattr(g, k).copy_(v, non_blocking=True)
+        S.target.copy_(tgt_h, non_blocking=True)
+        S.run()
+        rgb_h.copy_(S.st.rgb, non_blocking=True)
+        loss_h.copy_(S.loss, non_blocking=True)
+
+    for _ in range(max(2, args.warmup)):
+        one()
+    torch.cuda.synchronize()
+    n = max(3, args.steps // 2)
+    times = []
+    for _ in range(n):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        one()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = max_over_ranks(float(np.mean(times)), device="cuda")
+    world = dist_env()[0]
+    npix = S.cam.width * S.cam.height
+    return {"value": round(world * npix / (ms * 1e-3) / 1e6, 2), "unit": "Mpix/s", "ms_per_step": round(ms, 4),
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", type=int, default=3)
+    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -261,6 +261,16 @@ wsr_status wsr_loss_l1(const float* rgb, const float* target, int64_t count, flo
                        float* grad_rgb, void* stream);
 
 /*
+ * wsr_count_pairs — diagnostic: the number of (pixel, Gaussian) pairs with
+ * q <= 9 over all views, i.e. the terms of the sums of Eq. 7 that the render
+ * kernels evaluate (their algorithmic work), written to *count_dev (device
+ * uint64, overwritten).  Arguments as for wsr_render_fwd.
+ */
+wsr_status wsr_count_pairs(const float* records, int64_t n, const uint32_t* tile_offsets,
+                           const uint32_t* tile_list, const wsr_camera* cams, int32_t n_cams,
+                           const wsr_tiles* tiles, uint64_t* count_dev, void* stream);
+
+/*
  * wsr_check — synchronises `stream` and returns the first device-side error
  * recorded in the workspace (WSR_OK if none), then clears it.
  */

@@ -320,6 +320,17 @@ wsr_status wsr_render_bwd(const wsr_gaussians* g, const float* records, const ui
     return wsr_project_bwd(g, cams, n_cams, w, grad_records, grads, workspace, workspace_bytes, stream);
 }
 
+wsr_status wsr_count_pairs(const float* records, int64_t n, const uint32_t* tile_offsets, const uint32_t* tile_list,
+                           const wsr_camera* cams, int32_t n_cams, const wsr_tiles* tiles, uint64_t* count_dev,
+                           void* stream) {
+    static thread_local Views vs;
+    if (!tiles || !count_dev || !tile_offsets || n < 0) return WSR_ERR_INVALID_ARG;
+    if (n > 0 && (!records || !tile_list)) return WSR_ERR_INVALID_ARG;
+    WSR_TRY(make_views(cams, n_cams, tiles, &vs));
+    return cuda_status(launch_count_pairs(records, tile_offsets, tile_list, vs, (unsigned long long*)count_dev,
+                                          (cudaStream_t)stream));
+}
+
 wsr_status wsr_loss_l1(const float* rgb, const float* target, int64_t count, float* loss_out, float* grad_rgb,
                        void* stream) {
     if (count < 0 || !loss_out || (count > 0 && (!rgb || !target || !grad_rgb))) return WSR_ERR_INVALID_ARG;

@@ -276,6 +276,54 @@ cudaError_t bwd_t(const float* rec, const unsigned* off, const unsigned* list, c
     return cudaGetLastError();
 }
 
+// Diagnostic: (pixel, Gaussian) pairs inside the cutoff, i.e. the
+// algorithmic work of the render kernels (same arithmetic as the forward).
+template <int TW, int TH, int PPT>
+__global__ void __launch_bounds__(TileShape<TW, TH, PPT>::NT)
+    k_count_pairs(const float4* __restrict__ rec, const unsigned* __restrict__ offsets,
+                  const unsigned* __restrict__ list, const Views vs, unsigned long long* __restrict__ count) {
+    using S = TileShape<TW, TH, PPT>;
+    constexpr int NT = S::NT;
+    __shared__ float4 s0[NT];
+    __shared__ float s1[NT];
+    const int tile = blockIdx.x;
+    const TileCoord tc = tile_coord(vs, tile);
+    const View& V = vs.v[tc.v];
+    const int tid = threadIdx.x;
+    const int lx = tid % TW, ly = tid / TW;
+    const int x = tc.tx * TW + lx;
+    const int y0 = tc.ty * TH + ly * PPT;
+    const float px = (float)x + 0.5f;
+    unsigned long long cnt_pairs = 0;
+    const unsigned start = offsets[tile], end = offsets[tile + 1];
+    for (unsigned base = start; base < end; base += NT) {
+        const int cnt = (int)min((unsigned)NT, end - base);
+        __syncthreads();
+        if (tid < cnt) {
+            const float4* p = rec + 3ull * list[base + tid];
+            s0[tid] = __ldg(p);
+            s1[tid] = __ldg(reinterpret_cast<const float*>(p + 1));
+        }
+        __syncthreads();
+        if (x >= V.W) continue;
+        for (int j = 0; j < cnt; ++j) {
+            const float4 a = s0[j];
+            const float dx = px - a.x;
+            const float P = a.z * dx * dx;
+            const float Q = a.w * dx;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                const float dy = (float)(y0 + k) + 0.5f - a.y;
+                const float q = fmaf(dy, fmaf(s1[j], dy, Q), P);
+                if (q <= kQMax && y0 + k < V.H) ++cnt_pairs;
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) cnt_pairs += __shfl_xor_sync(0xffffffffu, cnt_pairs, off);
+    if ((tid & 31) == 0 && cnt_pairs) atomicAdd(count, cnt_pairs);
+}
+
 __global__ void k_loss_l1(const float* __restrict__ rgb, const float* __restrict__ target, long long count,
                           float* __restrict__ loss, float* __restrict__ grad) {
     const float inv = 1.0f / (float)count;
@@ -311,6 +359,19 @@ cudaError_t launch_render_bwd(const float* rec, const unsigned* off, const unsig
     if (vs.tile_w == 32 && vs.tile_h == 8) return bwd_t<32, 8, 2>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, s);
     if (vs.tile_w == 16 && vs.tile_h == 8) return bwd_t<16, 8, 2>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, s);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_count_pairs(const float* rec, const unsigned* off, const unsigned* list, const Views& vs,
+                               unsigned long long* count, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess || vs.total_tiles == 0) return e;
+    const float4* r = reinterpret_cast<const float4*>(rec);
+    if (vs.tile_w == 16 && vs.tile_h == 16) k_count_pairs<16, 16, 2><<<vs.total_tiles, 128, 0, s>>>(r, off, list, vs, count);
+    else if (vs.tile_w == 8 && vs.tile_h == 8) k_count_pairs<8, 8, 2><<<vs.total_tiles, 32, 0, s>>>(r, off, list, vs, count);
+    else if (vs.tile_w == 32 && vs.tile_h == 8) k_count_pairs<32, 8, 2><<<vs.total_tiles, 128, 0, s>>>(r, off, list, vs, count);
+    else if (vs.tile_w == 16 && vs.tile_h == 8) k_count_pairs<16, 8, 2><<<vs.total_tiles, 64, 0, s>>>(r, off, list, vs, count);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_loss_l1(const float* rgb, const float* target, long long count, float* loss, float* grad,

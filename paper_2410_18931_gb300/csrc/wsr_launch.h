@@ -47,6 +47,9 @@ cudaError_t launch_render_bwd(const float* records, const unsigned* tile_offsets
                               const float* out_rgb, const float* out_den, const float* grad_rgb,
                               float* grad_records, float* grad_wparams, cudaStream_t s);
 
+cudaError_t launch_count_pairs(const float* records, const unsigned* tile_offsets, const unsigned* tile_list,
+                               const Views& vs, unsigned long long* count, cudaStream_t s);
+
 cudaError_t launch_loss_l1(const float* rgb, const float* target, long long count,
                            float* loss, float* grad, cudaStream_t s);
 
