@@ -26,7 +26,8 @@ def _worker(rank, world, port, q):
         t = bench.max_over_ranks(10.0 + 5.0 * rank, device="cpu")
         cam = bench.ring_view_for_rank(rank, world, 64, 48)
         bench.barrier()
-        q.put((rank, w, r, t, np.asarray(cam.T).tolist()))
+        centre = -np.asarray(cam.R).T @ np.asarray(cam.T)
+        q.put((rank, w, r, t, centre.tolist()))
     finally:
         dist.destroy_process_group()
 
