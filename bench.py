@@ -201,15 +201,6 @@ def build_workload(args, rank, world):
     return scene, cam, weight, extra, target
 
 
-def crop_rows(cam, y0, rows):
-    """The same camera restricted to image rows [y0, y0 + rows)."""
-    import copy
-    c = copy.deepcopy(cam)
-    c.cy = cam.cy - y0
-    c.height = rows
-    return c
-
-
 def profile_traffic(kernel: str):
     """DRAM bytes per launch from a committed ncu summary, or None when the
     kernel source changed since it was captured."""
@@ -238,18 +229,18 @@ def cpu_oracle_leg(scene, cam, weight, target, gpu_rgb, budget_s: float):
     y0 = cam.height // 2
 
     def one(rows):
-        c = crop_rows(cam, y0 - rows // 2, rows)
+        band = (y0 - rows // 2, y0 - rows // 2 + rows)
         t0 = time.perf_counter()
-        out = oracle.render(scene, c, weight, threads=threads, amb_tau=0.02)
-        tgt = target[y0 - rows // 2: y0 - rows // 2 + rows]
+        out = oracle.render(scene, cam, weight, threads=threads, amb_tau=0.02, rows=band)
+        tgt = target[band[0]:band[1]]
         G = np.sign(out["rgb"] - tgt) / (3.0 * cam.width * cam.height)
-        oracle.grad(scene, c, weight, G, threads=threads)
-        return time.perf_counter() - t0, out, c
+        oracle.grad(scene, cam, weight, G, threads=threads, rows=band)
+        return time.perf_counter() - t0, out
 
-    t8, _, _ = one(8)
+    t8, _ = one(8)
     rows = int(min(cam.height, max(8, 8 * budget_s / max(t8, 1e-3))))
     rows -= rows % 2
-    t, out, c = one(rows)
+    t, out = one(rows)
     y = y0 - rows // 2
     gpu_band = gpu_rgb[y:y + rows]
     err = np.abs(gpu_band.astype(np.float64) - out["rgb"])
@@ -277,11 +268,11 @@ def run_reference(args):
     y0 = cam.height // 2
 
     def step(rows):
-        c = crop_rows(cam, y0 - rows // 2, rows)
-        out = oracle.render(scene, c, weight, threads=threads)
-        tgt = target[y0 - rows // 2: y0 - rows // 2 + rows]
+        band = (y0 - rows // 2, y0 - rows // 2 + rows)
+        out = oracle.render(scene, cam, weight, threads=threads, rows=band)
+        tgt = target[band[0]:band[1]]
         G = np.sign(out["rgb"] - tgt) / (3.0 * cam.width * cam.height)
-        oracle.grad(scene, c, weight, G, threads=threads)
+        oracle.grad(scene, cam, weight, G, threads=threads, rows=band)
 
     t0 = time.perf_counter()
     step(8)

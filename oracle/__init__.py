@@ -50,12 +50,12 @@ def _load():
             common = [ctypes.c_long, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, dp,
                       dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp]
             lib.wsro_project.argtypes = common + [dp]
-            lib.wsro_render.argtypes = common + [ctypes.c_int, dp, dp, dp, ctypes.c_double,
-                                                 ctypes.POINTER(ctypes.c_longlong)]
+            lib.wsro_render.argtypes = common + [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp,
+                                                 ctypes.c_double, ctypes.POINTER(ctypes.c_longlong)]
             lib.wsro_render_pixels.argtypes = common + [ctypes.c_int, ctypes.c_long,
                                                         ctypes.POINTER(ctypes.c_int), dp, dp, dp,
                                                         ctypes.c_double]
-            lib.wsro_grad.argtypes = common + [ctypes.c_int, dp] + [dp] * 8
+            lib.wsro_grad.argtypes = common + [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp] + [dp] * 8
             lib.wsro_sh_basis.argtypes = [ctypes.c_long, ctypes.c_int, dp, dp, dp]
             for f in (lib.wsro_project, lib.wsro_render, lib.wsro_render_pixels, lib.wsro_grad,
                       lib.wsro_sh_basis):
@@ -111,22 +111,25 @@ def project(scene, cam, weight) -> dict:
                 depth=out[:, 17], rx=out[:, 18], ry=out[:, 19])
 
 
-def render(scene, cam, weight, *, threads: int | None = None, amb_tau: float | None = None):
-    """Full-image WSR forward (Eq. 7).
+def render(scene, cam, weight, *, threads: int | None = None, amb_tau: float | None = None, rows=None):
+    """WSR forward (Eq. 7) over the whole image, or over image rows
+    ``rows = (y_lo, y_hi)`` of the same camera.
 
-    Returns dict(rgb [H, W, 3], den [H, W] = w_B + sum a_i, pairs, amb [H, W]
+    Returns dict(rgb [h, W, 3], den [h, W] = w_B + sum a_i, pairs, amb [h, W]
     or None).  ``amb`` bounds how far a pixel can move if the pairs within
     ``amb_tau`` of the q <= 9 cutoff were decided the other way.
     """
     lib = _load()
     a = _Args(scene, cam, weight)
-    H, W = cam.height, cam.width
+    y_lo, y_hi = rows if rows is not None else (0, cam.height)
+    H, W = y_hi - y_lo, cam.width
     rgb = np.zeros((H, W, 3), np.float64)
     den = np.zeros((H, W), np.float64)
     amb = np.zeros((H, W), np.float64) if amb_tau is not None else None
     pairs = ctypes.c_longlong(0)
-    rc = lib.wsro_render(*a.args, ctypes.c_int(threads or default_threads()), _ptr(rgb), _ptr(den),
-                         _ptr(amb), ctypes.c_double(amb_tau or 0.0), ctypes.byref(pairs))
+    rc = lib.wsro_render(*a.args, ctypes.c_int(threads or default_threads()), ctypes.c_int(y_lo),
+                         ctypes.c_int(y_hi), _ptr(rgb), _ptr(den), _ptr(amb), ctypes.c_double(amb_tau or 0.0),
+                         ctypes.byref(pairs))
     if rc:
         raise RuntimeError(f"wsro_render failed ({rc})")
     return dict(rgb=rgb, den=den, pairs=int(pairs.value), amb=amb)
@@ -150,16 +153,19 @@ def render_pixels(scene, cam, weight, xy, *, threads: int | None = None, amb_tau
     return dict(rgb=rgb, den=den, amb=amb)
 
 
-def grad(scene, cam, weight, grad_rgb, *, threads: int | None = None) -> dict:
-    """Analytic gradient of <grad_rgb, C> with respect to every parameter."""
+def grad(scene, cam, weight, grad_rgb, *, threads: int | None = None, rows=None) -> dict:
+    """Analytic gradient of <grad_rgb, C> with respect to every parameter;
+    with ``rows = (y_lo, y_hi)``, grad_rgb covers only those image rows."""
     lib = _load()
     a = _Args(scene, cam, weight)
     n, K = scene.n, a.K
-    G = _d(grad_rgb).reshape(cam.height, cam.width, 3)
+    y_lo, y_hi = rows if rows is not None else (0, cam.height)
+    G = _d(grad_rgb).reshape(y_hi - y_lo, cam.width, 3)
     out = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
                sh=np.zeros((n, K, 3)), opacity=np.zeros((n, K)) if a.vd else np.zeros(n),
                lc_v=np.zeros(n), wpar=np.zeros(6), g2d=np.zeros((n, 9)))
-    rc = lib.wsro_grad(*a.args, ctypes.c_int(threads or default_threads()), _ptr(G),
+    rc = lib.wsro_grad(*a.args, ctypes.c_int(threads or default_threads()), ctypes.c_int(y_lo),
+                       ctypes.c_int(y_hi), _ptr(G),
                        _ptr(out["means"]), _ptr(out["log_scales"]), _ptr(out["quats"]),
                        _ptr(out["sh"]), _ptr(out["opacity"]), _ptr(out["lc_v"]),
                        _ptr(out["wpar"]), _ptr(out["g2d"]))

@@ -378,7 +378,8 @@ int wsro_sh_basis(long n, int deg, const double* dirs, double* Y /* n x K */, do
 /* ------------------------------------------------------------------------ */
 typedef struct {
     const oproj* P; long n; const ocam* cam; const owt* wt;
-    double *num, *den;       /* [H*W*3], [H*W] sums (without background) */
+    int y_lo;                /* first image row of the window held in the buffers */
+    double *num, *den;       /* [rows*W*3], [rows*W] sums (without background) */
     long long* pairs;        /* per thread */
     double amb_tau;          /* window around the cutoff */
     double* amb;             /* [H*W] or NULL: filled in a second pass */
@@ -389,6 +390,8 @@ typedef struct {
 static void render_rows(void* arg, long r0, long r1, int tid)
 {
     render_ctx* c = (render_ctx*)arg;
+    r0 += c->y_lo;
+    r1 += c->y_lo;
     const int W = c->cam->W;
     long long pairs = 0;
     const double grow = c->amb ? sqrt((ORC_CUTOFF + c->amb_tau) / ORC_CUTOFF) : 1.0;
@@ -403,7 +406,7 @@ static void render_rows(void* arg, long r0, long r1, int tid)
             for (int x = x0; x <= x1; ++x) {
                 const double dx = x + 0.5 - o->mean2d[0], dy = y + 0.5 - o->mean2d[1];
                 const double q = quad_form(o->conic, dx, dy);
-                const long p = (long)y * W + x;
+                const long p = (long)(y - c->y_lo) * W + x;
                 if (c->amb) {
                     /* second pass: bound of what a near-cutoff pair can change */
                     if (fabs(q - ORC_CUTOFF) <= c->amb_tau) {
@@ -439,7 +442,8 @@ static oproj* project_all(const oscene* S, const ocam* cam, const owt* wt)
 }
 
 /*
- * out_rgb [H*W*3]: C per pixel (Eq. 7); out_den [H*W]: w_B + sum a_i.
+ * Rows [y_lo, y_hi) of the image (the whole image for 0, H).
+ * out_rgb [rows*W*3]: C per pixel (Eq. 7); out_den [rows*W]: w_B + sum a_i.
  * amb [H*W] (optional): for pixels having Gaussians with |q - 9| <= amb_tau,
  * a bound on how far C can move if those pairs were decided the other way.
  * n_pairs (optional): number of (pixel, Gaussian) pairs with q <= 9.
@@ -447,23 +451,25 @@ static oproj* project_all(const oscene* S, const ocam* cam, const owt* wt)
 int wsro_render(long n, int deg, int vd, const double* means, const double* log_scales,
                 const double* quats, const double* sh, const double* opac, const double* lc_v,
                 const double* cam16, int W, int H, double znear, int wkind, const double* wpar,
-                int nthreads, double* out_rgb, double* out_den, double* amb, double amb_tau,
-                long long* n_pairs)
+                int nthreads, int y_lo, int y_hi, double* out_rgb, double* out_den, double* amb,
+                double amb_tau, long long* n_pairs)
 {
     if (deg < 0 || deg > 3 || n < 0 || W <= 0 || H <= 0) return 1;
+    if (y_lo < 0 || y_hi > H || y_lo >= y_hi) return 1;
+    const int rows = y_hi - y_lo;
     oscene S; ocam cam; owt wt;
     fill_scene(&S, n, deg, vd, means, log_scales, quats, sh, opac, lc_v);
     make_cam(&cam, cam16, W, H, znear);
     make_wt(&wt, wkind, wpar);
     oproj* P = project_all(&S, &cam, &wt);
     if (!P) return 2;
-    const long np = (long)W * H;
+    const long np = (long)W * rows;
     double* num = (double*)calloc(np * 3, sizeof(double));
     double* den = (double*)calloc(np, sizeof(double));
     long long pairs[256] = {0};
-    render_ctx c = {P, n, &cam, &wt, num, den, pairs, amb_tau, NULL, NULL, NULL};
-    if (nthreads > H) nthreads = H;
-    run_parallel(render_rows, &c, H, nthreads);
+    render_ctx c = {P, n, &cam, &wt, y_lo, num, den, pairs, amb_tau, NULL, NULL, NULL};
+    if (nthreads > rows) nthreads = rows;
+    run_parallel(render_rows, &c, rows, nthreads);
     long long tot = 0;
     for (int t = 0; t < 256; ++t) tot += pairs[t];
     if (n_pairs) *n_pairs = tot;
@@ -474,8 +480,8 @@ int wsro_render(long n, int deg, int vd, const double* means, const double* log_
     }
     if (amb) {
         memset(amb, 0, np * sizeof(double));
-        render_ctx c2 = {P, n, &cam, &wt, NULL, NULL, pairs, amb_tau, amb, out_rgb, out_den};
-        run_parallel(render_rows, &c2, H, nthreads);
+        render_ctx c2 = {P, n, &cam, &wt, y_lo, NULL, NULL, pairs, amb_tau, amb, out_rgb, out_den};
+        run_parallel(render_rows, &c2, rows, nthreads);
         for (long p = 0; p < np; ++p) amb[p] *= 1.05;
     }
     free(num); free(den); free(P);
@@ -555,7 +561,8 @@ int wsro_render_pixels(long n, int deg, int vd, const double* means, const doubl
 /* ------------------------------------------------------------------------ */
 /* Public: analytic gradient                                                 */
 /*                                                                          */
-/* Given G = dL/dC per pixel, with C from Eq. 7:                            */
+/* Given G = dL/dC per pixel of rows [y_lo, y_hi), with C from Eq. 7 (the    */
+/* loss depends on those rows only):                                        */
 /*   dL/da_i(p)  = G_p . (c_i - C_p) / D_p                                  */
 /*   dL/dc_i     = sum_p G_p a_i(p) / D_p                                   */
 /*   dL/dc_B     = sum_p G_p w_B / D_p                                      */
@@ -575,6 +582,7 @@ int wsro_render_pixels(long n, int deg, int vd, const double* means, const doubl
 /* ------------------------------------------------------------------------ */
 typedef struct {
     const oscene* S; const oproj* P; const ocam* cam; const owt* wt;
+    int y_lo, y_hi;          /* image rows covered by rgb, den and G */
     const double *rgb, *den, *G;
     double *g_means, *g_log_scales, *g_quats, *g_sh, *g_opac, *g_lc_v, *g2d;
     double gw[256][2];     /* per-thread partial sums: sigma, beta */
@@ -596,13 +604,15 @@ static void grad_gaussians(void* arg, long lo, long hi, int tid)
         /* ---- per-pixel part: Eq. 7 and the Gaussian footprint ---- */
         int x0, x1, y0, y1;
         pixel_range(o, cam, 1.0, &x0, &x1, &y0, &y1);
+        if (y0 < c->y_lo) y0 = c->y_lo;
+        if (y1 > c->y_hi - 1) y1 = c->y_hi - 1;
         const double uw = o->u * o->w;
         for (int y = y0; y <= y1; ++y)
             for (int x = x0; x <= x1; ++x) {
                 const double dx = x + 0.5 - o->mean2d[0], dy = y + 0.5 - o->mean2d[1];
                 const double q = quad_form(o->conic, dx, dy);
                 if (q > ORC_CUTOFF) continue;
-                const long p = (long)y * W + x;
+                const long p = (long)(y - c->y_lo) * W + x;
                 const double g = exp(-0.5 * q);
                 const double a = uw * g;
                 const double D = c->den[p];
@@ -765,26 +775,27 @@ static void grad_gaussians(void* arg, long lo, long hi, int tid)
 int wsro_grad(long n, int deg, int vd, const double* means, const double* log_scales,
               const double* quats, const double* sh, const double* opac, const double* lc_v,
               const double* cam16, int W, int H, double znear, int wkind, const double* wpar,
-              int nthreads, const double* grad_rgb,
+              int nthreads, int y_lo, int y_hi, const double* grad_rgb,
               double* g_means, double* g_log_scales, double* g_quats, double* g_sh,
               double* g_opac, double* g_lc_v, double* g_wpar, double* g2d)
 {
     if (deg < 0 || deg > 3 || n < 0 || W <= 0 || H <= 0) return 1;
+    if (y_lo < 0 || y_hi > H || y_lo >= y_hi) return 1;
     oscene S; ocam cam; owt wt;
     fill_scene(&S, n, deg, vd, means, log_scales, quats, sh, opac, lc_v);
     make_cam(&cam, cam16, W, H, znear);
     make_wt(&wt, wkind, wpar);
-    const long np = (long)W * H;
+    const long np = (long)W * (y_hi - y_lo);
     double* rgb = (double*)malloc(np * 3 * sizeof(double));
     double* den = (double*)malloc(np * sizeof(double));
     if (!rgb || !den) { free(rgb); free(den); return 2; }
     int rc = wsro_render(n, deg, vd, means, log_scales, quats, sh, opac, lc_v, cam16, W, H, znear,
-                         wkind, wpar, nthreads, rgb, den, NULL, 0.0, NULL);
+                         wkind, wpar, nthreads, y_lo, y_hi, rgb, den, NULL, 0.0, NULL);
     if (rc) { free(rgb); free(den); return rc; }
     oproj* P = project_all(&S, &cam, &wt);
     if (!P) { free(rgb); free(den); return 2; }
     grad_ctx* c = (grad_ctx*)calloc(1, sizeof(grad_ctx));
-    c->S = &S; c->P = P; c->cam = &cam; c->wt = &wt;
+    c->S = &S; c->P = P; c->cam = &cam; c->wt = &wt; c->y_lo = y_lo; c->y_hi = y_hi;
     c->rgb = rgb; c->den = den; c->G = grad_rgb;
     c->g_means = g_means; c->g_log_scales = g_log_scales; c->g_quats = g_quats; c->g_sh = g_sh;
     c->g_opac = g_opac; c->g_lc_v = g_lc_v; c->g2d = g2d;

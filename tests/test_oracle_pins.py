@@ -395,3 +395,23 @@ def test_gradient_2d_records_match_finite_differences_of_projection_outputs():
         uw = P["u"][i] * P["w"][i]
         fd = (lp - lm) / (2 * h * uw)            # d/d(uw) since uw scales by (1 +- h)
         assert abs(fd - an["g2d"][i, 5]) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_row_window_equals_rows_of_the_full_image():
+    """A window of rows of the same camera (the same Jacobian clamp) is the
+    corresponding rows of the full image, and its gradient is the gradient
+    of a loss on those rows only."""
+    sc = tiny_scene(60, 3, True)
+    cam = tiny_cam()
+    w = WEIGHTS[2]
+    full = oracle.render(sc, cam, w, amb_tau=0.02)
+    win = oracle.render(sc, cam, w, rows=(7, 19), amb_tau=0.02)
+    assert np.array_equal(win["rgb"], full["rgb"][7:19])
+    assert np.array_equal(win["amb"], full["amb"][7:19])
+    R = np.random.default_rng(2).normal(size=(cam.height, cam.width, 3))
+    R[:7] = 0.0
+    R[19:] = 0.0
+    gf = oracle.grad(sc, cam, w, R)
+    gw = oracle.grad(sc, cam, w, R[7:19], rows=(7, 19))
+    for k in ("means", "log_scales", "quats", "sh", "opacity", "lc_v", "wpar"):
+        assert np.abs(gf[k] - gw[k]).max() <= 1e-12 * max(1.0, np.abs(gf[k]).max()), k
