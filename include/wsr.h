@@ -261,6 +261,38 @@ wsr_status wsr_loss_l1(const float* rgb, const float* target, int64_t count, flo
                        float* grad_rgb, void* stream);
 
 /*
+ * wsr_bin_static — wsr_bin for callers that cannot allocate device memory.
+ *
+ * Some callers cannot call cudaMalloc at all once they are running: a frame
+ * loop inside a host application that owns the GPU's memory budget and
+ * forbids device allocations after start-up (an allocation can synchronise
+ * the whole device and stall the frame), or a plug-in that is handed only its
+ * input and output buffers by its host.  This entry point needs no workspace:
+ * its scratch (per-tile counters, scan partial sums, a small header) lives in
+ * one fixed device array inside this library, about 257 KB, which every GPU
+ * that loads the library holds until the process exits.  The paper has no
+ * counterpart; this is an integration entry point, not part of the method.
+ *
+ * Arguments and results are those of wsr_bin, except:
+ *   - there is no workspace: at most WSR_BIN_STATIC_MAX_TILES tiles over all
+ *     views; more returns WSR_ERR_UNSUPPORTED before anything is enqueued;
+ *   - total_dev [1] uint64 device output (may be NULL): the true number of tile
+ *     instances.  When it exceeds list_capacity the list is incomplete and the
+ *     offsets are clamped to list_capacity, as in wsr_bin.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array, and the array keeps the last
+ * call's contents (each call clears what it needs cleared): calls that overlap
+ * on the GPU (on different streams, or from different threads) race on it.
+ * The call allocates nothing: no cudaMalloc, no cudaFree, no allocating
+ * library routine.
+ */
+#define WSR_BIN_STATIC_MAX_TILES 65536
+wsr_status wsr_bin_static(const float* records, int64_t n, const wsr_camera* cams, int32_t n_cams,
+                          const wsr_tiles* tiles, uint32_t* tile_offsets, uint32_t* tile_list,
+                          uint64_t list_capacity, uint64_t* total_dev, void* stream);
+
+/*
  * wsr_count_pairs — diagnostic: the number of (pixel, Gaussian) pairs with
  * q <= 9 over all views, i.e. the terms of the sums of Eq. 7 that the render
  * kernels evaluate (their algorithmic work), written to *count_dev (device

@@ -76,6 +76,8 @@ _SIGS = {
                                             _c_void_p, _c_void_p, _c_void_p, ctypes.c_size_t, _c_void_p]),
     "wsr_project_bwd": (ctypes.c_int, [_P(wsr_gaussians), _P(wsr_camera), ctypes.c_int32, _P(wsr_weight),
                                        _c_void_p, _P(wsr_grads), _c_void_p, ctypes.c_size_t, _c_void_p]),
+    "wsr_bin_static": (ctypes.c_int, [_c_void_p, ctypes.c_int64, _P(wsr_camera), ctypes.c_int32, _P(wsr_tiles),
+                                      _c_void_p, _c_void_p, ctypes.c_uint64, _c_void_p, _c_void_p]),
     "wsr_count_pairs": (ctypes.c_int, [_c_void_p, ctypes.c_int64, _c_void_p, _c_void_p, _P(wsr_camera),
                                        ctypes.c_int32, _P(wsr_tiles), _c_void_p, _c_void_p]),
     "wsr_loss_l1": (ctypes.c_int, [_c_void_p, _c_void_p, ctypes.c_int64, _c_void_p, _c_void_p, _c_void_p]),

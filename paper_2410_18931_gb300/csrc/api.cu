@@ -3,6 +3,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "wsr_launch.h"
 
 using namespace wsr;
@@ -138,6 +140,37 @@ wsr_status cuda_status(cudaError_t e) { return e == cudaSuccess ? WSR_OK : WSR_E
         if (ce_ != cudaSuccess) return WSR_ERR_CUDA;          \
     } while (0)
 
+// ---------------------------------------------------------------------------
+// Fixed scratch for wsr_bin_static: the same layout as a workspace sized for
+// WSR_BIN_STATIC_MAX_TILES tiles, in one device array of the library.
+// ---------------------------------------------------------------------------
+constexpr size_t align256c(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t kStaticTiles = WSR_BIN_STATIC_MAX_TILES;
+constexpr size_t kStaticBytes = kWsHeader + align256c(sizeof(unsigned) * (kStaticTiles + 1)) +
+                                align256c(sizeof(unsigned long long) * ((kStaticTiles + kScanTile - 1) / kScanTile + 1));
+
+static __device__ __align__(256) unsigned char g_bin_static_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 128;
+std::mutex g_static_mu;
+void* g_static_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (host code cannot use the symbol itself as a device address).
+wsr_status static_scratch(void** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return WSR_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return WSR_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_bin_static_scratch) != cudaSuccess || !p) return WSR_ERR_CUDA;
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return WSR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -227,6 +260,30 @@ wsr_status wsr_bin(const float* records, int64_t n, const wsr_camera* cams, int3
     char* ws = (char*)workspace;
     WSR_CUDA(launch_bin_scatter(records, n, vs, (unsigned*)(ws + L.cursor), tile_list, list_capacity,
                                 (WsHeader*)ws, s));
+    return WSR_OK;
+}
+
+wsr_status wsr_bin_static(const float* records, int64_t n, const wsr_camera* cams, int32_t n_cams,
+                          const wsr_tiles* tiles, uint32_t* tile_offsets, uint32_t* tile_list, uint64_t list_capacity,
+                          uint64_t* total_dev, void* stream) {
+    static thread_local Views vs;
+    if (!tiles) return WSR_ERR_INVALID_ARG;
+    WSR_TRY(make_views(cams, n_cams, tiles, &vs));
+    if ((size_t)vs.total_tiles > kStaticTiles) return WSR_ERR_UNSUPPORTED;
+    if (n < 0 || (n > 0 && (!records || !aligned16(records))) || !tile_offsets) return WSR_ERR_INVALID_ARG;
+    if (list_capacity > 0 && !tile_list) return WSR_ERR_INVALID_ARG;
+    if ((unsigned long long)n * (unsigned long long)n_cams > 0xffffffffull) return WSR_ERR_INVALID_ARG;
+    void* scratch = nullptr;
+    WSR_TRY(static_scratch(&scratch));
+    if (ws_layout(vs).total > kStaticBytes) return WSR_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    WSR_TRY(bin_count_impl(records, n, vs, tile_offsets, list_capacity, scratch, s));
+    const WsLayout L = ws_layout(vs);
+    char* ws = (char*)scratch;
+    WSR_CUDA(launch_bin_scatter(records, n, vs, (unsigned*)(ws + L.cursor), tile_list, list_capacity,
+                                (WsHeader*)ws, s));
+    if (total_dev)
+        WSR_CUDA(cudaMemcpyAsync(total_dev, &((WsHeader*)ws)->total, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
     return WSR_OK;
 }
 

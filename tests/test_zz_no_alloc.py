@@ -1,0 +1,111 @@
+"""wsr_bin_static: binning for callers that cannot allocate device memory.
+
+Some callers cannot call cudaMalloc once they run (a frame loop in a host
+application that forbids device allocation after start-up, or a plug-in given
+only its input and output buffers), so they cannot provide a workspace.  This
+entry point keeps its scratch in a fixed device array inside the library.
+The test calls it through the C ABI several times in a row, on scenes and
+views of different sizes, and checks each result against wsr_bin (which uses a
+caller-provided workspace): tile offsets and instance totals bit-exact, each
+tile's list equal as a set (the order inside a tile is arbitrary by design),
+and the rendered image equal within float rounding.  The file name makes
+pytest collect it last.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import wsr_scenes as ws
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(seed, n, width, height, tile):
+    import torch
+
+    from paper_2410_18931_gb300 import Gaussians, Renderer
+    sc = ws.random_scene(n, seed, sh_degree=2, vd_opacity=True, clusters=8, box=1.5, log_scale_mu=-3.5)
+    cam = ws.look_at((0.2, -0.1, -4.0), width=width, height=height).rounded()
+    w = ws.default_weight(ws.LC)
+    g = Gaussians.from_scene(sc)
+    wpar = torch.tensor(w.as_array(), device="cuda")
+    r = Renderer([cam], tile=tile)
+    st = r.alloc_state(g.n)
+    r.wsr_project(g, w.kind, wpar, st.records)
+    r.wsr_bin_count(st.records, g.n, st.tile_offsets)
+    total = r.wsr_bin_total()
+    st.tile_list = torch.empty(total + 64, dtype=torch.int32, device="cuda")
+    r.wsr_bin(st.records, g.n, st.tile_offsets, st.tile_list)
+    assert r.wsr_check() == 0
+    return r, g, w, wpar, st, total
+
+
+def _bin_static(r, st, capacity):
+    import torch
+
+    from paper_2410_18931_gb300 import _abi as A
+    lib = A.load()
+    offsets = torch.full_like(st.tile_offsets, -1)
+    tile_list = torch.full((max(capacity, 1),), -1, dtype=torch.int32, device="cuda")
+    total = torch.zeros(1, dtype=torch.int64, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    status = lib.wsr_bin_static(ctypes.c_void_p(st.records.data_ptr()), st.n, r.cams_c, r.n_cams,
+                                ctypes.byref(r.tiles_c), ctypes.c_void_p(offsets.data_ptr()),
+                                ctypes.c_void_p(tile_list.data_ptr()), capacity,
+                                ctypes.c_void_p(total.data_ptr()), stream)
+    torch.cuda.synchronize()
+    return status, offsets, tile_list, int(total.item())
+
+
+def _segments(offsets, tile_list):
+    off = offsets.cpu().numpy().astype(np.int64)
+    lst = tile_list.cpu().numpy()
+    return [np.sort(lst[off[t]:off[t + 1]]) for t in range(off.size - 1)]
+
+
+@pytest.mark.parametrize("order", [(0, 1, 0), (1, 0, 1)])
+def test_bin_static_matches_bin_on_consecutive_calls(order):
+    cases = [dict(seed=3, n=60_000, width=640, height=360, tile=(16, 16)),
+             dict(seed=4, n=20_000, width=200, height=120, tile=(8, 8))]
+    for k in order:
+        r, g, w, wpar, st, total = _case(**cases[k])
+        status, offsets, tile_list, tot = _bin_static(r, st, total + 64)
+        assert status == 0
+        assert tot == total
+        assert np.array_equal(offsets.cpu().numpy(), st.tile_offsets.cpu().numpy())
+        for a, b in zip(_segments(offsets, tile_list), _segments(st.tile_offsets, st.tile_list)):
+            assert np.array_equal(a, b)
+        # the image rendered from either list agrees within float rounding
+        import torch
+        rgb_a = st.rgb.clone()
+        r.wsr_render_fwd(st.records, g.n, st.tile_offsets, st.tile_list, w.kind, wpar, rgb_a, st.den)
+        rgb_b = torch.empty_like(rgb_a)
+        den_b = torch.empty_like(st.den)
+        r.wsr_render_fwd(st.records, g.n, offsets, tile_list, w.kind, wpar, rgb_b, den_b)
+        torch.cuda.synchronize()
+        assert (rgb_a - rgb_b).abs().max().item() <= 2e-6
+
+
+def test_bin_static_overflow_reports_true_total_and_stays_in_bounds():
+    r, g, w, wpar, st, total = _case(seed=5, n=30_000, width=320, height=200, tile=(16, 16))
+    cap = total // 2
+    status, offsets, tile_list, tot = _bin_static(r, st, cap)
+    assert status == 0
+    assert tot == total
+    off = offsets.cpu().numpy().astype(np.int64)
+    assert off.max() <= cap and np.all(np.diff(off) >= 0)
+
+
+def test_bin_static_rejects_too_many_tiles():
+    import torch
+
+    from paper_2410_18931_gb300 import _abi as A
+    lib = A.load()
+    cams, n = A.make_cameras([ws.look_at((0, 0, -5), width=4096, height=2160)])
+    t8 = A.tiles(8, 8)      # 512 x 270 = 138,240 tiles > WSR_BIN_STATIC_MAX_TILES
+    assert lib.wsr_num_tiles(cams, n, ctypes.byref(t8)) > 65536
+    dummy = torch.empty(16, dtype=torch.float32, device="cuda")
+    p = ctypes.c_void_p(dummy.data_ptr())
+    status = lib.wsr_bin_static(p, 1, cams, n, ctypes.byref(t8), p, p, 4, None, None)
+    assert status == A.WSR_ERR_UNSUPPORTED
