@@ -63,7 +63,7 @@ enum { WSR_OPACITY_LOGIT = 0, WSR_OPACITY_SH = 1 };
 
 #define WSR_MAX_VIEWS 32
 #define WSR_RECORD_FLOATS 12      /* one render record: 48 bytes */
-#define WSR_GRAD_RECORD_FLOATS 9  /* one 2D gradient record: 36 bytes */
+#define WSR_GRAD_RECORD_FLOATS 12 /* one 2D gradient record: 48 bytes (9 used) */
 
 /* Pinhole camera (passed by value through host memory). */
 typedef struct {
@@ -221,9 +221,9 @@ wsr_status wsr_render_fwd(const float* records, int64_t n, const uint32_t* tile_
  * wsr_render_bwd — gradient of a scalar loss L through Eq. 7 and the
  * projection, given grad_rgb = dL/dC.  Two stages:
  *   (1) per tile, recompute every (pixel, Gaussian) term from the records and
- *       reduce into grad_records [n_cams, n, 9] float32 (overwritten):
+ *       reduce into grad_records [n_cams, n, 12] float32 (overwritten):
  *       {dL/dmu_x, dL/dmu_y, dL/dA, dL/dB, dL/dC, dL/d(uw) at fixed c uw,
- *        dL/d(c uw) (3)}; (A, B, C) unscaled conic, B counted once;
+ *        dL/d(c uw) (3), 0, 0, 0}; (A, B, C) unscaled conic, B counted once;
  *       plus the background terms dL/dw_B, dL/dc_B;
  *   (2) per Gaussian, chain grad_records back to the stored parameters.
  * `g` must be the scene given to wsr_project; out_rgb / out_den come from

@@ -18,7 +18,7 @@ WSR_WEIGHT_DIR, WSR_WEIGHT_EXP, WSR_WEIGHT_LC = 0, 1, 2
 WSR_OPACITY_LOGIT, WSR_OPACITY_SH = 0, 1
 WSR_MAX_VIEWS = 32
 WSR_RECORD_FLOATS = 12
-WSR_GRAD_RECORD_FLOATS = 9
+WSR_GRAD_RECORD_FLOATS = 12
 
 _c_void_p = ctypes.c_void_p
 

@@ -6,63 +6,142 @@
 // left is a counting pass, an exclusive scan over tiles and an unordered
 // scatter (a counting sort by tile with arbitrary order inside each tile).
 //
-//   k_bin_count    one thread per (view, Gaussian): atomicAdd into its tiles
+//   k_bin<false>   count: atomicAdd into every tile the footprint reaches
 //   k_scan_*       exclusive scan of the per-tile counts (three phases)
-//   k_bin_scatter  one thread per (view, Gaussian): claim a slot per tile
+//   k_bin<true>    scatter: claim a slot per (Gaussian, tile) and store
+// A tile is listed when the footprint q <= 9 reaches one of its pixel
+// centres (exact ellipse-rectangle test), not merely its bounding box.
 #include "wsr_launch.h"
 
 namespace wsr {
 namespace {
 
-// Tile rectangle of a record: tiles holding a pixel centre within the
-// 3-sigma extents.  Returns false when the footprint misses the image.
-__device__ __forceinline__ bool tile_rect(const float4 r0, const float4 r2, const View& V, int tw,
-                                          int th, int& tx0, int& tx1, int& ty0, int& ty1) {
+// Pixel rectangle of a record: pixels whose centre lies within the 3-sigma
+// extents, clipped to the image.  Returns false when it misses the image.
+__device__ __forceinline__ bool pixel_rect(const float4 r0, const float4 r2, const View& V, int& jx0, int& jx1,
+                                           int& jy0, int& jy1) {
     if (!(r2.y >= 0.0f)) return false;          // culled (or NaN)
     if (!(fabsf(r0.x) < 1e30f) || !(fabsf(r0.y) < 1e30f) || !(r2.y < 1e30f) || !(r2.z < 1e30f)) return false;
     // pixel j is inside when |j + 0.5 - mu| <= extent; bounds kept within [-1, W]
     const float fw = (float)V.W, fh = (float)V.H;
     const float xlo = fminf(fmaxf(r0.x - r2.y - 0.5f, -1.0f), fw), xhi = fmaxf(fminf(r0.x + r2.y - 0.5f, fw), -1.0f);
     const float ylo = fminf(fmaxf(r0.y - r2.z - 0.5f, -1.0f), fh), yhi = fmaxf(fminf(r0.y + r2.z - 0.5f, fh), -1.0f);
-    const int jx0 = max((int)ceilf(xlo), 0), jx1 = min((int)floorf(xhi), V.W - 1);
-    const int jy0 = max((int)ceilf(ylo), 0), jy1 = min((int)floorf(yhi), V.H - 1);
-    if (jx0 > jx1 || jy0 > jy1) return false;
-    tx0 = jx0 / tw; tx1 = jx1 / tw;
-    ty0 = jy0 / th; ty1 = jy1 / th;
-    return true;
+    jx0 = max((int)ceilf(xlo), 0);
+    jx1 = min((int)floorf(xhi), V.W - 1);
+    jy0 = max((int)ceilf(ylo), 0);
+    jy1 = min((int)floorf(yhi), V.H - 1);
+    return jx0 <= jx1 && jy0 <= jy1;
 }
 
-__global__ void __launch_bounds__(256) k_bin_count(const float4* __restrict__ rec, long long n, const Views vs,
-                                                   unsigned* __restrict__ cursor) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int v = blockIdx.y;
-    if (i >= n) return;
-    const View& V = vs.v[v];
-    const long long r = (long long)v * n + i;
-    const float4 r0 = __ldg(rec + 3 * r), r2 = __ldg(rec + 3 * r + 2);
-    int tx0, tx1, ty0, ty1;
-    if (!tile_rect(r0, r2, V, vs.tile_w, vs.tile_h, tx0, tx1, ty0, ty1)) return;
-    for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(cursor + V.tile_base + ty * V.tiles_x + tx, 1u);
+// Does the footprint q' <= kQMax reach a pixel centre of the rectangle
+// [x0, x1] x [y0, y1] (pixel-centre coordinates)?  The minimum of the convex
+// quadratic over the rectangle is at the centre when the centre is inside,
+// otherwise on an edge, where it is a one-dimensional quadratic.  The
+// threshold is widened slightly so the test stays conservative with respect
+// to the renderers' FP32 per-pixel test.
+__device__ __forceinline__ bool footprint_hits(float mx, float my, float A, float B2, float C, float x0, float x1,
+                                               float y0, float y1) {
+    if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return true;
+    const float thr = kQMax * 1.0001f + 1e-4f;
+    float best = 3.4e38f;
+    // vertical edges x = x0, x1: minimise over dy
+    const float ex[2] = {x0 - mx, x1 - mx};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float dx = ex[k];
+        const float dy = fminf(fmaxf(-B2 * dx / (2.0f * C), y0 - my), y1 - my);
+        best = fminf(best, A * dx * dx + B2 * dx * dy + C * dy * dy);
+    }
+    const float ey[2] = {y0 - my, y1 - my};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float dy = ey[k];
+        const float dx = fminf(fmaxf(-B2 * dy / (2.0f * A), x0 - mx), x1 - mx);
+        best = fminf(best, A * dx * dx + B2 * dx * dy + C * dy * dy);
+    }
+    return best <= thr;
 }
 
-__global__ void __launch_bounds__(256) k_bin_scatter(const float4* __restrict__ rec, long long n, const Views vs,
-                                                     unsigned* __restrict__ cursor, unsigned* __restrict__ list,
-                                                     unsigned long long capacity, WsHeader* hdr) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// Binning pass.  Each warp takes 32 consecutive Gaussians of one view; their
+// tile rectangles are laid end to end (warp scan) and the lanes walk that
+// list of candidate (Gaussian, tile) pairs together, 32 at a time, so a large
+// footprint is spread over the warp.  A candidate counts when the footprint
+// reaches a pixel centre of the tile.  COUNT: atomicAdd per tile.  SCATTER:
+// claim a slot in the tile's segment and write the record index.
+template <bool SCATTER>
+__global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ rec, long long n, const Views vs,
+                                             unsigned* __restrict__ cursor, unsigned* __restrict__ list,
+                                             unsigned long long capacity, WsHeader* hdr) {
+    __shared__ int s_end[8][32];        // inclusive prefix of candidate counts
+    __shared__ int s_rect[8][32][3];    // tx0, ty0, tiles across
+    __shared__ float s_geo[8][32][5];   // mu_x, mu_y, A', 2B', C'
     const int v = blockIdx.y;
-    if (i >= n) return;
     const View& V = vs.v[v];
-    const long long r = (long long)v * n + i;
-    const float4 r0 = __ldg(rec + 3 * r), r2 = __ldg(rec + 3 * r + 2);
-    int tx0, tx1, ty0, ty1;
-    if (!tile_rect(r0, r2, V, vs.tile_w, vs.tile_h, tx0, tx1, ty0, ty1)) return;
-    for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) {
-            const unsigned slot = atomicAdd(cursor + V.tile_base + ty * V.tiles_x + tx, 1u);
-            if (slot < capacity) list[slot] = (unsigned)r;
-            else set_error(hdr, WSR_ERR_CAPACITY);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int tw = vs.tile_w, th = vs.tile_h;
+    int cnt = 0, tx0 = 0, ty0 = 0, nx = 0;
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+    if (i < n) {
+        const long long r = (long long)v * n + i;
+        r0 = __ldg(rec + 3 * r);
+        r1 = __ldg(rec + 3 * r + 1);
+        const float4 r2 = __ldg(rec + 3 * r + 2);
+        int jx0, jx1, jy0, jy1;
+        if (pixel_rect(r0, r2, V, jx0, jx1, jy0, jy1)) {
+            tx0 = jx0 / tw;
+            ty0 = jy0 / th;
+            nx = jx1 / tw - tx0 + 1;
+            cnt = nx * (jy1 / th - ty0 + 1);
         }
+    }
+    int inc = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
+    }
+    s_end[warp][lane] = inc;
+    s_rect[warp][lane][0] = tx0;
+    s_rect[warp][lane][1] = ty0;
+    s_rect[warp][lane][2] = nx;
+    s_geo[warp][lane][0] = r0.x;
+    s_geo[warp][lane][1] = r0.y;
+    s_geo[warp][lane][2] = r0.z;
+    s_geo[warp][lane][3] = r0.w;
+    s_geo[warp][lane][4] = r1.x;
+    __syncwarp();
+    const int total = __shfl_sync(0xffffffffu, inc, 31);
+    for (int base = 0; base < total; base += 32) {
+        const int c = base + lane;
+        if (c < total) {
+            // owner: first lane whose inclusive end exceeds c
+            int lo = 0, hi = 31;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_end[warp][mid] > c) hi = mid;
+                else lo = mid + 1;
+            }
+            const int k = c - (lo ? s_end[warp][lo - 1] : 0);   // candidate index within the owner's rectangle
+            const int w = s_rect[warp][lo][2];
+            const int tx = s_rect[warp][lo][0] + k % w;
+            const int ty = s_rect[warp][lo][1] + k / w;
+            const float x0 = (float)(tx * tw) + 0.5f, x1 = (float)min(tx * tw + tw, V.W) - 0.5f;
+            const float y0 = (float)(ty * th) + 0.5f, y1 = (float)min(ty * th + th, V.H) - 0.5f;
+            const float* geo = s_geo[warp][lo];
+            if (footprint_hits(geo[0], geo[1], geo[2], geo[3], geo[4], x0, x1, y0, y1)) {
+                unsigned* cur = cursor + V.tile_base + ty * V.tiles_x + tx;
+                if constexpr (SCATTER) {
+                    const unsigned slot = atomicAdd(cur, 1u);
+                    const long long rid = (long long)v * n + (long long)blockIdx.x * blockDim.x + warp * 32 + lo;
+                    if (slot < capacity) list[slot] = (unsigned)rid;
+                    else set_error(hdr, WSR_ERR_CAPACITY);
+                } else {
+                    atomicAdd(cur, 1u);
+                }
+            }
+        }
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -170,7 +249,8 @@ cudaError_t launch_bin_count(const float* records, long long n, const Views& vs,
     cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(unsigned) * (size_t)vs.total_tiles, s);
     if (e != cudaSuccess || n == 0) return e;
     dim3 grid((unsigned)((n + 255) / 256), (unsigned)vs.n);
-    k_bin_count<<<grid, 256, 0, s>>>(reinterpret_cast<const float4*>(records), n, vs, cursor);
+    k_bin<false><<<grid, 256, 0, s>>>(reinterpret_cast<const float4*>(records), n, vs, cursor, nullptr, 0ull,
+                                      nullptr);
     return cudaGetLastError();
 }
 
@@ -189,8 +269,7 @@ cudaError_t launch_bin_scatter(const float* records, long long n, const Views& v
                                unsigned* list, unsigned long long capacity, WsHeader* hdr, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     dim3 grid((unsigned)((n + 255) / 256), (unsigned)vs.n);
-    k_bin_scatter<<<grid, 256, 0, s>>>(reinterpret_cast<const float4*>(records), n, vs, cursor, list, capacity,
-                                       hdr);
+    k_bin<true><<<grid, 256, 0, s>>>(reinterpret_cast<const float4*>(records), n, vs, cursor, list, capacity, hdr);
     return cudaGetLastError();
 }
 

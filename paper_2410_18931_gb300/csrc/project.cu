@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(const GaussPtrs g, const Vi
 
         for (int v = 0; v < vs.n; ++v) {
             const View& V = vs.v[v];
-            const float* gr = grec + 9 * ((long long)v * g.n + i);
+            const float* gr = grec + WSR_GRAD_RECORD_FLOATS * ((long long)v * g.n + i);
             float g9[9];
             bool any = false;
 #pragma unroll

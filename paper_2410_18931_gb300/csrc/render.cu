@@ -10,10 +10,10 @@
 // The epilogue writes C = (c_B w_B + N) / (w_B + D) and the denominator.
 //
 // The backward recomputes every (pixel, Gaussian) term from the records and
-// the stored C and denominator (no per-pixel lists are kept), forms the nine
-// per-Gaussian partial derivatives per pixel, reduces them across the warp
-// with shuffles, across warps in shared memory, and adds one value per
-// Gaussian, tile and component to the global 2D gradient records.
+// the stored C and denominator (no per-pixel lists are kept).  It walks the
+// pixels inside each Gaussian's footprint (per-row spans) with the work split
+// evenly over the threads, so no lane idles on pixels outside a footprint and
+// no per-pair reduction across lanes is needed.
 #include "wsr_launch.h"
 
 namespace wsr {
@@ -127,129 +127,249 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-template <int TW, int TH, int PPT>
-__global__ void __launch_bounds__(TileShape<TW, TH, PPT>::NT)
+// a*b - c*d with one rounding error (Kahan's fma form)
+__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
+    const float w = c * d;
+    const float e = fmaf(-c, d, w);
+    const float f = fmaf(a, b, -w);
+    return f + e;
+}
+
+// Backward, one block per tile, balanced over (pixel, Gaussian) pairs.
+//
+// For each chunk of up to kBwdThreads Gaussians of the tile:
+//   A. thread j computes, for every row of the tile, the span of pixels whose
+//      centre can lie inside Gaussian j's footprint (the roots of the
+//      quadratic q(dx) = 9 on that row, widened slightly);
+//   B. a block scan lays the spans of all Gaussians end to end;
+//   C. every thread takes an equal slice of that pair list and walks it,
+//      accumulating the nine partial derivatives of the current Gaussian in
+//      registers and adding them to shared memory when the Gaussian changes;
+//   D. thread j adds Gaussian j's totals to its global 2D gradient record.
+// Every pair is still tested with the forward's exact arithmetic (q <= 9), so
+// forward and backward agree on which pairs exist.
+constexpr int kBwdThreads = 256;
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(kBwdThreads)
     k_render_bwd(const float4* __restrict__ rec, const unsigned* __restrict__ offsets,
                  const unsigned* __restrict__ list, const Views vs, const float* __restrict__ wparams,
                  const float* __restrict__ out_rgb, const float* __restrict__ out_den,
                  const float* __restrict__ grad_rgb, float* __restrict__ grec, float* __restrict__ gw) {
-    using S = TileShape<TW, TH, PPT>;
-    constexpr int NT = S::NT;
+    constexpr int NT = kBwdThreads;
     constexpr int NW = NT / 32;
+    constexpr int NPIX = TW * TH;
+    static_assert(TW <= 32 && TH <= 32, "span encoding");
+    __shared__ float4 spix[NPIX];               // per pixel: G/D (3), (G.C)/D
     __shared__ float4 s0[NT];
     __shared__ float4 s1[NT];
     __shared__ float s2[NT];
     __shared__ unsigned sidx[NT];
+    __shared__ unsigned short sspan[NT][TH];    // first pixel | count << 8, per row
+    __shared__ unsigned soff[NT + 1];
     __shared__ float sacc[9][NT];
+    __shared__ unsigned swarp[NW];
     __shared__ float sbg[4][NW];
 
     const int tile = blockIdx.x;
     const TileCoord tc = tile_coord(vs, tile);
     const View& V = vs.v[tc.v];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int lx = tid % TW, ly = tid / TW;
-    const int x = tc.tx * TW + lx;
-    const int y0 = tc.ty * TH + ly * PPT;
-    const float px = (float)x + 0.5f;
+    const int x_org = tc.tx * TW, y_org = tc.ty * TH;
+    const int x_lim = min(TW, V.W - x_org);    // pixels of the tile inside the image
+    const int y_lim = min(TH, V.H - y_org);
     const float wB = __ldg(wparams + 2);
-    const float cB[3] = {__ldg(wparams + 3), __ldg(wparams + 4), __ldg(wparams + 5)};
+    const float cB0 = __ldg(wparams + 3), cB1 = __ldg(wparams + 4), cB2 = __ldg(wparams + 5);
 
-    // per-pixel factors: Gd = G / D, s = (G . C) / D; background terms
-    float py[PPT], gdr[PPT], gdg[PPT], gdb[PPT], sg[PPT];
     float bg[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const int y = y0 + k;
-        py[k] = (float)y + 0.5f;
-        gdr[k] = gdg[k] = gdb[k] = sg[k] = 0.0f;
-        if (x < V.W && y < V.H) {
-            const long long pix = V.pix_base + (long long)y * V.W + x;
+    for (int p = tid; p < NPIX; p += NT) {
+        const int lx = p % TW, ly = p / TW;
+        float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lx < x_lim && ly < y_lim) {
+            const long long pix = V.pix_base + (long long)(y_org + ly) * V.W + x_org + lx;
             const float inv = 1.0f / out_den[pix];
             const float G0 = grad_rgb[3 * pix], G1 = grad_rgb[3 * pix + 1], G2 = grad_rgb[3 * pix + 2];
             const float C0 = out_rgb[3 * pix], C1 = out_rgb[3 * pix + 1], C2 = out_rgb[3 * pix + 2];
-            gdr[k] = G0 * inv;
-            gdg[k] = G1 * inv;
-            gdb[k] = G2 * inv;
-            sg[k] = (G0 * C0 + G1 * C1 + G2 * C2) * inv;
+            f = make_float4(G0 * inv, G1 * inv, G2 * inv, (G0 * C0 + G1 * C1 + G2 * C2) * inv);
             // dL/dw_B = G.(c_B - C)/D,  dL/dc_B = G w_B / D
-            bg[0] += gdr[k] * cB[0] + gdg[k] * cB[1] + gdb[k] * cB[2] - sg[k];
-            bg[1] += gdr[k] * wB;
-            bg[2] += gdg[k] * wB;
-            bg[3] += gdb[k] * wB;
+            bg[0] += f.x * cB0 + f.y * cB1 + f.z * cB2 - f.w;
+            bg[1] += f.x * wB;
+            bg[2] += f.y * wB;
+            bg[3] += f.z * wB;
         }
+        spix[p] = f;
     }
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         const float t = warp_sum(bg[c]);
         if (lane == 0) sbg[c][warp] = t;
     }
+#pragma unroll
     for (int c = 0; c < 9; ++c) sacc[c][tid] = 0.0f;
 
+    const float QM = kQMax * 1.0001f + 1e-4f;
     const unsigned start = offsets[tile], end = offsets[tile + 1];
     for (unsigned base = start; base < end; base += NT) {
         const int cnt = (int)min((unsigned)NT, end - base);
         __syncthreads();
+        // ---- A: record and per-row spans of Gaussian tid ----
+        unsigned npairs = 0;
         if (tid < cnt) {
             const unsigned r = list[base + tid];
-            const float4* p = rec + 3ull * r;
+            const float4* pr = rec + 3ull * r;
+            const float4 a = __ldg(pr);
+            const float4 b = __ldg(pr + 1);
+            const float cb = __ldg(reinterpret_cast<const float*>(pr + 2));
+            s0[tid] = a;
+            s1[tid] = b;
+            s2[tid] = cb;
             sidx[tid] = r;
-            s0[tid] = __ldg(p);
-            s1[tid] = __ldg(p + 1);
-            s2[tid] = __ldg(reinterpret_cast<const float*>(p + 2));
+            // row y: the footprint is mu_x + c(dy) +- h(dy) with
+            // c = -(B''/2) dy / A', h = sqrt(A' QM - det' dy^2) / A',
+            // det' = A' C' - (B''/2)^2 (both terms of the root are positive)
+            const float hb = 0.5f * a.w;
+            const float det = diff_of_products(a.z, b.x, hb, hb);
+            const float ia = 1.0f / a.z;
+#pragma unroll 4
+            for (int ly = 0; ly < TH; ++ly) {
+                unsigned short sp = 0;
+                if (ly < y_lim) {
+                    const float dy = (float)(y_org + ly) + 0.5f - a.y;
+                    const float d4 = fmaf(-det * dy, dy, a.z * QM);
+                    if (d4 >= 0.0f) {
+                        const float h = sqrtf(d4) * ia;
+                        const float cx = a.x - hb * dy * ia;
+                        const float fx0 = fmaxf(ceilf(cx - h - 0.52f), (float)x_org);
+                        const float fx1 = fminf(floorf(cx + h - 0.48f), (float)(x_org + x_lim - 1));
+                        if (fx0 <= fx1) {
+                            const int xs = (int)fx0 - x_org, len = (int)fx1 - (int)fx0 + 1;
+                            sp = (unsigned short)(xs | (len << 8));
+                            npairs += (unsigned)len;
+                        }
+                    }
+                }
+                sspan[tid][ly] = sp;
+            }
         }
+        // ---- B: exclusive scan of the pair counts ----
+        unsigned inc = npairs;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc += y;
+        }
+        if (lane == 31) swarp[warp] = inc;
         __syncthreads();
-        for (int j = 0; j < cnt; ++j) {
-            const float4 a = s0[j];
-            const float4 b = s1[j];
-            const float cb = s2[j];
-            const float dx = px - a.x;
-            const float P = a.z * dx * dx;
-            const float Q = a.w * dx;
+        unsigned wbase = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) wbase += (w < warp) ? swarp[w] : 0u;
+        soff[tid] = wbase + inc - npairs;
+        if (tid == NT - 1) soff[NT] = wbase + inc;
+        __syncthreads();
+        // ---- C: an equal slice of the pairs per thread ----
+        const unsigned total = soff[NT];
+        const unsigned p0 = (unsigned)(((unsigned long long)tid * total) / NT);
+        const unsigned p1 = (unsigned)(((unsigned long long)(tid + 1) * total) / NT);
+        if (p0 < p1) {
+            int j;
+            {
+                int lo = 0, hi = cnt - 1;      // last Gaussian whose first pair is <= p0
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (soff[mid] <= p0) lo = mid;
+                    else hi = mid - 1;
+                }
+                j = lo;
+            }
+            float4 a = s0[j], b = s1[j];
+            float cb = s2[j];
+            unsigned k = p0 - soff[j];
+            int ly = 0;
+            unsigned sp = sspan[j][0];
+            while (k >= (sp >> 8)) {
+                k -= sp >> 8;
+                sp = sspan[j][++ly];
+            }
+            int lx = (int)(sp & 0xffu) + (int)k;
+            int lx_end = (int)(sp & 0xffu) + (int)(sp >> 8);
+            float dy = (float)(y_org + ly) + 0.5f - a.y;
             float g[9];
 #pragma unroll
             for (int c = 0; c < 9; ++c) g[c] = 0.0f;
-            bool act = false;
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                const float dy = py[k] - a.y;
-                const float q = fmaf(dy, fmaf(b.x, dy, Q), P);   // same arithmetic as the forward
+            for (unsigned p = p0; p < p1; ++p) {
+                const float4 P = spix[ly * TW + lx];
+                const float dx = (float)(x_org + lx) + 0.5f - a.x;
+                const float Pq = a.z * dx * dx;
+                const float Q = a.w * dx;
+                const float q = fmaf(dy, fmaf(b.x, dy, Q), Pq);   // the forward's arithmetic
                 if (q <= kQMax) {
-                    act = true;
                     const float e = ex2_approx(-q);
-                    g[6] = fmaf(gdr[k], e, g[6]);           // d/d(c u w)
-                    g[7] = fmaf(gdg[k], e, g[7]);
-                    g[8] = fmaf(gdb[k], e, g[8]);
-                    g[5] = fmaf(-sg[k], e, g[5]);           // d/d(u w) at fixed c u w
-                    const float ge = gdr[k] * b.z + gdg[k] * b.w + gdb[k] * cb - sg[k] * b.y;
-                    const float gq = -kLn2 * e * ge;        // dL/dq'
-                    g[2] = fmaf(gq, dx * dx, g[2]);         // dL/dA'
-                    g[3] = fmaf(gq, dx * dy, g[3]);         // dL/d(2B')
-                    g[4] = fmaf(gq, dy * dy, g[4]);         // dL/dC'
-                    g[0] = fmaf(-gq, fmaf(2.0f * a.z, dx, a.w * dy), g[0]);   // dL/dmu_x
-                    g[1] = fmaf(-gq, fmaf(2.0f * b.x, dy, a.w * dx), g[1]);   // dL/dmu_y
+                    g[0] = fmaf(P.x, e, g[0]);                      // d/d(c u w)
+                    g[1] = fmaf(P.y, e, g[1]);
+                    g[2] = fmaf(P.z, e, g[2]);
+                    g[3] = fmaf(-P.w, e, g[3]);                     // d/d(u w) at fixed c u w
+                    const float ge = fmaf(P.x, b.z, fmaf(P.y, b.w, fmaf(P.z, cb, -P.w * b.y)));
+                    const float gq = -kLn2 * e * ge;                // dL/dq'
+                    const float t = gq * dx, u = gq * dy;
+                    g[4] = fmaf(t, dx, g[4]);                       // dL/dA'
+                    g[5] = fmaf(t, dy, g[5]);                       // dL/d(2B')
+                    g[6] = fmaf(u, dy, g[6]);                       // dL/dC'
+                    g[7] += t;                                      // sum dL/dq' dx
+                    g[8] += u;                                      // sum dL/dq' dy
+                }
+                if (++lx >= lx_end) {
+                    // next non-empty row of this Gaussian, else the next Gaussian
+                    do {
+                        ++ly;
+                    } while (ly < TH && (sspan[j][ly] >> 8) == 0);
+                    if (ly >= TH) {
+#pragma unroll
+                        for (int c = 0; c < 9; ++c) {
+                            if (g[c] != 0.0f) atomicAdd(&sacc[c][j], g[c]);
+                            g[c] = 0.0f;
+                        }
+                        if (p + 1 < p1) {
+                            do {
+                                ++j;
+                            } while (soff[j + 1] == soff[j]);
+                            a = s0[j];
+                            b = s1[j];
+                            cb = s2[j];
+                            ly = 0;
+                            while ((sspan[j][ly] >> 8) == 0) ++ly;
+                        }
+                    }
+                    if (p + 1 < p1) {
+                        sp = sspan[j][ly];
+                        lx = (int)(sp & 0xffu);
+                        lx_end = lx + (int)(sp >> 8);
+                        dy = (float)(y_org + ly) + 0.5f - a.y;
+                    }
                 }
             }
-            if (__any_sync(0xffffffffu, act)) {
 #pragma unroll
-                for (int c = 0; c < 9; ++c) g[c] = warp_sum(g[c]);
-                if (lane == 0) {
-#pragma unroll
-                    for (int c = 0; c < 9; ++c)
-                        if (g[c] != 0.0f) atomicAdd(&sacc[c][j], g[c]);
-                }
-            }
+            for (int c = 0; c < 9; ++c)
+                if (g[c] != 0.0f) atomicAdd(&sacc[c][j], g[c]);
         }
         __syncthreads();
+        // ---- D: totals of Gaussian tid to its global record ----
         if (tid < cnt) {
-            // prescaled -> unscaled conic: A' = k A, 2B' = 2k B, C' = k C
-            float* o = grec + 9ull * sidx[tid];
-            const float scale[9] = {1.f, 1.f, kHalfLog2e, 2.0f * kHalfLog2e, kHalfLog2e, 1.f, 1.f, 1.f, 1.f};
+            float v[9];
 #pragma unroll
             for (int c = 0; c < 9; ++c) {
-                const float v = sacc[c][tid];
-                if (v != 0.0f) atomicAdd(o + c, v * scale[c]);
+                v[c] = sacc[c][tid];
                 sacc[c][tid] = 0.0f;
             }
+            const float4 a = s0[tid];
+            const float Cp = s1[tid].x;
+            // q' = A' dx^2 + B'' dx dy + C' dy^2, dx = px - mu_x, dy = py - mu_y
+            const float gmx = -(2.0f * a.z * v[7] + a.w * v[8]);
+            const float gmy = -(a.w * v[7] + 2.0f * Cp * v[8]);
+            // prescaled -> unscaled conic: A' = k A, B'' = 2k B, C' = k C
+            float4* o = reinterpret_cast<float4*>(grec + (size_t)WSR_GRAD_RECORD_FLOATS * sidx[tid]);
+            atomicAdd(o, make_float4(gmx, gmy, kHalfLog2e * v[4], 2.0f * kHalfLog2e * v[5]));
+            atomicAdd(o + 1, make_float4(kHalfLog2e * v[6], v[3], v[0], v[1]));
+            atomicAdd(reinterpret_cast<float*>(o + 2), v[2]);
         }
     }
     __syncthreads();
@@ -268,11 +388,11 @@ cudaError_t fwd_t(const float* rec, const unsigned* off, const unsigned* list, c
     return cudaGetLastError();
 }
 
-template <int TW, int TH, int PPT>
+template <int TW, int TH>
 cudaError_t bwd_t(const float* rec, const unsigned* off, const unsigned* list, const Views& vs, WeightDev w,
                   const float* rgb, const float* den, const float* grgb, float* grec, float* gw, cudaStream_t s) {
-    k_render_bwd<TW, TH, PPT><<<vs.total_tiles, TileShape<TW, TH, PPT>::NT, 0, s>>>(
-        reinterpret_cast<const float4*>(rec), off, list, vs, w.params, rgb, den, grgb, grec, gw);
+    k_render_bwd<TW, TH><<<vs.total_tiles, kBwdThreads, 0, s>>>(reinterpret_cast<const float4*>(rec), off, list, vs,
+                                                                w.params, rgb, den, grgb, grec, gw);
     return cudaGetLastError();
 }
 
@@ -354,10 +474,10 @@ cudaError_t launch_render_bwd(const float* rec, const unsigned* off, const unsig
                               WeightDev w, const float* rgb, const float* den, const float* grgb, float* grec,
                               float* gw, cudaStream_t s) {
     if (vs.total_tiles == 0) return cudaSuccess;
-    if (vs.tile_w == 16 && vs.tile_h == 16) return bwd_t<16, 16, 2>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, s);
-    if (vs.tile_w == 8 && vs.tile_h == 8) return bwd_t<8, 8, 2>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, s);
-    if (vs.tile_w == 32 && vs.tile_h == 8) return bwd_t<32, 8, 2>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, s);
-    if (vs.tile_w == 16 && vs.tile_h == 8) return bwd_t<16, 8, 2>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, s);
+    if (vs.tile_w == 16 && vs.tile_h == 16) return bwd_t<16, 16>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, s);
+    if (vs.tile_w == 8 && vs.tile_h == 8) return bwd_t<8, 8>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, s);
+    if (vs.tile_w == 32 && vs.tile_h == 8) return bwd_t<32, 8>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, s);
+    if (vs.tile_w == 16 && vs.tile_h == 8) return bwd_t<16, 8>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, s);
     return cudaErrorInvalidValue;
 }
 

@@ -138,7 +138,9 @@ def test_gradient_records_match_oracle():
     cam = ws.look_at((0.0, 0.0, -3.0), width=80, height=64).rounded()
     w = ws.WeightParams(ws.EXP, 0.1, 0.8, 0.8, (0.1, 0.2, 0.3))
     out, ref = _grad_case(sc, cam, w)
-    gr = out["grad_records"].cpu().numpy().reshape(-1, 9).astype(np.float64)
+    gr = out["grad_records"].cpu().numpy().reshape(-1, 12).astype(np.float64)
+    assert np.all(gr[:, 9:] == 0.0)
+    gr = gr[:, :9]
     P = oracle.project(sc, cam, w)
     uw = P["u"] * P["w"]
     col = P["color"]
