@@ -166,8 +166,14 @@ __global__ void __launch_bounds__(kBwdThreads)
     __shared__ float s2[NT];
     __shared__ unsigned sidx[NT];
     __shared__ unsigned short sspan[NT][TH];    // first pixel | count << 8, per row
+    __shared__ unsigned char sly0[NT];          // first non-empty row (rows are contiguous)
     __shared__ unsigned soff[NT + 1];
-    __shared__ float sacc[9][NT];
+    // partial sums per (thread, Gaussian) segment of the pair list: a thread's
+    // slice covers Gaussians jfirst[t] .. jfirst[t] + nseg - 1, stored from
+    // segment sbase[t] on; at most NT + NT segments per chunk
+    __shared__ float sseg[2 * NT][9];
+    __shared__ unsigned short sjfirst[NT];
+    __shared__ unsigned short ssbase[NT];
     __shared__ unsigned swarp[NW];
     __shared__ float sbg[4][NW];
 
@@ -204,9 +210,6 @@ __global__ void __launch_bounds__(kBwdThreads)
         const float t = warp_sum(bg[c]);
         if (lane == 0) sbg[c][warp] = t;
     }
-#pragma unroll
-    for (int c = 0; c < 9; ++c) sacc[c][tid] = 0.0f;
-
     const float QM = kQMax * 1.0001f + 1e-4f;
     const unsigned start = offsets[tile], end = offsets[tile + 1];
     for (unsigned base = start; base < end; base += NT) {
@@ -230,6 +233,7 @@ __global__ void __launch_bounds__(kBwdThreads)
             const float hb = 0.5f * a.w;
             const float det = diff_of_products(a.z, b.x, hb, hb);
             const float ia = 1.0f / a.z;
+            int first = TH;
 #pragma unroll 4
             for (int ly = 0; ly < TH; ++ly) {
                 unsigned short sp = 0;
@@ -245,11 +249,14 @@ __global__ void __launch_bounds__(kBwdThreads)
                             const int xs = (int)fx0 - x_org, len = (int)fx1 - (int)fx0 + 1;
                             sp = (unsigned short)(xs | (len << 8));
                             npairs += (unsigned)len;
+                            first = min(first, ly);
                         }
                     }
                 }
                 sspan[tid][ly] = sp;
             }
+            // the footprint within the tile is convex, so its rows are contiguous
+            sly0[tid] = (unsigned char)(first < TH ? first : 0);
         }
         // ---- B: exclusive scan of the pair counts ----
         unsigned inc = npairs;
@@ -270,95 +277,145 @@ __global__ void __launch_bounds__(kBwdThreads)
         const unsigned total = soff[NT];
         const unsigned p0 = (unsigned)(((unsigned long long)tid * total) / NT);
         const unsigned p1 = (unsigned)(((unsigned long long)(tid + 1) * total) / NT);
-        if (p0 < p1) {
-            int j;
-            {
-                int lo = 0, hi = cnt - 1;      // last Gaussian whose first pair is <= p0
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (soff[mid] <= p0) lo = mid;
-                    else hi = mid - 1;
-                }
-                j = lo;
+        // owner(p): the last Gaussian whose first pair is <= p
+        auto owner = [&](unsigned p) {
+            int lo = 0, hi = cnt - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (soff[mid] <= p) lo = mid;
+                else hi = mid - 1;
             }
+            return lo;
+        };
+        int j = 0, jlast = -1;
+        if (p0 < p1) {
+            j = owner(p0);
+            jlast = owner(p1 - 1);
+        }
+        {
+            // segment slots: a block scan of the per-thread Gaussian counts
+            const unsigned nseg = (unsigned)(jlast - j + 1);
+            unsigned sinc = nseg;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, sinc, off);
+                if (lane >= off) sinc += y;
+            }
+            __syncthreads();                       // swarp reuse
+            if (lane == 31) swarp[warp] = sinc;
+            __syncthreads();
+            unsigned sb = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) sb += (w < warp) ? swarp[w] : 0u;
+            sjfirst[tid] = (unsigned short)j;
+            ssbase[tid] = (unsigned short)(sb + sinc - nseg);
+        }
+        if (p0 < p1) {
+            float* seg = sseg[ssbase[tid]];
             float4 a = s0[j], b = s1[j];
             float cb = s2[j];
+            // -ln2 (c u w, u w): dL/dq' = e * -ln2 (G/D . c u w - s u w)
+            float cwr = -kLn2 * b.z, cwg = -kLn2 * b.w, cwb = -kLn2 * cb, cwu = -kLn2 * b.y;
             unsigned k = p0 - soff[j];
-            int ly = 0;
-            unsigned sp = sspan[j][0];
+            int ly = sly0[j];
+            unsigned sp = sspan[j][ly];
             while (k >= (sp >> 8)) {
                 k -= sp >> 8;
                 sp = sspan[j][++ly];
             }
             int lx = (int)(sp & 0xffu) + (int)k;
             int lx_end = (int)(sp & 0xffu) + (int)(sp >> 8);
+            float xf = (float)(x_org + lx) + 0.5f;
             float dy = (float)(y_org + ly) + 0.5f - a.y;
             float g[9];
 #pragma unroll
             for (int c = 0; c < 9; ++c) g[c] = 0.0f;
-            for (unsigned p = p0; p < p1; ++p) {
+            for (unsigned left = p1 - p0; left > 0; --left) {
                 const float4 P = spix[ly * TW + lx];
-                const float dx = (float)(x_org + lx) + 0.5f - a.x;
+                const float dx = xf - a.x;
                 const float Pq = a.z * dx * dx;
                 const float Q = a.w * dx;
                 const float q = fmaf(dy, fmaf(b.x, dy, Q), Pq);   // the forward's arithmetic
-                if (q <= kQMax) {
-                    const float e = ex2_approx(-q);
-                    g[0] = fmaf(P.x, e, g[0]);                      // d/d(c u w)
-                    g[1] = fmaf(P.y, e, g[1]);
-                    g[2] = fmaf(P.z, e, g[2]);
-                    g[3] = fmaf(-P.w, e, g[3]);                     // d/d(u w) at fixed c u w
-                    const float ge = fmaf(P.x, b.z, fmaf(P.y, b.w, fmaf(P.z, cb, -P.w * b.y)));
-                    const float gq = -kLn2 * e * ge;                // dL/dq'
-                    const float t = gq * dx, u = gq * dy;
-                    g[4] = fmaf(t, dx, g[4]);                       // dL/dA'
-                    g[5] = fmaf(t, dy, g[5]);                       // dL/d(2B')
-                    g[6] = fmaf(u, dy, g[6]);                       // dL/dC'
-                    g[7] += t;                                      // sum dL/dq' dx
-                    g[8] += u;                                      // sum dL/dq' dy
-                }
-                if (++lx >= lx_end) {
-                    // next non-empty row of this Gaussian, else the next Gaussian
-                    do {
-                        ++ly;
-                    } while (ly < TH && (sspan[j][ly] >> 8) == 0);
-                    if (ly >= TH) {
+                // outside the cutoff the pair contributes nothing (a select, not a branch)
+                const float e = (q <= kQMax) ? ex2_approx(-q) : 0.0f;
+                g[0] = fmaf(P.x, e, g[0]);                          // d/d(c u w)
+                g[1] = fmaf(P.y, e, g[1]);
+                g[2] = fmaf(P.z, e, g[2]);
+                g[3] = fmaf(-P.w, e, g[3]);                         // d/d(u w) at fixed c u w
+                const float gq = e * fmaf(P.x, cwr, fmaf(P.y, cwg, fmaf(P.z, cwb, -P.w * cwu)));  // dL/dq'
+                const float t = gq * dx, u = gq * dy;
+                g[4] = fmaf(t, dx, g[4]);                           // dL/dA'
+                g[5] = fmaf(t, dy, g[5]);                           // dL/d(2B')
+                g[6] = fmaf(u, dy, g[6]);                           // dL/dC'
+                g[7] += t;                                          // sum dL/dq' dx
+                g[8] += u;                                          // sum dL/dq' dy
+                // advance: next pixel of the row, else the next row (selects)
+                ++lx;
+                xf += 1.0f;
+                const bool row_end = lx >= lx_end;
+                ly += row_end ? 1 : 0;
+                if (row_end) sp = (ly < TH) ? (unsigned)sspan[j][ly] : 0u;   // 0: past the last row
+                if (row_end && (sp >> 8) == 0) {
+                    // end of Gaussian j: store its partial sums in its segment
 #pragma unroll
-                        for (int c = 0; c < 9; ++c) {
-                            if (g[c] != 0.0f) atomicAdd(&sacc[c][j], g[c]);
-                            g[c] = 0.0f;
-                        }
-                        if (p + 1 < p1) {
-                            do {
-                                ++j;
-                            } while (soff[j + 1] == soff[j]);
-                            a = s0[j];
-                            b = s1[j];
-                            cb = s2[j];
-                            ly = 0;
-                            while ((sspan[j][ly] >> 8) == 0) ++ly;
-                        }
+                    for (int c = 0; c < 9; ++c) {
+                        seg[c] = g[c];
+                        g[c] = 0.0f;
                     }
-                    if (p + 1 < p1) {
+                    seg += 9;
+                    if (left > 1) {
+                        ++j;
+                        while (soff[j + 1] == soff[j]) {     // Gaussians without pairs here
+#pragma unroll
+                            for (int c = 0; c < 9; ++c) seg[c] = 0.0f;
+                            seg += 9;
+                            ++j;
+                        }
+                        a = s0[j];
+                        b = s1[j];
+                        cb = s2[j];
+                        cwr = -kLn2 * b.z;
+                        cwg = -kLn2 * b.w;
+                        cwb = -kLn2 * cb;
+                        cwu = -kLn2 * b.y;
+                        ly = sly0[j];
                         sp = sspan[j][ly];
-                        lx = (int)(sp & 0xffu);
-                        lx_end = lx + (int)(sp >> 8);
-                        dy = (float)(y_org + ly) + 0.5f - a.y;
                     }
                 }
+                const int xs = (int)(sp & 0xffu);
+                lx = row_end ? xs : lx;
+                lx_end = row_end ? xs + (int)(sp >> 8) : lx_end;
+                xf = row_end ? (float)(x_org + xs) + 0.5f : xf;
+                dy = row_end ? (float)(y_org + ly) + 0.5f - a.y : dy;
             }
+            if (jlast >= 0 && seg < sseg[ssbase[tid]] + 9 * (jlast - sjfirst[tid] + 1)) {
 #pragma unroll
-            for (int c = 0; c < 9; ++c)
-                if (g[c] != 0.0f) atomicAdd(&sacc[c][j], g[c]);
+                for (int c = 0; c < 9; ++c) seg[c] = g[c];
+            }
         }
         __syncthreads();
         // ---- D: totals of Gaussian tid to its global record ----
-        if (tid < cnt) {
+        if (tid < cnt && soff[tid + 1] > soff[tid]) {
+            // threads whose slices hold pairs of Gaussian tid: from the owner of
+            // its first pair to the owner of its last pair
+            auto slice_of = [&](unsigned p) {
+                int t = (int)(((unsigned long long)p * NT) / total);
+                while (t + 1 < NT && (unsigned)(((unsigned long long)(t + 1) * total) / NT) <= p) ++t;
+                while (t > 0 && (unsigned)(((unsigned long long)t * total) / NT) > p) --t;
+                return t;
+            };
+            const int t0 = slice_of(soff[tid]), t1 = slice_of(soff[tid + 1] - 1);
             float v[9];
 #pragma unroll
-            for (int c = 0; c < 9; ++c) {
-                v[c] = sacc[c][tid];
-                sacc[c][tid] = 0.0f;
+            for (int c = 0; c < 9; ++c) v[c] = 0.0f;
+            for (int t = t0; t <= t1; ++t) {
+                // threads with an empty slice hold no segment
+                const unsigned q0 = (unsigned)(((unsigned long long)t * total) / NT);
+                const unsigned q1 = (unsigned)(((unsigned long long)(t + 1) * total) / NT);
+                if (q0 == q1) continue;
+                const float* sg = sseg[ssbase[t] + (tid - sjfirst[t])];
+#pragma unroll
+                for (int c = 0; c < 9; ++c) v[c] += sg[c];
             }
             const float4 a = s0[tid];
             const float Cp = s1[tid].x;
