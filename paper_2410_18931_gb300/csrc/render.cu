@@ -2,8 +2,8 @@
 //
 // One thread block per tile.  The tile's Gaussian list (unordered: Eq. 7 is
 // a sum) is streamed through shared memory in chunks of one record per
-// thread; every thread owns PPT vertically adjacent pixels of the tile and
-// accumulates, in FP32 registers,
+// thread; every thread owns a 2x2 block of pixels (two columns share each
+// paired float2 FP32 instruction) and accumulates, in FP32 registers,
 //     N += (c u w) e,   D += (u w) e,   e = exp(-q/2) = 2^(-q'),   q <= 9
 // with q' = q log2(e)/2 evaluated from the prescaled conic of the record.
 // There is no early termination (App. D: every covering Gaussian counts).
@@ -19,14 +19,6 @@
 namespace wsr {
 namespace {
 
-template <int TW, int TH, int PPT>
-struct TileShape {
-    static constexpr int NT = TW * TH / PPT;    // threads per block
-    static constexpr int ROWS = TH / PPT;       // thread rows
-    static_assert(TH % PPT == 0, "PPT must divide the tile height");
-    static_assert(NT % 32 == 0, "whole warps");
-};
-
 struct TileCoord {
     int v, tx, ty;
 };
@@ -41,32 +33,52 @@ __device__ __forceinline__ TileCoord tile_coord(const Views& vs, int tile) {
     return t;
 }
 
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// Pixel-per-thread layout of the pair-count diagnostic.
 template <int TW, int TH, int PPT>
-__global__ void __launch_bounds__(TileShape<TW, TH, PPT>::NT)
+struct TileShape {
+    static constexpr int NT = TW * TH / PPT;
+    static_assert(TH % PPT == 0 && NT % 32 == 0, "whole warps");
+};
+
+// Forward tile shape: each thread owns a PX x 2 block of pixels (PX = 2 or 1),
+// so two horizontally adjacent pixels share one paired (float2) FP32 op.
+template <int TW, int TH, int PX>
+struct FwdShape {
+    static constexpr int PY = 2;
+    static constexpr int BX = TW / PX;                  // thread columns
+    static constexpr int NT = (TW / PX) * (TH / PY);    // threads per block
+    static_assert(NT % 32 == 0, "whole warps");
+};
+
+template <int TW, int TH, int PX>
+__global__ void __launch_bounds__(FwdShape<TW, TH, PX>::NT)
     k_render_fwd(const float4* __restrict__ rec, const unsigned* __restrict__ offsets,
                  const unsigned* __restrict__ list, const Views vs, const float* __restrict__ wparams,
                  float* __restrict__ out_rgb, float* __restrict__ out_den) {
-    using S = TileShape<TW, TH, PPT>;
+    using S = FwdShape<TW, TH, PX>;
     constexpr int NT = S::NT;
-    __shared__ float4 s0[NT];
-    __shared__ float4 s1[NT];
-    __shared__ float s2[NT];
+    __shared__ float4 s0[NT];   // mu_x, mu_y, A', 2B'
+    __shared__ float4 s1[NT];   // C', u w, c_r u w, c_g u w
+    __shared__ float2 s2[NT];   // c_b u w, u w
 
     const int tile = blockIdx.x;
     const TileCoord tc = tile_coord(vs, tile);
     const View& V = vs.v[tc.v];
     const int tid = threadIdx.x;
-    const int lx = tid % TW, ly = tid / TW;
-    const int x = tc.tx * TW + lx;
-    const int y0 = tc.ty * TH + ly * PPT;
-    const float px = (float)x + 0.5f;
-    float py[PPT];
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) py[k] = (float)(y0 + k) + 0.5f;
+    const int x0 = tc.tx * TW + (tid % S::BX) * PX;
+    const int y0 = tc.ty * TH + (tid / S::BX) * S::PY;
+    // pixel centres of the block (a second column is ignored when PX == 1)
+    const float2 px = f2((float)x0 + 0.5f, (float)(x0 + 1) + 0.5f);
+    const float py0 = (float)y0 + 0.5f, py1 = (float)(y0 + 1) + 0.5f;
 
-    float nr[PPT], ng[PPT], nb[PPT], dd[PPT];
+    // accumulators per pixel (column c, row r): (N_r, N_g) and (N_b, D)
+    float2 rg[2][2], bd[2][2];
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) nr[k] = ng[k] = nb[k] = dd[k] = 0.0f;
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) rg[r][c] = bd[r][c] = f2(0.f, 0.f);
 
     const unsigned start = offsets[tile], end = offsets[tile + 1];
     for (unsigned base = start; base < end; base += NT) {
@@ -76,27 +88,35 @@ __global__ void __launch_bounds__(TileShape<TW, TH, PPT>::NT)
             const unsigned r = list[base + tid];
             const float4* p = rec + 3ull * r;
             s0[tid] = __ldg(p);
-            s1[tid] = __ldg(p + 1);
-            s2[tid] = __ldg(reinterpret_cast<const float*>(p + 2));
+            const float4 b = __ldg(p + 1);
+            s1[tid] = b;
+            s2[tid] = f2(__ldg(reinterpret_cast<const float*>(p + 2)), b.y);
         }
         __syncthreads();
         for (int j = 0; j < cnt; ++j) {
-            const float4 a = s0[j];   // mu_x, mu_y, A', 2B'
-            const float4 b = s1[j];   // C', uw, cuw_r, cuw_g
-            const float cb = s2[j];   // cuw_b
-            const float dx = px - a.x;
-            const float P = a.z * dx * dx;
-            const float Q = a.w * dx;
+            const float4 a = s0[j];
+            const float4 b = s1[j];
+            const float2 cbuw = s2[j];
+            const float2 crg = f2(b.z, b.w);
+            // q' = A' dx^2 + 2B' dx dy + C' dy^2, evaluated as
+            // fma(dy, fma(C', dy, 2B' dx), (A' dx) dx) for both columns at once
+            const float2 dx = __fadd2_rn(px, f2(-a.x, -a.x));
+            const float2 P = __fmul2_rn(__fmul2_rn(f2(a.z, a.z), dx), dx);
+            const float2 Q = __fmul2_rn(f2(a.w, a.w), dx);
+            const float dys[2] = {py0 - a.y, py1 - a.y};
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                const float dy = py[k] - a.y;
-                const float q = fmaf(dy, fmaf(b.x, dy, Q), P);
-                if (q <= kQMax) {
-                    const float e = ex2_approx(-q);
-                    nr[k] = fmaf(b.z, e, nr[k]);
-                    ng[k] = fmaf(b.w, e, ng[k]);
-                    nb[k] = fmaf(cb, e, nb[k]);
-                    dd[k] = fmaf(b.y, e, dd[k]);
+            for (int r = 0; r < 2; ++r) {
+                const float2 dy = f2(dys[r], dys[r]);
+                const float2 q = __ffma2_rn(dy, __ffma2_rn(f2(b.x, b.x), dy, Q), P);
+                if (q.x <= kQMax) {
+                    const float e = ex2_approx(-q.x);
+                    rg[r][0] = __ffma2_rn(crg, f2(e, e), rg[r][0]);
+                    bd[r][0] = __ffma2_rn(cbuw, f2(e, e), bd[r][0]);
+                }
+                if (PX == 2 && q.y <= kQMax) {
+                    const float e = ex2_approx(-q.y);
+                    rg[r][1] = __ffma2_rn(crg, f2(e, e), rg[r][1]);
+                    bd[r][1] = __ffma2_rn(cbuw, f2(e, e), bd[r][1]);
                 }
             }
         }
@@ -104,21 +124,21 @@ __global__ void __launch_bounds__(TileShape<TW, TH, PPT>::NT)
 
     const float wB = __ldg(wparams + 2);
     const float cB0 = __ldg(wparams + 3) * wB, cB1 = __ldg(wparams + 4) * wB, cB2 = __ldg(wparams + 5) * wB;
-    if (x < V.W) {
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-            const int y = y0 + k;
-            if (y < V.H) {
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < PX; ++c) {
+            const int x = x0 + c, y = y0 + r;
+            if (x < V.W && y < V.H) {
                 const long long pix = V.pix_base + (long long)y * V.W + x;
-                const float D = wB + dd[k];
+                const float D = wB + bd[r][c].y;
                 const float inv = 1.0f / D;
-                out_rgb[3 * pix + 0] = (cB0 + nr[k]) * inv;
-                out_rgb[3 * pix + 1] = (cB1 + ng[k]) * inv;
-                out_rgb[3 * pix + 2] = (cB2 + nb[k]) * inv;
+                out_rgb[3 * pix + 0] = (cB0 + rg[r][c].x) * inv;
+                out_rgb[3 * pix + 1] = (cB1 + rg[r][c].y) * inv;
+                out_rgb[3 * pix + 2] = (cB2 + bd[r][c].x) * inv;
                 out_den[pix] = D;
             }
         }
-    }
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -137,44 +157,49 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
 
 // Backward, one block per tile, balanced over (pixel, Gaussian) pairs.
 //
-// For each chunk of up to kBwdThreads Gaussians of the tile:
+// For each chunk of up to kBwdChunk Gaussians of the tile:
 //   A. thread j computes, for every row of the tile, the span of pixels whose
 //      centre can lie inside Gaussian j's footprint (the roots of the
-//      quadratic q(dx) = 9 on that row, widened slightly);
-//   B. a block scan lays the spans of all Gaussians end to end;
-//   C. every thread takes an equal slice of that pair list and walks it,
+//      quadratic q(dx) = 9 on that row, widened slightly); the rows with a
+//      span are contiguous because the footprint is convex;
+//   B. a block scan lays the row spans of all Gaussians end to end as a list
+//      of row segments (one 32-bit descriptor each) in pair order;
+//   C. every thread takes an equal slice of the pair list, finds its first
+//      segment by binary search and walks pixel indices two at a time,
 //      accumulating the nine partial derivatives of the current Gaussian in
-//      registers and adding them to shared memory when the Gaussian changes;
-//   D. thread j adds Gaussian j's totals to its global 2D gradient record.
+//      registers; at the end of its slice, or when the Gaussian changes, it
+//      stores them in a (thread, Gaussian) slot;
+//   D. thread j sums Gaussian j's slots and adds them to its global record.
 // Every pair is still tested with the forward's exact arithmetic (q <= 9), so
 // forward and backward agree on which pairs exist.
 constexpr int kBwdThreads = 256;
+constexpr int kBwdChunk = 256;
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(kBwdThreads)
+__global__ void __launch_bounds__(kBwdThreads, 4)
     k_render_bwd(const float4* __restrict__ rec, const unsigned* __restrict__ offsets,
                  const unsigned* __restrict__ list, const Views vs, const float* __restrict__ wparams,
                  const float* __restrict__ out_rgb, const float* __restrict__ out_den,
                  const float* __restrict__ grad_rgb, float* __restrict__ grec, float* __restrict__ gw) {
     constexpr int NT = kBwdThreads;
+    constexpr int CH = kBwdChunk;
     constexpr int NW = NT / 32;
     constexpr int NPIX = TW * TH;
-    static_assert(TW <= 32 && TH <= 32, "span encoding");
-    __shared__ float4 spix[NPIX];               // per pixel: G/D (3), (G.C)/D
-    __shared__ float4 s0[NT];
-    __shared__ float4 s1[NT];
-    __shared__ float s2[NT];
-    __shared__ unsigned sidx[NT];
-    __shared__ unsigned short sspan[NT][TH];    // first pixel | count << 8, per row
-    __shared__ unsigned char sly0[NT];          // first non-empty row (rows are contiguous)
-    __shared__ unsigned soff[NT + 1];
-    // partial sums per (thread, Gaussian) segment of the pair list: a thread's
-    // slice covers Gaussians jfirst[t] .. jfirst[t] + nseg - 1, stored from
-    // segment sbase[t] on; at most NT + NT segments per chunk
-    __shared__ float sseg[2 * NT][9];
-    __shared__ unsigned short sjfirst[NT];
+    constexpr int MAXSEG = CH * TH;
+    static_assert(TW <= 32 && TH <= 32 && CH <= 256, "descriptor encoding");
+    __shared__ float4 spix[NPIX + 1];           // per pixel: G/D (3), -(G.C)/D; one pad entry
+    __shared__ float4 s0[CH];                   // mu_x, mu_y, A', 2B'
+    __shared__ float4 s1[CH];                   // C', u w, c_r u w, c_g u w
+    __shared__ float2 s2[CH];                   // c_b u w, u w
+    __shared__ unsigned sidx[CH];
+    __shared__ unsigned soff[CH + 1];           // first pair of each Gaussian
+    __shared__ unsigned short sgoff[CH + 1];    // first row segment of each Gaussian
+    __shared__ unsigned segd[MAXSEG];           // row segment: j << 16 | ly << 11 | xs << 6 | len
+    __shared__ float sslot[2 * NT][9];          // partial sums per (thread, Gaussian)
+    __shared__ unsigned char sslotj[2 * NT];    // the Gaussian of each slot (slots are sorted by it)
     __shared__ unsigned short ssbase[NT];
     __shared__ unsigned swarp[NW];
+    __shared__ unsigned stot[3];                // pairs, row segments and slots of the chunk
     __shared__ float sbg[4][NW];
 
     const int tile = blockIdx.x;
@@ -196,27 +221,30 @@ __global__ void __launch_bounds__(kBwdThreads)
             const float inv = 1.0f / out_den[pix];
             const float G0 = grad_rgb[3 * pix], G1 = grad_rgb[3 * pix + 1], G2 = grad_rgb[3 * pix + 2];
             const float C0 = out_rgb[3 * pix], C1 = out_rgb[3 * pix + 1], C2 = out_rgb[3 * pix + 2];
-            f = make_float4(G0 * inv, G1 * inv, G2 * inv, (G0 * C0 + G1 * C1 + G2 * C2) * inv);
+            f = make_float4(G0 * inv, G1 * inv, G2 * inv, -(G0 * C0 + G1 * C1 + G2 * C2) * inv);
             // dL/dw_B = G.(c_B - C)/D,  dL/dc_B = G w_B / D
-            bg[0] += f.x * cB0 + f.y * cB1 + f.z * cB2 - f.w;
+            bg[0] += f.x * cB0 + f.y * cB1 + f.z * cB2 + f.w;
             bg[1] += f.x * wB;
             bg[2] += f.y * wB;
             bg[3] += f.z * wB;
         }
         spix[p] = f;
     }
+    if (tid == 0) spix[NPIX] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         const float t = warp_sum(bg[c]);
         if (lane == 0) sbg[c][warp] = t;
     }
+
     const float QM = kQMax * 1.0001f + 1e-4f;
     const unsigned start = offsets[tile], end = offsets[tile + 1];
-    for (unsigned base = start; base < end; base += NT) {
-        const int cnt = (int)min((unsigned)NT, end - base);
+    for (unsigned base = start; base < end; base += CH) {
+        const int cnt = (int)min((unsigned)CH, end - base);
         __syncthreads();
         // ---- A: record and per-row spans of Gaussian tid ----
-        unsigned npairs = 0;
+        unsigned short span[TH];
+        unsigned nseg = 0, npairs = 0;
         if (tid < cnt) {
             const unsigned r = list[base + tid];
             const float4* pr = rec + 3ull * r;
@@ -225,7 +253,7 @@ __global__ void __launch_bounds__(kBwdThreads)
             const float cb = __ldg(reinterpret_cast<const float*>(pr + 2));
             s0[tid] = a;
             s1[tid] = b;
-            s2[tid] = cb;
+            s2[tid] = f2(cb, b.y);
             sidx[tid] = r;
             // row y: the footprint is mu_x + c(dy) +- h(dy) with
             // c = -(B''/2) dy / A', h = sqrt(A' QM - det' dy^2) / A',
@@ -233,11 +261,14 @@ __global__ void __launch_bounds__(kBwdThreads)
             const float hb = 0.5f * a.w;
             const float det = diff_of_products(a.z, b.x, hb, hb);
             const float ia = 1.0f / a.z;
-            int first = TH;
-#pragma unroll 4
+            // rows the footprint can reach: |dy| <= sqrt(A' QM / det'), with a pixel of slack
+            const float ext = fminf(sqrtf(fmaxf(a.z * QM / det, 0.0f)), 1e6f) + 1.0f;
+            const int ly_lo = max(0, (int)floorf(a.y - ext - 0.5f) - y_org);
+            const int ly_hi = min(y_lim - 1, (int)ceilf(a.y + ext - 0.5f) - y_org);
+#pragma unroll
             for (int ly = 0; ly < TH; ++ly) {
                 unsigned short sp = 0;
-                if (ly < y_lim) {
+                if (ly >= ly_lo && ly <= ly_hi) {
                     const float dy = (float)(y_org + ly) + 0.5f - a.y;
                     const float d4 = fmaf(-det * dy, dy, a.z * QM);
                     if (d4 >= 0.0f) {
@@ -249,17 +280,17 @@ __global__ void __launch_bounds__(kBwdThreads)
                             const int xs = (int)fx0 - x_org, len = (int)fx1 - (int)fx0 + 1;
                             sp = (unsigned short)(xs | (len << 8));
                             npairs += (unsigned)len;
-                            first = min(first, ly);
+                            ++nseg;
                         }
                     }
                 }
-                sspan[tid][ly] = sp;
+                span[ly] = sp;
             }
-            // the footprint within the tile is convex, so its rows are contiguous
-            sly0[tid] = (unsigned char)(first < TH ? first : 0);
         }
-        // ---- B: exclusive scan of the pair counts ----
-        unsigned inc = npairs;
+        // ---- B: block scan of (pairs, segments); write the segment list ----
+        const unsigned packed = (npairs << 13) | nseg;   // pairs <= 2^17, segments <= 2^13 per chunk
+        static_assert(CH * TW * TH < (1 << 19) && MAXSEG < (1 << 13), "packed scan fields");
+        unsigned inc = packed;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const unsigned y = __shfl_up_sync(0xffffffffu, inc, off);
@@ -270,11 +301,30 @@ __global__ void __launch_bounds__(kBwdThreads)
         unsigned wbase = 0;
 #pragma unroll
         for (int w = 0; w < NW; ++w) wbase += (w < warp) ? swarp[w] : 0u;
-        soff[tid] = wbase + inc - npairs;
-        if (tid == NT - 1) soff[NT] = wbase + inc;
+        const unsigned ex = wbase + inc - packed;
+        if (tid < cnt) {
+            unsigned k = ex & 0x1fffu;
+            soff[tid] = ex >> 13;
+            sgoff[tid] = (unsigned short)k;
+#pragma unroll
+            for (int ly = 0; ly < TH; ++ly) {
+                const unsigned sp = span[ly];
+                if (sp >> 8) {
+                    segd[k] = ((unsigned)tid << 16) | ((unsigned)ly << 11) | ((sp & 0xffu) << 6) | (sp >> 8);
+                    ++k;
+                }
+            }
+        }
+        if (tid == NT - 1) {
+            const unsigned tot = wbase + inc;
+            soff[cnt] = tot >> 13;
+            sgoff[cnt] = (unsigned short)(tot & 0x1fffu);
+            stot[0] = tot >> 13;
+            stot[1] = tot & 0x1fffu;
+        }
         __syncthreads();
         // ---- C: an equal slice of the pairs per thread ----
-        const unsigned total = soff[NT];
+        const unsigned total = stot[0];
         const unsigned p0 = (unsigned)(((unsigned long long)tid * total) / NT);
         const unsigned p1 = (unsigned)(((unsigned long long)(tid + 1) * total) / NT);
         // owner(p): the last Gaussian whose first pair is <= p
@@ -287,135 +337,142 @@ __global__ void __launch_bounds__(kBwdThreads)
             }
             return lo;
         };
-        int j = 0, jlast = -1;
+        int sg = 0, j = 0, jlast = -1;
+        unsigned k0 = 0;
         if (p0 < p1) {
             j = owner(p0);
             jlast = owner(p1 - 1);
+            // the row segment of Gaussian j holding pair p0
+            sg = sgoff[j];
+            k0 = p0 - soff[j];
+            while (k0 >= (segd[sg] & 63u)) k0 -= segd[sg++] & 63u;
         }
         {
-            // segment slots: a block scan of the per-thread Gaussian counts
-            const unsigned nseg = (unsigned)(jlast - j + 1);
-            unsigned sinc = nseg;
+            // slots: a block scan of the number of Gaussians each slice touches
+            const unsigned nslot = (unsigned)(jlast - j + 1);
+            unsigned sinc = nslot;
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
                 const unsigned y = __shfl_up_sync(0xffffffffu, sinc, off);
                 if (lane >= off) sinc += y;
             }
-            __syncthreads();                       // swarp reuse
-            if (lane == 31) swarp[warp] = sinc;
+            if (lane == 31) swarp[warp] = sinc;      // step B's reads of swarp ended at the last barrier
             __syncthreads();
             unsigned sb = 0;
 #pragma unroll
             for (int w = 0; w < NW; ++w) sb += (w < warp) ? swarp[w] : 0u;
-            sjfirst[tid] = (unsigned short)j;
-            ssbase[tid] = (unsigned short)(sb + sinc - nseg);
+            const unsigned b0 = sb + sinc - nslot;
+            ssbase[tid] = (unsigned short)b0;
+            for (unsigned k = 0; k < nslot; ++k) sslotj[b0 + k] = (unsigned char)(j + (int)k);
+            if (tid == NT - 1) stot[2] = sb + sinc;
         }
         if (p0 < p1) {
-            float* seg = sseg[ssbase[tid]];
-            float4 a = s0[j], b = s1[j];
-            float cb = s2[j];
-            // -ln2 (c u w, u w): dL/dq' = e * -ln2 (G/D . c u w - s u w)
-            float cwr = -kLn2 * b.z, cwg = -kLn2 * b.w, cwb = -kLn2 * cb, cwu = -kLn2 * b.y;
-            unsigned k = p0 - soff[j];
-            int ly = sly0[j];
-            unsigned sp = sspan[j][ly];
-            while (k >= (sp >> 8)) {
-                k -= sp >> 8;
-                sp = sspan[j][++ly];
-            }
-            int lx = (int)(sp & 0xffu) + (int)k;
-            int lx_end = (int)(sp & 0xffu) + (int)(sp >> 8);
-            float xf = (float)(x_org + lx) + 0.5f;
-            float dy = (float)(y_org + ly) + 0.5f - a.y;
-            float g[9];
+            int slot = ssbase[tid];
+            // per-Gaussian constants as float2 pairs (refreshed when the Gaussian changes)
+            float2 nmx, az2, aw2, cx2, cw0, cw1;
+            float amy;
+            auto load_gaussian = [&](int jj) {
+                const float4 a = s0[jj], b = s1[jj];
+                const float2 c2 = s2[jj];
+                nmx = f2(-a.x, -a.x);
+                amy = a.y;
+                az2 = f2(a.z, a.z);
+                aw2 = f2(a.w, a.w);
+                cx2 = f2(b.x, b.x);
+                cw0 = f2(-kLn2 * b.z, -kLn2 * b.w);    // -ln2 (c u w, u w): dL/dq' = e * (P . cw)
+                cw1 = f2(-kLn2 * c2.x, -kLn2 * c2.y);
+            };
+            load_gaussian(j);
+            unsigned d = segd[sg];
+            int ly = (int)((d >> 11) & 31u), xs = (int)((d >> 6) & 31u);
+            int pi = ly * TW + xs + (int)k0;                 // pixel index in the tile
+            int pend = ly * TW + xs + (int)(d & 63u);        // end of the row segment
+            float xf = (float)(x_org + xs + (int)k0) + 0.5f;
+            float dy = (float)(y_org + ly) + 0.5f - amy;
+            // accumulators, paired: (cuw_r, cuw_g), (cuw_b, uw), (A', C'), (sum dx, sum dy)
+            float2 g01 = f2(0.f, 0.f), g23 = f2(0.f, 0.f), g46 = f2(0.f, 0.f), g78 = f2(0.f, 0.f);
+            float g5 = 0.f;
+            auto store_slot = [&](int sl) {
+                float* o = sslot[sl];
+                o[0] = g01.x; o[1] = g01.y; o[2] = g23.x; o[3] = g23.y;
+                o[4] = g46.x; o[5] = g5; o[6] = g46.y; o[7] = g78.x; o[8] = g78.y;
+            };
+            int left = (int)(p1 - p0);
+            while (true) {
+                // two pixels of the current row segment when both are in the slice
+                const bool two = (pi + 1 < pend) && (left > 1);
+                const float4 P0 = spix[pi];
+                const float4 P1 = two ? spix[pi + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float2 dx = __fadd2_rn(f2(xf, xf + 1.0f), nmx);
+                const float2 dy2 = f2(dy, dy);
+                const float2 q = __ffma2_rn(dy2, __ffma2_rn(cx2, dy2, __fmul2_rn(aw2, dx)),
+                                            __fmul2_rn(__fmul2_rn(az2, dx), dx));   // the forward's arithmetic
+                const float e0 = (q.x <= kQMax) ? ex2_approx(-q.x) : 0.0f;
+                const float e1 = (two && q.y <= kQMax) ? ex2_approx(-q.y) : 0.0f;
+                // d/d(c u w) and d/d(u w) at fixed c u w
+                g01 = __ffma2_rn(f2(P0.x, P0.y), f2(e0, e0), g01);
+                g23 = __ffma2_rn(f2(P0.z, P0.w), f2(e0, e0), g23);
+                g01 = __ffma2_rn(f2(P1.x, P1.y), f2(e1, e1), g01);
+                g23 = __ffma2_rn(f2(P1.z, P1.w), f2(e1, e1), g23);
+                // dL/dq' per pixel: e * (P . cw)
+                const float2 m0 = __ffma2_rn(f2(P0.z, P0.w), cw1, __fmul2_rn(f2(P0.x, P0.y), cw0));
+                const float2 m1 = __ffma2_rn(f2(P1.z, P1.w), cw1, __fmul2_rn(f2(P1.x, P1.y), cw0));
+                const float2 gq = __fmul2_rn(f2(e0, e1), f2(m0.x + m0.y, m1.x + m1.y));
+                const float2 tu0 = __fmul2_rn(f2(gq.x, gq.x), f2(dx.x, dy));   // (gq dx, gq dy), pixel 0
+                const float2 tu1 = __fmul2_rn(f2(gq.y, gq.y), f2(dx.y, dy));   // pixel 1
+                g46 = __ffma2_rn(tu0, f2(dx.x, dy), g46);                     // dL/dA', dL/dC'
+                g46 = __ffma2_rn(tu1, f2(dx.y, dy), g46);
+                g5 = fmaf(tu0.x + tu1.x, dy, g5);                             // dL/d(2B')
+                g78 = __fadd2_rn(g78, __fadd2_rn(tu0, tu1));                  // sums of dL/dq' dx, dy
+                const int step = two ? 2 : 1;
+                pi += step;
+                xf += two ? 2.0f : 1.0f;
+                left -= step;
+                if (left <= 0) break;
+                if (pi >= pend) {
+                    // next row segment; when it belongs to another Gaussian, store this one's sums
+                    d = segd[++sg];
+                    const int nj = (int)(d >> 16);
+                    if (nj != j) {
+                        store_slot(slot);
+                        g01 = g23 = g46 = g78 = f2(0.f, 0.f);
+                        g5 = 0.f;
+                        for (int jj = j + 1; jj < nj; ++jj) {      // Gaussians without pairs here
+                            float* zz = sslot[++slot];
 #pragma unroll
-            for (int c = 0; c < 9; ++c) g[c] = 0.0f;
-            for (unsigned left = p1 - p0; left > 0; --left) {
-                const float4 P = spix[ly * TW + lx];
-                const float dx = xf - a.x;
-                const float Pq = a.z * dx * dx;
-                const float Q = a.w * dx;
-                const float q = fmaf(dy, fmaf(b.x, dy, Q), Pq);   // the forward's arithmetic
-                // outside the cutoff the pair contributes nothing (a select, not a branch)
-                const float e = (q <= kQMax) ? ex2_approx(-q) : 0.0f;
-                g[0] = fmaf(P.x, e, g[0]);                          // d/d(c u w)
-                g[1] = fmaf(P.y, e, g[1]);
-                g[2] = fmaf(P.z, e, g[2]);
-                g[3] = fmaf(-P.w, e, g[3]);                         // d/d(u w) at fixed c u w
-                const float gq = e * fmaf(P.x, cwr, fmaf(P.y, cwg, fmaf(P.z, cwb, -P.w * cwu)));  // dL/dq'
-                const float t = gq * dx, u = gq * dy;
-                g[4] = fmaf(t, dx, g[4]);                           // dL/dA'
-                g[5] = fmaf(t, dy, g[5]);                           // dL/d(2B')
-                g[6] = fmaf(u, dy, g[6]);                           // dL/dC'
-                g[7] += t;                                          // sum dL/dq' dx
-                g[8] += u;                                          // sum dL/dq' dy
-                // advance: next pixel of the row, else the next row (selects)
-                ++lx;
-                xf += 1.0f;
-                const bool row_end = lx >= lx_end;
-                ly += row_end ? 1 : 0;
-                if (row_end) sp = (ly < TH) ? (unsigned)sspan[j][ly] : 0u;   // 0: past the last row
-                if (row_end && (sp >> 8) == 0) {
-                    // end of Gaussian j: store its partial sums in its segment
-#pragma unroll
-                    for (int c = 0; c < 9; ++c) {
-                        seg[c] = g[c];
-                        g[c] = 0.0f;
-                    }
-                    seg += 9;
-                    if (left > 1) {
-                        ++j;
-                        while (soff[j + 1] == soff[j]) {     // Gaussians without pairs here
-#pragma unroll
-                            for (int c = 0; c < 9; ++c) seg[c] = 0.0f;
-                            seg += 9;
-                            ++j;
+                            for (int c = 0; c < 9; ++c) zz[c] = 0.0f;
                         }
-                        a = s0[j];
-                        b = s1[j];
-                        cb = s2[j];
-                        cwr = -kLn2 * b.z;
-                        cwg = -kLn2 * b.w;
-                        cwb = -kLn2 * cb;
-                        cwu = -kLn2 * b.y;
-                        ly = sly0[j];
-                        sp = sspan[j][ly];
+                        ++slot;
+                        j = nj;
+                        load_gaussian(j);
                     }
+                    ly = (int)((d >> 11) & 31u);
+                    xs = (int)((d >> 6) & 31u);
+                    pi = ly * TW + xs;
+                    pend = pi + (int)(d & 63u);
+                    xf = (float)(x_org + xs) + 0.5f;
+                    dy = (float)(y_org + ly) + 0.5f - amy;
                 }
-                const int xs = (int)(sp & 0xffu);
-                lx = row_end ? xs : lx;
-                lx_end = row_end ? xs + (int)(sp >> 8) : lx_end;
-                xf = row_end ? (float)(x_org + xs) + 0.5f : xf;
-                dy = row_end ? (float)(y_org + ly) + 0.5f - a.y : dy;
             }
-            if (jlast >= 0 && seg < sseg[ssbase[tid]] + 9 * (jlast - sjfirst[tid] + 1)) {
-#pragma unroll
-                for (int c = 0; c < 9; ++c) seg[c] = g[c];
-            }
+            store_slot(slot);
         }
         __syncthreads();
         // ---- D: totals of Gaussian tid to its global record ----
+        // the slots are sorted by Gaussian, so Gaussian tid's slots are a run
         if (tid < cnt && soff[tid + 1] > soff[tid]) {
-            // threads whose slices hold pairs of Gaussian tid: from the owner of
-            // its first pair to the owner of its last pair
-            auto slice_of = [&](unsigned p) {
-                int t = (int)(((unsigned long long)p * NT) / total);
-                while (t + 1 < NT && (unsigned)(((unsigned long long)(t + 1) * total) / NT) <= p) ++t;
-                while (t > 0 && (unsigned)(((unsigned long long)t * total) / NT) > p) --t;
-                return t;
-            };
-            const int t0 = slice_of(soff[tid]), t1 = slice_of(soff[tid + 1] - 1);
+            const int nslots = (int)stot[2];
+            int lo = 0, hi = nslots;
+            while (lo < hi) {            // first slot of a Gaussian >= tid
+                const int mid = (lo + hi) >> 1;
+                if ((int)sslotj[mid] < tid) lo = mid + 1;
+                else hi = mid;
+            }
             float v[9];
 #pragma unroll
             for (int c = 0; c < 9; ++c) v[c] = 0.0f;
-            for (int t = t0; t <= t1; ++t) {
-                // threads with an empty slice hold no segment
-                const unsigned q0 = (unsigned)(((unsigned long long)t * total) / NT);
-                const unsigned q1 = (unsigned)(((unsigned long long)(t + 1) * total) / NT);
-                if (q0 == q1) continue;
-                const float* sg = sseg[ssbase[t] + (tid - sjfirst[t])];
+            for (int t = lo; t < nslots && (int)sslotj[t] == tid; ++t) {
 #pragma unroll
-                for (int c = 0; c < 9; ++c) v[c] += sg[c];
+                for (int c = 0; c < 9; ++c) v[c] += sslot[t][c];
             }
             const float4 a = s0[tid];
             const float Cp = s1[tid].x;
@@ -437,10 +494,10 @@ __global__ void __launch_bounds__(kBwdThreads)
     }
 }
 
-template <int TW, int TH, int PPT>
+template <int TW, int TH, int PX>
 cudaError_t fwd_t(const float* rec, const unsigned* off, const unsigned* list, const Views& vs, WeightDev w,
                   float* rgb, float* den, cudaStream_t s) {
-    k_render_fwd<TW, TH, PPT><<<vs.total_tiles, TileShape<TW, TH, PPT>::NT, 0, s>>>(
+    k_render_fwd<TW, TH, PX><<<vs.total_tiles, FwdShape<TW, TH, PX>::NT, 0, s>>>(
         reinterpret_cast<const float4*>(rec), off, list, vs, w.params, rgb, den);
     return cudaGetLastError();
 }
@@ -521,7 +578,7 @@ cudaError_t launch_render_fwd(const float* rec, const unsigned* off, const unsig
                               WeightDev w, float* rgb, float* den, cudaStream_t s) {
     if (vs.total_tiles == 0) return cudaSuccess;
     if (vs.tile_w == 16 && vs.tile_h == 16) return fwd_t<16, 16, 2>(rec, off, list, vs, w, rgb, den, s);
-    if (vs.tile_w == 8 && vs.tile_h == 8) return fwd_t<8, 8, 2>(rec, off, list, vs, w, rgb, den, s);
+    if (vs.tile_w == 8 && vs.tile_h == 8) return fwd_t<8, 8, 1>(rec, off, list, vs, w, rgb, den, s);
     if (vs.tile_w == 32 && vs.tile_h == 8) return fwd_t<32, 8, 2>(rec, off, list, vs, w, rgb, den, s);
     if (vs.tile_w == 16 && vs.tile_h == 8) return fwd_t<16, 8, 2>(rec, off, list, vs, w, rgb, den, s);
     return cudaErrorInvalidValue;
