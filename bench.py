@@ -407,6 +407,10 @@ def run_ours(args):
             "wall_s_timed_region": round(wall, 4)}
     line.update(extra_out)
 
+    if world == 1 and not args.no_batched:
+        line["batched"] = run_batched()
+    if world == 1 and not args.no_reduced:
+        line["reduced"] = run_reduced()
     if rank == 0 and not args.no_cpu_baseline:
         gpu_rgb = S.st.rgb.reshape(cam.height, cam.width, 3).cpu().numpy()
         base, maxerr = cpu_oracle_leg(scene, cam, weight, target, gpu_rgb, args.cpu_budget)
@@ -461,6 +465,120 @@ def run_e2e(args, S, scene, target, flush):
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
 
+def _events_ms(fn, reps: int, warmup: int = 2) -> float:
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_batched(reps: int = 5) -> dict:
+    """3M Gaussians, 16 views of uneven size (4 each of 640x360 .. 2560x1440):
+    fwd + L1 + bwd for all views in one captured graph with the autotuned tile
+    shape and schedule, against the plain path (one view at a time, 16x16
+    tiles, one block per tile, eager calls) on the same scene."""
+    import torch
+
+    import wsr_scenes as ws
+    from paper_2410_18931_gb300 import Gaussians, GraphStep, autotune, time_step
+    scene, cams, weight, extra = ws.workload(4)
+    cams = [c.rounded() for c in cams]
+    g = Gaussians.from_scene(scene)
+    del scene
+    wpar = torch.tensor(weight.as_array(), device="cuda")
+    npix = sum(c.width * c.height for c in cams)
+    target = torch.rand(npix, 3, device="cuda", generator=torch.Generator("cuda").manual_seed(4))
+    tune = autotune(g, cams, weight.kind, wpar, target, reps=3)
+    step = GraphStep(g, cams, weight.kind, wpar, target, tile=tune["tile"], persistent=tune["persistent"])
+    ms = time_step(step, reps=reps)
+    assert step.check() == 0
+    kernels = step.kernels_per_step
+    del step
+    torch.cuda.empty_cache()
+    single_ms, o = 0.0, 0
+    for cam in cams:
+        m = cam.width * cam.height
+        one = GraphStep(g, [cam], weight.kind, wpar, target[o:o + m], tile=(16, 16), persistent=False,
+                        capture=False)
+        single_ms += time_step(one, reps=3)
+        assert one.check() == 0
+        o += m
+        del one
+        torch.cuda.empty_cache()
+    return {"workload": extra["name"], "gaussians": g.n, "views": len(cams), "mpix_per_step": round(npix / 1e6, 3),
+            "fwd_bwd_mpix_s": round(npix / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms, 3),
+            "tile": "%dx%d" % tune["tile"], "persistent": tune["persistent"], "graph": True,
+            "kernels_per_step": kernels,
+            "single_view_plain_mpix_s": round(npix / (single_ms * 1e-3) / 1e6, 2),
+            "speedup_vs_single_view": round(single_ms / ms, 3),
+            "autotune_ms": {("%dx%d" % t["tile"]) + ("/persistent" if t["persistent"] else "/per-tile"):
+                            round(t["ms"], 3) for t in tune["table"]}}
+
+
+def run_reduced(reps: int = 3) -> dict:
+    """6M Gaussians, 8 views of 3840x2160: forward with reduced storage (bf16
+    scales/quats, f16 SH/opacity, FP32 accumulation) for all views in one set
+    of launches, against the plain FP32 single-view forward on the same
+    scene; the image difference between the two is reported."""
+    import numpy as np
+    import torch
+
+    import wsr_scenes as ws
+    from paper_2410_18931_gb300 import Gaussians, Renderer
+    scene, cams, weight, extra = ws.workload(5)
+    cams = [c.rounded() for c in cams]
+    wpar = torch.tensor(weight.as_array(), device="cuda")
+    npix = sum(c.width * c.height for c in cams)
+    g32 = Gaussians.from_scene(scene)
+    g16 = Gaussians.from_scene(scene, reduced=True)
+    del scene
+    r = Renderer(cams, tile=(16, 16), persistent=True, headroom=1.2)
+    st = r.forward(g16, weight.kind, wpar)
+
+    def fwd():
+        r.wsr_project(g16, weight.kind, wpar, st.records)
+        r.wsr_bin(st.records, g16.n, st.tile_offsets, st.tile_list)
+        r.wsr_render_fwd(st.records, g16.n, st.tile_offsets, st.tile_list, weight.kind, wpar, st.rgb, st.den)
+    ms = _events_ms(fwd, reps)
+    assert r.wsr_check() == 0
+    red_rgb = st.rgb.clone()
+    del st, r
+    torch.cuda.empty_cache()
+    single_ms, o, err, se = 0.0, 0, 0.0, 0.0
+    for cam in cams:
+        m = cam.width * cam.height
+        rs = Renderer([cam], tile=(16, 16), headroom=1.2)
+        s1 = rs.forward(g32, weight.kind, wpar)
+
+        def f1():
+            rs.wsr_project(g32, weight.kind, wpar, s1.records)
+            rs.wsr_bin(s1.records, g32.n, s1.tile_offsets, s1.tile_list)
+            rs.wsr_render_fwd(s1.records, g32.n, s1.tile_offsets, s1.tile_list, weight.kind, wpar, s1.rgb, s1.den)
+        single_ms += _events_ms(f1, reps)
+        assert rs.wsr_check() == 0
+        d = (red_rgb[o:o + m] - s1.rgb).abs()
+        err = max(err, d.max().item())
+        se += (d.double() ** 2).sum().item()
+        o += m
+        del s1, rs
+        torch.cuda.empty_cache()
+    mse = se / (3 * npix)
+    return {"workload": extra["name"], "gaussians": g16.n, "views": len(cams), "mpix_per_step": round(npix / 1e6, 3),
+            "fwd_mpix_s": round(npix / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms, 3),
+            "storage": "bf16 log-scales/quats, f16 SH/opacity, f32 means, FP32 accumulation",
+            "single_view_fp32_fwd_mpix_s": round(npix / (single_ms * 1e-3) / 1e6, 2),
+            "speedup_vs_single_view_fp32": round(single_ms / ms, 3),
+            "max_abs_diff_vs_fp32_storage": err,
+            "psnr_db_vs_fp32_storage": round(10 * np.log10(1.0 / max(mse, 1e-30)), 2)}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -471,6 +589,8 @@ def main():
     ap.add_argument("--tile", default="16x16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 3M x 16-view batched measurement")
+    ap.add_argument("--no-reduced", action="store_true", help="skip the 6M x 8 x 4K reduced-precision measurement")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

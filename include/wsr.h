@@ -114,9 +114,24 @@ typedef struct {
     const float* params;         /* device [6] */
 } wsr_weight;
 
-/* Tile shape for binning and rendering.  Supported: 16x16, 8x8, 32x8, 16x8. */
+/* Work schedule of the render kernels. */
+enum {
+    WSR_SCHEDULE_TILE_BLOCKS = 0,  /* one thread block per tile */
+    WSR_SCHEDULE_PERSISTENT = 1    /* one block per SM slot, tiles taken heaviest first */
+};
+
+/*
+ * Tile shape for binning and rendering (supported: 16x16, 8x8, 32x8, 16x8)
+ * and the render schedule.  With WSR_SCHEDULE_PERSISTENT, wsr_bin also orders
+ * the tiles by decreasing instance count (a bucketed longest-first order kept
+ * in the workspace) and the render calls launch one block per resident slot
+ * that takes tiles from that order through a counter in the workspace; the
+ * same workspace and tiles must then be passed to wsr_bin and the renderers.
+ */
 typedef struct {
     int32_t tile_w, tile_h;
+    int32_t schedule;            /* WSR_SCHEDULE_* */
+    int32_t reserved;            /* must be 0 */
 } wsr_tiles;
 
 /*

@@ -10,7 +10,9 @@ from ._abi import (WSR_BF16, WSR_F16, WSR_F32, WSR_WEIGHT_DIR, WSR_WEIGHT_EXP, W
 load()
 
 from .render import FrameState, Gaussians, Renderer, WSRRender, render  # noqa: E402
+from .batch import GraphStep, autotune, time_step  # noqa: E402
 
-__all__ = ["Gaussians", "Renderer", "FrameState", "WSRRender", "render", "WSRError", "load",
+__all__ = ["Gaussians", "Renderer", "FrameState", "WSRRender", "render", "GraphStep", "autotune", "time_step",
+           "WSRError", "load",
            "exported_symbols", "WSR_F32", "WSR_F16", "WSR_BF16", "WSR_WEIGHT_DIR", "WSR_WEIGHT_EXP",
            "WSR_WEIGHT_LC"]

@@ -41,7 +41,8 @@ class wsr_weight(ctypes.Structure):
 
 
 class wsr_tiles(ctypes.Structure):
-    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32)]
+    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class wsr_grads(ctypes.Structure):
@@ -136,5 +137,8 @@ def make_cameras(cams) -> tuple:
     return arr, len(cams)
 
 
-def tiles(tw: int, th: int) -> wsr_tiles:
-    return wsr_tiles(int(tw), int(th))
+WSR_SCHEDULE_TILE_BLOCKS, WSR_SCHEDULE_PERSISTENT = 0, 1
+
+
+def tiles(tw: int, th: int, schedule: int = WSR_SCHEDULE_TILE_BLOCKS) -> wsr_tiles:
+    return wsr_tiles(int(tw), int(th), int(schedule), 0)

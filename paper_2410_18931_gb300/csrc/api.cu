@@ -24,16 +24,21 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 // Builds the per-view constant table.  Returns WSR_OK or the argument error.
 wsr_status make_views(const wsr_camera* cams, int32_t n_cams, const wsr_tiles* tiles, Views* vs) {
     if (!cams || n_cams < 1 || n_cams > WSR_MAX_VIEWS) return WSR_ERR_INVALID_ARG;
-    int tw = 16, th = 16;
+    int tw = 16, th = 16, sched = WSR_SCHEDULE_TILE_BLOCKS;
     if (tiles) {
+        if (tiles->reserved != 0) return WSR_ERR_INVALID_ARG;
+        if (tiles->schedule != WSR_SCHEDULE_TILE_BLOCKS && tiles->schedule != WSR_SCHEDULE_PERSISTENT)
+            return WSR_ERR_INVALID_ARG;
         if (!tiles_ok(tiles)) return WSR_ERR_UNSUPPORTED;
         tw = tiles->tile_w;
         th = tiles->tile_h;
+        sched = tiles->schedule;
     }
     memset(vs, 0, sizeof(Views));
     vs->n = n_cams;
     vs->tile_w = tw;
     vs->tile_h = th;
+    vs->schedule = sched;
     long long tile_base = 0, pix_base = 0;
     for (int v = 0; v < n_cams; ++v) {
         const wsr_camera& c = cams[v];
@@ -69,16 +74,33 @@ wsr_status make_views(const wsr_camera* cams, int32_t n_cams, const wsr_tiles* t
 }
 
 struct WsLayout {
-    size_t cursor, block_sums, total;
+    size_t cursor, block_sums, order, buckets, total;
 };
 
+// The tile order of the persistent schedule is only part of its layout.
 WsLayout ws_layout(const Views& vs) {
     WsLayout L;
     const size_t nb = (size_t)(vs.total_tiles + kScanTile - 1) / kScanTile;
     L.cursor = kWsHeader;
     L.block_sums = L.cursor + align256(sizeof(unsigned) * ((size_t)vs.total_tiles + 1));
     L.total = L.block_sums + align256(sizeof(unsigned long long) * (nb + 1));
+    L.order = L.buckets = 0;
+    if (vs.schedule == WSR_SCHEDULE_PERSISTENT) {
+        L.order = L.total;
+        L.buckets = L.order + align256(sizeof(unsigned) * (size_t)vs.total_tiles);
+        L.total = L.buckets + align256(sizeof(unsigned) * 66);
+    }
     return L;
+}
+
+Sched sched_of(const Views& vs, void* workspace, int which) {
+    Sched sc{nullptr, nullptr};
+    if (vs.schedule == WSR_SCHEDULE_PERSISTENT) {
+        const WsLayout L = ws_layout(vs);
+        sc.order = (const unsigned*)((char*)workspace + L.order);
+        sc.counter = &((WsHeader*)workspace)->work[which];
+    }
+    return sc;
 }
 
 wsr_status check_ws(const Views& vs, void* ws, size_t bytes) {
@@ -229,6 +251,8 @@ static wsr_status bin_count_impl(const float* records, int64_t n, const Views& v
     WSR_CUDA(cudaMemsetAsync(&hdr->err, 0, sizeof(int), s));
     WSR_CUDA(launch_bin_count(records, n, vs, cursor, s));
     WSR_CUDA(launch_scan(vs, cursor, bsum, tile_offsets, capacity, hdr, s));
+    if (vs.schedule == WSR_SCHEDULE_PERSISTENT)
+        WSR_CUDA(launch_tile_order(vs, tile_offsets, (unsigned*)(ws + L.buckets), (unsigned*)(ws + L.order), s));
     return WSR_OK;
 }
 
@@ -270,6 +294,7 @@ wsr_status wsr_bin_static(const float* records, int64_t n, const wsr_camera* cam
     if (!tiles) return WSR_ERR_INVALID_ARG;
     WSR_TRY(make_views(cams, n_cams, tiles, &vs));
     if ((size_t)vs.total_tiles > kStaticTiles) return WSR_ERR_UNSUPPORTED;
+    if (vs.schedule != WSR_SCHEDULE_TILE_BLOCKS) return WSR_ERR_UNSUPPORTED;
     if (n < 0 || (n > 0 && (!records || !aligned16(records))) || !tile_offsets) return WSR_ERR_INVALID_ARG;
     if (list_capacity > 0 && !tile_list) return WSR_ERR_INVALID_ARG;
     if ((unsigned long long)n * (unsigned long long)n_cams > 0xffffffffull) return WSR_ERR_INVALID_ARG;
@@ -308,8 +333,8 @@ wsr_status wsr_render_fwd(const float* records, int64_t n, const uint32_t* tile_
     WSR_TRY(check_ws(vs, workspace, workspace_bytes));
     if (n < 0 || !tile_offsets || !out_rgb || !out_den) return WSR_ERR_INVALID_ARG;
     if (n > 0 && (!records || !tile_list)) return WSR_ERR_INVALID_ARG;
-    return cuda_status(
-        launch_render_fwd(records, tile_offsets, tile_list, vs, wd, out_rgb, out_den, (cudaStream_t)stream));
+    return cuda_status(launch_render_fwd(records, tile_offsets, tile_list, vs, wd, out_rgb, out_den,
+                                         sched_of(vs, workspace, 0), (cudaStream_t)stream));
 }
 
 wsr_status wsr_render_bwd_tiles(const float* records, int64_t n, const uint32_t* tile_offsets,
@@ -332,7 +357,7 @@ wsr_status wsr_render_bwd_tiles(const float* records, int64_t n, const uint32_t*
     if (n > 0)
         WSR_CUDA(cudaMemsetAsync(grad_records, 0, sizeof(float) * WSR_GRAD_RECORD_FLOATS * (size_t)n * n_cams, s));
     WSR_CUDA(launch_render_bwd(records, tile_offsets, tile_list, vs, wd, out_rgb, out_den, grad_rgb, grad_records,
-                               hdr->gw, s));
+                               hdr->gw, sched_of(vs, workspace, 1), s));
     return WSR_OK;
 }
 

@@ -242,7 +242,54 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_apply(unsigned* __restrict_
     }
 }
 
+// Longest-first tile order for the persistent schedule: tiles are bucketed by
+// the magnitude of their instance count (floor(log2)), buckets taken from the
+// largest down; the order inside a bucket is arbitrary.
+__device__ __forceinline__ int cost_bucket(unsigned c) { return c ? 32 - __clz(c) : 0; }   // 0..32
+
+__global__ void __launch_bounds__(256) k_order_hist(const unsigned* __restrict__ offsets, int n,
+                                                    unsigned* __restrict__ hist) {
+    __shared__ unsigned h[33];
+    if (threadIdx.x < 33) h[threadIdx.x] = 0;
+    __syncthreads();
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+        atomicAdd(&h[cost_bucket(offsets[t + 1] - offsets[t])], 1u);
+    __syncthreads();
+    if (threadIdx.x < 33 && h[threadIdx.x]) atomicAdd(hist + threadIdx.x, h[threadIdx.x]);
+}
+
+__global__ void k_order_scan(unsigned* __restrict__ hist) {
+    // hist[0..32] -> cursors hist[33..65]: start of each bucket, largest bucket first
+    if (threadIdx.x == 0) {
+        unsigned run = 0;
+        for (int b = 32; b >= 0; --b) {
+            hist[33 + b] = run;
+            run += hist[b];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_order_scatter(const unsigned* __restrict__ offsets, int n,
+                                                       unsigned* __restrict__ hist, unsigned* __restrict__ order) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const unsigned pos = atomicAdd(hist + 33 + cost_bucket(offsets[t + 1] - offsets[t]), 1u);
+        order[pos] = (unsigned)t;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_tile_order(const Views& vs, const unsigned* offsets, unsigned* buckets, unsigned* order,
+                              cudaStream_t s) {
+    const int n = vs.total_tiles;
+    cudaError_t e = cudaMemsetAsync(buckets, 0, sizeof(unsigned) * 33, s);
+    if (e != cudaSuccess || n == 0) return e;
+    const int nb = min((n + 255) / 256, 1024);
+    k_order_hist<<<nb, 256, 0, s>>>(offsets, n, buckets);
+    k_order_scan<<<1, 32, 0, s>>>(buckets);
+    k_order_scatter<<<nb, 256, 0, s>>>(offsets, n, buckets, order);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_bin_count(const float* records, long long n, const Views& vs, unsigned* cursor,
                              cudaStream_t s) {

@@ -53,17 +53,16 @@ struct FwdShape {
 };
 
 template <int TW, int TH, int PX>
-__global__ void __launch_bounds__(FwdShape<TW, TH, PX>::NT)
-    k_render_fwd(const float4* __restrict__ rec, const unsigned* __restrict__ offsets,
-                 const unsigned* __restrict__ list, const Views vs, const float* __restrict__ wparams,
-                 float* __restrict__ out_rgb, float* __restrict__ out_den) {
+__device__ __forceinline__ void fwd_tile(const int tile, const float4* __restrict__ rec,
+                                         const unsigned* __restrict__ offsets, const unsigned* __restrict__ list,
+                                         const Views& vs, const float* __restrict__ wparams,
+                                         float* __restrict__ out_rgb, float* __restrict__ out_den) {
     using S = FwdShape<TW, TH, PX>;
     constexpr int NT = S::NT;
     __shared__ float4 s0[NT];   // mu_x, mu_y, A', 2B'
     __shared__ float4 s1[NT];   // C', u w, c_r u w, c_g u w
     __shared__ float2 s2[NT];   // c_b u w, u w
 
-    const int tile = blockIdx.x;
     const TileCoord tc = tile_coord(vs, tile);
     const View& V = vs.v[tc.v];
     const int tid = threadIdx.x;
@@ -141,6 +140,36 @@ __global__ void __launch_bounds__(FwdShape<TW, TH, PX>::NT)
         }
 }
 
+// Persistent schedule: blocks take tiles order[0..n) through *counter.
+template <typename F>
+__device__ __forceinline__ void for_each_tile(const unsigned* __restrict__ order, unsigned* __restrict__ counter,
+                                              int n_tiles, F&& body) {
+    if (order == nullptr) {
+        body((int)blockIdx.x);
+        return;
+    }
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();                      // the previous tile is done with shared memory
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_tiles) break;
+        body((int)order[item]);
+    }
+}
+
+template <int TW, int TH, int PX>
+__global__ void __launch_bounds__(FwdShape<TW, TH, PX>::NT)
+    k_render_fwd(const float4* __restrict__ rec, const unsigned* __restrict__ offsets,
+                 const unsigned* __restrict__ list, const Views vs, const float* __restrict__ wparams,
+                 float* __restrict__ out_rgb, float* __restrict__ out_den, const unsigned* __restrict__ order,
+                 unsigned* __restrict__ counter) {
+    for_each_tile(order, counter, vs.total_tiles, [&](int tile) {
+        fwd_tile<TW, TH, PX>(tile, rec, offsets, list, vs, wparams, out_rgb, out_den);
+    });
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -176,11 +205,12 @@ constexpr int kBwdThreads = 256;
 constexpr int kBwdChunk = 256;
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(kBwdThreads, 4)
-    k_render_bwd(const float4* __restrict__ rec, const unsigned* __restrict__ offsets,
-                 const unsigned* __restrict__ list, const Views vs, const float* __restrict__ wparams,
-                 const float* __restrict__ out_rgb, const float* __restrict__ out_den,
-                 const float* __restrict__ grad_rgb, float* __restrict__ grec, float* __restrict__ gw) {
+__device__ __forceinline__ void bwd_tile(const int tile, const float4* __restrict__ rec,
+                                         const unsigned* __restrict__ offsets, const unsigned* __restrict__ list,
+                                         const Views& vs, const float* __restrict__ wparams,
+                                         const float* __restrict__ out_rgb, const float* __restrict__ out_den,
+                                         const float* __restrict__ grad_rgb, float* __restrict__ grec,
+                                         float* __restrict__ gw) {
     constexpr int NT = kBwdThreads;
     constexpr int CH = kBwdChunk;
     constexpr int NW = NT / 32;
@@ -202,7 +232,6 @@ __global__ void __launch_bounds__(kBwdThreads, 4)
     __shared__ unsigned stot[3];                // pairs, row segments and slots of the chunk
     __shared__ float sbg[4][NW];
 
-    const int tile = blockIdx.x;
     const TileCoord tc = tile_coord(vs, tile);
     const View& V = vs.v[tc.v];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -494,19 +523,55 @@ __global__ void __launch_bounds__(kBwdThreads, 4)
     }
 }
 
+template <int TW, int TH>
+__global__ void __launch_bounds__(kBwdThreads, 4)
+    k_render_bwd(const float4* __restrict__ rec, const unsigned* __restrict__ offsets,
+                 const unsigned* __restrict__ list, const Views vs, const float* __restrict__ wparams,
+                 const float* __restrict__ out_rgb, const float* __restrict__ out_den,
+                 const float* __restrict__ grad_rgb, float* __restrict__ grec, float* __restrict__ gw,
+                 const unsigned* __restrict__ order, unsigned* __restrict__ counter) {
+    for_each_tile(order, counter, vs.total_tiles, [&](int tile) {
+        bwd_tile<TW, TH>(tile, rec, offsets, list, vs, wparams, out_rgb, out_den, grad_rgb, grec, gw);
+    });
+}
+
+// Grid of a launch: one block per tile, or, persistent, as many blocks as
+// fit on the device at once.
+template <typename K>
+unsigned grid_for(K kernel, int threads, const Views& vs, const Sched& sched) {
+    if (!sched.order) return (unsigned)vs.total_tiles;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+    return (unsigned)min(max(1, sms * max(per_sm, 1)), vs.total_tiles);
+}
+
 template <int TW, int TH, int PX>
 cudaError_t fwd_t(const float* rec, const unsigned* off, const unsigned* list, const Views& vs, WeightDev w,
-                  float* rgb, float* den, cudaStream_t s) {
-    k_render_fwd<TW, TH, PX><<<vs.total_tiles, FwdShape<TW, TH, PX>::NT, 0, s>>>(
-        reinterpret_cast<const float4*>(rec), off, list, vs, w.params, rgb, den);
+                  float* rgb, float* den, Sched sched, cudaStream_t s) {
+    constexpr int NT = FwdShape<TW, TH, PX>::NT;
+    const unsigned grid = grid_for(k_render_fwd<TW, TH, PX>, NT, vs, sched);
+    if (sched.order) {
+        cudaError_t e = cudaMemsetAsync(sched.counter, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+    }
+    k_render_fwd<TW, TH, PX><<<grid, NT, 0, s>>>(reinterpret_cast<const float4*>(rec), off, list, vs, w.params, rgb,
+                                                 den, sched.order, sched.counter);
     return cudaGetLastError();
 }
 
 template <int TW, int TH>
 cudaError_t bwd_t(const float* rec, const unsigned* off, const unsigned* list, const Views& vs, WeightDev w,
-                  const float* rgb, const float* den, const float* grgb, float* grec, float* gw, cudaStream_t s) {
-    k_render_bwd<TW, TH><<<vs.total_tiles, kBwdThreads, 0, s>>>(reinterpret_cast<const float4*>(rec), off, list, vs,
-                                                                w.params, rgb, den, grgb, grec, gw);
+                  const float* rgb, const float* den, const float* grgb, float* grec, float* gw, Sched sched,
+                  cudaStream_t s) {
+    const unsigned grid = grid_for(k_render_bwd<TW, TH>, kBwdThreads, vs, sched);
+    if (sched.order) {
+        cudaError_t e = cudaMemsetAsync(sched.counter, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+    }
+    k_render_bwd<TW, TH><<<grid, kBwdThreads, 0, s>>>(reinterpret_cast<const float4*>(rec), off, list, vs, w.params,
+                                                      rgb, den, grgb, grec, gw, sched.order, sched.counter);
     return cudaGetLastError();
 }
 
@@ -575,23 +640,23 @@ __global__ void k_loss_l1(const float* __restrict__ rgb, const float* __restrict
 }  // namespace
 
 cudaError_t launch_render_fwd(const float* rec, const unsigned* off, const unsigned* list, const Views& vs,
-                              WeightDev w, float* rgb, float* den, cudaStream_t s) {
+                              WeightDev w, float* rgb, float* den, Sched sc, cudaStream_t s) {
     if (vs.total_tiles == 0) return cudaSuccess;
-    if (vs.tile_w == 16 && vs.tile_h == 16) return fwd_t<16, 16, 2>(rec, off, list, vs, w, rgb, den, s);
-    if (vs.tile_w == 8 && vs.tile_h == 8) return fwd_t<8, 8, 1>(rec, off, list, vs, w, rgb, den, s);
-    if (vs.tile_w == 32 && vs.tile_h == 8) return fwd_t<32, 8, 2>(rec, off, list, vs, w, rgb, den, s);
-    if (vs.tile_w == 16 && vs.tile_h == 8) return fwd_t<16, 8, 2>(rec, off, list, vs, w, rgb, den, s);
+    if (vs.tile_w == 16 && vs.tile_h == 16) return fwd_t<16, 16, 2>(rec, off, list, vs, w, rgb, den, sc, s);
+    if (vs.tile_w == 8 && vs.tile_h == 8) return fwd_t<8, 8, 1>(rec, off, list, vs, w, rgb, den, sc, s);
+    if (vs.tile_w == 32 && vs.tile_h == 8) return fwd_t<32, 8, 2>(rec, off, list, vs, w, rgb, den, sc, s);
+    if (vs.tile_w == 16 && vs.tile_h == 8) return fwd_t<16, 8, 2>(rec, off, list, vs, w, rgb, den, sc, s);
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_render_bwd(const float* rec, const unsigned* off, const unsigned* list, const Views& vs,
                               WeightDev w, const float* rgb, const float* den, const float* grgb, float* grec,
-                              float* gw, cudaStream_t s) {
+                              float* gw, Sched sc, cudaStream_t s) {
     if (vs.total_tiles == 0) return cudaSuccess;
-    if (vs.tile_w == 16 && vs.tile_h == 16) return bwd_t<16, 16>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, s);
-    if (vs.tile_w == 8 && vs.tile_h == 8) return bwd_t<8, 8>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, s);
-    if (vs.tile_w == 32 && vs.tile_h == 8) return bwd_t<32, 8>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, s);
-    if (vs.tile_w == 16 && vs.tile_h == 8) return bwd_t<16, 8>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, s);
+    if (vs.tile_w == 16 && vs.tile_h == 16) return bwd_t<16, 16>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, sc, s);
+    if (vs.tile_w == 8 && vs.tile_h == 8) return bwd_t<8, 8>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, sc, s);
+    if (vs.tile_w == 32 && vs.tile_h == 8) return bwd_t<32, 8>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, sc, s);
+    if (vs.tile_w == 16 && vs.tile_h == 8) return bwd_t<16, 8>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, sc, s);
     return cudaErrorInvalidValue;
 }
 

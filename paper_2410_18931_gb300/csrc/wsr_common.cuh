@@ -39,16 +39,19 @@ struct Views {
     int tile_w, tile_h;
     int total_tiles;
     long long total_pix;
+    int schedule;         // WSR_SCHEDULE_*
+    int pad;
     View v[WSR_MAX_VIEWS];
 };
 
 // Workspace layout: [header 256 B][cursor: total_tiles + 1 u32][block sums]
+//                   [tile order: total_tiles u32][order buckets: 64 u32]
 struct WsHeader {
     int err;                   // first device-side error (wsr_status), 0 if none
     int pad0;
     float gw[8];               // gradient accumulators of sigma, beta, w_B, c_B (6 used)
     unsigned long long total;  // tile instances counted by the last binning
-    unsigned int work[4];
+    unsigned int work[4];      // persistent-schedule counters: [0] forward, [1] backward
 };
 
 constexpr size_t kWsHeader = 256;

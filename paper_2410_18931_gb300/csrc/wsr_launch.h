@@ -39,13 +39,24 @@ cudaError_t launch_bin_scatter(const float* records, long long n, const Views& v
                                unsigned* cursor, unsigned* tile_list,
                                unsigned long long capacity, WsHeader* hdr, cudaStream_t s);
 
+cudaError_t launch_tile_order(const Views& vs, const unsigned* tile_offsets, unsigned* buckets,
+                              unsigned* order, cudaStream_t s);
+
+// Work distribution of a render launch: order == nullptr means one block per
+// tile; otherwise a persistent grid takes tiles order[0..total) via *counter
+// (reset by the launcher).
+struct Sched {
+    const unsigned* order;
+    unsigned* counter;
+};
+
 cudaError_t launch_render_fwd(const float* records, const unsigned* tile_offsets,
                               const unsigned* tile_list, const Views& vs, WeightDev w,
-                              float* out_rgb, float* out_den, cudaStream_t s);
+                              float* out_rgb, float* out_den, Sched sched, cudaStream_t s);
 cudaError_t launch_render_bwd(const float* records, const unsigned* tile_offsets,
                               const unsigned* tile_list, const Views& vs, WeightDev w,
                               const float* out_rgb, const float* out_den, const float* grad_rgb,
-                              float* grad_records, float* grad_wparams, cudaStream_t s);
+                              float* grad_records, float* grad_wparams, Sched sched, cudaStream_t s);
 
 cudaError_t launch_count_pairs(const float* records, const unsigned* tile_offsets, const unsigned* tile_list,
                                const Views& vs, unsigned long long* count, cudaStream_t s);
