@@ -51,11 +51,12 @@ def _load():
                       dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp]
             lib.wsro_project.argtypes = common + [dp]
             lib.wsro_render.argtypes = common + [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp,
-                                                 ctypes.c_double, ctypes.POINTER(ctypes.c_longlong)]
+                                                 ctypes.c_double, ctypes.POINTER(ctypes.c_longlong),
+                                                 ctypes.c_double]
             lib.wsro_render_pixels.argtypes = common + [ctypes.c_int, ctypes.c_long,
                                                         ctypes.POINTER(ctypes.c_int), dp, dp, dp,
                                                         ctypes.c_double]
-            lib.wsro_grad.argtypes = common + [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp] + [dp] * 8
+            lib.wsro_grad.argtypes = common + [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp] + [dp] * 8 + [ctypes.c_double]
             lib.wsro_sh_basis.argtypes = [ctypes.c_long, ctypes.c_int, dp, dp, dp]
             for f in (lib.wsro_project, lib.wsro_render, lib.wsro_render_pixels, lib.wsro_grad,
                       lib.wsro_sh_basis):
@@ -111,7 +112,8 @@ def project(scene, cam, weight) -> dict:
                 depth=out[:, 17], rx=out[:, 18], ry=out[:, 19])
 
 
-def render(scene, cam, weight, *, threads: int | None = None, amb_tau: float | None = None, rows=None):
+def render(scene, cam, weight, *, threads: int | None = None, amb_tau: float | None = None, rows=None,
+           cutoff: float = 9.0):
     """WSR forward (Eq. 7) over the whole image, or over image rows
     ``rows = (y_lo, y_hi)`` of the same camera.
 
@@ -129,7 +131,7 @@ def render(scene, cam, weight, *, threads: int | None = None, amb_tau: float | N
     pairs = ctypes.c_longlong(0)
     rc = lib.wsro_render(*a.args, ctypes.c_int(threads or default_threads()), ctypes.c_int(y_lo),
                          ctypes.c_int(y_hi), _ptr(rgb), _ptr(den), _ptr(amb), ctypes.c_double(amb_tau or 0.0),
-                         ctypes.byref(pairs))
+                         ctypes.byref(pairs), ctypes.c_double(cutoff))
     if rc:
         raise RuntimeError(f"wsro_render failed ({rc})")
     return dict(rgb=rgb, den=den, pairs=int(pairs.value), amb=amb)
@@ -153,9 +155,10 @@ def render_pixels(scene, cam, weight, xy, *, threads: int | None = None, amb_tau
     return dict(rgb=rgb, den=den, amb=amb)
 
 
-def grad(scene, cam, weight, grad_rgb, *, threads: int | None = None, rows=None) -> dict:
+def grad(scene, cam, weight, grad_rgb, *, threads: int | None = None, rows=None, cutoff: float = 9.0) -> dict:
     """Analytic gradient of <grad_rgb, C> with respect to every parameter;
-    with ``rows = (y_lo, y_hi)``, grad_rgb covers only those image rows."""
+    with ``rows = (y_lo, y_hi)``, grad_rgb covers only those image rows.
+    ``cutoff`` is the footprint bound on q (9 for Eq. 7 as read here)."""
     lib = _load()
     a = _Args(scene, cam, weight)
     n, K = scene.n, a.K
@@ -168,7 +171,7 @@ def grad(scene, cam, weight, grad_rgb, *, threads: int | None = None, rows=None)
                        ctypes.c_int(y_hi), _ptr(G),
                        _ptr(out["means"]), _ptr(out["log_scales"]), _ptr(out["quats"]),
                        _ptr(out["sh"]), _ptr(out["opacity"]), _ptr(out["lc_v"]),
-                       _ptr(out["wpar"]), _ptr(out["g2d"]))
+                       _ptr(out["wpar"]), _ptr(out["g2d"]), ctypes.c_double(cutoff))
     if rc:
         raise RuntimeError(f"wsro_grad failed ({rc})")
     return out

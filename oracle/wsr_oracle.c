@@ -378,6 +378,7 @@ int wsro_sh_basis(long n, int deg, const double* dirs, double* Y /* n x K */, do
 /* ------------------------------------------------------------------------ */
 typedef struct {
     const oproj* P; long n; const ocam* cam; const owt* wt;
+    double cutoff;           /* footprint test q <= cutoff (9 for Eq. 7 as read here) */
     int y_lo;                /* first image row of the window held in the buffers */
     double *num, *den;       /* [rows*W*3], [rows*W] sums (without background) */
     long long* pairs;        /* per thread */
@@ -394,7 +395,7 @@ static void render_rows(void* arg, long r0, long r1, int tid)
     r1 += c->y_lo;
     const int W = c->cam->W;
     long long pairs = 0;
-    const double grow = c->amb ? sqrt((ORC_CUTOFF + c->amb_tau) / ORC_CUTOFF) : 1.0;
+    const double grow = sqrt((c->cutoff + (c->amb ? c->amb_tau : 0.0)) / ORC_CUTOFF);
     for (long i = 0; i < c->n; ++i) {
         const oproj* o = c->P + i;
         if (!o->visible) continue;
@@ -409,7 +410,7 @@ static void render_rows(void* arg, long r0, long r1, int tid)
                 const long p = (long)(y - c->y_lo) * W + x;
                 if (c->amb) {
                     /* second pass: bound of what a near-cutoff pair can change */
-                    if (fabs(q - ORC_CUTOFF) <= c->amb_tau) {
+                    if (fabs(q - c->cutoff) <= c->amb_tau) {
                         const double g = exp(-0.5 * q);
                         const double a = o->u * o->w * g;
                         double m = 0;
@@ -421,7 +422,7 @@ static void render_rows(void* arg, long r0, long r1, int tid)
                     }
                     continue;
                 }
-                if (q > ORC_CUTOFF) continue;
+                if (q > c->cutoff) continue;
                 const double g = exp(-0.5 * q);
                 const double a = o->u * o->w * g;            /* alpha_i w(d_i) */
                 for (int ch = 0; ch < 3; ++ch) c->num[3 * p + ch] += o->color[ch] * a;
@@ -442,7 +443,9 @@ static oproj* project_all(const oscene* S, const ocam* cam, const owt* wt)
 }
 
 /*
- * Rows [y_lo, y_hi) of the image (the whole image for 0, H).
+ * Rows [y_lo, y_hi) of the image (the whole image for 0, H).  `cutoff` is the
+ * footprint bound on q (9: the 3-sigma footprint); other values serve tests
+ * that bracket pairs whose q is within rounding of 9.
  * out_rgb [rows*W*3]: C per pixel (Eq. 7); out_den [rows*W]: w_B + sum a_i.
  * amb [H*W] (optional): for pixels having Gaussians with |q - 9| <= amb_tau,
  * a bound on how far C can move if those pairs were decided the other way.
@@ -452,7 +455,7 @@ int wsro_render(long n, int deg, int vd, const double* means, const double* log_
                 const double* quats, const double* sh, const double* opac, const double* lc_v,
                 const double* cam16, int W, int H, double znear, int wkind, const double* wpar,
                 int nthreads, int y_lo, int y_hi, double* out_rgb, double* out_den, double* amb,
-                double amb_tau, long long* n_pairs)
+                double amb_tau, long long* n_pairs, double cutoff)
 {
     if (deg < 0 || deg > 3 || n < 0 || W <= 0 || H <= 0) return 1;
     if (y_lo < 0 || y_hi > H || y_lo >= y_hi) return 1;
@@ -467,7 +470,7 @@ int wsro_render(long n, int deg, int vd, const double* means, const double* log_
     double* num = (double*)calloc(np * 3, sizeof(double));
     double* den = (double*)calloc(np, sizeof(double));
     long long pairs[256] = {0};
-    render_ctx c = {P, n, &cam, &wt, y_lo, num, den, pairs, amb_tau, NULL, NULL, NULL};
+    render_ctx c = {P, n, &cam, &wt, cutoff, y_lo, num, den, pairs, amb_tau, NULL, NULL, NULL};
     if (nthreads > rows) nthreads = rows;
     run_parallel(render_rows, &c, rows, nthreads);
     long long tot = 0;
@@ -480,7 +483,7 @@ int wsro_render(long n, int deg, int vd, const double* means, const double* log_
     }
     if (amb) {
         memset(amb, 0, np * sizeof(double));
-        render_ctx c2 = {P, n, &cam, &wt, y_lo, NULL, NULL, pairs, amb_tau, amb, out_rgb, out_den};
+        render_ctx c2 = {P, n, &cam, &wt, cutoff, y_lo, NULL, NULL, pairs, amb_tau, amb, out_rgb, out_den};
         run_parallel(render_rows, &c2, rows, nthreads);
         for (long p = 0; p < np; ++p) amb[p] *= 1.05;
     }
@@ -582,6 +585,7 @@ int wsro_render_pixels(long n, int deg, int vd, const double* means, const doubl
 /* ------------------------------------------------------------------------ */
 typedef struct {
     const oscene* S; const oproj* P; const ocam* cam; const owt* wt;
+    double cutoff;
     int y_lo, y_hi;          /* image rows covered by rgb, den and G */
     const double *rgb, *den, *G;
     double *g_means, *g_log_scales, *g_quats, *g_sh, *g_opac, *g_lc_v, *g2d;
@@ -603,7 +607,7 @@ static void grad_gaussians(void* arg, long lo, long hi, int tid)
         if (!o->visible) continue;
         /* ---- per-pixel part: Eq. 7 and the Gaussian footprint ---- */
         int x0, x1, y0, y1;
-        pixel_range(o, cam, 1.0, &x0, &x1, &y0, &y1);
+        pixel_range(o, cam, sqrt(c->cutoff / ORC_CUTOFF), &x0, &x1, &y0, &y1);
         if (y0 < c->y_lo) y0 = c->y_lo;
         if (y1 > c->y_hi - 1) y1 = c->y_hi - 1;
         const double uw = o->u * o->w;
@@ -611,7 +615,7 @@ static void grad_gaussians(void* arg, long lo, long hi, int tid)
             for (int x = x0; x <= x1; ++x) {
                 const double dx = x + 0.5 - o->mean2d[0], dy = y + 0.5 - o->mean2d[1];
                 const double q = quad_form(o->conic, dx, dy);
-                if (q > ORC_CUTOFF) continue;
+                if (q > c->cutoff) continue;
                 const long p = (long)(y - c->y_lo) * W + x;
                 const double g = exp(-0.5 * q);
                 const double a = uw * g;
@@ -777,7 +781,7 @@ int wsro_grad(long n, int deg, int vd, const double* means, const double* log_sc
               const double* cam16, int W, int H, double znear, int wkind, const double* wpar,
               int nthreads, int y_lo, int y_hi, const double* grad_rgb,
               double* g_means, double* g_log_scales, double* g_quats, double* g_sh,
-              double* g_opac, double* g_lc_v, double* g_wpar, double* g2d)
+              double* g_opac, double* g_lc_v, double* g_wpar, double* g2d, double cutoff)
 {
     if (deg < 0 || deg > 3 || n < 0 || W <= 0 || H <= 0) return 1;
     if (y_lo < 0 || y_hi > H || y_lo >= y_hi) return 1;
@@ -790,12 +794,12 @@ int wsro_grad(long n, int deg, int vd, const double* means, const double* log_sc
     double* den = (double*)malloc(np * sizeof(double));
     if (!rgb || !den) { free(rgb); free(den); return 2; }
     int rc = wsro_render(n, deg, vd, means, log_scales, quats, sh, opac, lc_v, cam16, W, H, znear,
-                         wkind, wpar, nthreads, y_lo, y_hi, rgb, den, NULL, 0.0, NULL);
+                         wkind, wpar, nthreads, y_lo, y_hi, rgb, den, NULL, 0.0, NULL, cutoff);
     if (rc) { free(rgb); free(den); return rc; }
     oproj* P = project_all(&S, &cam, &wt);
     if (!P) { free(rgb); free(den); return 2; }
     grad_ctx* c = (grad_ctx*)calloc(1, sizeof(grad_ctx));
-    c->S = &S; c->P = P; c->cam = &cam; c->wt = &wt; c->y_lo = y_lo; c->y_hi = y_hi;
+    c->S = &S; c->P = P; c->cam = &cam; c->wt = &wt; c->y_lo = y_lo; c->y_hi = y_hi; c->cutoff = cutoff;
     c->rgb = rgb; c->den = den; c->G = grad_rgb;
     c->g_means = g_means; c->g_log_scales = g_log_scales; c->g_quats = g_quats; c->g_sh = g_sh;
     c->g_opac = g_opac; c->g_lc_v = g_lc_v; c->g2d = g2d;

@@ -415,3 +415,19 @@ def test_row_window_equals_rows_of_the_full_image():
     gw = oracle.grad(sc, cam, w, R[7:19], rows=(7, 19))
     for k in ("means", "log_scales", "quats", "sh", "opacity", "lc_v", "wpar"):
         assert np.abs(gf[k] - gw[k]).max() <= 1e-12 * max(1.0, np.abs(gf[k]).max()), k
+
+
+def test_tie_bound_covers_a_shifted_cutoff():
+    """The per-pixel tie bound is an upper bound on what deciding the pairs
+    within tau of q = 9 the other way changes: rendering with the cutoff moved
+    to 9 + tau (or 9 - tau) stays within it."""
+    sc = tiny_scene(61, 3, True, n=60, ls=-2.5)
+    cam = tiny_cam(48, 36)
+    for w in WEIGHTS:
+        for tau in (0.02, 0.3):
+            base = oracle.render(sc, cam, w, amb_tau=tau)
+            assert (base["amb"] > 0).any()
+            for cut in (9.0 + tau, 9.0 - tau):
+                moved = oracle.render(sc, cam, w, cutoff=cut)
+                d = np.abs(moved["rgb"] - base["rgb"]).max(axis=2)
+                assert np.all(d <= base["amb"] + 1e-12), (w.kind, tau, cut)
