@@ -276,6 +276,86 @@ wsr_status wsr_loss_l1(const float* rgb, const float* target, int64_t count, flo
                        float* grad_rgb, void* stream);
 
 /*
+ * wsr_loss_3dgs — the rendering loss the paper trains with (Sec. 4.4,
+ * "Loss function": the 3DGS loss, L1 plus D-SSIM weighted 0.2) and its
+ * gradient with respect to the rendered pixels:
+ *     L = (1 - lambda) * L1 + lambda * (1 - SSIM)
+ *   L1    mean |rgb - target| over every pixel and channel of every view;
+ *   SSIM  mean of the SSIM map (Wang et al. 2004) over the same elements,
+ *         each view and channel filtered on its own with the 11 x 11 Gaussian
+ *         window of standard deviation 1.5 (normalised to sum 1), pixels
+ *         outside the image taken as zero, C1 = 0.01^2, C2 = 0.03^2.
+ *   rgb, target  [num_pixels * 3] float32 device, the views concatenated as
+ *                wsr_render_fwd writes them (row-major per view, RGB
+ *                interleaved); 4-byte aligned
+ *   cams, n_cams the views (only width and height are used)
+ *   lambda       weight of the D-SSIM term, in [0, 1] (the paper: 0.2)
+ *   loss_out     [3] float32 device, overwritten: {L, L1, SSIM}
+ *   grad_rgb     [num_pixels * 3] float32 device, overwritten: dL/drgb, with
+ *                d|d|/dd taken as 0 at d = 0
+ * Summation order across tiles is not fixed (float atomics), so L varies in
+ * the last bits between runs; grad_rgb does not.
+ * Errors: WSR_ERR_INVALID_ARG (null pointer, bad cameras, lambda outside
+ * [0, 1]) before anything is enqueued; WSR_ERR_CUDA on a launch failure.
+ */
+wsr_status wsr_loss_3dgs(const float* rgb, const float* target, const wsr_camera* cams, int32_t n_cams,
+                         float lambda, float* loss_out, float* grad_rgb, void* stream);
+
+/*
+ * wsr_adam_step — one Adam update (Kingma & Ba 2015) of a flat float32
+ * parameter buffer, the optimiser the paper's PyTorch training uses (Sec.
+ * 4.4, "Training and Evaluation", as 3DGS does):
+ *     m <- b1 m + (1 - b1) g,   v <- b2 v + (1 - b2) g^2,
+ *     p <- p - lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)
+ * with t the step number kept in the device state (advanced by this call).
+ *   params, grads, exp_avg, exp_avg_sq  flat float32 device buffers, 16-byte
+ *       aligned; exp_avg and exp_avg_sq start at zero (caller-owned)
+ *   groups[n_groups] (host, n_groups <= WSR_ADAM_MAX_GROUPS): element ranges
+ *       updated, each with its learning rate; offset a multiple of 4, count
+ *       below 2^32; ranges must not overlap.  Elements outside every group are
+ *       not touched.  Element e of a group (0-based) uses lr, or lr_tail when
+ *       period > 0 and e % period >= head (e.g. the higher SH bands of
+ *       [n, K, 3] coefficients: period 3K, head 3).
+ *   hp (host): beta1, beta2 in [0, 1), eps >= 0
+ *   state  device wsr_adam_state (16 bytes, 4-byte aligned), zeroed by the
+ *       caller before the first step; step counts the updates made, skipped
+ *       the calls that made none
+ *   guard_workspace, guard_bytes  optional (NULL, 0): a wsr_bin / render
+ *       workspace; when it holds a device-side error (e.g. WSR_ERR_CAPACITY
+ *       from a wsr_bin earlier on the stream) the call changes nothing but
+ *       state->skipped.  Everything is read on the device, so a captured
+ *       graph replays correct steps.
+ * Errors: WSR_ERR_INVALID_ARG before anything is enqueued; WSR_ERR_CUDA.
+ */
+#define WSR_ADAM_MAX_GROUPS 16
+typedef struct {
+    int64_t offset;
+    int64_t count;
+    float lr;
+    float lr_tail;
+    int32_t period;
+    int32_t head;
+} wsr_adam_group;
+
+typedef struct {
+    double beta1;
+    double beta2;
+    double eps;
+} wsr_adam_hparams;
+
+typedef struct {
+    int32_t step;     /* updates made so far */
+    float c1;         /* 1 / (1 - beta1^step) */
+    float c2;         /* 1 / sqrt(1 - beta2^step) */
+    int32_t skipped;  /* calls that updated nothing (guard error) */
+} wsr_adam_state;
+
+wsr_status wsr_adam_step(float* params, const float* grads, float* exp_avg, float* exp_avg_sq,
+                         const wsr_adam_group* groups, int32_t n_groups, const wsr_adam_hparams* hp,
+                         wsr_adam_state* state, const void* guard_workspace, size_t guard_bytes,
+                         void* stream);
+
+/*
  * wsr_bin_static — wsr_bin for callers that cannot allocate device memory.
  *
  * Some callers cannot call cudaMalloc at all once they are running: a frame

@@ -50,6 +50,23 @@ class wsr_grads(ctypes.Structure):
                 ("opacity", _c_void_p), ("lc_v", _c_void_p), ("weight_params", _c_void_p)]
 
 
+WSR_ADAM_MAX_GROUPS = 16
+
+
+class wsr_adam_group(ctypes.Structure):
+    _fields_ = [("offset", ctypes.c_int64), ("count", ctypes.c_int64), ("lr", ctypes.c_float),
+                ("lr_tail", ctypes.c_float), ("period", ctypes.c_int32), ("head", ctypes.c_int32)]
+
+
+class wsr_adam_hparams(ctypes.Structure):
+    _fields_ = [("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
+class wsr_adam_state(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int32), ("c1", ctypes.c_float), ("c2", ctypes.c_float),
+                ("skipped", ctypes.c_int32)]
+
+
 # name -> (restype, argtypes)
 _P = ctypes.POINTER
 _SIGS = {
@@ -82,6 +99,10 @@ _SIGS = {
     "wsr_count_pairs": (ctypes.c_int, [_c_void_p, ctypes.c_int64, _c_void_p, _c_void_p, _P(wsr_camera),
                                        ctypes.c_int32, _P(wsr_tiles), _c_void_p, _c_void_p]),
     "wsr_loss_l1": (ctypes.c_int, [_c_void_p, _c_void_p, ctypes.c_int64, _c_void_p, _c_void_p, _c_void_p]),
+    "wsr_loss_3dgs": (ctypes.c_int, [_c_void_p, _c_void_p, _P(wsr_camera), ctypes.c_int32, ctypes.c_float,
+                                     _c_void_p, _c_void_p, _c_void_p]),
+    "wsr_adam_step": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _P(wsr_adam_group), ctypes.c_int32,
+                                     _P(wsr_adam_hparams), _c_void_p, _c_void_p, ctypes.c_size_t, _c_void_p]),
     "wsr_check": (ctypes.c_int, [_c_void_p, ctypes.c_size_t, _c_void_p]),
 }
 

@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libwsr.so")
-SOURCES = ["api.cu", "project.cu", "bin.cu", "render.cu"]
+SOURCES = ["api.cu", "project.cu", "bin.cu", "render.cu", "train.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
          "-Xptxas", "-v", "-I" + INCLUDE, "-I" + CSRC]

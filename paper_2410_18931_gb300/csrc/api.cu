@@ -419,6 +419,84 @@ wsr_status wsr_loss_l1(const float* rgb, const float* target, int64_t count, flo
     return cuda_status(launch_loss_l1(rgb, target, count, loss_out, grad_rgb, (cudaStream_t)stream));
 }
 
+wsr_status wsr_loss_3dgs(const float* rgb, const float* target, const wsr_camera* cams, int32_t n_cams,
+                         float lambda, float* loss_out, float* grad_rgb, void* stream) {
+    if (!cams || n_cams < 1 || n_cams > WSR_MAX_VIEWS || !loss_out || !rgb || !target || !grad_rgb)
+        return WSR_ERR_INVALID_ARG;
+    if (!(lambda >= 0.0f && lambda <= 1.0f)) return WSR_ERR_INVALID_ARG;
+    static thread_local LossViews L;
+    memset(&L, 0, sizeof L);
+    const int side = loss_tile_side();
+    long long tiles = 0, pix = 0;
+    L.n = n_cams;
+    for (int v = 0; v < n_cams; ++v) {
+        const int W = cams[v].width, H = cams[v].height;
+        if (W <= 0 || H <= 0 || W > 32768 || H > 32768) return WSR_ERR_INVALID_ARG;
+        L.w[v] = W;
+        L.h[v] = H;
+        L.tiles_x[v] = (W + side - 1) / side;
+        L.tile_off[v] = (int)tiles;
+        L.pix_off[v] = pix;
+        tiles += (long long)L.tiles_x[v] * ((H + side - 1) / side);
+        pix += (long long)W * H;
+        if (tiles > (1ll << 30)) return WSR_ERR_INVALID_ARG;
+    }
+    L.tile_off[n_cams] = (int)tiles;
+    // the normalised 11-tap Gaussian of standard deviation 1.5
+    double g[11], sum = 0.0;
+    for (int k = 0; k < 11; ++k) sum += (g[k] = exp(-(double)((k - 5) * (k - 5)) / (2.0 * 1.5 * 1.5)));
+    for (int k = 0; k < 11; ++k) L.g[k] = (float)(g[k] / sum);
+    L.lam = lambda;
+    L.inv_count = (float)(1.0 / (3.0 * (double)pix));
+    L.c1 = 0.01f * 0.01f;
+    L.c2 = 0.03f * 0.03f;
+    return cuda_status(launch_loss_3dgs(rgb, target, L, loss_out, grad_rgb, (cudaStream_t)stream));
+}
+
+wsr_status wsr_adam_step(float* params, const float* grads, float* exp_avg, float* exp_avg_sq,
+                         const wsr_adam_group* groups, int32_t n_groups, const wsr_adam_hparams* hp,
+                         wsr_adam_state* state, const void* guard_workspace, size_t guard_bytes, void* stream) {
+    if (!params || !grads || !exp_avg || !exp_avg_sq || !hp || !state) return WSR_ERR_INVALID_ARG;
+    if (!aligned16(params) || !aligned16(grads) || !aligned16(exp_avg) || !aligned16(exp_avg_sq) ||
+        ((uintptr_t)state & 3u))
+        return WSR_ERR_INVALID_ARG;
+    if (n_groups < 0 || n_groups > WSR_ADAM_MAX_GROUPS || (n_groups > 0 && !groups)) return WSR_ERR_INVALID_ARG;
+    if (!(hp->beta1 >= 0.0 && hp->beta1 < 1.0) || !(hp->beta2 >= 0.0 && hp->beta2 < 1.0) || !(hp->eps >= 0.0))
+        return WSR_ERR_INVALID_ARG;
+    if (guard_workspace && (guard_bytes < kWsHeader || !aligned16(guard_workspace))) return WSR_ERR_INVALID_ARG;
+    static thread_local AdamGroups G;
+    memset(&G, 0, sizeof G);
+    G.n = n_groups;
+    long long units = 0;
+    for (int k = 0; k < n_groups; ++k) {
+        const wsr_adam_group& q = groups[k];
+        if (q.offset < 0 || (q.offset & 3) || q.count < 0 || q.count >= (1ll << 32)) return WSR_ERR_INVALID_ARG;
+        if (q.period < 0 || (q.period > 0 && (q.head < 0 || q.head > q.period))) return WSR_ERR_INVALID_ARG;
+        if (!isfinite(q.lr) || !isfinite(q.lr_tail)) return WSR_ERR_INVALID_ARG;
+        for (int j = 0; j < k; ++j) {
+            const wsr_adam_group& o = groups[j];
+            if (q.offset < o.offset + o.count && o.offset < q.offset + q.count) return WSR_ERR_INVALID_ARG;
+        }
+        G.ubase[k] = units;
+        G.off[k] = q.offset;
+        G.cnt[k] = (unsigned)q.count;
+        G.lr[k] = q.lr;
+        G.lr_tail[k] = q.lr_tail;
+        G.period[k] = q.period;
+        G.head[k] = q.head;
+        units += (q.count + 3) / 4;
+    }
+    G.ubase[n_groups] = units;
+    G.b1 = (float)hp->beta1;
+    G.omb1 = (float)(1.0 - hp->beta1);
+    G.b2 = (float)hp->beta2;
+    G.omb2 = (float)(1.0 - hp->beta2);
+    G.eps = (float)hp->eps;
+    return cuda_status(launch_adam(params, grads, exp_avg, exp_avg_sq, G, hp->beta1, hp->beta2,
+                                   reinterpret_cast<AdamState*>(state),
+                                   reinterpret_cast<const WsHeader*>(guard_workspace), (cudaStream_t)stream));
+}
+
 wsr_status wsr_check(void* workspace, size_t workspace_bytes, void* stream) {
     if (!workspace || workspace_bytes < kWsHeader) return WSR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;

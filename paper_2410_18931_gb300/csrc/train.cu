@@ -1,0 +1,285 @@
+// Training step around the renderer: the 3DGS rendering loss the paper
+// trains with (Sec. 4.4: L1 + 0.2 D-SSIM) with its gradient, and the Adam
+// update of the parameters.
+//
+// Loss.  One block per 32 x 32 output tile of one view.  For each channel the
+// block stages the rendered and target pixels of the tile plus a 10-pixel
+// halo in shared memory (zero outside the image), filters the five local
+// statistics (mu_x, mu_y, E[x^2], E[y^2], E[xy]) separably with the 11-tap
+// Gaussian over the tile plus a 5-pixel halo, forms the SSIM map and the three
+// partials of the loss with respect to (mu_x, E[x^2], E[xy]), and filters
+// those back (the window is symmetric, so the filter is its own adjoint) to
+// the gradient of the tile's pixels.  L1 and SSIM sums go to the loss with
+// one atomic per block and quantity.
+//
+// Adam.  One pass over a flat parameter buffer in float4 units, groups of
+// contiguous elements with their own learning rates.  The step count and the
+// bias corrections live in device memory (a one-thread kernel advances them),
+// so a captured CUDA graph replays correct steps; both kernels leave
+// everything untouched when a guard workspace recorded an error (a tile list
+// that overflowed in the same step).
+#include "wsr_common.cuh"
+#include "wsr_launch.h"
+
+namespace wsr {
+namespace {
+
+constexpr int kR = 5;                       // window radius: 11 taps
+constexpr int kLT = 32;                     // output tile side
+constexpr int kIn = kLT + 4 * kR;           // staged input side (52)
+constexpr int kSt = kLT + 2 * kR;           // statistics side (42)
+constexpr int kLossThreads = 256;
+constexpr int kLossSmemFloats = 2 * kIn * kIn + 5 * kIn * kSt + 3 * kSt * kSt;
+static_assert(3 * kSt * kLT <= 5 * kIn * kSt, "filtered partials reuse the statistics buffer");
+
+__device__ __forceinline__ float block_sum_to(float x, float* red) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) red[w] = x;
+    __syncthreads();
+    float t = 0.f;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    return t;   // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kLossThreads) k_loss_3dgs(const float* __restrict__ rgb,
+                                                            const float* __restrict__ tgt, const LossViews L,
+                                                            float* __restrict__ loss, float* __restrict__ grad) {
+    extern __shared__ float sm[];
+    float* sx = sm;                          // [kIn][kIn] rendered
+    float* sy = sx + kIn * kIn;              // [kIn][kIn] target
+    float* hs = sy + kIn * kIn;              // [5][kIn][kSt] horizontally filtered statistics
+    float* mm = hs + 5 * kIn * kSt;          // [3][kSt][kSt] partials of the loss
+    float* hm = hs;                          // [3][kSt][kLT] horizontally filtered partials
+    __shared__ float red[kLossThreads / 32];
+    const int tid = threadIdx.x;
+
+    int v = 0;
+    while (v + 1 < L.n && (int)blockIdx.x >= L.tile_off[v + 1]) ++v;
+    const int t = (int)blockIdx.x - L.tile_off[v];
+    const int W = L.w[v], H = L.h[v];
+    const int x0 = (t % L.tiles_x[v]) * kLT, y0 = (t / L.tiles_x[v]) * kLT;
+    const long long base = L.pix_off[v];
+    const float gs = -L.lam * L.inv_count;                 // dL / d(SSIM map value)
+    const float gl1 = (1.0f - L.lam) * L.inv_count;        // dL / d|x - y|
+    float l1 = 0.f, ss = 0.f;
+
+    for (int c = 0; c < 3; ++c) {
+        for (int i = tid; i < kIn * kIn; i += kLossThreads) {
+            const int iy = i / kIn, ix = i - iy * kIn;
+            const int gx = x0 - 2 * kR + ix, gy = y0 - 2 * kR + iy;
+            float a = 0.f, b = 0.f;
+            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+                const long long p = (base + (long long)gy * W + gx) * 3 + c;
+                a = rgb[p];
+                b = tgt[p];
+            }
+            sx[i] = a;
+            sy[i] = b;
+        }
+        __syncthreads();
+        for (int i = tid; i < kIn * kSt; i += kLossThreads) {
+            const int iy = i / kSt, jx = i - iy * kSt;
+            const float* rx = sx + iy * kIn + jx;
+            const float* ry = sy + iy * kIn + jx;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 2 * kR + 1; ++k) {
+                const float a = rx[k], b = ry[k], w = L.g[k];
+                const float wa = w * a, wb = w * b;
+                s0 += wa;
+                s1 += wb;
+                s2 = fmaf(wa, a, s2);
+                s3 = fmaf(wb, b, s3);
+                s4 = fmaf(wa, b, s4);
+            }
+            hs[i] = s0;
+            hs[kIn * kSt + i] = s1;
+            hs[2 * kIn * kSt + i] = s2;
+            hs[3 * kIn * kSt + i] = s3;
+            hs[4 * kIn * kSt + i] = s4;
+        }
+        __syncthreads();
+        for (int i = tid; i < kSt * kSt; i += kLossThreads) {
+            const int jy = i / kSt, jx = i - jy * kSt;
+            const int gx = x0 - kR + jx, gy = y0 - kR + jy;
+            float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+                float st[5];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    const float* col = hs + q * kIn * kSt + jy * kSt + jx;
+                    float acc = 0.f;
+#pragma unroll
+                    for (int k = 0; k < 2 * kR + 1; ++k) acc = fmaf(L.g[k], col[k * kSt], acc);
+                    st[q] = acc;
+                }
+                const float mx = st[0], my = st[1];
+                const float sxx = st[2] - mx * mx, syy = st[3] - my * my, sxy = st[4] - mx * my;
+                const float a1 = 2.f * mx * my + L.c1, a2 = 2.f * sxy + L.c2;
+                const float b1 = mx * mx + my * my + L.c1, b2 = sxx + syy + L.c2;
+                const float ib1 = 1.0f / b1, ib2 = 1.0f / b2;
+                const float s = a1 * a2 * ib1 * ib2;
+                m0 = gs * (2.f * my * (a2 - a1) * ib1 * ib2 + 2.f * mx * s * (ib2 - ib1));
+                m1 = gs * (-s * ib2);
+                m2 = gs * (2.f * a1 * ib1 * ib2);
+                if (jx >= kR && jx < kR + kLT && jy >= kR && jy < kR + kLT) ss += s;
+            }
+            mm[i] = m0;
+            mm[kSt * kSt + i] = m1;
+            mm[2 * kSt * kSt + i] = m2;
+        }
+        __syncthreads();
+        for (int i = tid; i < kSt * kLT; i += kLossThreads) {
+            const int jy = i / kLT, ox = i - jy * kLT;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float* row = mm + q * kSt * kSt + jy * kSt + ox;
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < 2 * kR + 1; ++k) acc = fmaf(L.g[k], row[k], acc);
+                hm[q * kSt * kLT + i] = acc;
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < kLT * kLT; i += kLossThreads) {
+            const int oy = i / kLT, ox = i - oy * kLT;
+            const int gx = x0 + ox, gy = y0 + oy;
+            if (gx >= W || gy >= H) continue;
+            float f[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float* col = hm + q * kSt * kLT + oy * kLT + ox;
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < 2 * kR + 1; ++k) acc = fmaf(L.g[k], col[k * kLT], acc);
+                f[q] = acc;
+            }
+            const float a = sx[(oy + 2 * kR) * kIn + ox + 2 * kR];
+            const float b = sy[(oy + 2 * kR) * kIn + ox + 2 * kR];
+            const float d = a - b;
+            l1 += fabsf(d);
+            const float gd = d > 0.f ? gl1 : (d < 0.f ? -gl1 : 0.f);
+            grad[(base + (long long)gy * W + gx) * 3 + c] = f[0] + 2.f * a * f[1] + b * f[2] + gd;
+        }
+        __syncthreads();
+    }
+    const float tl1 = block_sum_to(l1, red);
+    __syncthreads();
+    const float tss = block_sum_to(ss, red);
+    if (tid == 0) {
+        atomicAdd(loss, gl1 * tl1 + gs * tss + (blockIdx.x == 0 ? L.lam : 0.f));
+        atomicAdd(loss + 1, tl1 * L.inv_count);
+        atomicAdd(loss + 2, tss * L.inv_count);
+    }
+}
+
+__global__ void k_adam_tick(AdamState* st, const WsHeader* guard, double b1, double b2) {
+    if (guard && guard->err != 0) {
+        st->skipped += 1;
+        return;
+    }
+    const int t = st->step + 1;
+    st->step = t;
+    st->c1 = (float)(1.0 / (1.0 - pow(b1, (double)t)));
+    st->c2 = (float)(1.0 / sqrt(1.0 - pow(b2, (double)t)));
+}
+
+__global__ void __launch_bounds__(256) k_adam(float* __restrict__ p, const float* __restrict__ g,
+                                              float* __restrict__ m, float* __restrict__ v, const AdamGroups G,
+                                              const AdamState* __restrict__ st, const WsHeader* guard) {
+    if (guard && guard->err != 0) return;
+    const float c1 = st->c1, c2 = st->c2;
+    const long long units = G.ubase[G.n];
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < units;
+         u += (long long)gridDim.x * blockDim.x) {
+        int gi = 0;
+        while (u >= G.ubase[gi + 1]) ++gi;
+        const unsigned e0 = (unsigned)(u - G.ubase[gi]) * 4u;
+        const long long at = G.off[gi] + e0;
+        const unsigned left = G.cnt[gi] - e0;
+        const unsigned per = (unsigned)G.period[gi];
+        const unsigned r0 = per ? e0 % per : 0u;
+        float lr[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            unsigned r = r0 + (unsigned)k;
+            if (per) r = (r >= per) ? r - per * (r / per) : r;
+            lr[k] = (per && r >= (unsigned)G.head[gi]) ? G.lr_tail[gi] : G.lr[gi];
+        }
+        if (left >= 4) {
+            float4 pp = *reinterpret_cast<const float4*>(p + at);
+            const float4 gg = *reinterpret_cast<const float4*>(g + at);
+            float4 mv = *reinterpret_cast<const float4*>(m + at);
+            float4 vv = *reinterpret_cast<const float4*>(v + at);
+            float* P = &pp.x;
+            const float* Gr = &gg.x;
+            float* M = &mv.x;
+            float* V = &vv.x;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                M[k] = fmaf(G.b1, M[k], G.omb1 * Gr[k]);
+                V[k] = fmaf(G.b2, V[k], G.omb2 * Gr[k] * Gr[k]);
+                P[k] -= lr[k] * c1 * M[k] / (sqrtf(V[k]) * c2 + G.eps);
+            }
+            *reinterpret_cast<float4*>(p + at) = pp;
+            *reinterpret_cast<float4*>(m + at) = mv;
+            *reinterpret_cast<float4*>(v + at) = vv;
+        } else {
+            for (unsigned k = 0; k < left; ++k) {
+                const float gk = g[at + k];
+                const float mk = fmaf(G.b1, m[at + k], G.omb1 * gk);
+                const float vk = fmaf(G.b2, v[at + k], G.omb2 * gk * gk);
+                m[at + k] = mk;
+                v[at + k] = vk;
+                p[at + k] -= lr[k] * c1 * mk / (sqrtf(vk) * c2 + G.eps);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_loss_3dgs(const float* rgb, const float* target, const LossViews& L, float* loss, float* grad,
+                             cudaStream_t s) {
+    const size_t smem = (size_t)kLossSmemFloats * sizeof(float);
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_set[dev]) {
+        e = cudaFuncSetAttribute(k_loss_3dgs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
+    e = cudaMemsetAsync(loss, 0, 3 * sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    const int tiles = L.tile_off[L.n];
+    if (tiles == 0) return cudaSuccess;
+    k_loss_3dgs<<<tiles, kLossThreads, smem, s>>>(rgb, target, L, loss, grad);
+    return cudaGetLastError();
+}
+
+int loss_tile_side() { return kLT; }
+
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, const AdamGroups& G, double beta1,
+                        double beta2, AdamState* st, const WsHeader* guard, cudaStream_t s) {
+    k_adam_tick<<<1, 1, 0, s>>>(st, guard, beta1, beta2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long units = G.ubase[G.n];
+    if (units == 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const long long want = (units + 255) / 256;
+    const long long cap = (long long)sms * 8;
+    k_adam<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(p, g, m, v, G, st, guard);
+    return cudaGetLastError();
+}
+
+}  // namespace wsr

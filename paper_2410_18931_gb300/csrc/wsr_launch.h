@@ -64,4 +64,47 @@ cudaError_t launch_count_pairs(const float* records, const unsigned* tile_offset
 cudaError_t launch_loss_l1(const float* rgb, const float* target, long long count,
                            float* loss, float* grad, cudaStream_t s);
 
+// Views of the 3DGS loss: tiles of loss_tile_side() square per view, in view
+// order; the Gaussian window taps g[] are normalised to sum 1.
+struct LossViews {
+    int n;
+    int tile_off[WSR_MAX_VIEWS + 1];
+    int tiles_x[WSR_MAX_VIEWS];
+    int w[WSR_MAX_VIEWS];
+    int h[WSR_MAX_VIEWS];
+    long long pix_off[WSR_MAX_VIEWS];
+    float g[11];
+    float lam, inv_count, c1, c2;
+};
+
+int loss_tile_side();
+cudaError_t launch_loss_3dgs(const float* rgb, const float* target, const LossViews& L, float* loss,
+                             float* grad, cudaStream_t s);
+
+// Adam groups in float4 units: group k covers units [ubase[k], ubase[k+1])
+// and elements [off[k], off[k] + cnt[k]) of the flat buffers.
+struct AdamGroups {
+    int n;
+    long long ubase[WSR_ADAM_MAX_GROUPS + 1];
+    long long off[WSR_ADAM_MAX_GROUPS];
+    unsigned cnt[WSR_ADAM_MAX_GROUPS];
+    float lr[WSR_ADAM_MAX_GROUPS];
+    float lr_tail[WSR_ADAM_MAX_GROUPS];
+    int period[WSR_ADAM_MAX_GROUPS];
+    int head[WSR_ADAM_MAX_GROUPS];
+    float b1, omb1, b2, omb2, eps;
+};
+
+// Device-resident Adam state (the wsr_adam_state of the C ABI).
+struct AdamState {
+    int step;
+    float c1;      // 1 / (1 - beta1^step)
+    float c2;      // 1 / sqrt(1 - beta2^step)
+    int skipped;
+};
+static_assert(sizeof(AdamState) == sizeof(wsr_adam_state), "Adam state layout");
+
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, const AdamGroups& G, double beta1,
+                        double beta2, AdamState* st, const WsHeader* guard, cudaStream_t s);
+
 }  // namespace wsr

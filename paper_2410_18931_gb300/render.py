@@ -218,6 +218,11 @@ class Renderer:
         A.check("wsr_loss_l1", self.lib.wsr_loss_l1(_ptr(rgb), _ptr(target), rgb.numel(), _ptr(loss), _ptr(grad),
                                                     _stream(stream)))
 
+    def wsr_loss_3dgs(self, rgb, target, lam, loss, grad, stream=None):
+        """L1 + lam * D-SSIM over this renderer's views; loss [3] = {L, L1, SSIM}."""
+        A.check("wsr_loss_3dgs", self.lib.wsr_loss_3dgs(_ptr(rgb), _ptr(target), self.cams_c, self.n_cams,
+                                                        float(lam), _ptr(loss), _ptr(grad), _stream(stream)))
+
 
 class WSRRender(torch.autograd.Function):
     """Differentiable WSR image (Eq. 7) of ``renderer``'s views.

@@ -111,3 +111,49 @@ def test_argument_errors_are_returned(lib):
     # negative counts
     assert lib.wsr_loss_l1(fake, fake, -1, fake, fake, None) == A.WSR_ERR_INVALID_ARG
     assert lib.wsr_check(None, 0, None) == A.WSR_ERR_INVALID_ARG
+
+
+def test_training_entry_points_reject_bad_arguments(lib):
+    from paper_2410_18931_gb300 import _abi as A
+    cams, n = _cam(64, 48)
+    fake = 1 << 20   # never dereferenced: validation fails first
+    # 3DGS loss: lambda outside [0, 1], null outputs, zero-size view
+    for lam in (-0.5, 1.01, float("nan")):
+        assert lib.wsr_loss_3dgs(fake, fake, cams, n, lam, fake, fake, None) == A.WSR_ERR_INVALID_ARG
+    assert lib.wsr_loss_3dgs(fake, fake, cams, n, 0.2, None, fake, None) == A.WSR_ERR_INVALID_ARG
+    assert lib.wsr_loss_3dgs(fake, fake, cams, 0, 0.2, fake, fake, None) == A.WSR_ERR_INVALID_ARG
+    zc = (A.wsr_camera * 1)(cams[0])
+    zc[0].height = 0
+    assert lib.wsr_loss_3dgs(fake, fake, zc, 1, 0.2, fake, fake, None) == A.WSR_ERR_INVALID_ARG
+    hp = A.wsr_adam_hparams(0.9, 0.999, 1e-15)
+
+    def adam(groups, hp=hp, p=fake, state=fake, guard=None, guard_bytes=0):
+        arr = (A.wsr_adam_group * max(1, len(groups)))(*groups)
+        return lib.wsr_adam_step(p, fake, fake, fake, arr, len(groups), ctypes.byref(hp), state, guard,
+                                 guard_bytes, None)
+
+    ok = A.wsr_adam_group(0, 100, 1e-3, 1e-3, 0, 0)
+    assert adam([ok], p=fake + 4) == A.WSR_ERR_INVALID_ARG                       # misaligned buffer
+    assert adam([ok], state=fake + 2) == A.WSR_ERR_INVALID_ARG                   # misaligned state
+    assert adam([A.wsr_adam_group(2, 100, 1e-3, 1e-3, 0, 0)]) == A.WSR_ERR_INVALID_ARG      # offset % 4
+    assert adam([A.wsr_adam_group(0, 1 << 32, 1e-3, 1e-3, 0, 0)]) == A.WSR_ERR_INVALID_ARG  # count
+    assert adam([A.wsr_adam_group(0, 100, 1e-3, 1e-3, 8, 9)]) == A.WSR_ERR_INVALID_ARG     # head > period
+    assert adam([ok, A.wsr_adam_group(96, 10, 1e-3, 1e-3, 0, 0)]) == A.WSR_ERR_INVALID_ARG  # overlap
+    assert adam([ok] * (A.WSR_ADAM_MAX_GROUPS + 1)) == A.WSR_ERR_INVALID_ARG
+    assert adam([A.wsr_adam_group(0, 100, float("inf"), 1e-3, 0, 0)]) == A.WSR_ERR_INVALID_ARG
+    assert adam([ok], hp=A.wsr_adam_hparams(1.0, 0.999, 1e-8)) == A.WSR_ERR_INVALID_ARG
+    assert adam([ok], hp=A.wsr_adam_hparams(0.9, 0.999, -1.0)) == A.WSR_ERR_INVALID_ARG
+    assert adam([ok], guard=fake, guard_bytes=16) == A.WSR_ERR_INVALID_ARG        # guard smaller than a header
+    assert lib.wsr_adam_step(fake, fake, fake, fake, None, 0, ctypes.byref(hp), None, None, 0,
+                             None) == A.WSR_ERR_INVALID_ARG                       # no state
+
+
+def test_weight_params_rounded_are_float32_exact():
+    import numpy as np
+    import wsr_scenes as ws
+    w = ws.default_weight(ws.EXP, c_bg=(0.1, 0.2, 0.3))
+    r = w.rounded()
+    assert r.kind == w.kind
+    vals = [r.sigma, r.beta, r.w_bg, *r.c_bg]
+    assert all(float(np.float32(v)) == v for v in vals)
+    assert np.array_equal(r.as_array(), w.as_array())

@@ -86,6 +86,14 @@ class WeightParams:
         return np.array([self.sigma, self.beta, self.w_bg, *self.c_bg],
                         dtype=np.float32)
 
+    def rounded(self) -> "WeightParams":
+        """The same parameters rounded to float32, the values the GPU reads
+        from ``as_array()``; the oracle then sees exactly those numbers (which
+        matters where a result depends on an exact tie, e.g. the L1 gradient
+        of a background pixel equal to its target)."""
+        a = [float(x) for x in self.as_array()]
+        return WeightParams(self.kind, a[0], a[1], a[2], tuple(a[3:6]))
+
 
 @dataclass
 class Scene:
