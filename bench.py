@@ -411,6 +411,8 @@ def run_ours(args):
         line["batched"] = run_batched()
     if world == 1 and not args.no_reduced:
         line["reduced"] = run_reduced()
+    if world == 1 and not args.no_training:
+        line["training"] = run_training()
     if rank == 0 and not args.no_cpu_baseline:
         gpu_rgb = S.st.rgb.reshape(cam.height, cam.width, 3).cpu().numpy()
         base, maxerr = cpu_oracle_leg(scene, cam, weight, target, gpu_rgb, args.cpu_budget)
@@ -522,6 +524,87 @@ def run_batched(reps: int = 5) -> dict:
                             round(t["ms"], 3) for t in tune["table"]}}
 
 
+def run_training(steps: int = 10, warmup: int = 3) -> dict:
+    """1M Gaussians, 1920x1080 (the headline workload), one optimisation step
+    per replay: project, bin, render, 3DGS loss (L1 + 0.2 D-SSIM), render
+    backward, projection backward and Adam, captured as one CUDA graph over a
+    flat parameter buffer.  Each replay is timed with its own events, the L2
+    flushed in between; the loss and Adam kernels are also timed alone and
+    reported against HBM."""
+    import numpy as np
+    import torch
+
+    import wsr_scenes as ws
+    from paper_2410_18931_gb300 import FlatParams, TrainStep
+    scene, cams, weight, extra = ws.workload(3)
+    cam = cams[0].rounded()
+    tgt = torch.from_numpy(ws.target_image(extra["target_seed"], cam.height, cam.width).reshape(-1, 3)).cuda()
+    flat = FlatParams.from_scene(scene, weight.as_array())
+    del scene
+    step = TrainStep(flat, 3, True, [cam], weight.kind, tgt, tile=(16, 16), persistent=False, capture=True)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        step.replay()
+    torch.cuda.synchronize()
+    losses, times = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step.replay()
+        e1.record()
+        losses.append(step.loss.clone())
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in times]))
+    st = step.opt.read_state()
+    assert st["skipped"] == 0, "tile list overflowed during the timed steps"
+    L = torch.stack(losses).cpu().numpy()
+    npix = cam.width * cam.height
+
+    def timed(fn, reps=5):
+        for _ in range(2):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.mean(ts))
+
+    r = step.r
+    loss_ms = timed(lambda: r.wsr_loss_3dgs(step.st.rgb, step.target, step.lam, step.loss, step.grad_rgb))
+    snap = step.opt.snapshot()
+    adam_ms = timed(lambda: step.opt.wsr_adam_step(guard=r.workspace))
+    step.opt.restore(snap)
+    hbm = _hbm_peak()
+    loss_bytes = npix * 3 * 4 * 3                  # rgb and target read, gradient written
+    n_upd = sum(g.count for g in step.opt.groups[:step.opt.n_groups])
+    adam_bytes = n_upd * 4 * 7                     # p, g, m, v read; p, m, v written
+    return {"workload": extra["name"], "gaussians": flat.count("means") // 3, "width": cam.width,
+            "height": cam.height, "graph": True, "kernels_per_step": step.kernels_per_step,
+            "ms_per_step": round(ms, 3), "train_mpix_s": round(npix / (ms * 1e-3) / 1e6, 2),
+            "steps_per_s": round(1e3 / ms, 2), "adam_steps_made": st["step"],
+            "loss_first_last": [round(float(L[0, 0]), 6), round(float(L[-1, 0]), 6)],
+            "ssim_first_last": [round(float(L[0, 2]), 6), round(float(L[-1, 2]), 6)],
+            "loss_3dgs_ms": round(loss_ms, 4),
+            "loss_3dgs_hbm_frac": round(loss_bytes / (loss_ms * 1e-3) / 1e9 / hbm, 4),
+            "adam_ms": round(adam_ms, 4), "adam_params": int(n_upd),
+            "adam_hbm_frac": round(adam_bytes / (adam_ms * 1e-3) / 1e9 / hbm, 4),
+            "l2": "flushed between steps (512 MB write outside the step events)"}
+
+
+def _hbm_peak() -> float:
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6780.0))
+    except Exception:
+        return 6780.0
+
+
 def run_reduced(reps: int = 3) -> dict:
     """6M Gaussians, 8 views of 3840x2160: forward with reduced storage (bf16
     scales/quats, f16 SH/opacity, FP32 accumulation) for all views in one set
@@ -591,6 +674,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
     ap.add_argument("--no-batched", action="store_true", help="skip the 3M x 16-view batched measurement")
     ap.add_argument("--no-reduced", action="store_true", help="skip the 6M x 8 x 4K reduced-precision measurement")
+    ap.add_argument("--no-training", action="store_true", help="skip the training-step (loss + Adam) measurement")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
