@@ -31,6 +31,12 @@ constexpr int kSt = kLT + 2 * kR;           // statistics side (42)
 constexpr int kLossThreads = 256;
 constexpr int kLossSmemFloats = 2 * kIn * kIn + 5 * kIn * kSt + 3 * kSt * kSt;
 static_assert(3 * kSt * kLT <= 5 * kIn * kSt, "filtered partials reuse the statistics buffer");
+// register blocking of the four filter passes (outputs per item along the filtered axis)
+constexpr int kH1 = kSt / 3;                // horizontal statistics: 3 columns
+constexpr int kV2 = 7, kS2 = kSt / kV2;     // vertical statistics: 7 rows
+constexpr int kH3 = 4, kB3 = kLT / kH3;     // horizontal partials: 4 columns
+constexpr int kV4 = 4, kS4 = kLT / kV4;     // vertical partials: 4 rows
+static_assert(kH1 * 3 == kSt && kS2 * kV2 == kSt && kB3 * kH3 == kLT && kS4 * kV4 == kLT, "exact blocking");
 
 __device__ __forceinline__ float block_sum_to(float x, float* red) {
 #pragma unroll
@@ -80,89 +86,130 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_3dgs(const float* __restr
             sy[i] = b;
         }
         __syncthreads();
-        for (int i = tid; i < kIn * kSt; i += kLossThreads) {
-            const int iy = i / kSt, jx = i - iy * kSt;
-            const float* rx = sx + iy * kIn + jx;
-            const float* ry = sy + iy * kIn + jx;
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+        // horizontal statistics: three neighbouring columns per item from one window of 13
+        for (int it = tid; it < kIn * kH1; it += kLossThreads) {
+            const int iy = it / kH1, jx0 = (it - iy * kH1) * 3;
+            const float* rx = sx + iy * kIn + jx0;
+            const float* ry = sy + iy * kIn + jx0;
+            float a[2 * kR + 3], b[2 * kR + 3];
 #pragma unroll
-            for (int k = 0; k < 2 * kR + 1; ++k) {
-                const float a = rx[k], b = ry[k], w = L.g[k];
-                const float wa = w * a, wb = w * b;
-                s0 += wa;
-                s1 += wb;
-                s2 = fmaf(wa, a, s2);
-                s3 = fmaf(wb, b, s3);
-                s4 = fmaf(wa, b, s4);
+            for (int k = 0; k < 2 * kR + 3; ++k) {
+                a[k] = rx[k];
+                b[k] = ry[k];
             }
-            hs[i] = s0;
-            hs[kIn * kSt + i] = s1;
-            hs[2 * kIn * kSt + i] = s2;
-            hs[3 * kIn * kSt + i] = s3;
-            hs[4 * kIn * kSt + i] = s4;
+#pragma unroll
+            for (int o = 0; o < 3; ++o) {
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+#pragma unroll
+                for (int k = 0; k < 2 * kR + 1; ++k) {
+                    const float w = L.g[k], wa = w * a[o + k], wb = w * b[o + k];
+                    s0 += wa;
+                    s1 += wb;
+                    s2 = fmaf(wa, a[o + k], s2);
+                    s3 = fmaf(wb, b[o + k], s3);
+                    s4 = fmaf(wa, b[o + k], s4);
+                }
+                const int i = iy * kSt + jx0 + o;
+                hs[i] = s0;
+                hs[kIn * kSt + i] = s1;
+                hs[2 * kIn * kSt + i] = s2;
+                hs[3 * kIn * kSt + i] = s3;
+                hs[4 * kIn * kSt + i] = s4;
+            }
         }
         __syncthreads();
-        for (int i = tid; i < kSt * kSt; i += kLossThreads) {
-            const int jy = i / kSt, jx = i - jy * kSt;
-            const int gx = x0 - kR + jx, gy = y0 - kR + jy;
-            float m0 = 0.f, m1 = 0.f, m2 = 0.f;
-            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-                float st[5];
+        // vertical statistics, SSIM map and the loss partials: seven rows per item
+        for (int it = tid; it < kSt * kS2; it += kLossThreads) {
+            const int strip = it / kSt, jx = it - strip * kSt, jy0 = strip * kV2;
+            float st[5][kV2];
 #pragma unroll
-                for (int q = 0; q < 5; ++q) {
-                    const float* col = hs + q * kIn * kSt + jy * kSt + jx;
+            for (int q = 0; q < 5; ++q) {
+                float h[kV2 + 2 * kR];
+#pragma unroll
+                for (int r = 0; r < kV2 + 2 * kR; ++r) h[r] = hs[q * kIn * kSt + (jy0 + r) * kSt + jx];
+#pragma unroll
+                for (int o = 0; o < kV2; ++o) {
                     float acc = 0.f;
 #pragma unroll
-                    for (int k = 0; k < 2 * kR + 1; ++k) acc = fmaf(L.g[k], col[k * kSt], acc);
-                    st[q] = acc;
+                    for (int k = 0; k < 2 * kR + 1; ++k) acc = fmaf(L.g[k], h[o + k], acc);
+                    st[q][o] = acc;
                 }
-                const float mx = st[0], my = st[1];
-                const float sxx = st[2] - mx * mx, syy = st[3] - my * my, sxy = st[4] - mx * my;
-                const float a1 = 2.f * mx * my + L.c1, a2 = 2.f * sxy + L.c2;
-                const float b1 = mx * mx + my * my + L.c1, b2 = sxx + syy + L.c2;
-                const float ib1 = 1.0f / b1, ib2 = 1.0f / b2;
-                const float s = a1 * a2 * ib1 * ib2;
-                m0 = gs * (2.f * my * (a2 - a1) * ib1 * ib2 + 2.f * mx * s * (ib2 - ib1));
-                m1 = gs * (-s * ib2);
-                m2 = gs * (2.f * a1 * ib1 * ib2);
-                if (jx >= kR && jx < kR + kLT && jy >= kR && jy < kR + kLT) ss += s;
             }
-            mm[i] = m0;
-            mm[kSt * kSt + i] = m1;
-            mm[2 * kSt * kSt + i] = m2;
+            const int gx = x0 - kR + jx;
+            const bool col_in = gx >= 0 && gx < W;
+            const bool col_own = jx >= kR && jx < kR + kLT;
+#pragma unroll
+            for (int o = 0; o < kV2; ++o) {
+                const int jy = jy0 + o, gy = y0 - kR + jy;
+                float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+                if (col_in && gy >= 0 && gy < H) {
+                    const float mx = st[0][o], my = st[1][o];
+                    const float sxx = st[2][o] - mx * mx, syy = st[3][o] - my * my, sxy = st[4][o] - mx * my;
+                    const float a1 = 2.f * mx * my + L.c1, a2 = 2.f * sxy + L.c2;
+                    const float b1 = mx * mx + my * my + L.c1, b2 = sxx + syy + L.c2;
+                    const float ib1 = 1.0f / b1, ib2 = 1.0f / b2;
+                    const float sv = a1 * a2 * ib1 * ib2;
+                    m0 = gs * (2.f * my * (a2 - a1) * ib1 * ib2 + 2.f * mx * sv * (ib2 - ib1));
+                    m1 = gs * (-sv * ib2);
+                    m2 = gs * (2.f * a1 * ib1 * ib2);
+                    if (col_own && jy >= kR && jy < kR + kLT) ss += sv;
+                }
+                const int i = jy * kSt + jx;
+                mm[i] = m0;
+                mm[kSt * kSt + i] = m1;
+                mm[2 * kSt * kSt + i] = m2;
+            }
         }
         __syncthreads();
-        for (int i = tid; i < kSt * kLT; i += kLossThreads) {
-            const int jy = i / kLT, ox = i - jy * kLT;
+        // horizontal pass of the partials: four columns per item
+        for (int it = tid; it < kSt * kB3; it += kLossThreads) {
+            const int jy = it / kB3, ox0 = (it - jy * kB3) * kH3;
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                const float* row = mm + q * kSt * kSt + jy * kSt + ox;
-                float acc = 0.f;
+                const float* row = mm + q * kSt * kSt + jy * kSt + ox0;
+                float r[kH3 + 2 * kR];
 #pragma unroll
-                for (int k = 0; k < 2 * kR + 1; ++k) acc = fmaf(L.g[k], row[k], acc);
-                hm[q * kSt * kLT + i] = acc;
+                for (int k = 0; k < kH3 + 2 * kR; ++k) r[k] = row[k];
+#pragma unroll
+                for (int o = 0; o < kH3; ++o) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int k = 0; k < 2 * kR + 1; ++k) acc = fmaf(L.g[k], r[o + k], acc);
+                    hm[q * kSt * kLT + jy * kLT + ox0 + o] = acc;
+                }
             }
         }
         __syncthreads();
-        for (int i = tid; i < kLT * kLT; i += kLossThreads) {
-            const int oy = i / kLT, ox = i - oy * kLT;
-            const int gx = x0 + ox, gy = y0 + oy;
-            if (gx >= W || gy >= H) continue;
-            float f[3];
+        // vertical pass of the partials and the gradient: four rows per item
+        for (int it = tid; it < kLT * kS4; it += kLossThreads) {
+            const int strip = it / kLT, ox = it - strip * kLT, oy0 = strip * kV4;
+            const int gx = x0 + ox;
+            float f[3][kV4];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                const float* col = hm + q * kSt * kLT + oy * kLT + ox;
-                float acc = 0.f;
+                float c[kV4 + 2 * kR];
 #pragma unroll
-                for (int k = 0; k < 2 * kR + 1; ++k) acc = fmaf(L.g[k], col[k * kLT], acc);
-                f[q] = acc;
+                for (int r = 0; r < kV4 + 2 * kR; ++r) c[r] = hm[q * kSt * kLT + (oy0 + r) * kLT + ox];
+#pragma unroll
+                for (int o = 0; o < kV4; ++o) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int k = 0; k < 2 * kR + 1; ++k) acc = fmaf(L.g[k], c[o + k], acc);
+                    f[q][o] = acc;
+                }
             }
-            const float a = sx[(oy + 2 * kR) * kIn + ox + 2 * kR];
-            const float b = sy[(oy + 2 * kR) * kIn + ox + 2 * kR];
-            const float d = a - b;
-            l1 += fabsf(d);
-            const float gd = d > 0.f ? gl1 : (d < 0.f ? -gl1 : 0.f);
-            grad[(base + (long long)gy * W + gx) * 3 + c] = f[0] + 2.f * a * f[1] + b * f[2] + gd;
+            if (gx >= W) continue;
+#pragma unroll
+            for (int o = 0; o < kV4; ++o) {
+                const int oy = oy0 + o, gy = y0 + oy;
+                if (gy >= H) break;
+                const float a = sx[(oy + 2 * kR) * kIn + ox + 2 * kR];
+                const float b = sy[(oy + 2 * kR) * kIn + ox + 2 * kR];
+                const float d = a - b;
+                l1 += fabsf(d);
+                const float gd = d > 0.f ? gl1 : (d < 0.f ? -gl1 : 0.f);
+                grad[(base + (long long)gy * W + gx) * 3 + c] = f[0][o] + 2.f * a * f[1][o] + b * f[2][o] + gd;
+            }
         }
         __syncthreads();
     }
