@@ -676,8 +676,15 @@ def main():
     ap.add_argument("--no-reduced", action="store_true", help="skip the 6M x 8 x 4K reduced-precision measurement")
     ap.add_argument("--no-training", action="store_true", help="skip the training-step (loss + Adam) measurement")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--training-only", action="store_true",
+                    help="only the training-step measurement (one JSON object), e.g. for profiling its kernels")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.training_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(run_training(steps=args.steps, warmup=args.warmup)), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
