@@ -187,22 +187,30 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
 // Backward, one block per tile, balanced over (pixel, Gaussian) pairs.
 //
 // For each chunk of up to kBwdChunk Gaussians of the tile:
-//   A. thread j computes, for every row of the tile, the span of pixels whose
-//      centre can lie inside Gaussian j's footprint (the roots of the
-//      quadratic q(dx) = 9 on that row, widened slightly); the rows with a
-//      span are contiguous because the footprint is convex;
-//   B. a block scan lays the row spans of all Gaussians end to end as a list
-//      of row segments (one 32-bit descriptor each) in pair order;
-//   C. every thread takes an equal slice of the pair list, finds its first
-//      segment by binary search and walks pixel indices two at a time,
-//      accumulating the nine partial derivatives of the current Gaussian in
-//      registers; at the end of its slice, or when the Gaussian changes, it
-//      stores them in a (thread, Gaussian) slot;
+//   A. two threads per Gaussian compute, for their half of the tile's rows,
+//      the span of pixels whose centre can lie inside the footprint (the
+//      roots of the quadratic q(dx) = 9 on that row, widened slightly);
+//   B. every span is padded to an even length and cut into units of two
+//      horizontally adjacent pixels; a block scan lays the units of all
+//      Gaussians end to end (Gaussian-major) and each thread writes one byte
+//      per unit (row and column of its first pixel).  A padding pixel lies
+//      outside the footprint or in a zero column of the pixel table, so it
+//      adds nothing;
+//   C. every thread takes an equal slice of the units and walks it one unit
+//      (two pixels, one paired FP32 op each) per step, accumulating the nine
+//      partial derivatives of the current Gaussian in registers; when the
+//      Gaussian changes, or at the end of its slice, it stores them in a
+//      (thread, Gaussian) slot.  The only branch in the walk is that change;
 //   D. thread j sums Gaussian j's slots and adds them to its global record.
 // Every pair is still tested with the forward's exact arithmetic (q <= 9), so
 // forward and backward agree on which pairs exist.
 constexpr int kBwdThreads = 256;
-constexpr int kBwdChunk = 256;
+constexpr int kBwdChunk = 128;
+
+template <int TW> struct UnitCode;                    // bits of the column in a unit byte
+template <> struct UnitCode<8> { static constexpr int XB = 3; };
+template <> struct UnitCode<16> { static constexpr int XB = 4; };
+template <> struct UnitCode<32> { static constexpr int XB = 5; };
 
 template <int TW, int TH>
 __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restrict__ rec,
@@ -214,22 +222,24 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
     constexpr int NT = kBwdThreads;
     constexpr int CH = kBwdChunk;
     constexpr int NW = NT / 32;
-    constexpr int NPIX = TW * TH;
-    constexpr int MAXSEG = CH * TH;
-    static_assert(TW <= 32 && TH <= 32 && CH <= 256, "descriptor encoding");
-    __shared__ float4 spix[NPIX + 1];           // per pixel: G/D (3), -(G.C)/D; one pad entry
+    constexpr int PW = TW + 1;                          // pixel-table row pitch: one zero column
+    constexpr int XB = UnitCode<TW>::XB;
+    constexpr int HR = TH / 2;                          // rows per thread in step A
+    constexpr int MAXU = CH * TH * (TW / 2);            // units when every span covers its whole row
+    constexpr int NSLOT = NT + CH;                      // slices touch at most NT + CH (thread, Gaussian) pairs
+    static_assert(NT == 2 * CH && TH % 2 == 0 && ((TH - 1) << XB) < 256 && CH <= 256, "unit encoding");
+    __shared__ float4 spix[PW * TH + 1];        // per pixel: G/D (3), -(G.C)/D; zero column and pad entry
     __shared__ float4 s0[CH];                   // mu_x, mu_y, A', 2B'
     __shared__ float4 s1[CH];                   // C', u w, c_r u w, c_g u w
     __shared__ float2 s2[CH];                   // c_b u w, u w
     __shared__ unsigned sidx[CH];
-    __shared__ unsigned soff[CH + 1];           // first pair of each Gaussian
-    __shared__ unsigned short sgoff[CH + 1];    // first row segment of each Gaussian
-    __shared__ unsigned segd[MAXSEG];           // row segment: j << 16 | ly << 11 | xs << 6 | len
-    __shared__ float sslot[2 * NT][9];          // partial sums per (thread, Gaussian)
-    __shared__ unsigned char sslotj[2 * NT];    // the Gaussian of each slot (slots are sorted by it)
+    __shared__ unsigned soff[CH + 1];           // first unit of each Gaussian
+    __shared__ unsigned char sunit[MAXU];       // unit: row << XB | column of its first pixel
+    __shared__ float2 sslot[NSLOT][5];          // partial sums per (thread, Gaussian), paired as accumulated
+    __shared__ unsigned char sslotj[NSLOT];     // the Gaussian of each slot (slots are sorted by it)
     __shared__ unsigned short ssbase[NT];
     __shared__ unsigned swarp[NW];
-    __shared__ unsigned stot[3];                // pairs, row segments and slots of the chunk
+    __shared__ unsigned stot[2];                // units and slots of the chunk
     __shared__ float sbg[4][NW];
 
     const TileCoord tc = tile_coord(vs, tile);
@@ -242,8 +252,8 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
     const float cB0 = __ldg(wparams + 3), cB1 = __ldg(wparams + 4), cB2 = __ldg(wparams + 5);
 
     float bg[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int p = tid; p < NPIX; p += NT) {
-        const int lx = p % TW, ly = p / TW;
+    for (int p = tid; p < PW * TH + 1; p += NT) {
+        const int ly = p / PW, lx = p - ly * PW;
         float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
         if (lx < x_lim && ly < y_lim) {
             const long long pix = V.pix_base + (long long)(y_org + ly) * V.W + x_org + lx;
@@ -259,7 +269,6 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
         }
         spix[p] = f;
     }
-    if (tid == 0) spix[NPIX] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         const float t = warp_sum(bg[c]);
@@ -271,19 +280,22 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
     for (unsigned base = start; base < end; base += CH) {
         const int cnt = (int)min((unsigned)CH, end - base);
         __syncthreads();
-        // ---- A: record and per-row spans of Gaussian tid ----
-        unsigned short span[TH];
-        unsigned nseg = 0, npairs = 0;
-        if (tid < cnt) {
-            const unsigned r = list[base + tid];
+        // ---- A: record and the spans of half the rows of Gaussian tid / 2 ----
+        const int gj = tid >> 1, half = tid & 1;
+        unsigned short span[HR];
+        unsigned nunits = 0;
+        if (gj < cnt) {
+            const unsigned r = list[base + gj];
             const float4* pr = rec + 3ull * r;
             const float4 a = __ldg(pr);
             const float4 b = __ldg(pr + 1);
-            const float cb = __ldg(reinterpret_cast<const float*>(pr + 2));
-            s0[tid] = a;
-            s1[tid] = b;
-            s2[tid] = f2(cb, b.y);
-            sidx[tid] = r;
+            if (half == 0) {
+                const float cb = __ldg(reinterpret_cast<const float*>(pr + 2));
+                s0[gj] = a;
+                s1[gj] = b;
+                s2[gj] = f2(cb, b.y);
+                sidx[gj] = r;
+            }
             // row y: the footprint is mu_x + c(dy) +- h(dy) with
             // c = -(B''/2) dy / A', h = sqrt(A' QM - det' dy^2) / A',
             // det' = A' C' - (B''/2)^2 (both terms of the root are positive)
@@ -292,10 +304,11 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
             const float ia = 1.0f / a.z;
             // rows the footprint can reach: |dy| <= sqrt(A' QM / det'), with a pixel of slack
             const float ext = fminf(sqrtf(fmaxf(a.z * QM / det, 0.0f)), 1e6f) + 1.0f;
-            const int ly_lo = max(0, (int)floorf(a.y - ext - 0.5f) - y_org);
-            const int ly_hi = min(y_lim - 1, (int)ceilf(a.y + ext - 0.5f) - y_org);
+            const int ly_lo = max(half * HR, (int)floorf(a.y - ext - 0.5f) - y_org);
+            const int ly_hi = min(min(y_lim, half * HR + HR) - 1, (int)ceilf(a.y + ext - 0.5f) - y_org);
 #pragma unroll
-            for (int ly = 0; ly < TH; ++ly) {
+            for (int k = 0; k < HR; ++k) {
+                const int ly = half * HR + k;
                 unsigned short sp = 0;
                 if (ly >= ly_lo && ly <= ly_hi) {
                     const float dy = (float)(y_org + ly) + 0.5f - a.y;
@@ -307,19 +320,16 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                         const float fx1 = fminf(floorf(cx + h - 0.48f), (float)(x_org + x_lim - 1));
                         if (fx0 <= fx1) {
                             const int xs = (int)fx0 - x_org, len = (int)fx1 - (int)fx0 + 1;
-                            sp = (unsigned short)(xs | (len << 8));
-                            npairs += (unsigned)len;
-                            ++nseg;
+                            sp = (unsigned short)(xs | (((len + 1) >> 1) << 8));   // start, units
+                            nunits += (unsigned)((len + 1) >> 1);
                         }
                     }
                 }
-                span[ly] = sp;
+                span[k] = sp;
             }
         }
-        // ---- B: block scan of (pairs, segments); write the segment list ----
-        const unsigned packed = (npairs << 13) | nseg;   // pairs <= 2^17, segments <= 2^13 per chunk
-        static_assert(CH * TW * TH < (1 << 19) && MAXSEG < (1 << 13), "packed scan fields");
-        unsigned inc = packed;
+        // ---- B: block scan of the units (thread order = Gaussian, then half); unit bytes ----
+        unsigned inc = nunits;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const unsigned y = __shfl_up_sync(0xffffffffu, inc, off);
@@ -330,51 +340,40 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
         unsigned wbase = 0;
 #pragma unroll
         for (int w = 0; w < NW; ++w) wbase += (w < warp) ? swarp[w] : 0u;
-        const unsigned ex = wbase + inc - packed;
-        if (tid < cnt) {
-            unsigned k = ex & 0x1fffu;
-            soff[tid] = ex >> 13;
-            sgoff[tid] = (unsigned short)k;
+        const unsigned ex = wbase + inc - nunits;
+        if (gj < cnt) {
+            if (half == 0) soff[gj] = ex;
+            unsigned k = ex;
 #pragma unroll
-            for (int ly = 0; ly < TH; ++ly) {
-                const unsigned sp = span[ly];
-                if (sp >> 8) {
-                    segd[k] = ((unsigned)tid << 16) | ((unsigned)ly << 11) | ((sp & 0xffu) << 6) | (sp >> 8);
-                    ++k;
-                }
+            for (int r = 0; r < HR; ++r) {
+                const unsigned sp = span[r];
+                const unsigned code = ((unsigned)(half * HR + r) << XB) | (sp & 0xffu);
+                for (unsigned u = 0; u < (sp >> 8); ++u) sunit[k++] = (unsigned char)(code + 2u * u);
             }
         }
         if (tid == NT - 1) {
-            const unsigned tot = wbase + inc;
-            soff[cnt] = tot >> 13;
-            sgoff[cnt] = (unsigned short)(tot & 0x1fffu);
-            stot[0] = tot >> 13;
-            stot[1] = tot & 0x1fffu;
+            soff[cnt] = wbase + inc;
+            stot[0] = wbase + inc;
         }
         __syncthreads();
-        // ---- C: an equal slice of the pairs per thread ----
+        // ---- C: an equal slice of the units per thread ----
         const unsigned total = stot[0];
-        const unsigned p0 = (unsigned)(((unsigned long long)tid * total) / NT);
-        const unsigned p1 = (unsigned)(((unsigned long long)(tid + 1) * total) / NT);
-        // owner(p): the last Gaussian whose first pair is <= p
-        auto owner = [&](unsigned p) {
+        const unsigned u0 = (unsigned)(((unsigned long long)tid * total) / NT);
+        const unsigned u1 = (unsigned)(((unsigned long long)(tid + 1) * total) / NT);
+        // owner(u): the last Gaussian whose first unit is <= u
+        auto owner = [&](unsigned u) {
             int lo = 0, hi = cnt - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (soff[mid] <= p) lo = mid;
+                if (soff[mid] <= u) lo = mid;
                 else hi = mid - 1;
             }
             return lo;
         };
-        int sg = 0, j = 0, jlast = -1;
-        unsigned k0 = 0;
-        if (p0 < p1) {
-            j = owner(p0);
-            jlast = owner(p1 - 1);
-            // the row segment of Gaussian j holding pair p0
-            sg = sgoff[j];
-            k0 = p0 - soff[j];
-            while (k0 >= (segd[sg] & 63u)) k0 -= segd[sg++] & 63u;
+        int j = 0, jlast = -1;
+        if (u0 < u1) {
+            j = owner(u0);
+            jlast = owner(u1 - 1);
         }
         {
             // slots: a block scan of the number of Gaussians each slice touches
@@ -393,51 +392,52 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
             const unsigned b0 = sb + sinc - nslot;
             ssbase[tid] = (unsigned short)b0;
             for (unsigned k = 0; k < nslot; ++k) sslotj[b0 + k] = (unsigned char)(j + (int)k);
-            if (tid == NT - 1) stot[2] = sb + sinc;
+            if (tid == NT - 1) stot[1] = sb + sinc;
         }
-        if (p0 < p1) {
+        if (u0 < u1) {
             int slot = ssbase[tid];
             // per-Gaussian constants as float2 pairs (refreshed when the Gaussian changes)
             float2 nmx, az2, aw2, cx2, cw0, cw1;
-            float amy;
+            float gy0;
+            unsigned uend = 0;
             auto load_gaussian = [&](int jj) {
                 const float4 a = s0[jj], b = s1[jj];
                 const float2 c2 = s2[jj];
-                nmx = f2(-a.x, -a.x);
-                amy = a.y;
+                const float gx0 = (float)x_org + 0.5f - a.x;            // dx of column 0
+                nmx = f2(gx0, gx0 + 1.0f);
+                gy0 = (float)y_org + 0.5f - a.y;                        // dy of row 0
                 az2 = f2(a.z, a.z);
                 aw2 = f2(a.w, a.w);
                 cx2 = f2(b.x, b.x);
                 cw0 = f2(-kLn2 * b.z, -kLn2 * b.w);    // -ln2 (c u w, u w): dL/dq' = e * (P . cw)
                 cw1 = f2(-kLn2 * c2.x, -kLn2 * c2.y);
+                uend = soff[jj + 1];
             };
             load_gaussian(j);
-            unsigned d = segd[sg];
-            int ly = (int)((d >> 11) & 31u), xs = (int)((d >> 6) & 31u);
-            int pi = ly * TW + xs + (int)k0;                 // pixel index in the tile
-            int pend = ly * TW + xs + (int)(d & 63u);        // end of the row segment
-            float xf = (float)(x_org + xs + (int)k0) + 0.5f;
-            float dy = (float)(y_org + ly) + 0.5f - amy;
-            // accumulators, paired: (cuw_r, cuw_g), (cuw_b, uw), (A', C'), (sum dx, sum dy)
+            // accumulators, paired: (cuw_r, cuw_g), (cuw_b, uw), (A', C'), (sum dx, sum dy), (2B', -)
             float2 g01 = f2(0.f, 0.f), g23 = f2(0.f, 0.f), g46 = f2(0.f, 0.f), g78 = f2(0.f, 0.f);
             float g5 = 0.f;
             auto store_slot = [&](int sl) {
-                float* o = sslot[sl];
-                o[0] = g01.x; o[1] = g01.y; o[2] = g23.x; o[3] = g23.y;
-                o[4] = g46.x; o[5] = g5; o[6] = g46.y; o[7] = g78.x; o[8] = g78.y;
+                sslot[sl][0] = g01;
+                sslot[sl][1] = g23;
+                sslot[sl][2] = g46;
+                sslot[sl][3] = g78;
+                sslot[sl][4] = f2(g5, 0.f);
             };
-            int left = (int)(p1 - p0);
-            while (true) {
-                // two pixels of the current row segment when both are in the slice
-                const bool two = (pi + 1 < pend) && (left > 1);
+            // one or two units per step: two independent chains overlap their latencies; the second
+            // unit is masked out (e = 0) when it lies past the slice or the current Gaussian
+            auto unit_terms = [&](unsigned d, bool valid) {
+                const int x = (int)(d & ((1u << XB) - 1u)), ly = (int)(d >> XB);
+                const int pi = ly * PW + x;
                 const float4 P0 = spix[pi];
-                const float4 P1 = two ? spix[pi + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
-                const float2 dx = __fadd2_rn(f2(xf, xf + 1.0f), nmx);
+                const float4 P1 = spix[pi + 1];
+                const float xf = (float)x, dy = (float)ly + gy0;
+                const float2 dx = __fadd2_rn(f2(xf, xf), nmx);
                 const float2 dy2 = f2(dy, dy);
                 const float2 q = __ffma2_rn(dy2, __ffma2_rn(cx2, dy2, __fmul2_rn(aw2, dx)),
                                             __fmul2_rn(__fmul2_rn(az2, dx), dx));   // the forward's arithmetic
-                const float e0 = (q.x <= kQMax) ? ex2_approx(-q.x) : 0.0f;
-                const float e1 = (two && q.y <= kQMax) ? ex2_approx(-q.y) : 0.0f;
+                const float e0 = ex2_approx((valid && q.x <= kQMax) ? -q.x : -256.0f);  // 2^-256 flushes to 0
+                const float e1 = ex2_approx((valid && q.y <= kQMax) ? -q.y : -256.0f);
                 // d/d(c u w) and d/d(u w) at fixed c u w
                 g01 = __ffma2_rn(f2(P0.x, P0.y), f2(e0, e0), g01);
                 g23 = __ffma2_rn(f2(P0.z, P0.w), f2(e0, e0), g23);
@@ -453,35 +453,28 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 g46 = __ffma2_rn(tu1, f2(dx.y, dy), g46);
                 g5 = fmaf(tu0.x + tu1.x, dy, g5);                             // dL/d(2B')
                 g78 = __fadd2_rn(g78, __fadd2_rn(tu0, tu1));                  // sums of dL/dq' dx, dy
-                const int step = two ? 2 : 1;
-                pi += step;
-                xf += two ? 2.0f : 1.0f;
-                left -= step;
-                if (left <= 0) break;
-                if (pi >= pend) {
-                    // next row segment; when it belongs to another Gaussian, store this one's sums
-                    d = segd[++sg];
-                    const int nj = (int)(d >> 16);
-                    if (nj != j) {
-                        store_slot(slot);
-                        g01 = g23 = g46 = g78 = f2(0.f, 0.f);
-                        g5 = 0.f;
-                        for (int jj = j + 1; jj < nj; ++jj) {      // Gaussians without pairs here
-                            float* zz = sslot[++slot];
+            };
+            for (unsigned u = u0; u < u1;) {
+                if (u == uend) {
+                    // the next Gaussian with units: store this one's sums, zero slots for any between
+                    store_slot(slot++);
+                    g01 = g23 = g46 = g78 = f2(0.f, 0.f);
+                    g5 = 0.f;
+                    ++j;
+                    while (soff[j + 1] <= u) {
 #pragma unroll
-                            for (int c = 0; c < 9; ++c) zz[c] = 0.0f;
-                        }
+                        for (int c = 0; c < 5; ++c) sslot[slot][c] = f2(0.f, 0.f);
                         ++slot;
-                        j = nj;
-                        load_gaussian(j);
+                        ++j;
                     }
-                    ly = (int)((d >> 11) & 31u);
-                    xs = (int)((d >> 6) & 31u);
-                    pi = ly * TW + xs;
-                    pend = pi + (int)(d & 63u);
-                    xf = (float)(x_org + xs) + 0.5f;
-                    dy = (float)(y_org + ly) + 0.5f - amy;
+                    load_gaussian(j);
                 }
+                const bool two = u + 1 < min(u1, uend);
+                const unsigned d0 = sunit[u];
+                const unsigned d1 = sunit[two ? u + 1 : u];
+                unit_terms(d0, true);
+                unit_terms(d1, two);
+                u += two ? 2u : 1u;
             }
             store_slot(slot);
         }
@@ -489,30 +482,32 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
         // ---- D: totals of Gaussian tid to its global record ----
         // the slots are sorted by Gaussian, so Gaussian tid's slots are a run
         if (tid < cnt && soff[tid + 1] > soff[tid]) {
-            const int nslots = (int)stot[2];
+            const int nslots = (int)stot[1];
             int lo = 0, hi = nslots;
             while (lo < hi) {            // first slot of a Gaussian >= tid
                 const int mid = (lo + hi) >> 1;
                 if ((int)sslotj[mid] < tid) lo = mid + 1;
                 else hi = mid;
             }
-            float v[9];
-#pragma unroll
-            for (int c = 0; c < 9; ++c) v[c] = 0.0f;
+            float2 v01 = f2(0.f, 0.f), v23 = f2(0.f, 0.f), v46 = f2(0.f, 0.f), v78 = f2(0.f, 0.f);
+            float v5 = 0.f;
             for (int t = lo; t < nslots && (int)sslotj[t] == tid; ++t) {
-#pragma unroll
-                for (int c = 0; c < 9; ++c) v[c] += sslot[t][c];
+                v01 = __fadd2_rn(v01, sslot[t][0]);
+                v23 = __fadd2_rn(v23, sslot[t][1]);
+                v46 = __fadd2_rn(v46, sslot[t][2]);
+                v78 = __fadd2_rn(v78, sslot[t][3]);
+                v5 += sslot[t][4].x;
             }
             const float4 a = s0[tid];
             const float Cp = s1[tid].x;
             // q' = A' dx^2 + B'' dx dy + C' dy^2, dx = px - mu_x, dy = py - mu_y
-            const float gmx = -(2.0f * a.z * v[7] + a.w * v[8]);
-            const float gmy = -(a.w * v[7] + 2.0f * Cp * v[8]);
+            const float gmx = -(2.0f * a.z * v78.x + a.w * v78.y);
+            const float gmy = -(a.w * v78.x + 2.0f * Cp * v78.y);
             // prescaled -> unscaled conic: A' = k A, B'' = 2k B, C' = k C
             float4* o = reinterpret_cast<float4*>(grec + (size_t)WSR_GRAD_RECORD_FLOATS * sidx[tid]);
-            atomicAdd(o, make_float4(gmx, gmy, kHalfLog2e * v[4], 2.0f * kHalfLog2e * v[5]));
-            atomicAdd(o + 1, make_float4(kHalfLog2e * v[6], v[3], v[0], v[1]));
-            atomicAdd(reinterpret_cast<float*>(o + 2), v[2]);
+            atomicAdd(o, make_float4(gmx, gmy, kHalfLog2e * v46.x, 2.0f * kHalfLog2e * v5));
+            atomicAdd(o + 1, make_float4(kHalfLog2e * v46.y, v23.y, v01.x, v01.y));
+            atomicAdd(reinterpret_cast<float*>(o + 2), v23.x);
         }
     }
     __syncthreads();
