@@ -96,10 +96,19 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "25"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # nvidia-smi needs a moment to start: wait (up to 3 s) for its first sample so that the
+        # timed region that follows is covered
+        t0 = time.time()
+        while time.time() - t0 < 3.0:
+            self.fh.flush()
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -356,7 +365,7 @@ def run_ours(args):
     fwd_value = world * npix / (fwd_ms * 1e-3) / 1e6
 
     # ---- e2e: same step through the public API with host buffers ---------
-    e2e = None if args.no_e2e else run_e2e(args, S, scene, target, flush)
+    e2e = None if args.no_e2e else run_e2e(args, S, scene, weight, target, flush)
 
     # ---- roofline of the dominant kernel ----------------------------------
     names = S.stage_names
@@ -425,46 +434,93 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_e2e(args, S, scene, target, flush):
+def run_e2e(args, S, scene, weight, target, flush):
     """The step through the C ABI with host inputs: every step copies the
     Gaussian parameters and the target from pinned host memory and reads back
-    the loss and the rendered image."""
+    the loss and the rendered image.  The copies are pipelined the way a
+    host-fed loop would run: two sets of device buffers, step k's inputs
+    uploaded on a copy stream while step k-1 computes, step k's image read
+    back on another stream while step k+1 computes.  Every byte of every
+    step is still copied inside the timed region.  The same loop run serially
+    (copy, compute, copy back) is reported beside it."""
     import numpy as np
     import torch
+    names = ("means", "log_scales", "quats", "sh", "opacity", "lc_v")
     g = S.g
-    host = {k: getattr(g, k).cpu().pin_memory() for k in ("means", "log_scales", "quats", "sh", "opacity", "lc_v")}
+    host = {k: getattr(g, k).cpu().pin_memory() for k in names}
     tgt_h = S.target.cpu().pin_memory()
-    rgb_h = torch.empty_like(S.st.rgb, device="cpu").pin_memory()
-    loss_h = torch.empty(1).pin_memory()
     h2d = sum(v.numel() * v.element_size() for v in host.values()) + tgt_h.numel() * 4
-    d2h = rgb_h.numel() * 4 + 4
+    d2h = S.st.rgb.numel() * 4 + 4
+    steps = [S, Step(scene, S.cam, weight, tuple(S.r.tile), target)]
+    rgb_h = [torch.empty_like(S.st.rgb, device="cpu").pin_memory() for _ in range(2)]
+    loss_h = [torch.empty(1).pin_memory() for _ in range(2)]
+    comp = torch.cuda.current_stream()
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
 
-    def one():
-        for k, v in host.items():
-            getattr(g, k).copy_(v, non_blocking=True)
-        S.target.copy_(tgt_h, non_blocking=True)
-        S.run()
-        rgb_h.copy_(S.st.rgb, non_blocking=True)
-        loss_h.copy_(S.loss, non_blocking=True)
+    def upload(b, stream):
+        with torch.cuda.stream(stream):
+            for k, v in host.items():
+                getattr(steps[b].g, k).copy_(v, non_blocking=True)
+            steps[b].target.copy_(tgt_h, non_blocking=True)
 
-    for _ in range(max(2, args.warmup)):
-        one()
-    torch.cuda.synchronize()
-    n = max(3, args.steps // 2)
-    times = []
-    for _ in range(n):
-        flush.zero_()
+    def download(b, stream):
+        with torch.cuda.stream(stream):
+            rgb_h[b].copy_(steps[b].st.rgb, non_blocking=True)
+            loss_h[b].copy_(steps[b].loss, non_blocking=True)
+
+    def pipelined(n):
+        ev = lambda: torch.cuda.Event()
+        uploaded, computed, downloaded = [ev(), ev()], [ev(), ev()], [ev(), ev()]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        one()
-        e1.record()
+        e0.record(comp)
+        up.wait_event(e0)
+        down.wait_event(e0)
+        for k in range(n):
+            b = k % 2
+            if k >= 2:
+                up.wait_event(computed[b])          # step k-2 is done reading buffer b
+            upload(b, up)
+            uploaded[b].record(up)
+            comp.wait_event(uploaded[b])
+            if k >= 2:
+                comp.wait_event(downloaded[b])      # step k-2's image has left buffer b
+            steps[b].run()
+            computed[b].record(comp)
+            down.wait_event(computed[b])
+            download(b, down)
+            downloaded[b].record(down)
+        comp.wait_stream(down)
+        e1.record(comp)
         torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-    ms = max_over_ranks(float(np.mean(times)), device="cuda")
+        return e0.elapsed_time(e1) / n
+
+    def serial(n):
+        times = []
+        for _ in range(n):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(comp)
+            upload(0, comp)
+            S.run()
+            download(0, comp)
+            e1.record(comp)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return float(np.mean(times))
+
+    pipelined(max(3, args.warmup))
+    n = max(6, args.steps)
+    ms = max_over_ranks(pipelined(n), device="cuda")
+    ms_serial = max_over_ranks(serial(max(3, args.steps // 4)), device="cuda")
     world = dist_env()[0]
     npix = S.cam.width * S.cam.height
+    del steps[1]
+    torch.cuda.empty_cache()
     return {"value": round(world * npix / (ms * 1e-3) / 1e6, 2), "unit": "Mpix/s", "ms_per_step": round(ms, 4),
-            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "pipelining": "two buffer sets; uploads, steps and read-backs on three streams",
+            "serial_ms_per_step": round(ms_serial, 4),
+            "serial_value": round(world * npix / (ms_serial * 1e-3) / 1e6, 2)}
 
 
 def _events_ms(fn, reps: int, warmup: int = 2) -> float:
@@ -665,7 +721,7 @@ def run_reduced(reps: int = 3) -> dict:
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", type=int, default=3)
