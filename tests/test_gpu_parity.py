@@ -300,3 +300,72 @@ def test_l1_loss_kernel():
     ref = (a.double() - b.double()).abs().mean()
     assert abs(loss.item() - ref.item()) < 1e-6
     assert torch.equal(g, torch.sign(a - b) / a.numel())
+
+
+def test_workload3_subset_gradients_match_fp64_finite_differences():
+    """The 1M x 1920x1080 workload's first 1,000 visible Gaussians: GPU
+    gradients of the linear loss <R, C> against central finite differences
+    of the FP64 oracle's forward, for sampled entries of every parameter
+    tensor and for sigma, w_B and c_B.  An entry is skipped when the set of
+    pairs with q <= 9 changes between +h and -h; the tolerance is 1e-3 of the
+    tensor's largest GPU gradient plus the oracle's tie envelope at that entry."""
+    import torch
+    from paper_2410_18931_gb300 import Gaussians, Renderer
+    scene, cams, w, _ = ws.workload(3)
+    cam = cams[0].rounded()
+    w = w.rounded()
+    vis = np.nonzero(oracle.project(scene, cam, w)["visible"])[0][:1000]
+    sc = scene.subset(vis)
+    rng = np.random.default_rng(7)
+    R = rng.normal(size=(cam.height, cam.width, 3)).astype(np.float32)
+    g = Gaussians.from_scene(sc)
+    wpar = torch.tensor(w.as_array(), device="cuda")
+    r = Renderer([cam])
+    st = r.forward(g, w.kind, wpar)
+    out = r.backward(g, w.kind, wpar, st, torch.from_numpy(R.reshape(-1, 3)).cuda())
+    torch.cuda.synchronize()
+    lo, _, hi = grad_envelope(sc, cam, w, R.astype(np.float64))
+    Rd = R.astype(np.float64)
+
+    def loss_pairs(s, wp):
+        o = oracle.render(s, cam, wp)
+        return float((o["rgb"] * Rd).sum()), o["pairs"]
+
+    checked = 0
+    # steps per tensor: small against the footprint (means move ~0.003 px), far above float32 rounding;
+    # the parameters are float32, so the difference quotient uses the step actually taken
+    steps = dict(means=1e-5, log_scales=1e-4, quats=1e-4, sh=1e-3, opacity=1e-3, lc_v=1e-3)
+    for name, hstep in steps.items():
+        gpu = out[name].cpu().numpy().astype(np.float64).reshape(-1)
+        slack = np.abs(np.asarray(hi[name]) - np.asarray(lo[name])).reshape(-1)
+        scale = np.abs(gpu).max()
+        flat = getattr(sc, name).reshape(-1)
+        for k in rng.choice(flat.size, 12, replace=False):
+            x0 = flat[k]
+            xp, xm = np.float32(x0 + hstep), np.float32(x0 - hstep)
+            flat[k] = xp
+            lp, pp = loss_pairs(sc, w)
+            flat[k] = xm
+            lm, pm = loss_pairs(sc, w)
+            flat[k] = x0
+            if pp != pm:
+                continue
+            fd = (lp - lm) / (float(xp) - float(xm))
+            assert abs(gpu[k] - fd) <= GRAD_TOL * scale + slack[k], (name, k, gpu[k], fd, scale)
+            checked += 1
+    gw = out["weight_params"].cpu().numpy().astype(np.float64)
+    base = [w.sigma, w.beta, w.w_bg, *w.c_bg]
+    for k in (0, 2, 3, 4, 5):             # sigma, w_B, c_B (beta is unused by the LC weight)
+        h = 1e-4 * max(1.0, abs(base[k]))
+        vals = list(base)
+        vals[k] = base[k] + h
+        lp, pp = loss_pairs(sc, ws.WeightParams(w.kind, vals[0], vals[1], vals[2], tuple(vals[3:])))
+        vals[k] = base[k] - h
+        lm, pm = loss_pairs(sc, ws.WeightParams(w.kind, vals[0], vals[1], vals[2], tuple(vals[3:])))
+        if pp != pm:
+            continue
+        fd = (lp - lm) / (2 * h)
+        tie = abs(hi["wpar"][k] - lo["wpar"][k])
+        assert abs(gw[k] - fd) <= 1e-3 * max(abs(fd), 1e-3) + tie, (k, gw[k], fd)
+        checked += 1
+    assert checked >= 50
