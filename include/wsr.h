@@ -177,9 +177,13 @@ size_t wsr_workspace_size(const wsr_camera* cams, int32_t n_cams, const wsr_tile
  * RGB = max(0, Y.H + 0.5)), Eq. 11 / Eq. 3 (opacity), Eqs. 8-10 (weight),
  * App. C (near-plane culling).
  *   records  [n_cams, n, 12] float32 output.  Per Gaussian and view:
- *            {mu_x, mu_y, A', 2B', C', u w, c_r u w, c_g u w, c_b u w,
- *             rx, ry, depth}, where (A, B, C) is the conic Sigma_2D^{-1},
- *            primed entries are multiplied by log2(e)/2, and rx, ry are the
+ *            {mu_x, mu_y, qs, qw, qd, u w, c_r u w, c_g u w, c_b u w,
+ *             rx, ry, depth}, where the Mahalanobis distance of a pixel
+ *            offset (dx, dy) is written as a sum of squares,
+ *              q log2(e)/2 = (qs dy + qw dx)^2 + qd dx^2,
+ *            i.e. with Sigma_2D = [[a, b], [b, c]] and det its determinant:
+ *            qs = sqrt(k a / det), qw = -(b / a) qs, qd = k / a, k = log2(e)/2
+ *            (no cancellation for needle-like footprints), and rx, ry are the
  *            3-sigma half extents in pixels.  rx < 0 marks a culled Gaussian.
  */
 wsr_status wsr_project(const wsr_gaussians* g, const wsr_camera* cams, int32_t n_cams,
@@ -237,8 +241,9 @@ wsr_status wsr_render_fwd(const float* records, int64_t n, const uint32_t* tile_
  * projection, given grad_rgb = dL/dC.  Two stages:
  *   (1) per tile, recompute every (pixel, Gaussian) term from the records and
  *       reduce into grad_records [n_cams, n, 12] float32 (overwritten):
- *       {dL/dmu_x, dL/dmu_y, dL/dA, dL/dB, dL/dC, dL/d(uw) at fixed c uw,
- *        dL/d(c uw) (3), 0, 0, 0}; (A, B, C) unscaled conic, B counted once;
+ *       {dL/dmu_x, dL/dmu_y, dL/da, dL/db, dL/dc, dL/d(uw) at fixed c uw,
+ *        dL/d(c uw) (3), 0, 0, 0}; (a, b, c) the entries of
+ *       Sigma_2D = [[a, b], [b, c]] (dilation included, b one variable);
  *       plus the background terms dL/dw_B, dL/dc_B;
  *   (2) per Gaussian, chain grad_records back to the stored parameters.
  * `g` must be the scene given to wsr_project; out_rgb / out_den come from

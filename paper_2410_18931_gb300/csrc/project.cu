@@ -28,6 +28,9 @@ struct Geom {
     float r0[3], r1[3];    // rows of T = J W R S
     float a, b, c;         // Sigma_2D with dilation
     float A, B, C;         // conic
+    // the same quadratic form as a sum of squares, prescaled by log2(e)/2:
+    // q' = (qs dy + qw dx)^2 + qd dx^2, i.e. q = (a/det)(dy - (b/a) dx)^2 + dx^2 / a
+    float qs, qw, qd;
 };
 
 __device__ __forceinline__ void geometry(const View& V, const float* Rg, const float* s, float px,
@@ -77,11 +80,19 @@ __device__ __forceinline__ void geometry(const View& V, const float* Rg, const f
         G.A = (float)((cd + 0.3) / dd);
         G.B = (float)(-bd / dd);
         G.C = (float)((ad + 0.3) / dd);
+        const double k = (double)kHalfLog2e, a_ = ad + 0.3;
+        const double qs = sqrt(k * a_ / dd);
+        G.qs = (float)qs;
+        G.qw = (float)(-(bd / a_) * qs);
+        G.qd = (float)(k / a_);
     } else {
         const float id = 1.0f / det;
         G.A = G.c * id;
         G.B = -G.b * id;
         G.C = G.a * id;
+        G.qs = sqrtf(kHalfLog2e * G.a * id);
+        G.qw = -(G.b / G.a) * G.qs;
+        G.qd = kHalfLog2e / G.a;
     }
 }
 
@@ -190,8 +201,8 @@ __global__ void __launch_bounds__(256) k_project(const GaussPtrs g, const Views 
             u = 1.0f / (1.0f + expf(-P.Ha[0]));
         }
         const float uw = u * w;
-        o[0] = make_float4(mx, my, G.A * kHalfLog2e, 2.0f * G.B * kHalfLog2e);
-        o[1] = make_float4(G.C * kHalfLog2e, uw, col[0] * uw, col[1] * uw);
+        o[0] = make_float4(mx, my, G.qs, G.qw);
+        o[1] = make_float4(G.qd, uw, col[0] * uw, col[1] * uw);
         o[2] = make_float4(col[2] * uw, rx, ry, G.tz);
     }
 }
@@ -330,13 +341,9 @@ __global__ void __launch_bounds__(128) k_project_bwd(const GaussPtrs g, const Vi
             gt[1] += g9[1] * V.fy * iz;
             gt[2] += -(g9[0] * V.fx * tx + g9[1] * V.fy * ty) * iz2;
 
-            // conic = Sigma_2D^{-1}: dL/dSigma = -K Gk K,  Gk = [[gA, gB/2], [gB/2, gC]]
-            const float gA = g9[2], gB = 0.5f * g9[3], gC = g9[4];
-            const float P00 = G.A * gA + G.B * gB, P01 = G.A * gB + G.B * gC;
-            const float P10 = G.B * gA + G.C * gB, P11 = G.B * gB + G.C * gC;
-            const float ga = -(P00 * G.A + P01 * G.B);
-            const float gb = -(P00 * G.B + P01 * G.C) - (P10 * G.A + P11 * G.B);
-            const float gc = -(P10 * G.B + P11 * G.C);
+            // the gradient record holds dL/d(a, b, c) of Sigma_2D = [[a, b], [b, c]] directly (formed
+            // per pixel from Sigma_2D^{-1} d, without passing through the conic's entries)
+            const float ga = g9[2], gb = g9[3], gc = g9[4];
             // Sigma_2D = (r0.r0 + 0.3, r0.r1, r1.r1 + 0.3)
             float gr0[3], gr1[3];
 #pragma unroll

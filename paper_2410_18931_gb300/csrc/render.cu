@@ -5,7 +5,9 @@
 // thread; every thread owns a 2x2 block of pixels (two columns share each
 // paired float2 FP32 instruction) and accumulates, in FP32 registers,
 //     N += (c u w) e,   D += (u w) e,   e = exp(-q/2) = 2^(-q'),   q <= 9
-// with q' = q log2(e)/2 evaluated from the prescaled conic of the record.
+// with q' = q log2(e)/2 evaluated from the record's sum of squares
+// q' = (qs dy + qw dx)^2 + qd dx^2, which has no cancellation even for
+// needle-like footprints.
 // There is no early termination (App. D: every covering Gaussian counts).
 // The epilogue writes C = (c_B w_B + N) / (w_B + D) and the denominator.
 //
@@ -59,8 +61,8 @@ __device__ __forceinline__ void fwd_tile(const int tile, const float4* __restric
                                          float* __restrict__ out_rgb, float* __restrict__ out_den) {
     using S = FwdShape<TW, TH, PX>;
     constexpr int NT = S::NT;
-    __shared__ float4 s0[NT];   // mu_x, mu_y, A', 2B'
-    __shared__ float4 s1[NT];   // C', u w, c_r u w, c_g u w
+    __shared__ float4 s0[NT];   // mu_x, mu_y, qs, qw
+    __shared__ float4 s1[NT];   // qd, u w, c_r u w, c_g u w
     __shared__ float2 s2[NT];   // c_b u w, u w
 
     const TileCoord tc = tile_coord(vs, tile);
@@ -97,16 +99,17 @@ __device__ __forceinline__ void fwd_tile(const int tile, const float4* __restric
             const float4 b = s1[j];
             const float2 cbuw = s2[j];
             const float2 crg = f2(b.z, b.w);
-            // q' = A' dx^2 + 2B' dx dy + C' dy^2, evaluated as
-            // fma(dy, fma(C', dy, 2B' dx), (A' dx) dx) for both columns at once
+            // q' = (qs dy + qw dx)^2 + qd dx^2, evaluated as
+            // fma(r, r, (qd dx) dx) with r = fma(qs, dy, qw dx), for both columns at once
             const float2 dx = __fadd2_rn(px, f2(-a.x, -a.x));
-            const float2 P = __fmul2_rn(__fmul2_rn(f2(a.z, a.z), dx), dx);
+            const float2 P = __fmul2_rn(__fmul2_rn(f2(b.x, b.x), dx), dx);
             const float2 Q = __fmul2_rn(f2(a.w, a.w), dx);
             const float dys[2] = {py0 - a.y, py1 - a.y};
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 const float2 dy = f2(dys[r], dys[r]);
-                const float2 q = __ffma2_rn(dy, __ffma2_rn(f2(b.x, b.x), dy, Q), P);
+                const float2 rr = __ffma2_rn(f2(a.z, a.z), dy, Q);
+                const float2 q = __ffma2_rn(rr, rr, P);
                 if (q.x <= kQMax) {
                     const float e = ex2_approx(-q.x);
                     rg[r][0] = __ffma2_rn(crg, f2(e, e), rg[r][0]);
@@ -229,8 +232,8 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
     constexpr int NSLOT = NT + CH;                      // slices touch at most NT + CH (thread, Gaussian) pairs
     static_assert(NT == 2 * CH && TH % 2 == 0 && ((TH - 1) << XB) < 256 && CH <= 256, "unit encoding");
     __shared__ float4 spix[PW * TH + 1];        // per pixel: G/D (3), -(G.C)/D; zero column and pad entry
-    __shared__ float4 s0[CH];                   // mu_x, mu_y, A', 2B'
-    __shared__ float4 s1[CH];                   // C', u w, c_r u w, c_g u w
+    __shared__ float4 s0[CH];                   // mu_x, mu_y, qs, qw
+    __shared__ float4 s1[CH];                   // qd, u w, c_r u w, c_g u w
     __shared__ float2 s2[CH];                   // c_b u w, u w
     __shared__ unsigned sidx[CH];
     __shared__ unsigned soff[CH + 1];           // first unit of each Gaussian
@@ -296,14 +299,15 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 s2[gj] = f2(cb, b.y);
                 sidx[gj] = r;
             }
-            // row y: the footprint is mu_x + c(dy) +- h(dy) with
-            // c = -(B''/2) dy / A', h = sqrt(A' QM - det' dy^2) / A',
-            // det' = A' C' - (B''/2)^2 (both terms of the root are positive)
-            const float hb = 0.5f * a.w;
-            const float det = diff_of_products(a.z, b.x, hb, hb);
-            const float ia = 1.0f / a.z;
+            // row y: the footprint is mu_x + c(dy) +- h(dy) with the conic entries
+            // A' = qw^2 + qd, B' = qs qw, C' = qs^2, det' = A' C' - B'^2 = qd qs^2:
+            // c = -B' dy / A', h = sqrt(A' QM - det' dy^2) / A' (no cancellation anywhere)
+            const float Ap = fmaf(a.w, a.w, b.x);
+            const float hb = a.z * a.w;
+            const float det = b.x * a.z * a.z;
+            const float ia = 1.0f / Ap;
             // rows the footprint can reach: |dy| <= sqrt(A' QM / det'), with a pixel of slack
-            const float ext = fminf(sqrtf(fmaxf(a.z * QM / det, 0.0f)), 1e6f) + 1.0f;
+            const float ext = fminf(sqrtf(fmaxf(Ap * QM / det, 0.0f)), 1e6f) + 1.0f;
             const int ly_lo = max(half * HR, (int)floorf(a.y - ext - 0.5f) - y_org);
             const int ly_hi = min(min(y_lim, half * HR + HR) - 1, (int)ceilf(a.y + ext - 0.5f) - y_org);
 #pragma unroll
@@ -312,7 +316,7 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 unsigned short sp = 0;
                 if (ly >= ly_lo && ly <= ly_hi) {
                     const float dy = (float)(y_org + ly) + 0.5f - a.y;
-                    const float d4 = fmaf(-det * dy, dy, a.z * QM);
+                    const float d4 = fmaf(-det * dy, dy, Ap * QM);
                     if (d4 >= 0.0f) {
                         const float h = sqrtf(d4) * ia;
                         const float cx = a.x - hb * dy * ia;
@@ -397,7 +401,7 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
         if (u0 < u1) {
             int slot = ssbase[tid];
             // per-Gaussian constants as float2 pairs (refreshed when the Gaussian changes)
-            float2 nmx, az2, aw2, cx2, cw0, cw1;
+            float2 nmx, qs2, qw2, qd2, cw0, cw1;
             float gy0;
             unsigned uend = 0;
             auto load_gaussian = [&](int jj) {
@@ -406,23 +410,25 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 const float gx0 = (float)x_org + 0.5f - a.x;            // dx of column 0
                 nmx = f2(gx0, gx0 + 1.0f);
                 gy0 = (float)y_org + 0.5f - a.y;                        // dy of row 0
-                az2 = f2(a.z, a.z);
-                aw2 = f2(a.w, a.w);
-                cx2 = f2(b.x, b.x);
+                qs2 = f2(a.z, a.z);
+                qw2 = f2(a.w, a.w);
+                qd2 = f2(b.x, b.x);
                 cw0 = f2(-kLn2 * b.z, -kLn2 * b.w);    // -ln2 (c u w, u w): dL/dq' = e * (P . cw)
                 cw1 = f2(-kLn2 * c2.x, -kLn2 * c2.y);
                 uend = soff[jj + 1];
             };
             load_gaussian(j);
-            // accumulators, paired: (cuw_r, cuw_g), (cuw_b, uw), (A', C'), (sum dx, sum dy), (2B', -)
-            float2 g01 = f2(0.f, 0.f), g23 = f2(0.f, 0.f), g46 = f2(0.f, 0.f), g78 = f2(0.f, 0.f);
-            float g5 = 0.f;
+            // accumulators, paired: (cuw_r, cuw_g), (cuw_b, uw); and, over the two pixels of a unit, with
+            // v = (r qw + qd dx, r qs) = log2(e)/2 Sigma_2D^{-1} (dx, dy) and gq = dL/dq':
+            // sum gq v_x^2, sum gq v_x v_y, sum gq v_y^2, sum gq v_x, sum gq v_y
+            float2 g01 = f2(0.f, 0.f), g23 = f2(0.f, 0.f);
+            float2 sxx = f2(0.f, 0.f), sxy = sxx, syy = sxx, sx = sxx, sy = sxx;
             auto store_slot = [&](int sl) {
                 sslot[sl][0] = g01;
                 sslot[sl][1] = g23;
-                sslot[sl][2] = g46;
-                sslot[sl][3] = g78;
-                sslot[sl][4] = f2(g5, 0.f);
+                sslot[sl][2] = f2(sxx.x + sxx.y, syy.x + syy.y);
+                sslot[sl][3] = f2(sx.x + sx.y, sy.x + sy.y);
+                sslot[sl][4] = f2(sxy.x + sxy.y, 0.f);
             };
             // one or two units per step: two independent chains overlap their latencies; the second
             // unit is masked out (e = 0) when it lies past the slice or the current Gaussian
@@ -434,8 +440,8 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 const float xf = (float)x, dy = (float)ly + gy0;
                 const float2 dx = __fadd2_rn(f2(xf, xf), nmx);
                 const float2 dy2 = f2(dy, dy);
-                const float2 q = __ffma2_rn(dy2, __ffma2_rn(cx2, dy2, __fmul2_rn(aw2, dx)),
-                                            __fmul2_rn(__fmul2_rn(az2, dx), dx));   // the forward's arithmetic
+                const float2 rr = __ffma2_rn(qs2, dy2, __fmul2_rn(qw2, dx));        // the forward's arithmetic
+                const float2 q = __ffma2_rn(rr, rr, __fmul2_rn(__fmul2_rn(qd2, dx), dx));
                 const float e0 = ex2_approx((valid && q.x <= kQMax) ? -q.x : -256.0f);  // 2^-256 flushes to 0
                 const float e1 = ex2_approx((valid && q.y <= kQMax) ? -q.y : -256.0f);
                 // d/d(c u w) and d/d(u w) at fixed c u w
@@ -447,19 +453,21 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 const float2 m0 = __ffma2_rn(f2(P0.z, P0.w), cw1, __fmul2_rn(f2(P0.x, P0.y), cw0));
                 const float2 m1 = __ffma2_rn(f2(P1.z, P1.w), cw1, __fmul2_rn(f2(P1.x, P1.y), cw0));
                 const float2 gq = __fmul2_rn(f2(e0, e1), f2(m0.x + m0.y, m1.x + m1.y));
-                const float2 tu0 = __fmul2_rn(f2(gq.x, gq.x), f2(dx.x, dy));   // (gq dx, gq dy), pixel 0
-                const float2 tu1 = __fmul2_rn(f2(gq.y, gq.y), f2(dx.y, dy));   // pixel 1
-                g46 = __ffma2_rn(tu0, f2(dx.x, dy), g46);                     // dL/dA', dL/dC'
-                g46 = __ffma2_rn(tu1, f2(dx.y, dy), g46);
-                g5 = fmaf(tu0.x + tu1.x, dy, g5);                             // dL/d(2B')
-                g78 = __fadd2_rn(g78, __fadd2_rn(tu0, tu1));                  // sums of dL/dq' dx, dy
+                // v for both pixels, from the sum of squares: no cancelling large terms even for needles
+                const float2 vx = __ffma2_rn(rr, qw2, __fmul2_rn(qd2, dx));
+                const float2 vy = __fmul2_rn(rr, qs2);
+                const float2 tx = __fmul2_rn(gq, vx), ty = __fmul2_rn(gq, vy);
+                sxx = __ffma2_rn(tx, vx, sxx);
+                sxy = __ffma2_rn(tx, vy, sxy);
+                syy = __ffma2_rn(ty, vy, syy);
+                sx = __fadd2_rn(sx, tx);
+                sy = __fadd2_rn(sy, ty);
             };
             for (unsigned u = u0; u < u1;) {
                 if (u == uend) {
                     // the next Gaussian with units: store this one's sums, zero slots for any between
                     store_slot(slot++);
-                    g01 = g23 = g46 = g78 = f2(0.f, 0.f);
-                    g5 = 0.f;
+                    g01 = g23 = sxx = sxy = syy = sx = sy = f2(0.f, 0.f);
                     ++j;
                     while (soff[j + 1] <= u) {
 #pragma unroll
@@ -489,24 +497,22 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 if ((int)sslotj[mid] < tid) lo = mid + 1;
                 else hi = mid;
             }
-            float2 v01 = f2(0.f, 0.f), v23 = f2(0.f, 0.f), v46 = f2(0.f, 0.f), v78 = f2(0.f, 0.f);
-            float v5 = 0.f;
+            float2 v01 = f2(0.f, 0.f), v23 = f2(0.f, 0.f), vxy = f2(0.f, 0.f), vm = f2(0.f, 0.f);
+            float vc = 0.f;
             for (int t = lo; t < nslots && (int)sslotj[t] == tid; ++t) {
                 v01 = __fadd2_rn(v01, sslot[t][0]);
                 v23 = __fadd2_rn(v23, sslot[t][1]);
-                v46 = __fadd2_rn(v46, sslot[t][2]);
-                v78 = __fadd2_rn(v78, sslot[t][3]);
-                v5 += sslot[t][4].x;
+                vxy = __fadd2_rn(vxy, sslot[t][2]);
+                vm = __fadd2_rn(vm, sslot[t][3]);
+                vc += sslot[t][4].x;
             }
-            const float4 a = s0[tid];
-            const float Cp = s1[tid].x;
-            // q' = A' dx^2 + B'' dx dy + C' dy^2, dx = px - mu_x, dy = py - mu_y
-            const float gmx = -(2.0f * a.z * v78.x + a.w * v78.y);
-            const float gmy = -(a.w * v78.x + 2.0f * Cp * v78.y);
-            // prescaled -> unscaled conic: A' = k A, B'' = 2k B, C' = k C
+            // q' = k d^T Sigma_2D^{-1} d, d = p - mu, k = log2(e)/2, v = k Sigma_2D^{-1} d:
+            // dq'/dmu = -2 v, and for Sigma_2D = [[a, b], [b, c]] (b one variable)
+            // dq'/da = -v_x^2 / k, dq'/db = -2 v_x v_y / k, dq'/dc = -v_y^2 / k
+            constexpr float ik = 1.0f / kHalfLog2e;
             float4* o = reinterpret_cast<float4*>(grec + (size_t)WSR_GRAD_RECORD_FLOATS * sidx[tid]);
-            atomicAdd(o, make_float4(gmx, gmy, kHalfLog2e * v46.x, 2.0f * kHalfLog2e * v5));
-            atomicAdd(o + 1, make_float4(kHalfLog2e * v46.y, v23.y, v01.x, v01.y));
+            atomicAdd(o, make_float4(-2.0f * vm.x, -2.0f * vm.y, -ik * vxy.x, -2.0f * ik * vc));
+            atomicAdd(o + 1, make_float4(-ik * vxy.y, v23.y, v01.x, v01.y));
             atomicAdd(reinterpret_cast<float*>(o + 2), v23.x);
         }
     }
@@ -603,12 +609,13 @@ __global__ void __launch_bounds__(TileShape<TW, TH, PPT>::NT)
         for (int j = 0; j < cnt; ++j) {
             const float4 a = s0[j];
             const float dx = px - a.x;
-            const float P = a.z * dx * dx;
+            const float P = s1[j] * dx * dx;
             const float Q = a.w * dx;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
                 const float dy = (float)(y0 + k) + 0.5f - a.y;
-                const float q = fmaf(dy, fmaf(s1[j], dy, Q), P);
+                const float rr = fmaf(a.z, dy, Q);
+                const float q = fmaf(rr, rr, P);
                 if (q <= kQMax && y0 + k < V.H) ++cnt_pairs;
             }
         }

@@ -150,8 +150,23 @@ def test_gradient_records_match_oracle():
     conv = gr.copy()
     conv[:, 6:9] = gr[:, 6:9] * uw[:, None]
     conv[:, 5] = gr[:, 5] + (gr[:, 6:9] * col).sum(1)
-    for c, name in [((0, 2), "mean"), ((2, 5), "conic"), ((5, 6), "uw"), ((6, 9), "color")]:
-        part = tuple({"g2d": e["g2d"][:, c[0]:c[1]]} for e in env)
+    # the kernel stores dL/d(a, b, c) of Sigma_2D = [[a, b], [b, c]]; the oracle gives dL/d(A, B, C) of the
+    # conic K = Sigma_2D^{-1} (q = A dx^2 + 2B dx dy + C dy^2): dL/dSigma = -K G K, G = [[dA, dB/2], [dB/2, dC]]
+    A, B, C = (P["conic"][:, k] for k in range(3))
+
+    def to_sigma(g):
+        g = g.copy()
+        dA, dB, dC = g[:, 2], 0.5 * g[:, 3], g[:, 4]
+        p00, p01 = A * dA + B * dB, A * dB + B * dC
+        p10, p11 = B * dA + C * dB, B * dB + C * dC
+        g[:, 2] = -(p00 * A + p01 * B)
+        g[:, 3] = -(p00 * B + p01 * C) - (p10 * A + p11 * B)
+        g[:, 4] = -(p10 * B + p11 * C)
+        return g
+
+    env_s = tuple({"g2d": to_sigma(e["g2d"])} for e in env)
+    for c, name in [((0, 2), "mean"), ((2, 5), "Sigma_2D"), ((5, 6), "uw"), ((6, 9), "color")]:
+        part = tuple({"g2d": e["g2d"][:, c[0]:c[1]]} for e in env_s)
         err = grad_excess(conv[:, c[0]:c[1]], part, "g2d")
         assert err <= GRAD_TOL, (name, err)
 
