@@ -33,42 +33,6 @@ __device__ __forceinline__ bool pixel_rect(const float4 r0, const float4 r2, con
     return jx0 <= jx1 && jy0 <= jy1;
 }
 
-// Does the footprint q' <= kQMax reach a pixel centre of the rectangle
-// [x0, x1] x [y0, y1] (pixel-centre coordinates)?  The record holds the
-// quadratic as a sum of squares, q' = (qs dy + qw dx)^2 + qd dx^2.  Its
-// minimum over the rectangle is at the centre when the centre is inside,
-// otherwise on an edge, where it is a one-dimensional quadratic.  The
-// threshold is widened slightly so the test stays conservative with respect
-// to the renderers' FP32 per-pixel test.
-__device__ __forceinline__ bool footprint_hits(float mx, float my, float qs, float qw, float qd, float x0,
-                                               float x1, float y0, float y1) {
-    if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return true;
-    const float thr = kQMax * 1.0001f + 1e-4f;
-    auto q = [&](float dx, float dy) {
-        const float r = fmaf(qs, dy, qw * dx);
-        return fmaf(r, r, qd * dx * dx);
-    };
-    float best = 3.4e38f;
-    // vertical edges x = x0, x1: the minimum over dy is at qs dy = -qw dx
-    const float ex[2] = {x0 - mx, x1 - mx};
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const float dx = ex[k];
-        const float dy = fminf(fmaxf(-qw * dx / qs, y0 - my), y1 - my);
-        best = fminf(best, q(dx, dy));
-    }
-    // horizontal edges y = y0, y1: the minimum over dx is at dx = -qw qs dy / (qw^2 + qd)
-    const float ey[2] = {y0 - my, y1 - my};
-    const float den = fmaf(qw, qw, qd);
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const float dy = ey[k];
-        const float dx = fminf(fmaxf(-qw * qs * dy / den, x0 - mx), x1 - mx);
-        best = fminf(best, q(dx, dy));
-    }
-    return best <= thr;
-}
-
 // Binning pass.  Each warp takes 32 consecutive Gaussians of one view; their
 // tile rectangles are laid end to end (warp scan) and the lanes walk that
 // list of candidate (Gaussian, tile) pairs together, 32 at a time, so a large

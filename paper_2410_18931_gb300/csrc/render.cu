@@ -51,7 +51,11 @@ struct FwdShape {
     static constexpr int PY = 2;
     static constexpr int BX = TW / PX;                  // thread columns
     static constexpr int NT = (TW / PX) * (TH / PY);    // threads per block
-    static_assert(NT % 32 == 0, "whole warps");
+    static constexpr int NW = NT / 32;
+    static_assert(NT % 32 == 0 && 32 % BX == 0, "whole warps of whole thread rows");
+    // first and last pixel row (within the tile) of warp w
+    __host__ __device__ static constexpr int row_lo(int w) { return (32 * w / BX) * PY; }
+    __host__ __device__ static constexpr int row_hi(int w) { return ((32 * w + 31) / BX) * PY + PY - 1; }
 };
 
 template <int TW, int TH, int PX>
@@ -61,9 +65,14 @@ __device__ __forceinline__ void fwd_tile(const int tile, const float4* __restric
                                          float* __restrict__ out_rgb, float* __restrict__ out_den) {
     using S = FwdShape<TW, TH, PX>;
     constexpr int NT = S::NT;
+    constexpr int NW = S::NW;
     __shared__ float4 s0[NT];   // mu_x, mu_y, qs, qw
     __shared__ float4 s1[NT];   // qd, u w, c_r u w, c_g u w
     __shared__ float2 s2[NT];   // c_b u w, u w
+    // with several warps: bit w of smask[j] = Gaussian j reaches a pixel centre of warp w's rows,
+    // and each warp walks only the Gaussians of its own list
+    __shared__ unsigned smask[NT];
+    __shared__ unsigned char swl[NW][NT];
 
     const TileCoord tc = tile_coord(vs, tile);
     const View& V = vs.v[tc.v];
@@ -88,13 +97,42 @@ __device__ __forceinline__ void fwd_tile(const int tile, const float4* __restric
         if (tid < cnt) {
             const unsigned r = list[base + tid];
             const float4* p = rec + 3ull * r;
-            s0[tid] = __ldg(p);
+            const float4 a = __ldg(p);
+            s0[tid] = a;
             const float4 b = __ldg(p + 1);
             s1[tid] = b;
             s2[tid] = f2(__ldg(reinterpret_cast<const float*>(p + 2)), b.y);
+            if constexpr (NW > 1) {
+                const float xl = (float)(tc.tx * TW) + 0.5f, xh = xl + (float)(TW - 1);
+                unsigned m = 0;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    const float yl = (float)(tc.ty * TH + S::row_lo(w)) + 0.5f;
+                    const float yh = (float)(tc.ty * TH + S::row_hi(w)) + 0.5f;
+                    m |= footprint_hits(a.x, a.y, a.z, a.w, b.x, xl, xh, yl, yh) ? (1u << w) : 0u;
+                }
+                smask[tid] = m;
+            }
         }
         __syncthreads();
-        for (int j = 0; j < cnt; ++j) {
+        int nj = cnt;
+        if constexpr (NW > 1) {
+            // this warp's list: a ballot over the chunk, 32 Gaussians at a time
+            const int w = tid >> 5, lane = tid & 31;
+            nj = 0;
+            for (int j0 = 0; j0 < cnt; j0 += 32) {
+                const int jj = j0 + lane;
+                const bool hit = jj < cnt && ((smask[jj] >> w) & 1u);
+                const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                if (hit) swl[w][nj + __popc(bal & ((1u << lane) - 1u))] = (unsigned char)jj;
+                nj += __popc(bal);
+            }
+            __syncwarp();
+        }
+#pragma unroll 8
+        for (int k = 0; k < nj; ++k) {
+            int j = k;
+            if constexpr (NW > 1) j = swl[threadIdx.x >> 5][k];
             const float4 a = s0[j];
             const float4 b = s1[j];
             const float2 cbuw = s2[j];
