@@ -262,6 +262,43 @@ def cpu_oracle_leg(scene, cam, weight, target, gpu_rgb, budget_s: float):
     return base, maxerr
 
 
+def cpu_band_rate(scene, cam, weight, budget_s: float, with_grad: bool, what: str) -> dict:
+    """The FP64 oracle, as it stands, on bands of rows of one view (about
+    ``budget_s`` seconds on the host cores in all), extrapolated to the whole
+    view: a call costs a fixed part (projecting every Gaussian) plus a part
+    per row, both fitted from two band heights.  Reported as Mpix/s of the
+    whole view."""
+    import numpy as np
+
+    import oracle
+    threads = os.cpu_count() or 1
+    y0 = cam.height // 2
+
+    def one(rows):
+        band = (y0 - rows // 2, y0 - rows // 2 + rows)
+        t0 = time.perf_counter()
+        out = oracle.render(scene, cam, weight, threads=threads, rows=band)
+        if with_grad:
+            G = np.full(out["rgb"].shape, 1.0 / (3.0 * cam.width * cam.height))
+            oracle.grad(scene, cam, weight, G, threads=threads, rows=band)
+        return time.perf_counter() - t0
+
+    r1 = 4
+    t1 = one(r1)
+    # the second band spends what is left of the budget on rows
+    per_row0 = t1 / r1
+    r2 = int(min(cam.height, max(2 * r1, r1 + max(budget_s - 2 * t1, 0.0) / max(per_row0, 1e-6))))
+    t2 = one(r2)
+    per_row = max((t2 - t1) / (r2 - r1), 1e-9)
+    fixed = max(t1 - r1 * per_row, 0.0)
+    frame = fixed + cam.height * per_row
+    return {"value": round(cam.width * cam.height / frame / 1e6, 4), "unit": "Mpix/s", "cores": threads,
+            "kind": "oracle",
+            "sample": f"{'fwd+bwd' if with_grad else 'fwd'} (FP64) on bands of {r1} and {r2} rows of one "
+                      f"{cam.width}x{cam.height} view of {what} ({t1 + t2:.1f} s); whole view extrapolated as "
+                      f"{fixed:.2f} s per call + {per_row * 1e3:.1f} ms per row"}
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle, as it stands, on host cores."""
     import numpy as np
@@ -417,9 +454,9 @@ def run_ours(args):
     line.update(extra_out)
 
     if world == 1 and not args.no_batched:
-        line["batched"] = run_batched()
+        line["batched"] = run_batched(cpu_leg=not args.no_cpu_baseline)
     if world == 1 and not args.no_reduced:
-        line["reduced"] = run_reduced()
+        line["reduced"] = run_reduced(cpu_leg=not args.no_cpu_baseline)
     if world == 1 and not args.no_training:
         line["training"] = run_training()
     if rank == 0 and not args.no_cpu_baseline:
@@ -537,7 +574,7 @@ def _events_ms(fn, reps: int, warmup: int = 2) -> float:
     return e0.elapsed_time(e1) / reps
 
 
-def run_batched(reps: int = 5) -> dict:
+def run_batched(reps: int = 5, cpu_leg: bool = True) -> dict:
     """3M Gaussians, 16 views of uneven size (4 each of 640x360 .. 2560x1440):
     fwd + L1 + bwd for all views in one captured graph with the autotuned tile
     shape and schedule, against the plain path (one view at a time, 16x16
@@ -549,7 +586,6 @@ def run_batched(reps: int = 5) -> dict:
     scene, cams, weight, extra = ws.workload(4)
     cams = [c.rounded() for c in cams]
     g = Gaussians.from_scene(scene)
-    del scene
     wpar = torch.tensor(weight.as_array(), device="cuda")
     npix = sum(c.width * c.height for c in cams)
     target = torch.rand(npix, 3, device="cuda", generator=torch.Generator("cuda").manual_seed(4))
@@ -570,7 +606,9 @@ def run_batched(reps: int = 5) -> dict:
         o += m
         del one
         torch.cuda.empty_cache()
+    cpu = None if not cpu_leg else cpu_band_rate(scene, cams[2], weight, 8.0, True, "the 3M-Gaussian 16-view workload")
     return {"workload": extra["name"], "gaussians": g.n, "views": len(cams), "mpix_per_step": round(npix / 1e6, 3),
+            "cpu_baseline": cpu,
             "fwd_bwd_mpix_s": round(npix / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms, 3),
             "tile": "%dx%d" % tune["tile"], "persistent": tune["persistent"], "graph": True,
             "kernels_per_step": kernels,
@@ -661,7 +699,7 @@ def _hbm_peak() -> float:
         return 6780.0
 
 
-def run_reduced(reps: int = 3) -> dict:
+def run_reduced(reps: int = 3, cpu_leg: bool = True) -> dict:
     """6M Gaussians, 8 views of 3840x2160: forward with reduced storage (bf16
     scales/quats, f16 SH/opacity, FP32 accumulation) for all views in one set
     of launches, against the plain FP32 single-view forward on the same
@@ -677,6 +715,7 @@ def run_reduced(reps: int = 3) -> dict:
     npix = sum(c.width * c.height for c in cams)
     g32 = Gaussians.from_scene(scene)
     g16 = Gaussians.from_scene(scene, reduced=True)
+    stored = ws.quantize_reduced(scene) if cpu_leg else None     # the values the reduced path stores
     del scene
     r = Renderer(cams, tile=(16, 16), persistent=True, headroom=1.2)
     st = r.forward(g16, weight.kind, wpar)
@@ -709,7 +748,10 @@ def run_reduced(reps: int = 3) -> dict:
         del s1, rs
         torch.cuda.empty_cache()
     mse = se / (3 * npix)
+    cpu = None if not cpu_leg else cpu_band_rate(stored, cams[0], weight, 8.0, False,
+                                                  "the 6M-Gaussian 8-view 4K workload (stored values)")
     return {"workload": extra["name"], "gaussians": g16.n, "views": len(cams), "mpix_per_step": round(npix / 1e6, 3),
+            "cpu_baseline": cpu,
             "fwd_mpix_s": round(npix / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms, 3),
             "storage": "bf16 log-scales/quats, f16 SH/opacity, f32 means, FP32 accumulation",
             "single_view_fp32_fwd_mpix_s": round(npix / (single_ms * 1e-3) / 1e6, 2),
