@@ -18,6 +18,8 @@
 // so a captured CUDA graph replays correct steps; both kernels leave
 // everything untouched when a guard workspace recorded an error (a tile list
 // that overflowed in the same step).
+#include <mutex>
+
 #include "wsr_common.cuh"
 #include "wsr_launch.h"
 
@@ -292,16 +294,17 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ p, const float
 cudaError_t launch_loss_3dgs(const float* rgb, const float* target, const LossViews& L, float* loss, float* grad,
                              cudaStream_t s) {
     const size_t smem = (size_t)kLossSmemFloats * sizeof(float);
-    static bool attr_set[64] = {};
+    // the shared-memory opt-in is a per-device function attribute: set it once per device (thread-safe)
+    static std::once_flag once[64];
+    static cudaError_t once_err[64];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!attr_set[dev]) {
-        e = cudaFuncSetAttribute(k_loss_3dgs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set[dev] = true;
-    }
+    std::call_once(once[dev], [&] {
+        once_err[dev] = cudaFuncSetAttribute(k_loss_3dgs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (once_err[dev] != cudaSuccess) return once_err[dev];
     e = cudaMemsetAsync(loss, 0, 3 * sizeof(float), s);
     if (e != cudaSuccess) return e;
     const int tiles = L.tile_off[L.n];
