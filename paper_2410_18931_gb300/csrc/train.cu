@@ -31,7 +31,10 @@ constexpr int kLT = 32;                     // output tile side
 constexpr int kIn = kLT + 4 * kR;           // staged input side (52)
 constexpr int kSt = kLT + 2 * kR;           // statistics side (42)
 constexpr int kLossThreads = 256;
-constexpr int kLossSmemFloats = 2 * kIn * kIn + 5 * kIn * kSt + 3 * kSt * kSt;
+// the partials reuse the staged pixels (no longer needed after the statistics), the filtered
+// partials reuse the statistics
+constexpr int kLossSmemFloats = 2 * kIn * kIn + 5 * kIn * kSt;
+static_assert(3 * kSt * kSt <= 2 * kIn * kIn, "partials reuse the staged pixels");
 static_assert(3 * kSt * kLT <= 5 * kIn * kSt, "filtered partials reuse the statistics buffer");
 // register blocking of the four filter passes (outputs per item along the filtered axis)
 constexpr int kH1 = kSt / 3;                // horizontal statistics: 3 columns
@@ -59,7 +62,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_3dgs(const float* __restr
     float* sx = sm;                          // [kIn][kIn] rendered
     float* sy = sx + kIn * kIn;              // [kIn][kIn] target
     float* hs = sy + kIn * kIn;              // [5][kIn][kSt] horizontally filtered statistics
-    float* mm = hs + 5 * kIn * kSt;          // [3][kSt][kSt] partials of the loss
+    float* mm = sx;                          // [3][kSt][kSt] partials of the loss (reuses sx, sy)
     float* hm = hs;                          // [3][kSt][kLT] horizontally filtered partials
     __shared__ float red[kLossThreads / 32];
     const int tid = threadIdx.x;
@@ -205,12 +208,12 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_3dgs(const float* __restr
             for (int o = 0; o < kV4; ++o) {
                 const int oy = oy0 + o, gy = y0 + oy;
                 if (gy >= H) break;
-                const float a = sx[(oy + 2 * kR) * kIn + ox + 2 * kR];
-                const float b = sy[(oy + 2 * kR) * kIn + ox + 2 * kR];
+                    const long long pix = (base + (long long)gy * W + gx) * 3 + c;
+                const float a = rgb[pix], b = tgt[pix];      // the staged copies are overwritten by now
                 const float d = a - b;
                 l1 += fabsf(d);
                 const float gd = d > 0.f ? gl1 : (d < 0.f ? -gl1 : 0.f);
-                grad[(base + (long long)gy * W + gx) * 3 + c] = f[0][o] + 2.f * a * f[1][o] + b * f[2][o] + gd;
+                grad[pix] = f[0][o] + 2.f * a * f[1][o] + b * f[2][o] + gd;
             }
         }
         __syncthreads();
