@@ -591,7 +591,8 @@ def run_batched(reps: int = 5, cpu_leg: bool = True) -> dict:
     npix = sum(c.width * c.height for c in cams)
     target = torch.rand(npix, 3, device="cuda", generator=torch.Generator("cuda").manual_seed(4))
     tune = autotune(g, cams, weight.kind, wpar, target, reps=3)
-    step = GraphStep(g, cams, weight.kind, wpar, target, tile=tune["tile"], persistent=tune["persistent"])
+    step = GraphStep(g, cams, weight.kind, wpar, target, tile=tune["tile"], persistent=tune["persistent"],
+                     chunk=tune["chunk"])
     ms = time_step(step, reps=reps)
     assert step.check() == 0
     kernels = step.kernels_per_step
@@ -611,12 +612,12 @@ def run_batched(reps: int = 5, cpu_leg: bool = True) -> dict:
     return {"workload": extra["name"], "gaussians": g.n, "views": len(cams), "mpix_per_step": round(npix / 1e6, 3),
             "cpu_baseline": cpu,
             "fwd_bwd_mpix_s": round(npix / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms, 3),
-            "tile": "%dx%d" % tune["tile"], "persistent": tune["persistent"], "graph": True,
+            "tile": "%dx%d" % tune["tile"], "persistent": tune["persistent"], "chunk": tune["chunk"], "graph": True,
             "kernels_per_step": kernels,
             "single_view_plain_mpix_s": round(npix / (single_ms * 1e-3) / 1e6, 2),
             "speedup_vs_single_view": round(single_ms / ms, 3),
-            "autotune_ms": {("%dx%d" % t["tile"]) + ("/persistent" if t["persistent"] else "/per-tile"):
-                            round(t["ms"], 3) for t in tune["table"]}}
+            "autotune_ms": {("%dx%d" % t["tile"]) + ("/persistent" if t["persistent"] else "/per-tile")
+                            + "/chunk%d" % t["chunk"]: round(t["ms"], 3) for t in tune["table"]}}
 
 
 def run_training(steps: int = 10, warmup: int = 3) -> dict:

@@ -121,17 +121,22 @@ enum {
 };
 
 /*
- * Tile shape for binning and rendering (supported: 16x16, 8x8, 32x8, 16x8)
- * and the render schedule.  With WSR_SCHEDULE_PERSISTENT, wsr_bin also orders
- * the tiles by decreasing instance count (a bucketed longest-first order kept
- * in the workspace) and the render calls launch one block per resident slot
- * that takes tiles from that order through a counter in the workspace; the
- * same workspace and tiles must then be passed to wsr_bin and the renderers.
+ * Tile shape for binning and rendering (supported: 16x16, 8x8, 32x8, 16x8),
+ * the render schedule and the backward's Gaussians per block.  With
+ * WSR_SCHEDULE_PERSISTENT, wsr_bin also orders the tiles by decreasing
+ * instance count (a bucketed longest-first order kept in the workspace) and
+ * the render calls launch one block per resident slot that takes tiles from
+ * that order through a counter in the workspace; the same workspace and tiles
+ * must then be passed to wsr_bin and the renderers.  `chunk` is how many of a
+ * tile's Gaussians one block of wsr_render_bwd takes at a time (two threads
+ * per Gaussian): 0 for the default 128, or 64 (blocks of 128 threads, twice as
+ * many resident); other values return WSR_ERR_UNSUPPORTED.  It changes the
+ * schedule only, not the result beyond rounding order.
  */
 typedef struct {
     int32_t tile_w, tile_h;
     int32_t schedule;            /* WSR_SCHEDULE_* */
-    int32_t reserved;            /* must be 0 */
+    int32_t chunk;               /* Gaussians per backward block: 0 (128) or 64 */
 } wsr_tiles;
 
 /*

@@ -42,7 +42,7 @@ class wsr_weight(ctypes.Structure):
 
 class wsr_tiles(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("schedule", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("chunk", ctypes.c_int32)]
 
 
 class wsr_grads(ctypes.Structure):
@@ -161,5 +161,6 @@ def make_cameras(cams) -> tuple:
 WSR_SCHEDULE_TILE_BLOCKS, WSR_SCHEDULE_PERSISTENT = 0, 1
 
 
-def tiles(tw: int, th: int, schedule: int = WSR_SCHEDULE_TILE_BLOCKS) -> wsr_tiles:
-    return wsr_tiles(int(tw), int(th), int(schedule), 0)
+def tiles(tw: int, th: int, schedule: int = WSR_SCHEDULE_TILE_BLOCKS, chunk: int = 0) -> wsr_tiles:
+    """Tile shape, schedule and the backward's Gaussians per block (0: the default)."""
+    return wsr_tiles(int(tw), int(th), int(schedule), int(chunk))

@@ -15,6 +15,7 @@ from . import _abi as A
 from .render import Gaussians, Renderer
 
 DEFAULT_SHAPES = ((8, 8), (16, 16), (32, 8))
+DEFAULT_CHUNKS = (128, 64)      # Gaussians per block of the backward
 
 
 class GraphStep:
@@ -26,9 +27,10 @@ class GraphStep:
     """
 
     def __init__(self, g: Gaussians, cams, kind: int, wparams: torch.Tensor, target: torch.Tensor,
-                 tile=(16, 16), persistent: bool = True, headroom: float = 1.3, capture: bool = True):
+                 tile=(16, 16), persistent: bool = True, headroom: float = 1.3, capture: bool = True,
+                 chunk: int = 0):
         self.g, self.kind, self.wparams = g, kind, wparams
-        self.r = Renderer(cams, tile=tile, persistent=persistent, headroom=headroom)
+        self.r = Renderer(cams, tile=tile, persistent=persistent, headroom=headroom, chunk=chunk)
         self.st = self.r.forward(g, kind, wparams)           # sizes the tile list exactly (+ headroom)
         self.target = target.reshape(-1, 3).contiguous()
         dev = self.r.device
@@ -99,23 +101,26 @@ _cache: dict = {}
 
 
 def autotune(g: Gaussians, cams, kind: int, wparams: torch.Tensor, target: torch.Tensor,
-             shapes=DEFAULT_SHAPES, schedules=(False, True), reps: int = 3) -> dict:
-    """Time every (tile shape, schedule) on this workload and return the
-    fastest as dict(tile=, persistent=, ms=, table=[...]).  Results are cached
-    per (Gaussian count, view sizes, storage types, weight kind)."""
-    key = (g.n, tuple((c.width, c.height) for c in cams), str(g.sh.dtype), str(g.log_scales.dtype), kind)
+             shapes=DEFAULT_SHAPES, schedules=(False, True), chunks=DEFAULT_CHUNKS, reps: int = 3) -> dict:
+    """Time every (tile shape, schedule, Gaussians per backward block) on this
+    workload and return the fastest as dict(tile=, persistent=, chunk=, ms=,
+    table=[...]).  Results are cached per (Gaussian count, view sizes, storage
+    types, weight kind)."""
+    key = (g.n, tuple((c.width, c.height) for c in cams), str(g.sh.dtype), str(g.log_scales.dtype), kind,
+           tuple(shapes), tuple(schedules), tuple(chunks))
     if key in _cache:
         return _cache[key]
     table = []
     for shape in shapes:
         for persistent in schedules:
-            step = GraphStep(g, cams, kind, wparams, target, tile=shape, persistent=persistent)
-            ms = time_step(step, reps=reps)
-            ok = step.check() == A.WSR_OK
-            table.append(dict(tile=shape, persistent=persistent, ms=ms, ok=ok))
-            del step
-            torch.cuda.empty_cache()
+            for chunk in chunks:
+                step = GraphStep(g, cams, kind, wparams, target, tile=shape, persistent=persistent, chunk=chunk)
+                ms = time_step(step, reps=reps)
+                ok = step.check() == A.WSR_OK
+                table.append(dict(tile=shape, persistent=persistent, chunk=chunk, ms=ms, ok=ok))
+                del step
+                torch.cuda.empty_cache()
     best = min((t for t in table if t["ok"]), key=lambda t: t["ms"])
-    res = dict(tile=best["tile"], persistent=best["persistent"], ms=best["ms"], table=table)
+    res = dict(tile=best["tile"], persistent=best["persistent"], chunk=best["chunk"], ms=best["ms"], table=table)
     _cache[key] = res
     return res

@@ -24,21 +24,24 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 // Builds the per-view constant table.  Returns WSR_OK or the argument error.
 wsr_status make_views(const wsr_camera* cams, int32_t n_cams, const wsr_tiles* tiles, Views* vs) {
     if (!cams || n_cams < 1 || n_cams > WSR_MAX_VIEWS) return WSR_ERR_INVALID_ARG;
-    int tw = 16, th = 16, sched = WSR_SCHEDULE_TILE_BLOCKS;
+    int tw = 16, th = 16, sched = WSR_SCHEDULE_TILE_BLOCKS, chunk = 128;
     if (tiles) {
-        if (tiles->reserved != 0) return WSR_ERR_INVALID_ARG;
+        if (tiles->chunk < 0) return WSR_ERR_INVALID_ARG;
         if (tiles->schedule != WSR_SCHEDULE_TILE_BLOCKS && tiles->schedule != WSR_SCHEDULE_PERSISTENT)
             return WSR_ERR_INVALID_ARG;
         if (!tiles_ok(tiles)) return WSR_ERR_UNSUPPORTED;
+        if (tiles->chunk != 0 && tiles->chunk != 64 && tiles->chunk != 128) return WSR_ERR_UNSUPPORTED;
         tw = tiles->tile_w;
         th = tiles->tile_h;
         sched = tiles->schedule;
+        chunk = tiles->chunk ? tiles->chunk : 128;
     }
     memset(vs, 0, sizeof(Views));
     vs->n = n_cams;
     vs->tile_w = tw;
     vs->tile_h = th;
     vs->schedule = sched;
+    vs->chunk = chunk;
     long long tile_base = 0, pix_base = 0;
     for (int v = 0; v < n_cams; ++v) {
         const wsr_camera& c = cams[v];

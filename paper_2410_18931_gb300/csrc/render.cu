@@ -227,7 +227,7 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
 
 // Backward, one block per tile, balanced over (pixel, Gaussian) pairs.
 //
-// For each chunk of up to kBwdChunk Gaussians of the tile:
+// For each chunk of up to CH Gaussians of the tile:
 //   A. two threads per Gaussian compute, for their half of the tile's rows,
 //      the span of pixels whose centre can lie inside the footprint (the
 //      roots of the quadratic q(dx) = 9 on that row, widened slightly);
@@ -245,23 +245,22 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
 //   D. thread j sums Gaussian j's slots and adds them to its global record.
 // Every pair is still tested with the forward's exact arithmetic (q <= 9), so
 // forward and backward agree on which pairs exist.
-constexpr int kBwdThreads = 256;
-constexpr int kBwdChunk = 128;
+// Gaussians per chunk (CH, a template parameter: 128 by default, or 64) and
+// threads per block (2 CH).
 
 template <int TW> struct UnitCode;                    // bits of the column in a unit byte
 template <> struct UnitCode<8> { static constexpr int XB = 3; };
 template <> struct UnitCode<16> { static constexpr int XB = 4; };
 template <> struct UnitCode<32> { static constexpr int XB = 5; };
 
-template <int TW, int TH>
+template <int TW, int TH, int CH>
 __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restrict__ rec,
                                          const unsigned* __restrict__ offsets, const unsigned* __restrict__ list,
                                          const Views& vs, const float* __restrict__ wparams,
                                          const float* __restrict__ out_rgb, const float* __restrict__ out_den,
                                          const float* __restrict__ grad_rgb, float* __restrict__ grec,
                                          float* __restrict__ gw) {
-    constexpr int NT = kBwdThreads;
-    constexpr int CH = kBwdChunk;
+    constexpr int NT = 2 * CH;
     constexpr int NW = NT / 32;
     constexpr int PW = TW + 1;                          // pixel-table row pitch: one zero column
     constexpr int XB = UnitCode<TW>::XB;
@@ -562,15 +561,15 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
     }
 }
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(kBwdThreads, 4)
+template <int TW, int TH, int CH>
+__global__ void __launch_bounds__(2 * CH, 512 / CH)
     k_render_bwd(const float4* __restrict__ rec, const unsigned* __restrict__ offsets,
                  const unsigned* __restrict__ list, const Views vs, const float* __restrict__ wparams,
                  const float* __restrict__ out_rgb, const float* __restrict__ out_den,
                  const float* __restrict__ grad_rgb, float* __restrict__ grec, float* __restrict__ gw,
                  const unsigned* __restrict__ order, unsigned* __restrict__ counter) {
     for_each_tile(order, counter, vs.total_tiles, [&](int tile) {
-        bwd_tile<TW, TH>(tile, rec, offsets, list, vs, wparams, out_rgb, out_den, grad_rgb, grec, gw);
+        bwd_tile<TW, TH, CH>(tile, rec, offsets, list, vs, wparams, out_rgb, out_den, grad_rgb, grec, gw);
     });
 }
 
@@ -600,18 +599,26 @@ cudaError_t fwd_t(const float* rec, const unsigned* off, const unsigned* list, c
     return cudaGetLastError();
 }
 
-template <int TW, int TH>
-cudaError_t bwd_t(const float* rec, const unsigned* off, const unsigned* list, const Views& vs, WeightDev w,
-                  const float* rgb, const float* den, const float* grgb, float* grec, float* gw, Sched sched,
-                  cudaStream_t s) {
-    const unsigned grid = grid_for(k_render_bwd<TW, TH>, kBwdThreads, vs, sched);
+template <int TW, int TH, int CH>
+cudaError_t bwd_chunk(const float* rec, const unsigned* off, const unsigned* list, const Views& vs, WeightDev w,
+                      const float* rgb, const float* den, const float* grgb, float* grec, float* gw, Sched sched,
+                      cudaStream_t s) {
+    const unsigned grid = grid_for(k_render_bwd<TW, TH, CH>, 2 * CH, vs, sched);
     if (sched.order) {
         cudaError_t e = cudaMemsetAsync(sched.counter, 0, sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
     }
-    k_render_bwd<TW, TH><<<grid, kBwdThreads, 0, s>>>(reinterpret_cast<const float4*>(rec), off, list, vs, w.params,
-                                                      rgb, den, grgb, grec, gw, sched.order, sched.counter);
+    k_render_bwd<TW, TH, CH><<<grid, 2 * CH, 0, s>>>(reinterpret_cast<const float4*>(rec), off, list, vs, w.params,
+                                                     rgb, den, grgb, grec, gw, sched.order, sched.counter);
     return cudaGetLastError();
+}
+
+template <int TW, int TH>
+cudaError_t bwd_t(const float* rec, const unsigned* off, const unsigned* list, const Views& vs, WeightDev w,
+                  const float* rgb, const float* den, const float* grgb, float* grec, float* gw, Sched sched,
+                  cudaStream_t s) {
+    if (vs.chunk == 64) return bwd_chunk<TW, TH, 64>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, sched, s);
+    return bwd_chunk<TW, TH, 128>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, sched, s);
 }
 
 // Diagnostic: (pixel, Gaussian) pairs inside the cutoff, i.e. the

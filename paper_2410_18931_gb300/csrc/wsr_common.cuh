@@ -40,7 +40,7 @@ struct Views {
     int total_tiles;
     long long total_pix;
     int schedule;         // WSR_SCHEDULE_*
-    int pad;
+    int chunk;            // Gaussians per block of the backward (64 or 128)
     View v[WSR_MAX_VIEWS];
 };
 

@@ -75,13 +75,16 @@ class FrameState:
 class Renderer:
     """Renders a fixed set of views at a fixed tile shape."""
 
-    def __init__(self, cams, tile=(16, 16), device="cuda", headroom: float = 1.25, persistent: bool = False):
+    def __init__(self, cams, tile=(16, 16), device="cuda", headroom: float = 1.25, persistent: bool = False,
+                 chunk: int = 0):
         self.lib = A.load()
         self.device = torch.device(device)
         self.cams = list(cams)
         self.cams_c, self.n_cams = A.make_cameras(self.cams)
         self.persistent = bool(persistent)
-        self.tiles_c = A.tiles(*tile, A.WSR_SCHEDULE_PERSISTENT if persistent else A.WSR_SCHEDULE_TILE_BLOCKS)
+        self.tiles_c = A.tiles(*tile, A.WSR_SCHEDULE_PERSISTENT if persistent else A.WSR_SCHEDULE_TILE_BLOCKS,
+                               chunk)
+        self.chunk = int(chunk)
         self.tile = tuple(tile)
         self.num_tiles = int(self.lib.wsr_num_tiles(self.cams_c, self.n_cams, ctypes.byref(self.tiles_c)))
         self.num_pix = int(self.lib.wsr_num_pixels(self.cams_c, self.n_cams))

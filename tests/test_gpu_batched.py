@@ -83,6 +83,31 @@ def test_autotune_returns_a_measured_valid_choice():
     npix = sum(c.width * c.height for c in cams)
     target = torch.rand(npix, 3, device="cuda")
     res = autotune(g, cams, w.kind, wpar, target, reps=2)
-    assert len(res["table"]) == 6 and all(t["ok"] for t in res["table"])
+    assert len(res["table"]) == 12 and all(t["ok"] for t in res["table"])      # 3 shapes x 2 schedules x 2 chunks
+    assert res["chunk"] in (64, 128)
     assert res["ms"] == min(t["ms"] for t in res["table"])
     assert autotune(g, cams, w.kind, wpar, target) is res      # cached
+
+
+@pytest.mark.parametrize("tile,persistent", [((16, 16), False), ((32, 8), True), ((8, 8), True)])
+def test_backward_with_64_gaussians_per_block_matches_oracle(tile, persistent):
+    """The backward's chunk size changes only the schedule: gradients with 64
+    Gaussians per block against the oracle (summed over the views)."""
+    import torch
+    from paper_2410_18931_gb300 import Gaussians, Renderer
+    sc, cams, w = _scene_and_views()
+    g = Gaussians.from_scene(sc)
+    wpar = torch.tensor(w.as_array(), device="cuda")
+    r = Renderer(cams, tile=tile, persistent=persistent, chunk=64)
+    st = r.forward(g, w.kind, wpar)
+    rng = np.random.default_rng(9)
+    Gs = [rng.normal(size=(c.height, c.width, 3)).astype(np.float32) for c in cams]
+    out = r.backward(g, w.kind, wpar, st, torch.from_numpy(np.concatenate([x.reshape(-1, 3) for x in Gs])).cuda())
+    torch.cuda.synchronize()
+    env = None
+    for cam, Gv in zip(cams, Gs):
+        e = grad_envelope(sc, cam, w, Gv.astype(np.float64))
+        env = e if env is None else add_envelopes(env, e)
+    for k in ("means", "log_scales", "quats", "sh", "opacity", "lc_v"):
+        ex = grad_excess(out[k].cpu().numpy(), env, k)
+        assert ex <= GRAD_TOL, (tile, persistent, k, ex)
