@@ -704,8 +704,9 @@ def _hbm_peak() -> float:
 def run_reduced(reps: int = 3, cpu_leg: bool = True) -> dict:
     """6M Gaussians, 8 views of 3840x2160: forward with reduced storage (bf16
     scales/quats, f16 SH/opacity, FP32 accumulation) for all views in one set
-    of launches, against the plain FP32 single-view forward on the same
-    scene; the image difference between the two is reported."""
+    of launches with the fastest tile shape (each timed), against the plain
+    FP32 single-view forward (16x16 tiles) on the same scene; the image
+    difference between the two is reported."""
     import numpy as np
     import torch
 
@@ -719,18 +720,25 @@ def run_reduced(reps: int = 3, cpu_leg: bool = True) -> dict:
     g16 = Gaussians.from_scene(scene, reduced=True)
     stored = ws.quantize_reduced(scene) if cpu_leg else None     # the values the reduced path stores
     del scene
-    r = Renderer(cams, tile=(16, 16), persistent=True, headroom=1.2)
-    st = r.forward(g16, weight.kind, wpar)
+    # the forward's tile shape, picked by timing each (all views in one set of launches, persistent)
+    tile_ms = {}
+    best = None
+    for tile in ((16, 16), (16, 8), (32, 8), (8, 8)):
+        r = Renderer(cams, tile=tile, persistent=True, headroom=1.2)
+        st = r.forward(g16, weight.kind, wpar)
 
-    def fwd():
-        r.wsr_project(g16, weight.kind, wpar, st.records)
-        r.wsr_bin(st.records, g16.n, st.tile_offsets, st.tile_list)
-        r.wsr_render_fwd(st.records, g16.n, st.tile_offsets, st.tile_list, weight.kind, wpar, st.rgb, st.den)
-    ms = _events_ms(fwd, reps)
-    assert r.wsr_check() == 0
-    red_rgb = st.rgb.clone()
-    del st, r
-    torch.cuda.empty_cache()
+        def fwd():
+            r.wsr_project(g16, weight.kind, wpar, st.records)
+            r.wsr_bin(st.records, g16.n, st.tile_offsets, st.tile_list)
+            r.wsr_render_fwd(st.records, g16.n, st.tile_offsets, st.tile_list, weight.kind, wpar, st.rgb, st.den)
+        t = _events_ms(fwd, reps)
+        assert r.wsr_check() == 0
+        tile_ms["%dx%d" % tile] = round(t, 3)
+        if best is None or t < best[0]:
+            best = (t, tile, st.rgb.clone())
+        del st, r
+        torch.cuda.empty_cache()
+    ms, best_tile, red_rgb = best
     single_ms, o, err, se = 0.0, 0, 0.0, 0.0
     for cam in cams:
         m = cam.width * cam.height
@@ -755,6 +763,7 @@ def run_reduced(reps: int = 3, cpu_leg: bool = True) -> dict:
     return {"workload": extra["name"], "gaussians": g16.n, "views": len(cams), "mpix_per_step": round(npix / 1e6, 3),
             "cpu_baseline": cpu,
             "fwd_mpix_s": round(npix / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms, 3),
+            "tile": "%dx%d" % best_tile, "persistent": True, "tile_ms": tile_ms,
             "storage": "bf16 log-scales/quats, f16 SH/opacity, f32 means, FP32 accumulation",
             "single_view_fp32_fwd_mpix_s": round(npix / (single_ms * 1e-3) / 1e6, 2),
             "speedup_vs_single_view_fp32": round(single_ms / ms, 3),
