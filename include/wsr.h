@@ -280,7 +280,8 @@ wsr_status wsr_project_bwd(const wsr_gaussians* g, const wsr_camera* cams, int32
 /*
  * wsr_loss_l1 — mean absolute error against a target and its gradient
  * (the L1 part of the 3DGS loss of Sec. 4.4, used to drive the backward).
- *   loss_out [1] float32 (overwritten), grad_rgb [num_pixels * 3] (overwritten)
+ *   loss_out [1] float32 (overwritten), grad_rgb [num_pixels * 3] (overwritten);
+ *   rgb, target and grad_rgb 16-byte aligned (WSR_ERR_INVALID_ARG otherwise)
  */
 wsr_status wsr_loss_l1(const float* rgb, const float* target, int64_t count, float* loss_out,
                        float* grad_rgb, void* stream);

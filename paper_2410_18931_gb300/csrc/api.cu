@@ -419,6 +419,7 @@ wsr_status wsr_count_pairs(const float* records, int64_t n, const uint32_t* tile
 wsr_status wsr_loss_l1(const float* rgb, const float* target, int64_t count, float* loss_out, float* grad_rgb,
                        void* stream) {
     if (count < 0 || !loss_out || (count > 0 && (!rgb || !target || !grad_rgb))) return WSR_ERR_INVALID_ARG;
+    if (count > 0 && (!aligned16(rgb) || !aligned16(target) || !aligned16(grad_rgb))) return WSR_ERR_INVALID_ARG;
     return cuda_status(launch_loss_l1(rgb, target, count, loss_out, grad_rgb, (cudaStream_t)stream));
 }
 

@@ -110,6 +110,9 @@ def test_argument_errors_are_returned(lib):
                               fake, fake, fake, fake, None, fake, ws, None) == A.WSR_ERR_INVALID_ARG
     # negative counts
     assert lib.wsr_loss_l1(fake, fake, -1, fake, fake, None) == A.WSR_ERR_INVALID_ARG
+    # the L1 loss reads and writes float4: every array 16-byte aligned
+    assert lib.wsr_loss_l1(fake + 4, fake, 12, fake, fake, None) == A.WSR_ERR_INVALID_ARG
+    assert lib.wsr_loss_l1(fake, fake, 12, fake, fake + 8, None) == A.WSR_ERR_INVALID_ARG
     assert lib.wsr_check(None, 0, None) == A.WSR_ERR_INVALID_ARG
 
 

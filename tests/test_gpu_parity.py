@@ -302,18 +302,26 @@ def test_autograd_function_matches_raw_backward():
     assert rel_err(wpar.grad.cpu().numpy(), raw["weight_params"].cpu().numpy()) < 1e-5
 
 
-def test_l1_loss_kernel():
+@pytest.mark.parametrize("pixels", [1, 33 * 17, 1920 * 1080 + 7])
+def test_l1_loss_kernel(pixels):
+    """Mean absolute error and its sign gradient, vectorised body plus the
+    scalar tail (3 * pixels is 3, 1683 and 6,220,821: tails of 3, 3 and 1),
+    with exact ties where the gradient is zero."""
     import torch
     from paper_2410_18931_gb300 import Renderer
     cam = ws.look_at((0.0, 0.0, -3.0), width=33, height=17)
     r = Renderer([cam])
-    a = torch.rand(33 * 17, 3, device="cuda")
-    b = torch.rand(33 * 17, 3, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(pixels)
+    a = torch.rand(pixels, 3, device="cuda", generator=gen)
+    b = torch.rand(pixels, 3, device="cuda", generator=gen)
+    b.view(-1)[::5] = a.view(-1)[::5]
     loss = torch.empty(1, device="cuda")
     g = torch.empty_like(a)
     r.loss_l1(a, b, loss, g)
     ref = (a.double() - b.double()).abs().mean()
-    assert abs(loss.item() - ref.item()) < 1e-6
+    # FP32 summation: the longest chain of additions (a thread's strided terms,
+    # the warp and block trees, one atomic per block) stays under 700 terms
+    assert abs(loss.item() - ref.item()) <= 700 * 2.0 ** -24 * ref.item() + 1e-9
     assert torch.equal(g, torch.sign(a - b) / a.numel())
 
 
