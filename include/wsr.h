@@ -246,9 +246,15 @@ wsr_status wsr_render_fwd(const float* records, int64_t n, const uint32_t* tile_
  * projection, given grad_rgb = dL/dC.  Two stages:
  *   (1) per tile, recompute every (pixel, Gaussian) term from the records and
  *       reduce into grad_records [n_cams, n, 12] float32 (overwritten):
- *       {dL/dmu_x, dL/dmu_y, dL/da, dL/db, dL/dc, dL/d(uw) at fixed c uw,
- *        dL/d(c uw) (3), 0, 0, 0}; (a, b, c) the entries of
- *       Sigma_2D = [[a, b], [b, c]] (dilation included, b one variable);
+ *       {Sr, Sx, Srr, Srx, Sxx, dL/d(uw) at fixed c uw, dL/d(c uw) (3),
+ *        0, 0, 0}, where, over the Gaussian's pixels with q <= 9 and with
+ *       gq = dL/dq' (q' = q log2(e)/2 = r^2 + qd dx^2, r = qs dy + qw dx,
+ *       dx, dy = pixel centre - mu, qs, qw, qd as in the render record):
+ *       Sr = sum gq r, Sx = sum gq dx, Srr = sum gq r^2, Srx = sum gq r dx,
+ *       Sxx = sum gq dx^2.  Then dL/dmu_x = -2 (qw Sr + qd Sx),
+ *       dL/dmu_y = -2 qs Sr and, with w = (qw, qs), e1 = (1, 0),
+ *       dL/dSigma_2D = -(Srr w w^t + qd Srx (w e1^t + e1 w^t)
+ *                        + qd^2 Sxx e1 e1^t) / (log2(e)/2);
  *       plus the background terms dL/dw_B, dL/dc_B;
  *   (2) per Gaussian, chain grad_records back to the stored parameters.
  * `g` must be the scene given to wsr_project; out_rgb / out_den come from

@@ -335,21 +335,35 @@ __global__ void __launch_bounds__(128) k_project_bwd(const GaussPtrs g, const Vi
                 gsig += gw * P.lcv * tz / (sigma * sigma);
                 gt[2] += gw * (-P.lcv / sigma);
             }
-            // projected mean
+            // The record holds moments of gq = dL/dq' over the Gaussian's pixels in the sum-of-squares
+            // frame of q' = r^2 + qd dx^2, r = qs dy + qw dx (qs, qw, qd exactly as rendered):
+            // Sr = sum gq r, Sx = sum gq dx, Srr = sum gq r^2, Srx = sum gq r dx, Sxx = sum gq dx^2.
+            const float Sr = g9[0], Sx = g9[1], Srr = g9[2], Srx = g9[3], Sxx = g9[4];
+            const float qs = G.qs, qw = G.qw, qd = G.qd;
+            // projected mean: dq'/dmu_x = -2 (r qw + qd dx), dq'/dmu_y = -2 r qs
+            const float gmx = -2.0f * fmaf(qw, Sr, qd * Sx), gmy = -2.0f * qs * Sr;
             const float iz = 1.0f / tz, iz2 = iz * iz;
-            gt[0] += g9[0] * V.fx * iz;
-            gt[1] += g9[1] * V.fy * iz;
-            gt[2] += -(g9[0] * V.fx * tx + g9[1] * V.fy * ty) * iz2;
+            gt[0] += gmx * V.fx * iz;
+            gt[1] += gmy * V.fy * iz;
+            gt[2] += -(gmx * V.fx * tx + gmy * V.fy * ty) * iz2;
 
-            // the gradient record holds dL/d(a, b, c) of Sigma_2D = [[a, b], [b, c]] directly (formed
-            // per pixel from Sigma_2D^{-1} d, without passing through the conic's entries)
-            const float ga = g9[2], gb = g9[3], gc = g9[4];
-            // Sigma_2D = (r0.r0 + 0.3, r0.r1, r1.r1 + 0.3)
+            // Sigma_2D = T T^t + 0.3 I with rows r0, r1 of T = J W R S.  With v = k Sigma_2D^{-1} d =
+            // r w + qd dx e1 (w = (qw, qs), e1 = (1, 0), k = log2(e)/2), dq'/dSigma_2D = -v v^t / k, so
+            //   dL/dSigma_2D = -(Srr w w^t + qd Srx (w e1^t + e1 w^t) + qd^2 Sxx e1 e1^t) / k
+            // and dL/dT = 2 dL/dSigma_2D T is taken in that factored form: with z = w^t T = qw r0 + qs r1,
+            //   dL/dr0 = -2/k (qw P1 + P2),  dL/dr1 = -2/k qs P1,
+            //   P1 = Srr z + qd Srx r0,  P2 = qd Srx z + qd^2 Sxx r0.
+            // For a thin footprint z is nearly orthogonal to the long axis, so the large Srr terms
+            // stay off that axis instead of cancelling there in FP32.
+            const float c2 = -2.0f / kHalfLog2e, qsx = qd * Srx, qxx = qd * qd * Sxx;
             float gr0[3], gr1[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                gr0[k] = 2.0f * ga * G.r0[k] + gb * G.r1[k];
-                gr1[k] = 2.0f * gc * G.r1[k] + gb * G.r0[k];
+                const float z = fmaf(qw, G.r0[k], qs * G.r1[k]);
+                const float P1 = fmaf(Srr, z, qsx * G.r0[k]);
+                const float P2 = fmaf(qsx, z, qxx * G.r0[k]);
+                gr0[k] = c2 * fmaf(qw, P1, P2);
+                gr1[k] = c2 * qs * P1;
             }
             // r0 = J00 m0 + J02 m2,  r1 = J11 m1 + J12 m2  (m_k: rows of M = W R S)
             float gJ00 = 0.f, gJ02 = 0.f, gJ11 = 0.f, gJ12 = 0.f, gM[9];

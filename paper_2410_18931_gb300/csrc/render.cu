@@ -455,17 +455,18 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 uend = soff[jj + 1];
             };
             load_gaussian(j);
-            // accumulators, paired: (cuw_r, cuw_g), (cuw_b, uw); and, over the two pixels of a unit, with
-            // v = (r qw + qd dx, r qs) = log2(e)/2 Sigma_2D^{-1} (dx, dy) and gq = dL/dq':
-            // sum gq v_x^2, sum gq v_x v_y, sum gq v_y^2, sum gq v_x, sum gq v_y
+            // accumulators, paired: (cuw_r, cuw_g), (cuw_b, uw); and, over the two pixels of a unit, the
+            // moments of gq = dL/dq' in the record's own frame (r = qs dy + qw dx, dx):
+            // sum gq r^2, sum gq r dx, sum gq dx^2, sum gq r, sum gq dx.  Kept apart, a thin
+            // footprint's small along-axis terms (dx) are not rounded away under its large r terms.
             float2 g01 = f2(0.f, 0.f), g23 = f2(0.f, 0.f);
-            float2 sxx = f2(0.f, 0.f), sxy = sxx, syy = sxx, sx = sxx, sy = sxx;
+            float2 srr = f2(0.f, 0.f), srx = srr, sxx = srr, sr = srr, sx = srr;
             auto store_slot = [&](int sl) {
                 sslot[sl][0] = g01;
                 sslot[sl][1] = g23;
-                sslot[sl][2] = f2(sxx.x + sxx.y, syy.x + syy.y);
-                sslot[sl][3] = f2(sx.x + sx.y, sy.x + sy.y);
-                sslot[sl][4] = f2(sxy.x + sxy.y, 0.f);
+                sslot[sl][2] = f2(srr.x + srr.y, sxx.x + sxx.y);
+                sslot[sl][3] = f2(sr.x + sr.y, sx.x + sx.y);
+                sslot[sl][4] = f2(srx.x + srx.y, 0.f);
             };
             // one or two units per step: two independent chains overlap their latencies; the second
             // unit is masked out (e = 0) when it lies past the slice or the current Gaussian
@@ -490,21 +491,18 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 const float2 m0 = __ffma2_rn(f2(P0.z, P0.w), cw1, __fmul2_rn(f2(P0.x, P0.y), cw0));
                 const float2 m1 = __ffma2_rn(f2(P1.z, P1.w), cw1, __fmul2_rn(f2(P1.x, P1.y), cw0));
                 const float2 gq = __fmul2_rn(f2(e0, e1), f2(m0.x + m0.y, m1.x + m1.y));
-                // v for both pixels, from the sum of squares: no cancelling large terms even for needles
-                const float2 vx = __ffma2_rn(rr, qw2, __fmul2_rn(qd2, dx));
-                const float2 vy = __fmul2_rn(rr, qs2);
-                const float2 tx = __fmul2_rn(gq, vx), ty = __fmul2_rn(gq, vy);
-                sxx = __ffma2_rn(tx, vx, sxx);
-                sxy = __ffma2_rn(tx, vy, sxy);
-                syy = __ffma2_rn(ty, vy, syy);
+                const float2 tr = __fmul2_rn(gq, rr), tx = __fmul2_rn(gq, dx);
+                srr = __ffma2_rn(tr, rr, srr);
+                srx = __ffma2_rn(tr, dx, srx);
+                sxx = __ffma2_rn(tx, dx, sxx);
+                sr = __fadd2_rn(sr, tr);
                 sx = __fadd2_rn(sx, tx);
-                sy = __fadd2_rn(sy, ty);
             };
             for (unsigned u = u0; u < u1;) {
                 if (u == uend) {
                     // the next Gaussian with units: store this one's sums, zero slots for any between
                     store_slot(slot++);
-                    g01 = g23 = sxx = sxy = syy = sx = sy = f2(0.f, 0.f);
+                    g01 = g23 = srr = srx = sxx = sr = sx = f2(0.f, 0.f);
                     ++j;
                     while (soff[j + 1] <= u) {
 #pragma unroll
@@ -534,22 +532,19 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 if ((int)sslotj[mid] < tid) lo = mid + 1;
                 else hi = mid;
             }
-            float2 v01 = f2(0.f, 0.f), v23 = f2(0.f, 0.f), vxy = f2(0.f, 0.f), vm = f2(0.f, 0.f);
+            float2 v01 = f2(0.f, 0.f), v23 = f2(0.f, 0.f), vrx = f2(0.f, 0.f), vm = f2(0.f, 0.f);
             float vc = 0.f;
             for (int t = lo; t < nslots && (int)sslotj[t] == tid; ++t) {
                 v01 = __fadd2_rn(v01, sslot[t][0]);
                 v23 = __fadd2_rn(v23, sslot[t][1]);
-                vxy = __fadd2_rn(vxy, sslot[t][2]);
+                vrx = __fadd2_rn(vrx, sslot[t][2]);
                 vm = __fadd2_rn(vm, sslot[t][3]);
                 vc += sslot[t][4].x;
             }
-            // q' = k d^T Sigma_2D^{-1} d, d = p - mu, k = log2(e)/2, v = k Sigma_2D^{-1} d:
-            // dq'/dmu = -2 v, and for Sigma_2D = [[a, b], [b, c]] (b one variable)
-            // dq'/da = -v_x^2 / k, dq'/db = -2 v_x v_y / k, dq'/dc = -v_y^2 / k
-            constexpr float ik = 1.0f / kHalfLog2e;
+            // record: sum gq r, sum gq dx, sum gq r^2, sum gq r dx, sum gq dx^2, d/d(u w), d/d(c u w)
             float4* o = reinterpret_cast<float4*>(grec + (size_t)WSR_GRAD_RECORD_FLOATS * sidx[tid]);
-            atomicAdd(o, make_float4(-2.0f * vm.x, -2.0f * vm.y, -ik * vxy.x, -2.0f * ik * vc));
-            atomicAdd(o + 1, make_float4(-ik * vxy.y, v23.y, v01.x, v01.y));
+            atomicAdd(o, make_float4(vm.x, vm.y, vrx.x, vc));
+            atomicAdd(o + 1, make_float4(vrx.y, v23.y, v01.x, v01.y));
             atomicAdd(reinterpret_cast<float*>(o + 2), v23.x);
         }
     }

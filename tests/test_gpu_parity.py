@@ -109,6 +109,7 @@ def _grad_case(scene, cam, weight, tile=(16, 16)):
     G = np.random.default_rng(5).normal(size=(cam.height, cam.width, 3)).astype(np.float32)
     out = r.backward(g, weight.kind, wpar, st, torch.tensor(G, device="cuda").reshape(-1, 3))
     torch.cuda.synchronize()
+    out["records"] = st.records
     env = grad_envelope(scene, cam, weight, G.astype(np.float64))
     return out, env
 
@@ -150,8 +151,21 @@ def test_gradient_records_match_oracle():
     conv = gr.copy()
     conv[:, 6:9] = gr[:, 6:9] * uw[:, None]
     conv[:, 5] = gr[:, 5] + (gr[:, 6:9] * col).sum(1)
-    # the kernel stores dL/d(a, b, c) of Sigma_2D = [[a, b], [b, c]]; the oracle gives dL/d(A, B, C) of the
-    # conic K = Sigma_2D^{-1} (q = A dx^2 + 2B dx dy + C dy^2): dL/dSigma = -K G K, G = [[dA, dB/2], [dB/2, dC]]
+    # the kernel stores moments of gq = dL/dq' in the frame of the render record's sum of squares
+    # q' = r^2 + qd dx^2, r = qs dy + qw dx: {Sr, Sx, Srr, Srx, Sxx}.  In FP64, with the record's own
+    # (qs, qw, qd) and v = (qw r + qd dx, qs r) = k Sigma_2D^{-1} d, they give dL/dmu = -2 sum gq v and
+    # dL/d(a, b, c) of Sigma_2D = [[a, b], [b, c]] (b one variable) = -sum gq (vx^2, 2 vx vy, vy^2) / k
+    rec = out["records"].cpu().numpy().reshape(-1, 12).astype(np.float64)
+    qs, qw, qd = rec[:, 2], rec[:, 3], rec[:, 4]
+    Sr, Sx, Srr, Srx, Sxx = (gr[:, k].copy() for k in range(5))
+    kk = 0.5 / np.log(2.0)
+    conv[:, 0] = -2.0 * (qw * Sr + qd * Sx)
+    conv[:, 1] = -2.0 * qs * Sr
+    conv[:, 2] = -(qw * qw * Srr + 2.0 * qw * qd * Srx + qd * qd * Sxx) / kk
+    conv[:, 3] = -2.0 * qs * (qw * Srr + qd * Srx) / kk
+    conv[:, 4] = -qs * qs * Srr / kk
+    # the oracle gives dL/d(A, B, C) of the conic K = Sigma_2D^{-1} (q = A dx^2 + 2B dx dy + C dy^2):
+    # dL/dSigma = -K G K, G = [[dA, dB/2], [dB/2, dC]]
     A, B, C = (P["conic"][:, k] for k in range(3))
 
     def to_sigma(g):
