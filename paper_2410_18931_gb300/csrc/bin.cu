@@ -9,8 +9,9 @@
 //   k_bin<false>   count: atomicAdd into every tile the footprint reaches
 //   k_scan_*       exclusive scan of the per-tile counts (three phases)
 //   k_bin<true>    scatter: claim a slot per (Gaussian, tile) and store
-// A tile is listed when the footprint q <= 9 reaches one of its pixel
-// centres (exact ellipse-rectangle test), not merely its bounding box.
+// A tile is listed when a pixel-centre column of it meets the footprint
+// q <= 9 within the tile's band of pixel-centre rows (the ellipse's exact
+// extent per tile row), not merely when it meets the bounding box.
 #include "wsr_launch.h"
 
 namespace wsr {
@@ -33,85 +34,140 @@ __device__ __forceinline__ bool pixel_rect(const float4 r0, const float4 r2, con
     return jx0 <= jx1 && jy0 <= jy1;
 }
 
-// Binning pass.  Each warp takes 32 consecutive Gaussians of one view; their
-// tile rectangles are laid end to end (warp scan) and the lanes walk that
-// list of candidate (Gaussian, tile) pairs together, 32 at a time, so a large
-// footprint is spread over the warp.  A candidate counts when the footprint
-// reaches a pixel centre of the tile.  COUNT: atomicAdd per tile.  SCATTER:
-// claim a slot in the tile's segment and write the record index.
+// Binning pass.  Each warp takes 32 consecutive Gaussians of one view.  A
+// Gaussian's work is cut into segments, one per tile row of its pixel
+// rectangle (and, for footprints wider than kPiece tiles, one per kPiece
+// tiles of that row); the warp lays its segments end to end and takes them
+// 32 at a time, one per lane, so a large footprint is spread over the warp.
+//
+// A segment needs no per-tile test: the footprint q' <= QM is an ellipse, and
+// its part inside the row's band of pixel-centre rows [y_a, y_b] is convex,
+// so the tiles of the row it reaches are those whose pixel-centre columns
+// meet that part's x-extent [x_l, x_r].  With A' = qw^2 + qd, B' = qs qw,
+// C' = qs^2 the right edge of the ellipse at height dy is
+//     x(dy) = (-B' dy + sqrt(A' QM - qd C' dy^2)) / A',
+// a concave function whose maximum sqrt(QM / qd) lies at dy* = -(qw/qs)
+// sqrt(QM / qd); x_r is x at the point of the band nearest dy*, and x_l
+// follows by symmetry.  The extent is widened by a margin far above its FP32
+// rounding error, so every pixel centre with q' <= QM is kept (a tile the
+// ellipse only passes near is listed at worst).
+//
+// The 32 segments' tile ranges are then laid end to end again and the lanes
+// take consecutive tiles, so the atomics of a warp fall on neighbouring
+// counters of a few rows.  COUNT: atomicAdd per tile.  SCATTER: claim a slot
+// in the tile's segment and write the record index.
+constexpr int kPiece = 8;
+
 template <bool SCATTER>
 __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ rec, long long n, const Views vs,
                                              unsigned* __restrict__ cursor, unsigned* __restrict__ list,
                                              unsigned long long capacity, WsHeader* hdr) {
-    __shared__ int s_end[8][32];        // inclusive prefix of candidate counts
-    __shared__ int s_rect[8][32][3];    // tx0, ty0, tiles across
-    __shared__ float s_geo[8][32][5];   // mu_x, mu_y, qs, qw, qd
+    __shared__ int s_end[8][32];        // inclusive prefix of segment counts
+    __shared__ int4 s_rect[8][32];      // pixel rectangle: jx0, jx1, jy0, jy1
+    __shared__ float4 s_geo[8][32][2];  // mu_x, mu_y, B'/A', A' QM | det', 1/A', dy*, margin
+    __shared__ int s_wend[8][32];       // inclusive prefix of the batch's tile counts
+    __shared__ int2 s_run[8][32];       // first tile (global index) and owning lane of each segment
     const int v = blockIdx.y;
     const View& V = vs.v[v];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int tw = vs.tile_w, th = vs.tile_h;
-    int cnt = 0, tx0 = 0, ty0 = 0, nx = 0;
-    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+    const int lw = __ffs(vs.tile_w) - 1, lh = __ffs(vs.tile_h) - 1;   // tile sides are powers of two
+    const float QM = kQMax * 1.0001f + 1e-4f;
+    int nseg = 0, jx0 = 0, jx1 = -1, jy0 = 0, jy1 = -1;
+    float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
     if (i < n) {
         const long long r = (long long)v * n + i;
-        r0 = __ldg(rec + 3 * r);
-        r1 = __ldg(rec + 3 * r + 1);
+        const float4 r0 = __ldg(rec + 3 * r);
+        const float qd = __ldg(reinterpret_cast<const float*>(rec + 3 * r + 1));
         const float4 r2 = __ldg(rec + 3 * r + 2);
-        int jx0, jx1, jy0, jy1;
         if (pixel_rect(r0, r2, V, jx0, jx1, jy0, jy1)) {
-            tx0 = jx0 / tw;
-            ty0 = jy0 / th;
-            nx = jx1 / tw - tx0 + 1;
-            cnt = nx * (jy1 / th - ty0 + 1);
+            const float qs = r0.z, qw = r0.w;
+            const float A = fmaf(qw, qw, qd), ia = 1.0f / A;
+            const float dxm = sqrtf(QM / qd);                   // half-width of the ellipse
+            g0 = make_float4(r0.x, r0.y, qs * qw * ia, A * QM);
+            g1 = make_float4(qd * qs * qs, ia, -(qw / qs) * dxm, fminf(2e-3f * dxm, 1e6f) + 0.01f);
+            const int pcs = ((jx1 >> lw) - (jx0 >> lw) + kPiece) / kPiece;
+            nseg = ((jy1 >> lh) - (jy0 >> lh) + 1) * pcs;
         }
     }
-    int inc = cnt;
+    int inc = nseg;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, inc, off);
         if (lane >= off) inc += y;
     }
     s_end[warp][lane] = inc;
-    s_rect[warp][lane][0] = tx0;
-    s_rect[warp][lane][1] = ty0;
-    s_rect[warp][lane][2] = nx;
-    s_geo[warp][lane][0] = r0.x;
-    s_geo[warp][lane][1] = r0.y;
-    s_geo[warp][lane][2] = r0.z;
-    s_geo[warp][lane][3] = r0.w;
-    s_geo[warp][lane][4] = r1.x;
+    s_rect[warp][lane] = make_int4(jx0, jx1, jy0, jy1);
+    s_geo[warp][lane][0] = g0;
+    s_geo[warp][lane][1] = g1;
     __syncwarp();
     const int total = __shfl_sync(0xffffffffu, inc, 31);
-    for (int base = 0; base < total; base += 32) {
-        const int c = base + lane;
+    for (int c0 = 0; c0 < total; c0 += 32) {
+        // ---- this lane's segment: its range of tiles [ta, tb] ----
+        const int c = c0 + lane;
+        int ta = 0, tb = -1, lo = 0, row = 0;
         if (c < total) {
-            // owner: first lane whose inclusive end exceeds c
-            int lo = 0, hi = 31;
+            int hi = 31;            // owner: first lane whose inclusive end exceeds c
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
                 if (s_end[warp][mid] > c) hi = mid;
                 else lo = mid + 1;
             }
-            const int k = c - (lo ? s_end[warp][lo - 1] : 0);   // candidate index within the owner's rectangle
-            const int w = s_rect[warp][lo][2];
-            const int tx = s_rect[warp][lo][0] + k % w;
-            const int ty = s_rect[warp][lo][1] + k / w;
-            const float x0 = (float)(tx * tw) + 0.5f, x1 = (float)min(tx * tw + tw, V.W) - 0.5f;
-            const float y0 = (float)(ty * th) + 0.5f, y1 = (float)min(ty * th + th, V.H) - 0.5f;
-            const float* geo = s_geo[warp][lo];
-            if (footprint_hits(geo[0], geo[1], geo[2], geo[3], geo[4], x0, x1, y0, y1)) {
-                unsigned* cur = cursor + V.tile_base + ty * V.tiles_x + tx;
-                if constexpr (SCATTER) {
-                    const unsigned slot = atomicAdd(cur, 1u);
-                    const long long rid = (long long)v * n + (long long)blockIdx.x * blockDim.x + warp * 32 + lo;
-                    if (slot < capacity) list[slot] = (unsigned)rid;
-                    else set_error(hdr, WSR_ERR_CAPACITY);
-                } else {
-                    atomicAdd(cur, 1u);
-                }
+            const int k = c - (lo ? s_end[warp][lo - 1] : 0);   // segment index within the owner
+            const int4 rc = s_rect[warp][lo];
+            const float4 a = s_geo[warp][lo][0], b = s_geo[warp][lo][1];
+            const int np = ((rc.y >> lw) - (rc.x >> lw) + kPiece) / kPiece;
+            const int kr = np == 1 ? k : k / np, kp = k - kr * np;
+            const int ty = (rc.z >> lh) + kr;
+            // the row's band of pixel-centre rows, inside the footprint's rows
+            const float dya = (float)max(ty << lh, rc.z) + 0.5f - a.y;
+            const float dyb = (float)min(((ty + 1) << lh) - 1, rc.w) + 0.5f - a.y;
+            auto edge = [&](float dy, float side) {
+                return fmaf(-a.z, dy, side * sqrtf(fmaxf(fmaf(-b.x * dy, dy, a.w), 0.0f)) * b.y);
+            };
+            const float xr = edge(fminf(fmaxf(b.z, dya), dyb), 1.0f);
+            const float xl = edge(fminf(fmaxf(-b.z, dya), dyb), -1.0f);
+            // pixel columns whose centre lies in [mu_x + x_l, mu_x + x_r] (widened), clipped to the rectangle
+            const float fa = fmaxf(ceilf(a.x + xl - b.w - 0.5f), (float)rc.x);
+            const float fb = fminf(floorf(a.x + xr + b.w - 0.5f), (float)rc.y);
+            if (fa <= fb) {
+                const int p0 = (rc.x >> lw) + kp * kPiece;       // this segment's tiles of the row
+                ta = max((int)fa >> lw, p0);
+                tb = min((int)fb >> lw, p0 + kPiece - 1);
+                row = V.tile_base + ty * V.tiles_x;
             }
         }
+        // ---- the batch's tiles end to end, consecutive tiles to consecutive lanes ----
+        const int wdt = max(tb - ta + 1, 0);   // a piece the band does not reach has none
+        int winc = wdt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, winc, off);
+            if (lane >= off) winc += y;
+        }
+        const int nt = __shfl_sync(0xffffffffu, winc, 31);
+        s_wend[warp][lane] = winc;
+        s_run[warp][lane] = make_int2(row + ta, lo);
+        __syncwarp();
+        for (int j = lane; j < nt; j += 32) {
+            int sl = 0, sh = 31;    // segment: first lane whose inclusive end exceeds j
+            while (sl < sh) {
+                const int mid = (sl + sh) >> 1;
+                if (s_wend[warp][mid] > j) sh = mid;
+                else sl = mid + 1;
+            }
+            const int2 run = s_run[warp][sl];
+            unsigned* cur = cursor + run.x + (j - (sl ? s_wend[warp][sl - 1] : 0));
+            if constexpr (SCATTER) {
+                const unsigned slot = atomicAdd(cur, 1u);
+                const long long rid = (long long)v * n + (long long)blockIdx.x * blockDim.x + warp * 32 + run.y;
+                if (slot < capacity) list[slot] = (unsigned)rid;
+                else set_error(hdr, WSR_ERR_CAPACITY);
+            } else {
+                atomicAdd(cur, 1u);
+            }
+        }
+        __syncwarp();
     }
 }
 

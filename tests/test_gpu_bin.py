@@ -1,0 +1,112 @@
+"""Sort-free tile binning (Sec. 4.1: no depth sort, each Gaussian listed in
+every tile its footprint reaches), checked as sets against FP64 geometry from
+the oracle's projection.
+
+What is unique: the (Gaussian, tile) pairs where some pixel centre of the tile
+has q <= 9 must all be listed (pairs within 1e-4 of the cutoff are ties and
+may go either way).  What is free: the order inside a tile, and extra pairs
+the kernel keeps for safety; each extra must still be near the footprint --
+a pixel-centre column of the tile meets the ellipse's x-extent within the
+tile's band of pixel-centre rows, widened by a small fraction of its size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import wsr_scenes as ws
+
+pytestmark = pytest.mark.gpu
+
+CUT = 9.0
+
+
+def _scene():
+    rng = np.random.default_rng(71)
+    base = ws.random_scene(2500, 72, sh_degree=1, vd_opacity=False, clusters=6, box=1.2, log_scale_mu=-3.6)
+    needles = ws.random_scene(300, 73, sh_degree=1, vd_opacity=False, box=0.9)
+    needles.log_scales[:, 0] = rng.uniform(np.log(0.2), np.log(1.2), 300).astype(np.float32)
+    needles.log_scales[:, 1:] = np.float32(np.log(2e-3))
+    big = ws.random_scene(8, 74, sh_degree=1, vd_opacity=False, box=0.6, log_scale_mu=-0.7, log_scale_sd=0.3)
+    parts = (base, needles, big)
+    return ws.Scene(*(np.concatenate([getattr(p, k) for p in parts]) for k in
+                      ("means", "log_scales", "quats", "sh", "opacity", "lc_v")), 1, False)
+
+
+def _truth(P, W, H, tw, th):
+    """Per visible Gaussian: the set of tiles holding a pixel centre with
+    q <= 9 (1 - 1e-4), and a function telling whether a tile is allowed."""
+    must, allowed = {}, {}
+    for i in np.flatnonzero(P["visible"]):
+        mx, my = P["mean2d"][i]
+        a, b, c = P["cov2d"][i]
+        det = a * c - b * b
+        A, B, C = c / det, -b / det, a / det                 # conic: q = A dx^2 + 2 B dx dy + C dy^2
+        ex, ey = np.sqrt(CUT * a), np.sqrt(CUT * c)           # extents of q <= 9
+        x0, x1 = max(int(np.ceil(mx - ex - 0.5)), 0), min(int(np.floor(mx + ex - 0.5)), W - 1)
+        y0, y1 = max(int(np.ceil(my - ey - 0.5)), 0), min(int(np.floor(my + ey - 0.5)), H - 1)
+        if x0 > x1 or y0 > y1:
+            must[i] = set()
+        else:
+            dx = np.arange(x0, x1 + 1) + 0.5 - mx
+            dy = np.arange(y0, y1 + 1) + 0.5 - my
+            q = A * dx[None, :] ** 2 + 2 * B * dx[None, :] * dy[:, None] + C * dy[:, None] ** 2
+            yy, xx = np.nonzero(q <= CUT * (1 - 1e-4))
+            must[i] = set(zip(((yy + y0) // th).tolist(), ((xx + x0) // tw).tolist()))
+        allowed[i] = (mx, my, A, B, C, ex, ey)
+    return must, allowed
+
+
+def _allowed(g, ty, tx, W, H, tw, th):
+    mx, my, A, B, C, ex, ey = g
+    # the tile's band of pixel-centre rows, inside the footprint's y-extent (the kernel pads
+    # the extents by a relative 1e-4 and 0.01 pixel: rows that close are allowed too)
+    sy = 1e-3 * ey + 0.02
+    ya = max(ty * th + 0.5, my - ey - sy) - my
+    yb = min(min(ty * th + th, H) - 0.5, my + ey + sy) - my
+    if ya > yb + 1e-9:
+        return False
+    # x-extent of {q <= 9} over dy in [ya, yb]: for fixed dy, dx = (-B dy +- sqrt(B^2 dy^2 - A (C dy^2 - 9))) / A
+    dys = np.linspace(ya, yb, 257)
+    disc = np.maximum(B * B * dys ** 2 - A * (C * dys ** 2 - CUT), 0.0)
+    xl = np.min((-B * dys - np.sqrt(disc)) / A)
+    xr = np.max((-B * dys + np.sqrt(disc)) / A)
+    d = 5e-3 * ex + 0.05 + (yb - ya) / 256 * abs(B / A)       # margin plus the sampling step in dy
+    cols = np.arange(tx * tw, min(tx * tw + tw, W)) + 0.5 - mx
+    return bool(np.any((cols >= xl - d) & (cols <= xr + d)))
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8), (16, 8)])
+def test_tile_lists_hold_exactly_the_footprint_tiles(tile):
+    import torch
+    from paper_2410_18931_gb300 import Gaussians, Renderer
+    sc = _scene()
+    cam = ws.look_at((0.3, -0.2, -3.6), width=200, height=150).rounded()
+    w = ws.WeightParams(ws.EXP, 0.1, 0.8, 0.9, (0.1, 0.2, 0.1))
+    g = Gaussians.from_scene(sc)
+    r = Renderer([cam], tile=tile)
+    st = r.forward(g, w.kind, torch.tensor(w.as_array(), device="cuda"))
+    torch.cuda.synchronize()
+    off = st.tile_offsets.cpu().numpy().astype(np.int64)
+    lst = st.tile_list.cpu().numpy().astype(np.int64)
+    tw, th = tile
+    tiles_x = -(-cam.width // tw)
+    listed = {}
+    for t in range(len(off) - 1):
+        ids = lst[off[t]:off[t + 1]]
+        assert len(np.unique(ids)) == len(ids), t                # no pair twice
+        for i in ids.tolist():
+            listed.setdefault(i, set()).add((t // tiles_x, t % tiles_x))
+    P = oracle.project(sc, cam, w)
+    must, allowed = _truth(P, cam.width, cam.height, tw, th)
+    n_must = sum(len(s) for s in must.values())
+    assert n_must > 5000
+    for i, s in must.items():
+        missing = s - listed.get(i, set())
+        assert not missing, (i, sorted(missing)[:5])
+    extra = 0
+    for i, s in listed.items():
+        assert i in allowed, i                                   # culled Gaussians are never listed
+        for ty, tx in s - must.get(i, set()):
+            assert _allowed(allowed[i], ty, tx, cam.width, cam.height, tw, th), (i, ty, tx)
+            extra += 1
+    assert extra <= 0.03 * n_must, (extra, n_must)
