@@ -37,6 +37,19 @@ __device__ __forceinline__ TileCoord tile_coord(const Views& vs, int tile) {
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
+// Hardware square root and reciprocal (relative error ~2^-22), for the
+// backward's per-row spans: they are widened by 0.02 pixel, far above that.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Pixel-per-thread layout of the pair-count diagnostic.
 template <int TW, int TH, int PPT>
 struct TileShape {
@@ -69,6 +82,7 @@ __device__ __forceinline__ void fwd_tile(const int tile, const float4* __restric
     __shared__ float4 s0[NT];   // mu_x, mu_y, qs, qw
     __shared__ float4 s1[NT];   // qd, u w, c_r u w, c_g u w
     __shared__ float2 s2[NT];   // c_b u w, u w
+    __shared__ float4 s3[NT];   // at the tile's first pixel centre: r, qd dx^2, 2 qd dx; and qd
     // with several warps: bit w of smask[j] = Gaussian j reaches a pixel centre of warp w's rows,
     // and each warp walks only the Gaussians of its own list
     __shared__ unsigned smask[NT];
@@ -79,9 +93,9 @@ __device__ __forceinline__ void fwd_tile(const int tile, const float4* __restric
     const int tid = threadIdx.x;
     const int x0 = tc.tx * TW + (tid % S::BX) * PX;
     const int y0 = tc.ty * TH + (tid / S::BX) * S::PY;
-    // pixel centres of the block (a second column is ignored when PX == 1)
-    const float2 px = f2((float)x0 + 0.5f, (float)(x0 + 1) + 0.5f);
-    const float py0 = (float)y0 + 0.5f, py1 = (float)(y0 + 1) + 0.5f;
+    // offsets of the block's pixels from the tile's first pixel (a second column is ignored when PX == 1)
+    const float2 ox = f2((float)(x0 - tc.tx * TW), (float)(x0 - tc.tx * TW + 1));
+    const float oy0 = (float)(y0 - tc.ty * TH), oy1 = oy0 + 1.0f;
 
     // accumulators per pixel (column c, row r): (N_r, N_g) and (N_b, D)
     float2 rg[2][2], bd[2][2];
@@ -102,6 +116,10 @@ __device__ __forceinline__ void fwd_tile(const int tile, const float4* __restric
             const float4 b = __ldg(p + 1);
             s1[tid] = b;
             s2[tid] = f2(__ldg(reinterpret_cast<const float*>(p + 2)), b.y);
+            {
+                const float gx = (float)(tc.tx * TW) + 0.5f - a.x, gy = (float)(tc.ty * TH) + 0.5f - a.y;
+                s3[tid] = make_float4(fmaf(a.z, gy, a.w * gx), b.x * gx * gx, 2.0f * b.x * gx, b.x);
+            }
             if constexpr (NW > 1) {
                 const float xl = (float)(tc.tx * TW) + 0.5f, xh = xl + (float)(TW - 1);
                 unsigned m = 0;
@@ -136,17 +154,15 @@ __device__ __forceinline__ void fwd_tile(const int tile, const float4* __restric
             const float4 a = s0[j];
             const float4 b = s1[j];
             const float2 cbuw = s2[j];
+            const float4 t = s3[j];
             const float2 crg = f2(b.z, b.w);
-            // q' = (qs dy + qw dx)^2 + qd dx^2, evaluated as
-            // fma(r, r, (qd dx) dx) with r = fma(qs, dy, qw dx), for both columns at once
-            const float2 dx = __fadd2_rn(px, f2(-a.x, -a.x));
-            const float2 P = __fmul2_rn(__fmul2_rn(f2(b.x, b.x), dx), dx);
-            const float2 Q = __fmul2_rn(f2(a.w, a.w), dx);
-            const float dys[2] = {py0 - a.y, py1 - a.y};
+            // q' = r^2 + qd dx^2 with dx = g_x + o_x: qd dx^2 = qd g_x^2 + o_x (2 qd g_x + o_x qd) and
+            // r = r_0 + qs o_y + qw o_x from the values at the tile's first pixel centre
+            const float2 P = __ffma2_rn(ox, __ffma2_rn(ox, f2(t.w, t.w), f2(t.z, t.z)), f2(t.y, t.y));
+            const float rys[2] = {fmaf(a.z, oy0, t.x), fmaf(a.z, oy1, t.x)};
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
-                const float2 dy = f2(dys[r], dys[r]);
-                const float2 rr = __ffma2_rn(f2(a.z, a.z), dy, Q);
+                const float2 rr = __ffma2_rn(f2(a.w, a.w), ox, f2(rys[r], rys[r]));
                 const float2 q = __ffma2_rn(rr, rr, P);
                 if (q.x <= kQMax) {
                     const float e = ex2_approx(-q.x);
@@ -277,6 +293,7 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
     __shared__ unsigned char sunit[MAXU];       // unit: row << XB | column of its first pixel
     __shared__ float2 sslot[NSLOT][5];          // partial sums per (thread, Gaussian), paired as accumulated
     __shared__ unsigned char sslotj[NSLOT];     // the Gaussian of each slot (slots are sorted by it)
+    __shared__ unsigned short sfirst[CH];       // first slot of each Gaussian with units
     __shared__ unsigned short ssbase[NT];
     __shared__ unsigned swarp[NW];
     __shared__ unsigned stot[2];                // units and slots of the chunk
@@ -342,9 +359,9 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
             const float Ap = fmaf(a.w, a.w, b.x);
             const float hb = a.z * a.w;
             const float det = b.x * a.z * a.z;
-            const float ia = 1.0f / Ap;
+            const float ia = rcp_approx(Ap);
             // rows the footprint can reach: |dy| <= sqrt(A' QM / det'), with a pixel of slack
-            const float ext = fminf(sqrtf(fmaxf(Ap * QM / det, 0.0f)), 1e6f) + 1.0f;
+            const float ext = fminf(sqrt_approx(fmaxf(Ap * QM * rcp_approx(det), 0.0f)), 1e6f) + 1.0f;
             const int ly_lo = max(half * HR, (int)floorf(a.y - ext - 0.5f) - y_org);
             const int ly_hi = min(min(y_lim, half * HR + HR) - 1, (int)ceilf(a.y + ext - 0.5f) - y_org);
 #pragma unroll
@@ -355,7 +372,7 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                     const float dy = (float)(y_org + ly) + 0.5f - a.y;
                     const float d4 = fmaf(-det * dy, dy, Ap * QM);
                     if (d4 >= 0.0f) {
-                        const float h = sqrtf(d4) * ia;
+                        const float h = sqrt_approx(d4) * ia;
                         const float cx = a.x - hb * dy * ia;
                         const float fx0 = fmaxf(ceilf(cx - h - 0.52f), (float)x_org);
                         const float fx1 = fminf(floorf(cx + h - 0.48f), (float)(x_org + x_lim - 1));
@@ -433,6 +450,11 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
             const unsigned b0 = sb + sinc - nslot;
             ssbase[tid] = (unsigned short)b0;
             for (unsigned k = 0; k < nslot; ++k) sslotj[b0 + k] = (unsigned char)(j + (int)k);
+            // a Gaussian's first slot belongs to the slice holding its first unit
+            if (nslot > 0u) {
+                if (soff[j] == u0) sfirst[j] = (unsigned short)b0;
+                for (unsigned k = 1; k < nslot; ++k) sfirst[j + (int)k] = (unsigned short)(b0 + k);
+            }
             if (tid == NT - 1) stot[1] = sb + sinc;
         }
         if (u0 < u1) {
@@ -526,12 +548,7 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
         // the slots are sorted by Gaussian, so Gaussian tid's slots are a run
         if (tid < cnt && soff[tid + 1] > soff[tid]) {
             const int nslots = (int)stot[1];
-            int lo = 0, hi = nslots;
-            while (lo < hi) {            // first slot of a Gaussian >= tid
-                const int mid = (lo + hi) >> 1;
-                if ((int)sslotj[mid] < tid) lo = mid + 1;
-                else hi = mid;
-            }
+            const int lo = sfirst[tid];
             float2 v01 = f2(0.f, 0.f), v23 = f2(0.f, 0.f), vrx = f2(0.f, 0.f), vm = f2(0.f, 0.f);
             float vc = 0.f;
             for (int t = lo; t < nslots && (int)sslotj[t] == tid; ++t) {
@@ -617,7 +634,8 @@ cudaError_t bwd_t(const float* rec, const unsigned* off, const unsigned* list, c
 }
 
 // Diagnostic: (pixel, Gaussian) pairs inside the cutoff, i.e. the
-// algorithmic work of the render kernels (same arithmetic as the forward).
+// algorithmic work of the render kernels (q' from each pixel's own dx, dy; the
+// renderers may decide pairs within rounding of the cutoff differently).
 template <int TW, int TH, int PPT>
 __global__ void __launch_bounds__(TileShape<TW, TH, PPT>::NT)
     k_count_pairs(const float4* __restrict__ rec, const unsigned* __restrict__ offsets,

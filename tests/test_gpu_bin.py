@@ -110,3 +110,48 @@ def test_tile_lists_hold_exactly_the_footprint_tiles(tile):
             assert _allowed(allowed[i], ty, tx, cam.width, cam.height, tw, th), (i, ty, tx)
             extra += 1
     assert extra <= 0.03 * n_must, (extra, n_must)
+
+
+def test_tile_lists_of_several_uneven_views_in_one_call():
+    """Three views of uneven, ragged sizes binned in one call: view v's tiles
+    follow view v-1's, and its list entries are record indices v n + i."""
+    import torch
+    from paper_2410_18931_gb300 import Gaussians, Renderer
+    sc = _scene()
+    cams = [ws.look_at((0.3, -0.2, -3.6), width=200, height=150).rounded(),
+            ws.look_at((-1.2, 0.4, -3.2), width=67, height=45).rounded(),
+            ws.look_at((2.0, 1.0, -2.8), width=130, height=97).rounded()]
+    w = ws.WeightParams(ws.EXP, 0.1, 0.8, 0.9, (0.1, 0.2, 0.1))
+    g = Gaussians.from_scene(sc)
+    tw, th = 16, 16
+    r = Renderer(cams, tile=(tw, th), persistent=True)
+    st = r.forward(g, w.kind, torch.tensor(w.as_array(), device="cuda"))
+    torch.cuda.synchronize()
+    off = st.tile_offsets.cpu().numpy().astype(np.int64)
+    lst = st.tile_list.cpu().numpy().astype(np.int64)
+    n = sc.n
+    t0 = 0
+    for v, cam in enumerate(cams):
+        tiles_x, tiles_y = -(-cam.width // tw), -(-cam.height // th)
+        listed = {}
+        for t in range(tiles_x * tiles_y):
+            ids = lst[off[t0 + t]:off[t0 + t + 1]]
+            assert len(np.unique(ids)) == len(ids)
+            assert np.all(ids // n == v), (v, t)                 # only this view's records
+            for i in (ids % n).tolist():
+                listed.setdefault(i, set()).add((t // tiles_x, t % tiles_x))
+        P = oracle.project(sc, cam, w)
+        must, allowed = _truth(P, cam.width, cam.height, tw, th)
+        n_must = sum(len(s) for s in must.values())
+        assert n_must > 500, (v, n_must)
+        for i, s in must.items():
+            assert not (s - listed.get(i, set())), (v, i)
+        extra = 0
+        for i, s in listed.items():
+            assert i in allowed, (v, i)
+            for ty, tx in s - must.get(i, set()):
+                assert _allowed(allowed[i], ty, tx, cam.width, cam.height, tw, th), (v, i, ty, tx)
+                extra += 1
+        assert extra <= 0.03 * n_must, (v, extra, n_must)
+        t0 += tiles_x * tiles_y
+    assert t0 == len(off) - 1
