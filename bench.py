@@ -35,10 +35,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# FP32 work per (pixel, Gaussian) pair inside the cutoff, counted from the
-# inner loops of the render kernels (an FMA counts 2): forward 15, backward 45.
-FLOPS_PER_PAIR_FWD = 15
-FLOPS_PER_PAIR_BWD = 45
+# FP32 work per (pixel, Gaussian) pair inside the cutoff (an FMA counts 2).
+# Forward: dx, dy 2; r = qs dy + qw dx 3; q' = r^2 + qd dx^2 4; the three
+# colour sums and the weight sum 8 -> 17.  Backward: q' as above 9; the four
+# d/d(c u w), d/d(u w) sums 8; dL/dq' = e (P . cw) 8; g r, g dx 2; the five
+# moments (three FMAs, two adds) 8 -> 35.
+FLOPS_PER_PAIR_FWD = 17
+FLOPS_PER_PAIR_BWD = 35
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 METRIC = "fwd and fwd+bwd Mpix/s at 1M Gaussians 1080p vs plain FP32 path; max err"
