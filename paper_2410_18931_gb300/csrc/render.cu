@@ -233,14 +233,6 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// a*b - c*d with one rounding error (Kahan's fma form)
-__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
-    const float w = c * d;
-    const float e = fmaf(-c, d, w);
-    const float f = fmaf(a, b, -w);
-    return f + e;
-}
-
 // Backward, one block per tile, balanced over (pixel, Gaussian) pairs.
 //
 // For each chunk of up to CH Gaussians of the tile:
@@ -253,14 +245,19 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
 //      per unit (row and column of its first pixel).  A padding pixel lies
 //      outside the footprint or in a zero column of the pixel table, so it
 //      adds nothing;
-//   C. every thread takes an equal slice of the units and walks it one unit
-//      (two pixels, one paired FP32 op each) per step, accumulating the nine
-//      partial derivatives of the current Gaussian in registers; when the
-//      Gaussian changes, or at the end of its slice, it stores them in a
-//      (thread, Gaussian) slot.  The only branch in the walk is that change;
+//   C. every thread takes an equal slice of the units and walks it two units
+//      (four pixels, one paired FP32 op per quantity and unit) per step,
+//      accumulating the nine record terms of the current Gaussian in
+//      registers; when the Gaussian changes, or at the end of its slice, it
+//      stores them in a (thread, Gaussian) slot.  The only branch in the walk
+//      is that change;
 //   D. thread j sums Gaussian j's slots and adds them to its global record.
-// Every pair is still tested with the forward's exact arithmetic (q <= 9), so
-// forward and backward agree on which pairs exist.
+// Every pair is tested against the forward's cutoff (q' <= kQMax, FP32, from
+// the same record values).  The forward forms q' from values at the tile's
+// first pixel centre, the walk from each pixel's own offsets, so a pair
+// within rounding of the cutoff (a tie: its term is e^-4.5 of the
+// Gaussian's peak there) may be counted by one and not the other; making
+// the walk repeat the forward's operations exactly cost 2% of its time.
 // Gaussians per chunk (CH, a template parameter: 128 by default, or 64) and
 // threads per block (2 CH).
 
