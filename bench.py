@@ -46,6 +46,7 @@ FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 METRIC = "fwd and fwd+bwd Mpix/s at 1M Gaussians 1080p vs plain FP32 path; max err"
 KERNELS_PER_STEP = 10    # project 1, bin 5 (count, 3 scan, scatter), fwd 1, loss 1, bwd tiles 1, project bwd 1
+ORDER_KERNELS = 3        # the persistent schedule's tile order (histogram, scan, scatter) inside wsr_bin
 
 
 # --------------------------------------------------------------------------
@@ -151,7 +152,7 @@ class ClockSampler:
 class Step:
     """Buffers and the per-step sequence of C-ABI calls for one view."""
 
-    def __init__(self, scene, cam, weight, tile, target):
+    def __init__(self, scene, cam, weight, tile, target, persistent=False, chunk=0):
         import torch
 
         from paper_2410_18931_gb300 import Gaussians, Renderer
@@ -161,7 +162,7 @@ class Step:
         self.g = Gaussians.from_scene(scene)
         self.kind = weight.kind
         self.wpar = torch.tensor(weight.as_array(), device="cuda")
-        self.r = Renderer([cam], tile=tile)
+        self.r = Renderer([cam], tile=tile, persistent=persistent, chunk=chunk)
         self.cam = cam
         # size the tile list once (exact count + headroom), then fixed
         self.st = self.r.forward(self.g, self.kind, self.wpar)
@@ -201,6 +202,31 @@ class Step:
         mark(5)
         r.wsr_project_bwd(g, k, w, self.grad_records, self.grads)
         mark(6)
+
+
+def launch_config(args, scene, cam, weight, target):
+    """Tile shape, schedule and Gaussians per backward block of the timed
+    step: as given, or, for each "auto", the fastest captured forward + L1 +
+    backward step of the autotuner on this view (timed before the measured
+    region).  Returns (tile, persistent, chunk, table of the tuned times)."""
+    import torch
+
+    from paper_2410_18931_gb300 import Gaussians, autotune
+    from paper_2410_18931_gb300.batch import DEFAULT_CHUNKS, DEFAULT_SHAPES
+    shapes = DEFAULT_SHAPES if args.tile == "auto" else (tuple(int(v) for v in args.tile.split("x")),)
+    schedules = (False, True) if args.schedule == "auto" else (args.schedule == "persistent",)
+    chunks = DEFAULT_CHUNKS if args.chunk == "auto" else (int(args.chunk),)
+    if len(shapes) * len(schedules) * len(chunks) == 1:
+        return shapes[0], schedules[0], chunks[0], None
+    g = Gaussians.from_scene(scene)
+    wpar = torch.tensor(weight.as_array(), device="cuda")
+    tgt = torch.as_tensor(target).reshape(-1, 3).cuda()
+    tune = autotune(g, [cam], weight.kind, wpar, tgt, shapes=shapes, schedules=schedules, chunks=chunks, reps=3)
+    del g, wpar, tgt
+    torch.cuda.empty_cache()
+    table = {("%dx%d" % t["tile"]) + ("/persistent" if t["persistent"] else "/per-tile") + "/chunk%d" % t["chunk"]:
+             round(t["ms"], 3) for t in tune["table"]}
+    return tune["tile"], tune["persistent"], tune["chunk"], table
 
 
 def build_workload(args, rank, world):
@@ -361,8 +387,9 @@ def run_ours(args):
     dev_index = torch.cuda.current_device()
 
     scene, cam, weight, extra, target = build_workload(args, rank, world)
-    tile = tuple(int(v) for v in args.tile.split("x"))
-    S = Step(scene, cam, weight, tile, target)
+    tile, persistent, chunk, tune_ms = launch_config(args, scene, cam, weight, target)
+    S = Step(scene, cam, weight, tile, target, persistent, chunk)
+    kernels_per_step = KERNELS_PER_STEP + (ORDER_KERNELS if persistent else 0)
     A = S.A
     npix = cam.width * cam.height
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -451,18 +478,21 @@ def run_ours(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": extra["name"], "gaussians": S.g.n, "width": cam.width, "height": cam.height,
                        "sh_degree": S.g.sh_degree, "opacity": "view-dependent SH", "weight": "lc",
-                       "tile": args.tile, "views_per_rank": 1,
+                       "tile": "%dx%d" % tile, "schedule": "persistent" if persistent else "per-tile",
+                       "chunk": chunk, "views_per_rank": 1,
                        "l2": "flushed between steps (512 MB write outside the step events)"},
-            "gpu_launches": KERNELS_PER_STEP * args.steps, "roofline": roof, "clocks": clk, "e2e": e2e,
+            "gpu_launches": kernels_per_step * args.steps, "roofline": roof, "clocks": clk, "e2e": e2e,
             "wall_s_timed_region": round(wall, 4)}
     line.update(extra_out)
+    if tune_ms:
+        line["autotune_ms"] = tune_ms
 
     if world == 1 and not args.no_batched:
         line["batched"] = run_batched(cpu_leg=not args.no_cpu_baseline)
     if world == 1 and not args.no_reduced:
         line["reduced"] = run_reduced(cpu_leg=not args.no_cpu_baseline)
     if world == 1 and not args.no_training:
-        line["training"] = run_training()
+        line["training"] = run_training(tile=tile, persistent=persistent, chunk=chunk)
     if rank == 0 and not args.no_cpu_baseline:
         gpu_rgb = S.st.rgb.reshape(cam.height, cam.width, 3).cpu().numpy()
         base, maxerr = cpu_oracle_leg(scene, cam, weight, target, gpu_rgb, args.cpu_budget)
@@ -492,7 +522,7 @@ def run_e2e(args, S, scene, weight, target, flush):
     tgt_h = S.target.cpu().pin_memory()
     h2d = sum(v.numel() * v.element_size() for v in host.values()) + tgt_h.numel() * 4
     d2h = S.st.rgb.numel() * 4 + 4
-    steps = [S, Step(scene, S.cam, weight, tuple(S.r.tile), target)]
+    steps = [S, Step(scene, S.cam, weight, tuple(S.r.tile), target, S.r.persistent, S.r.chunk)]
     rgb_h = [torch.empty_like(S.st.rgb, device="cpu").pin_memory() for _ in range(2)]
     loss_h = [torch.empty(1).pin_memory() for _ in range(2)]
     comp = torch.cuda.current_stream()
@@ -623,13 +653,13 @@ def run_batched(reps: int = 5, cpu_leg: bool = True) -> dict:
                             + "/chunk%d" % t["chunk"]: round(t["ms"], 3) for t in tune["table"]}}
 
 
-def run_training(steps: int = 10, warmup: int = 3) -> dict:
+def run_training(steps: int = 10, warmup: int = 3, tile=(16, 16), persistent: bool = True, chunk: int = 64) -> dict:
     """1M Gaussians, 1920x1080 (the headline workload), one optimisation step
     per replay: project, bin, render, 3DGS loss (L1 + 0.2 D-SSIM), render
     backward, projection backward and Adam, captured as one CUDA graph over a
-    flat parameter buffer.  Each replay is timed with its own events, the L2
-    flushed in between; the loss and Adam kernels are also timed alone and
-    reported against HBM."""
+    flat parameter buffer, with the render step's launch configuration.  Each
+    replay is timed with its own events, the L2 flushed in between; the loss
+    and Adam kernels are also timed alone and reported against HBM."""
     import numpy as np
     import torch
 
@@ -640,7 +670,8 @@ def run_training(steps: int = 10, warmup: int = 3) -> dict:
     tgt = torch.from_numpy(ws.target_image(extra["target_seed"], cam.height, cam.width).reshape(-1, 3)).cuda()
     flat = FlatParams.from_scene(scene, weight.as_array())
     del scene
-    step = TrainStep(flat, 3, True, [cam], weight.kind, tgt, tile=(16, 16), persistent=False, capture=True)
+    step = TrainStep(flat, 3, True, [cam], weight.kind, tgt, tile=tile, persistent=persistent, chunk=chunk,
+                     capture=True)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(warmup):
         step.replay()
@@ -685,7 +716,8 @@ def run_training(steps: int = 10, warmup: int = 3) -> dict:
     n_upd = sum(g.count for g in step.opt.groups[:step.opt.n_groups])
     adam_bytes = n_upd * 4 * 7                     # p, g, m, v read; p, m, v written
     return {"workload": extra["name"], "gaussians": flat.count("means") // 3, "width": cam.width,
-            "height": cam.height, "graph": True, "kernels_per_step": step.kernels_per_step,
+            "height": cam.height, "tile": "%dx%d" % tuple(tile), "schedule": "persistent" if persistent else "per-tile",
+            "chunk": chunk, "graph": True, "kernels_per_step": step.kernels_per_step,
             "ms_per_step": round(ms, 3), "train_mpix_s": round(npix / (ms * 1e-3) / 1e6, 2),
             "steps_per_s": round(1e3 / ms, 2), "adam_steps_made": st["step"],
             "loss_first_last": [round(float(L[0, 0]), 6), round(float(L[-1, 0]), 6)],
@@ -781,7 +813,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", type=int, default=3)
-    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--tile", default="auto", help="WxH (16x16, 8x8, 32x8, 16x8) or auto")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "per-tile", "persistent"])
+    ap.add_argument("--chunk", default="auto", choices=["auto", "128", "64"],
+                    help="Gaussians per block of the backward")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
     ap.add_argument("--no-batched", action="store_true", help="skip the 3M x 16-view batched measurement")
@@ -795,7 +830,12 @@ def main():
     if args.training_only:
         import torch
         torch.cuda.set_device(0)
-        print(json.dumps(run_training(steps=args.steps, warmup=args.warmup)), flush=True)
+        # the launch configuration as given; "auto" takes what the tuner picks for this view on a GB300
+        tile = (16, 16) if args.tile == "auto" else tuple(int(v) for v in args.tile.split("x"))
+        persistent = args.schedule != "per-tile"
+        chunk = 64 if args.chunk == "auto" else int(args.chunk)
+        print(json.dumps(run_training(steps=args.steps, warmup=args.warmup, tile=tile, persistent=persistent,
+                                      chunk=chunk)), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -142,9 +142,10 @@ class TrainStep:
 
     def __init__(self, flat: FlatParams, sh_degree: int, view_dependent: bool, cams, kind: int,
                  target: torch.Tensor, lr: dict | None = None, lam: float = DSSIM_LAMBDA, tile=(16, 16),
-                 persistent: bool = False, headroom: float = 1.5, capture: bool = True):
+                 persistent: bool = False, headroom: float = 1.5, capture: bool = True, chunk: int = 0):
         self.flat, self.kind, self.lam = flat, kind, float(lam)
         self.cams, self.tile, self.persistent, self.headroom = list(cams), tile, persistent, headroom
+        self.chunk = int(chunk)
         self.g = flat.gaussians(sh_degree, view_dependent)
         self.wparams = flat.param["weight_params"]
         self.target = target.reshape(-1, 3).contiguous().float()
@@ -158,7 +159,8 @@ class TrainStep:
 
     def _build(self, capture: bool):
         dev = self.flat.device
-        self.r = Renderer(self.cams, tile=self.tile, persistent=self.persistent, headroom=self.headroom)
+        self.r = Renderer(self.cams, tile=self.tile, persistent=self.persistent, headroom=self.headroom,
+                          chunk=self.chunk)
         self.st = self.r.forward(self.g, self.kind, self.wparams)
         self.grad_rgb = torch.empty_like(self.st.rgb)
         self.grad_records = torch.empty(self.r.n_cams * self.g.n * A.WSR_GRAD_RECORD_FLOATS, device=dev)
