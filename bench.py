@@ -3,9 +3,12 @@
 
 Workload (default): 1,000,000 Gaussians in 64 clusters, SH degree 3,
 view-dependent opacity, LC weight, one 1920x1080 view on a ring of radius 5,
-16x16 tiles, L1 loss against a seeded random target.  One step is the whole
-hot path: project -> sort-free bin -> render forward -> L1 loss -> render
-backward (tiles) -> projection backward, every stage a C-ABI call.
+L1 loss against a seeded random target.  One step is the whole hot path:
+project -> sort-free bin -> render forward -> L1 loss -> render backward
+(tiles) -> projection backward, every stage a C-ABI call.  Tile shape, tile
+schedule and Gaussians per backward block are picked by the autotuner before
+the measured region (16x16, persistent, 64 on a GB300) unless --tile,
+--schedule and --chunk fix them.
 
 Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
 on the launching stream; L2 is flushed (a 512 MB write) between steps outside
