@@ -14,7 +14,7 @@ import torch
 from . import _abi as A
 from .render import Gaussians, Renderer
 
-DEFAULT_SHAPES = ((8, 8), (16, 16), (32, 8))
+DEFAULT_SHAPES = ((8, 8), (16, 8), (16, 16), (32, 8))
 DEFAULT_CHUNKS = (128, 64)      # Gaussians per block of the backward
 
 

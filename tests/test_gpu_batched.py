@@ -83,7 +83,7 @@ def test_autotune_returns_a_measured_valid_choice():
     npix = sum(c.width * c.height for c in cams)
     target = torch.rand(npix, 3, device="cuda")
     res = autotune(g, cams, w.kind, wpar, target, reps=2)
-    assert len(res["table"]) == 12 and all(t["ok"] for t in res["table"])      # 3 shapes x 2 schedules x 2 chunks
+    assert len(res["table"]) == 16 and all(t["ok"] for t in res["table"])      # 4 shapes x 2 schedules x 2 chunks
     assert res["chunk"] in (64, 128)
     assert res["ms"] == min(t["ms"] for t in res["table"])
     assert autotune(g, cams, w.kind, wpar, target) is res      # cached
