@@ -174,3 +174,15 @@ def test_tiles_chunk_is_validated(lib):
         t = A.tiles(16, 16, 0, chunk)
         assert lib.wsr_render_fwd(fake, 10, fake, fake, cams, n, ctypes.byref(t), ctypes.byref(w), fake, fake,
                                   fake, ws, None) == status
+
+
+def test_bench_uses_a_fixed_launch_configuration_as_given():
+    """With tile shape, schedule and backward block size all given, the bench
+    runs them without tuning (nothing is launched)."""
+    import argparse
+
+    import bench
+    args = argparse.Namespace(tile="16x8", schedule="persistent", chunk="64")
+    assert bench.launch_config(args, None, None, None, None) == ((16, 8), True, 64, None)
+    args = argparse.Namespace(tile="32x8", schedule="per-tile", chunk="128")
+    assert bench.launch_config(args, None, None, None, None) == ((32, 8), False, 128, None)
