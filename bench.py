@@ -211,7 +211,8 @@ def launch_config(args, scene, cam, weight, target):
     """Tile shape, schedule and Gaussians per backward block of the timed
     step: as given, or, for each "auto", the fastest captured forward + L1 +
     backward step of the autotuner on this view (timed before the measured
-    region).  Returns (tile, persistent, chunk, table of the tuned times)."""
+    region, each option over ten steps from a flushed L2).  Returns (tile,
+    persistent, chunk, table of the tuned times)."""
     import torch
 
     from paper_2410_18931_gb300 import Gaussians, autotune
@@ -224,8 +225,11 @@ def launch_config(args, scene, cam, weight, target):
     g = Gaussians.from_scene(scene)
     wpar = torch.tensor(weight.as_array(), device="cuda")
     tgt = torch.as_tensor(target).reshape(-1, 3).cuda()
-    tune = autotune(g, [cam], weight.kind, wpar, tgt, shapes=shapes, schedules=schedules, chunks=chunks, reps=3)
-    del g, wpar, tgt
+    # as the measured steps run: L2 flushed before each step; ten steps per option
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    tune = autotune(g, [cam], weight.kind, wpar, tgt, shapes=shapes, schedules=schedules, chunks=chunks, reps=10,
+                    flush=flush)
+    del g, wpar, tgt, flush
     torch.cuda.empty_cache()
     table = {("%dx%d" % t["tile"]) + ("/persistent" if t["persistent"] else "/per-tile") + "/chunk%d" % t["chunk"]:
              round(t["ms"], 3) for t in tune["table"]}

@@ -83,29 +83,41 @@ class GraphStep:
         return 10 + (3 if self.r.persistent else 0)
 
 
-def time_step(step: GraphStep, reps: int = 5, warmup: int = 2) -> float:
-    """Mean milliseconds per replay (CUDA events on the current stream)."""
+def time_step(step: GraphStep, reps: int = 5, warmup: int = 2, flush: torch.Tensor | None = None) -> float:
+    """Mean milliseconds per replay (CUDA events on the current stream).  With
+    ``flush`` (a buffer larger than L2), the buffer is overwritten before each
+    replay, outside the events, so every replay starts from a cold L2."""
     for _ in range(warmup):
         step.replay()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
+    if flush is None:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            step.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record()
         step.replay()
-    e1.record()
+        e1.record()
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / reps
+    return sum(e0.elapsed_time(e1) for e0, e1 in ev) / reps
 
 
 _cache: dict = {}
 
 
 def autotune(g: Gaussians, cams, kind: int, wparams: torch.Tensor, target: torch.Tensor,
-             shapes=DEFAULT_SHAPES, schedules=(False, True), chunks=DEFAULT_CHUNKS, reps: int = 3) -> dict:
+             shapes=DEFAULT_SHAPES, schedules=(False, True), chunks=DEFAULT_CHUNKS, reps: int = 3,
+             flush: torch.Tensor | None = None) -> dict:
     """Time every (tile shape, schedule, Gaussians per backward block) on this
     workload and return the fastest as dict(tile=, persistent=, chunk=, ms=,
-    table=[...]).  Results are cached per (Gaussian count, view sizes, storage
-    types, weight kind)."""
+    table=[...]); ``reps`` and ``flush`` as in ``time_step``.  Results are
+    cached per (Gaussian count, view sizes, storage types, weight kind)."""
     key = (g.n, tuple((c.width, c.height) for c in cams), str(g.sh.dtype), str(g.log_scales.dtype), kind,
            tuple(shapes), tuple(schedules), tuple(chunks))
     if key in _cache:
@@ -115,7 +127,7 @@ def autotune(g: Gaussians, cams, kind: int, wparams: torch.Tensor, target: torch
         for persistent in schedules:
             for chunk in chunks:
                 step = GraphStep(g, cams, kind, wparams, target, tile=shape, persistent=persistent, chunk=chunk)
-                ms = time_step(step, reps=reps)
+                ms = time_step(step, reps=reps, flush=flush)
                 ok = step.check() == A.WSR_OK
                 table.append(dict(tile=shape, persistent=persistent, chunk=chunk, ms=ms, ok=ok))
                 del step

@@ -10,8 +10,8 @@ import pytest
 
 import oracle
 import wsr_scenes as ws
-from tests.gpu_util import (AMB_TAU, FWD_TOL, GRAD_TOL, compare_image, gpu_render, grad_envelope, grad_excess,
-                            rel_err)
+from tests.gpu_util import (AMB_TAU, FWD_TOL, GRAD_TOL, add_envelopes, compare_image, gpu_render, grad_envelope,
+                            grad_excess, rel_err)
 
 pytestmark = pytest.mark.gpu
 
@@ -101,6 +101,34 @@ def test_reduced_precision_storage_matches_oracle_on_stored_values():
     ref = _oracle(q, cam, w)
     excess, raw, n_amb = compare_image(rgb, ref)
     assert excess <= FWD_TOL, (excess, raw, n_amb)
+
+
+@pytest.mark.parametrize("n_views", [1, 3])
+def test_reduced_precision_storage_gradients_match_oracle_on_stored_values(n_views):
+    """bf16 scales/quats and f16 SH/opacity, backward over one view and over
+    three: every gradient tensor (FP32, with respect to the stored values)
+    against the oracle's analytic gradient on the stored (rounded) values."""
+    import torch
+    sc = ws.random_scene(3_000, 24, sh_degree=3, vd_opacity=True, clusters=6, box=1.2, log_scale_mu=-3.2,
+                         log_scale_sd=0.5)
+    q = ws.quantize_reduced(sc)
+    cams = [ws.look_at((0.2, 0.1, -3.5), width=96, height=72).rounded(),
+            ws.look_at((-1.5, 0.6, -3.0), width=70, height=50).rounded(),
+            ws.look_at((1.8, -0.4, -2.9), width=88, height=61).rounded()][:n_views]
+    w = ws.WeightParams(ws.LC, 4.8, 0.8, 0.6, (0.3, 0.2, 0.1))
+    views, (r, g, wpar, st) = gpu_render(q, cams, w, reduced=True, want_state=True)
+    rng = np.random.default_rng(6)
+    Gs = [rng.normal(size=(c.height, c.width, 3)).astype(np.float32) for c in cams]
+    G = np.concatenate([x.reshape(-1, 3) for x in Gs])
+    out = r.backward(g, w.kind, wpar, st, torch.tensor(G, device="cuda"))
+    torch.cuda.synchronize()
+    env = None
+    for c, Gv in zip(cams, Gs):
+        e = grad_envelope(q, c, w, Gv.astype(np.float64))
+        env = e if env is None else add_envelopes(env, e)
+    for k in ("means", "log_scales", "quats", "sh", "opacity", "lc_v"):
+        e = grad_excess(out[k].cpu().numpy(), env, k)
+        assert e <= GRAD_TOL, (k, e)
 
 
 def _grad_case(scene, cam, weight, tile=(16, 16)):
