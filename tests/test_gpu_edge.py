@@ -117,3 +117,16 @@ def test_thirty_two_views_in_one_call():
     for persistent in (False, True):
         r, g, wpar, st = _check_forward(sc, cams, w, tile=(8, 8), persistent=persistent)
     _check_gradients(sc, cams, w, r, g, wpar, st, keys=("means", "log_scales", "quats", "sh", "opacity", "lc_v"))
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+def test_degenerate_image_shapes(persistent):
+    """Views of 1x1, one row, one column and a 17x3 strip in one call: ragged
+    tiles in both directions, forward and gradients against the oracle."""
+    sc = ws.random_scene(2000, 61, sh_degree=2, vd_opacity=True, box=1.0, log_scale_mu=-2.6)
+    sizes = [(1, 1), (57, 1), (1, 43), (17, 3)]
+    cams = [ws.look_at((0.3 * k, 0.2, -3.0), width=wd, height=ht).rounded() for k, (wd, ht) in enumerate(sizes)]
+    w = ws.WeightParams(ws.EXP, 0.1, 0.8, 0.7, (0.2, 0.1, 0.3))
+    for tile in [(16, 16), (8, 8)]:
+        r, g, wpar, st = _check_forward(sc, cams, w, tile=tile, persistent=persistent)
+    _check_gradients(sc, cams, w, r, g, wpar, st)
