@@ -293,8 +293,8 @@ wsr_status wsr_loss_l1(const float* rgb, const float* target, int64_t count, flo
                        float* grad_rgb, void* stream);
 
 /*
- * wsr_loss_3dgs — the rendering loss the paper trains with (Sec. 4.4,
- * "Loss function": the 3DGS loss, L1 plus D-SSIM weighted 0.2) and its
+ * wsr_loss_3dgs — the rendering loss the paper trains with (Sec. 4.4:
+ * the 3DGS loss, L1 plus D-SSIM weighted 0.2) and its
  * gradient with respect to the rendered pixels:
  *     L = (1 - lambda) * L1 + lambda * (1 - SSIM)
  *   L1    mean |rgb - target| over every pixel and channel of every view;
@@ -321,7 +321,7 @@ wsr_status wsr_loss_3dgs(const float* rgb, const float* target, const wsr_camera
 /*
  * wsr_adam_step — one Adam update (Kingma & Ba 2015) of a flat float32
  * parameter buffer, the optimiser the paper's PyTorch training uses (Sec.
- * 4.4, "Training and Evaluation", as 3DGS does):
+ * 4.4, as 3DGS does):
  *     m <- b1 m + (1 - b1) g,   v <- b2 v + (1 - b2) g^2,
  *     p <- p - lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)
  * with t the step number kept in the device state (advanced by this call).
