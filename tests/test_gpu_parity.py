@@ -289,7 +289,12 @@ def test_permutation_changes_only_rounding():
     assert np.abs(a - b).max() < 2e-6
 
 
-def test_capacity_overflow_is_reported_and_recovered():
+@pytest.mark.parametrize("persistent", [False, True])
+def test_capacity_overflow_is_reported_and_recovered(persistent):
+    """A tile list too small for the frame: the overflow is reported with the
+    true total, nothing is written past the list, offsets stay clamped (the
+    persistent schedule's tile order is built from them), and the renderer
+    regrows the list and renders the full image."""
     import torch
     from paper_2410_18931_gb300 import Gaussians, Renderer
     from paper_2410_18931_gb300 import _abi as A
@@ -298,7 +303,7 @@ def test_capacity_overflow_is_reported_and_recovered():
     w = ws.default_weight(ws.EXP)
     g = Gaussians.from_scene(sc)
     wpar = torch.tensor(w.as_array(), device="cuda")
-    r = Renderer([cam])
+    r = Renderer([cam], persistent=persistent)
     st = r.alloc_state(g.n)
     r.wsr_project(g, w.kind, wpar, st.records)
     r.wsr_bin_count(st.records, g.n, st.tile_offsets)
@@ -314,7 +319,7 @@ def test_capacity_overflow_is_reported_and_recovered():
     assert (guard.cpu().numpy() == -7).all()
     assert r.wsr_check() == A.WSR_OK                                    # cleared
     # the Renderer grows the list and renders the full image
-    r2 = Renderer([cam])
+    r2 = Renderer([cam], persistent=persistent)
     r2.capacity = total // 3
     st2 = r2.forward(g, w.kind, wpar)
     ref = _oracle(sc, cam, w)
