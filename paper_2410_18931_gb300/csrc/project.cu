@@ -7,7 +7,15 @@
 //   Sec. 3 Eq. 4   c = max(0, Y(dir) . H + 0.5)
 //   Eq. 11 / Eq. 3 u = Y(dir) . H^alpha (unclamped) or sigmoid(o)
 //   Eqs. 8-10      w(d) with d = camera z
-// and writes the 48-byte render record {mu, conic*log2(e)/2, u w, c u w, extents}.
+// and writes the 48-byte render record {mu, qs, qw, qd, u w, c u w, extents}
+// with the footprint's quadratic form, prescaled by log2(e)/2, as the sum of
+// squares q' = (qs dy + qw dx)^2 + qd dx^2.
+//
+// Backward, one thread per Gaussian: the render backward's record of each
+// (view, Gaussian) holds moments of dL/dq' in that sum-of-squares frame plus
+// d/d(u w) and d/d(c u w); they are chained to the mean, the 2D covariance
+// (in factored form), the colour and opacity SH, the depth weight and the
+// stored parameters, summed over views.
 //
 // The 2D covariance is formed as T T^t with T = J W R S (2x3), so its
 // determinant is the squared norm of the cross product of T's rows (plus the

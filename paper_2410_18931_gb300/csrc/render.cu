@@ -1,6 +1,7 @@
 // Per-pixel Weighted Sum Rendering, forward and backward (Eq. 7).
 //
-// One thread block per tile.  The tile's Gaussian list (unordered: Eq. 7 is
+// One thread block per tile (or, with the persistent schedule, one per
+// resident slot taking tiles longest first).  The tile's Gaussian list (unordered: Eq. 7 is
 // a sum) is streamed through shared memory in chunks of one record per
 // thread; every thread owns a 2x2 block of pixels (two columns share each
 // paired float2 FP32 instruction) and accumulates, in FP32 registers,
@@ -15,7 +16,8 @@
 // the stored C and denominator (no per-pixel lists are kept).  It walks the
 // pixels inside each Gaussian's footprint (per-row spans) with the work split
 // evenly over the threads, so no lane idles on pixels outside a footprint and
-// no per-pair reduction across lanes is needed.
+// no per-pair reduction across lanes is needed; per Gaussian it adds d/d(u w),
+// d/d(c u w) and moments of dL/dq' to a gradient record.
 #include "wsr_launch.h"
 
 namespace wsr {
