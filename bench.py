@@ -494,6 +494,10 @@ def run_ours(args):
                 "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": profile_traffic(kern),
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 (FMA) x {SM_MAX_MHZ:.0f} MHz",
                 "work": f"{pairs} pairs with q <= 9 x {fl} FP32 flops"}
+        if kern == "k_render_bwd":
+            # what bounds it (from the kernel's ncu capture): not FP32 throughput
+            roof["note"] = ("limited by the shared-memory pipe (~0.84 wavefronts per SM-cycle of 1, about half "
+                            "of them bank conflicts from random per-lane pixel loads) and by issue (~73%)")
     else:
         roof = {"bound": "hbm", "kernel": names[dom], "achieved": None, "peak": None, "unit": "GB/s",
                 "frac": None, "traffic": None}
