@@ -155,7 +155,7 @@ class ClockSampler:
 class Step:
     """Buffers and the per-step sequence of C-ABI calls for one view."""
 
-    def __init__(self, scene, cam, weight, tile, target, persistent=False, chunk=0):
+    def __init__(self, scene, cam, weight, tile, target, persistent=False, chunk=0, deterministic=False):
         import torch
 
         from paper_2410_18931_gb300 import Gaussians, Renderer
@@ -165,7 +165,7 @@ class Step:
         self.g = Gaussians.from_scene(scene)
         self.kind = weight.kind
         self.wpar = torch.tensor(weight.as_array(), device="cuda")
-        self.r = Renderer([cam], tile=tile, persistent=persistent, chunk=chunk)
+        self.r = Renderer([cam], tile=tile, persistent=persistent, chunk=chunk, deterministic=deterministic)
         self.cam = cam
         # size the tile list once (exact count + headroom), then fixed
         self.st = self.r.forward(self.g, self.kind, self.wpar)
@@ -180,7 +180,7 @@ class Step:
                         lc_v=torch.empty(n, device=dev), weight_params=torch.empty(6, device=dev))
         self.grads = A.wsr_grads(*[self.out[k].data_ptr() for k in
                                    ("means", "log_scales", "quats", "sh", "opacity", "lc_v", "weight_params")])
-        self.grad_records = torch.empty(n * A.WSR_GRAD_RECORD_FLOATS, device=dev)
+        self.grad_records = torch.empty(n * self.r.record_floats, device=dev)
         self.stream = torch.cuda.current_stream()
         self.stage_names = ["project", "bin", "render_fwd", "loss", "render_bwd_tiles", "project_bwd"]
 
@@ -536,6 +536,8 @@ def run_ours(args):
     if tune_ms:
         line["autotune_ms"] = tune_ms
 
+    if world == 1 and not args.no_deterministic:
+        line["deterministic"] = run_deterministic(S, scene, cam, weight, target, tile, persistent, chunk, flush)
     if world == 1 and not args.no_batched:
         line["batched"] = run_batched(cpu_leg=not args.no_cpu_baseline)
     if world == 1 and not args.no_reduced:
@@ -552,6 +554,48 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_deterministic(S, scene, cam, weight, target, tile, persistent, chunk, flush, reps: int = 5) -> dict:
+    """The same step in the deterministic mode (tile lists sorted by record
+    index, fixed-point gradient sums in two backward passes): its time, and
+    whether two runs give the same bits.  The sort holds a bounded number of
+    instances per tile; when the step's tiles hold more, the leg takes 8x8
+    tiles."""
+    import numpy as np
+    import torch
+    off = S.st.tile_offsets.to(torch.int64)
+    longest = int((off[1:] - off[:-1]).max())
+    if longest > S.A.WSR_DET_MAX_SEGMENT:
+        tile, chunk = (8, 8), 128
+    try:
+        D = Step(scene, cam, weight, tile, target, persistent, chunk, deterministic=True)
+    except S.A.WSRError as e:
+        if e.status != S.A.WSR_ERR_UNSUPPORTED:
+            raise
+        return {"unsupported": f"a tile holds more than {S.A.WSR_DET_MAX_SEGMENT} instances ({tile[0]}x{tile[1]} tiles)"}
+    outs = []
+    for _ in range(2):
+        D.run()
+        torch.cuda.synchronize()
+        outs.append([D.st.rgb.clone()] + [v.clone() for v in D.out.values()])
+    S.A.check("deterministic step", D.r.wsr_check())
+    same = all(torch.equal(a, b) for a, b in zip(*outs))
+    times = []
+    for _ in range(reps):
+        flush.zero_()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+        D.run(evs)
+        torch.cuda.synchronize()
+        times.append(evs[0].elapsed_time(evs[6]))
+    ms = float(np.mean(times))
+    del D, outs
+    torch.cuda.empty_cache()
+    return {"ms_per_step": round(ms, 4), "fwd_bwd_mpix_s": round(cam.width * cam.height / (ms * 1e-3) / 1e6, 2),
+            "tile": "%dx%d" % tile, "schedule": "persistent" if persistent else "per-tile", "chunk": chunk,
+            "longest_tile_list": longest, "bitwise_repeat": bool(same),
+            # + the list sort, the backward's magnitude pass and the two ordered reductions
+            "kernels_per_step": KERNELS_PER_STEP + (ORDER_KERNELS if persistent else 0) + 4}
 
 
 def run_e2e(args, S, scene, weight, target, flush):
@@ -870,6 +914,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
     ap.add_argument("--no-batched", action="store_true", help="skip the 3M x 16-view batched measurement")
     ap.add_argument("--no-reduced", action="store_true", help="skip the 6M x 8 x 4K reduced-precision measurement")
+    ap.add_argument("--no-deterministic", action="store_true", help="skip the deterministic-mode measurement")
     ap.add_argument("--no-training", action="store_true", help="skip the training-step (loss + Adam) measurement")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--training-only", action="store_true",

@@ -64,6 +64,8 @@ enum { WSR_OPACITY_LOGIT = 0, WSR_OPACITY_SH = 1 };
 #define WSR_MAX_VIEWS 32
 #define WSR_RECORD_FLOATS 12      /* one render record: 48 bytes */
 #define WSR_GRAD_RECORD_FLOATS 12 /* one 2D gradient record: 48 bytes (9 used) */
+#define WSR_GRAD_RECORD_FLOATS_DET 32 /* one record in deterministic mode: 128 bytes */
+#define WSR_DET_MAX_SEGMENT 8192  /* deterministic mode: most instances one tile may hold */
 
 /* Pinhole camera (passed by value through host memory). */
 typedef struct {
@@ -132,11 +134,27 @@ enum {
  * per Gaussian): 0 for the default 128, or 64 (blocks of 128 threads, twice as
  * many resident); other values return WSR_ERR_UNSUPPORTED.  It changes the
  * schedule only, not the result beyond rounding order.
+ *
+ * `deterministic` = 1 makes every result bitwise reproducible from run to run
+ * for the same inputs and tiles (0, the default, lets the order of atomics
+ * decide the last bits):
+ *   - wsr_bin sorts each tile's list by record index after the scatter (a tile
+ *     with more than WSR_DET_MAX_SEGMENT instances leaves WSR_ERR_UNSUPPORTED
+ *     in the workspace for wsr_check);
+ *   - wsr_render_bwd_tiles walks the tiles twice: first for the largest
+ *     magnitude of every record term, then adding each term as 64-bit fixed
+ *     point scaled from it (exact integer sums); grad_records then holds
+ *     WSR_GRAD_RECORD_FLOATS_DET floats per record (9 int64 sums, 9 int32
+ *     magnitudes), and the background terms are reduced in tile order;
+ *   - wsr_project_bwd, given the same tiles, reads those records and reduces
+ *     its sigma/beta terms in a fixed order.
+ * The backward then takes about twice as long.
  */
 typedef struct {
     int32_t tile_w, tile_h;
     int32_t schedule;            /* WSR_SCHEDULE_* */
     int32_t chunk;               /* Gaussians per backward block: 0 (128) or 64 */
+    int32_t deterministic;       /* 0, or 1: bitwise-reproducible results */
 } wsr_tiles;
 
 /*
@@ -272,7 +290,9 @@ wsr_status wsr_render_bwd(const wsr_gaussians* g, const float* records, const ui
  * semantics; wsr_render_bwd is exactly wsr_render_bwd_tiles followed by
  * wsr_project_bwd).  wsr_render_bwd_tiles overwrites grad_records and
  * accumulates the background terms in the workspace; wsr_project_bwd adds the
- * sigma/beta terms there and writes grads (weight_params included).
+ * sigma/beta terms there and writes grads (weight_params included).  `tiles`
+ * of wsr_project_bwd may be NULL; only its `deterministic` field is read, and
+ * it must match the wsr_render_bwd_tiles call that wrote grad_records.
  */
 wsr_status wsr_render_bwd_tiles(const float* records, int64_t n, const uint32_t* tile_offsets,
                                 const uint32_t* tile_list, const wsr_camera* cams, int32_t n_cams,
@@ -280,8 +300,8 @@ wsr_status wsr_render_bwd_tiles(const float* records, int64_t n, const uint32_t*
                                 const float* out_den, const float* grad_rgb, float* grad_records,
                                 void* workspace, size_t workspace_bytes, void* stream);
 wsr_status wsr_project_bwd(const wsr_gaussians* g, const wsr_camera* cams, int32_t n_cams,
-                           const wsr_weight* w, const float* grad_records, const wsr_grads* grads,
-                           void* workspace, size_t workspace_bytes, void* stream);
+                           const wsr_tiles* tiles, const wsr_weight* w, const float* grad_records,
+                           const wsr_grads* grads, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * wsr_loss_l1 — mean absolute error against a target and its gradient

@@ -19,6 +19,8 @@ WSR_OPACITY_LOGIT, WSR_OPACITY_SH = 0, 1
 WSR_MAX_VIEWS = 32
 WSR_RECORD_FLOATS = 12
 WSR_GRAD_RECORD_FLOATS = 12
+WSR_GRAD_RECORD_FLOATS_DET = 32      # deterministic mode: 9 int64 sums and 9 magnitudes per record
+WSR_DET_MAX_SEGMENT = 8192
 
 _c_void_p = ctypes.c_void_p
 
@@ -42,7 +44,7 @@ class wsr_weight(ctypes.Structure):
 
 class wsr_tiles(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("schedule", ctypes.c_int32),
-                ("chunk", ctypes.c_int32)]
+                ("chunk", ctypes.c_int32), ("deterministic", ctypes.c_int32)]
 
 
 class wsr_grads(ctypes.Structure):
@@ -92,8 +94,9 @@ _SIGS = {
     "wsr_render_bwd_tiles": (ctypes.c_int, [_c_void_p, ctypes.c_int64, _c_void_p, _c_void_p, _P(wsr_camera),
                                             ctypes.c_int32, _P(wsr_tiles), _P(wsr_weight), _c_void_p, _c_void_p,
                                             _c_void_p, _c_void_p, _c_void_p, ctypes.c_size_t, _c_void_p]),
-    "wsr_project_bwd": (ctypes.c_int, [_P(wsr_gaussians), _P(wsr_camera), ctypes.c_int32, _P(wsr_weight),
-                                       _c_void_p, _P(wsr_grads), _c_void_p, ctypes.c_size_t, _c_void_p]),
+    "wsr_project_bwd": (ctypes.c_int, [_P(wsr_gaussians), _P(wsr_camera), ctypes.c_int32, _P(wsr_tiles),
+                                       _P(wsr_weight), _c_void_p, _P(wsr_grads), _c_void_p, ctypes.c_size_t,
+                                       _c_void_p]),
     "wsr_bin_static": (ctypes.c_int, [_c_void_p, ctypes.c_int64, _P(wsr_camera), ctypes.c_int32, _P(wsr_tiles),
                                       _c_void_p, _c_void_p, ctypes.c_uint64, _c_void_p, _c_void_p]),
     "wsr_count_pairs": (ctypes.c_int, [_c_void_p, ctypes.c_int64, _c_void_p, _c_void_p, _P(wsr_camera),
@@ -161,6 +164,8 @@ def make_cameras(cams) -> tuple:
 WSR_SCHEDULE_TILE_BLOCKS, WSR_SCHEDULE_PERSISTENT = 0, 1
 
 
-def tiles(tw: int, th: int, schedule: int = WSR_SCHEDULE_TILE_BLOCKS, chunk: int = 0) -> wsr_tiles:
-    """Tile shape, schedule and the backward's Gaussians per block (0: the default)."""
-    return wsr_tiles(int(tw), int(th), int(schedule), int(chunk))
+def tiles(tw: int, th: int, schedule: int = WSR_SCHEDULE_TILE_BLOCKS, chunk: int = 0,
+          deterministic: int = 0) -> wsr_tiles:
+    """Tile shape, schedule, the backward's Gaussians per block (0: the default) and
+    the deterministic mode (1: bitwise-reproducible results)."""
+    return wsr_tiles(int(tw), int(th), int(schedule), int(chunk), int(deterministic))

@@ -28,16 +28,17 @@ class GraphStep:
 
     def __init__(self, g: Gaussians, cams, kind: int, wparams: torch.Tensor, target: torch.Tensor,
                  tile=(16, 16), persistent: bool = True, headroom: float = 1.3, capture: bool = True,
-                 chunk: int = 0):
+                 chunk: int = 0, deterministic: bool = False):
         self.g, self.kind, self.wparams = g, kind, wparams
-        self.r = Renderer(cams, tile=tile, persistent=persistent, headroom=headroom, chunk=chunk)
+        self.r = Renderer(cams, tile=tile, persistent=persistent, headroom=headroom, chunk=chunk,
+                          deterministic=deterministic)
         self.st = self.r.forward(g, kind, wparams)           # sizes the tile list exactly (+ headroom)
         self.target = target.reshape(-1, 3).contiguous()
         dev = self.r.device
         n, K = g.n, (g.sh_degree + 1) ** 2
         self.loss = torch.zeros(1, device=dev)
         self.grad_rgb = torch.empty_like(self.st.rgb)
-        self.grad_records = torch.empty(self.r.n_cams * n * A.WSR_GRAD_RECORD_FLOATS, device=dev)
+        self.grad_records = torch.empty(self.r.n_cams * n * self.r.record_floats, device=dev)
         self.out = dict(means=torch.empty(n, 3, device=dev), log_scales=torch.empty(n, 3, device=dev),
                         quats=torch.empty(n, 4, device=dev), sh=torch.empty(n, K, 3, device=dev),
                         opacity=torch.empty((n, K) if g.view_dependent else (n,), device=dev),
@@ -79,8 +80,9 @@ class GraphStep:
 
     @property
     def kernels_per_step(self) -> int:
-        # project 1, bin 5 (+3 tile-order kernels when persistent), fwd 1, loss 1, bwd 1, project bwd 1
-        return 10 + (3 if self.r.persistent else 0)
+        # project 1, bin 5 (+3 tile-order kernels when persistent), fwd 1, loss 1, bwd 1, project bwd 1;
+        # deterministic: + the list sort, a second backward pass and two ordered reductions
+        return 10 + (3 if self.r.persistent else 0) + (4 if self.r.deterministic else 0)
 
 
 def time_step(step: GraphStep, reps: int = 5, warmup: int = 2, flush: torch.Tensor | None = None) -> float:

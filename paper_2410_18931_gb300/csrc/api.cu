@@ -24,9 +24,10 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 // Builds the per-view constant table.  Returns WSR_OK or the argument error.
 wsr_status make_views(const wsr_camera* cams, int32_t n_cams, const wsr_tiles* tiles, Views* vs) {
     if (!cams || n_cams < 1 || n_cams > WSR_MAX_VIEWS) return WSR_ERR_INVALID_ARG;
-    int tw = 16, th = 16, sched = WSR_SCHEDULE_TILE_BLOCKS, chunk = 128;
+    int tw = 16, th = 16, sched = WSR_SCHEDULE_TILE_BLOCKS, chunk = 128, det = 0;
     if (tiles) {
         if (tiles->chunk < 0) return WSR_ERR_INVALID_ARG;
+        if (tiles->deterministic != 0 && tiles->deterministic != 1) return WSR_ERR_INVALID_ARG;
         if (tiles->schedule != WSR_SCHEDULE_TILE_BLOCKS && tiles->schedule != WSR_SCHEDULE_PERSISTENT)
             return WSR_ERR_INVALID_ARG;
         if (!tiles_ok(tiles)) return WSR_ERR_UNSUPPORTED;
@@ -35,6 +36,7 @@ wsr_status make_views(const wsr_camera* cams, int32_t n_cams, const wsr_tiles* t
         th = tiles->tile_h;
         sched = tiles->schedule;
         chunk = tiles->chunk ? tiles->chunk : 128;
+        det = tiles->deterministic;
     }
     memset(vs, 0, sizeof(Views));
     vs->n = n_cams;
@@ -42,6 +44,7 @@ wsr_status make_views(const wsr_camera* cams, int32_t n_cams, const wsr_tiles* t
     vs->tile_h = th;
     vs->schedule = sched;
     vs->chunk = chunk;
+    vs->det = det;
     long long tile_base = 0, pix_base = 0;
     for (int v = 0; v < n_cams; ++v) {
         const wsr_camera& c = cams[v];
@@ -77,7 +80,7 @@ wsr_status make_views(const wsr_camera* cams, int32_t n_cams, const wsr_tiles* t
 }
 
 struct WsLayout {
-    size_t cursor, block_sums, order, buckets, total;
+    size_t cursor, block_sums, order, buckets, bg_tiles, total;
 };
 
 // The tile order of the persistent schedule is only part of its layout.
@@ -87,11 +90,15 @@ WsLayout ws_layout(const Views& vs) {
     L.cursor = kWsHeader;
     L.block_sums = L.cursor + align256(sizeof(unsigned) * ((size_t)vs.total_tiles + 1));
     L.total = L.block_sums + align256(sizeof(unsigned long long) * (nb + 1));
-    L.order = L.buckets = 0;
+    L.order = L.buckets = L.bg_tiles = 0;
     if (vs.schedule == WSR_SCHEDULE_PERSISTENT) {
         L.order = L.total;
         L.buckets = L.order + align256(sizeof(unsigned) * (size_t)vs.total_tiles);
         L.total = L.buckets + align256(sizeof(unsigned) * 66);
+    }
+    if (vs.det) {
+        L.bg_tiles = L.total;
+        L.total = L.bg_tiles + align256(4 * sizeof(float) * (size_t)vs.total_tiles);
     }
     return L;
 }
@@ -287,6 +294,7 @@ wsr_status wsr_bin(const float* records, int64_t n, const wsr_camera* cams, int3
     char* ws = (char*)workspace;
     WSR_CUDA(launch_bin_scatter(records, n, vs, (unsigned*)(ws + L.cursor), tile_list, list_capacity,
                                 (WsHeader*)ws, s));
+    if (vs.det) WSR_CUDA(launch_sort_segments(vs, tile_offsets, tile_list, (WsHeader*)ws, s));
     return WSR_OK;
 }
 
@@ -303,13 +311,16 @@ wsr_status wsr_bin_static(const float* records, int64_t n, const wsr_camera* cam
     if ((unsigned long long)n * (unsigned long long)n_cams > 0xffffffffull) return WSR_ERR_INVALID_ARG;
     void* scratch = nullptr;
     WSR_TRY(static_scratch(&scratch));
-    if (ws_layout(vs).total > kStaticBytes) return WSR_ERR_UNSUPPORTED;
+    Views vb = vs;                 // the binning's part of the layout (no backward regions)
+    vb.det = 0;
+    if (ws_layout(vb).total > kStaticBytes) return WSR_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     WSR_TRY(bin_count_impl(records, n, vs, tile_offsets, list_capacity, scratch, s));
     const WsLayout L = ws_layout(vs);
     char* ws = (char*)scratch;
     WSR_CUDA(launch_bin_scatter(records, n, vs, (unsigned*)(ws + L.cursor), tile_list, list_capacity,
                                 (WsHeader*)ws, s));
+    if (vs.det) WSR_CUDA(launch_sort_segments(vs, tile_offsets, tile_list, (WsHeader*)ws, s));
     if (total_dev)
         WSR_CUDA(cudaMemcpyAsync(total_dev, &((WsHeader*)ws)->total, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
     return WSR_OK;
@@ -357,20 +368,32 @@ wsr_status wsr_render_bwd_tiles(const float* records, int64_t n, const uint32_t*
     cudaStream_t s = (cudaStream_t)stream;
     WsHeader* hdr = (WsHeader*)workspace;
     WSR_CUDA(cudaMemsetAsync(hdr->gw, 0, sizeof hdr->gw, s));
-    if (n > 0)
-        WSR_CUDA(cudaMemsetAsync(grad_records, 0, sizeof(float) * WSR_GRAD_RECORD_FLOATS * (size_t)n * n_cams, s));
-    WSR_CUDA(launch_render_bwd(records, tile_offsets, tile_list, vs, wd, out_rgb, out_den, grad_rgb, grad_records,
-                               hdr->gw, sched_of(vs, workspace, 1), s));
+    const size_t rec_floats = vs.det ? WSR_GRAD_RECORD_FLOATS_DET : WSR_GRAD_RECORD_FLOATS;
+    if (n > 0) WSR_CUDA(cudaMemsetAsync(grad_records, 0, sizeof(float) * rec_floats * (size_t)n * n_cams, s));
+    if (!vs.det) {
+        WSR_CUDA(launch_render_bwd(records, tile_offsets, tile_list, vs, wd, out_rgb, out_den, grad_rgb, grad_records,
+                                   hdr->gw, 0, nullptr, sched_of(vs, workspace, 1), s));
+        return WSR_OK;
+    }
+    // deterministic: the largest magnitude of every record term, then the terms as exact fixed-point sums;
+    // the background terms per tile, then summed in tile order
+    float* bg_tiles = (float*)((char*)workspace + ws_layout(vs).bg_tiles);
+    for (int pass = 1; pass <= 2; ++pass)
+        WSR_CUDA(launch_render_bwd(records, tile_offsets, tile_list, vs, wd, out_rgb, out_den, grad_rgb, grad_records,
+                                   hdr->gw, pass, bg_tiles, sched_of(vs, workspace, 1), s));
+    WSR_CUDA(launch_det_bg_reduce(bg_tiles, vs.total_tiles, hdr->gw, s));
     return WSR_OK;
 }
 
-wsr_status wsr_project_bwd(const wsr_gaussians* g, const wsr_camera* cams, int32_t n_cams, const wsr_weight* w,
-                           const float* grad_records, const wsr_grads* grads, void* workspace,
+wsr_status wsr_project_bwd(const wsr_gaussians* g, const wsr_camera* cams, int32_t n_cams, const wsr_tiles* tiles,
+                           const wsr_weight* w, const float* grad_records, const wsr_grads* grads, void* workspace,
                            size_t workspace_bytes, void* stream) {
     static thread_local Views vs;
     WeightDev wd;
     GaussPtrs gp;
     if (!grads || !workspace || workspace_bytes < kWsHeader || !aligned16(workspace)) return WSR_ERR_INVALID_ARG;
+    if (tiles && tiles->deterministic != 0 && tiles->deterministic != 1) return WSR_ERR_INVALID_ARG;
+    const bool det = tiles && tiles->deterministic == 1;
     WSR_TRY(check_weight(w, &wd));
     WSR_TRY(make_views(cams, n_cams, nullptr, &vs));
     WSR_TRY(check_gauss(g, n_cams, wd.kind, &gp));
@@ -379,7 +402,8 @@ wsr_status wsr_project_bwd(const wsr_gaussians* g, const wsr_camera* cams, int32
     WsHeader* hdr = (WsHeader*)workspace;
     wsr_grads inner = *grads;
     inner.weight_params = hdr->gw;
-    WSR_CUDA(launch_project_bwd(gp, vs, wd, grad_records, inner, s));
+    float* sb = det ? (float*)((char*)workspace + kWsDetSB) : nullptr;   // sigma/beta per block
+    WSR_CUDA(launch_project_bwd(gp, vs, wd, grad_records, inner, sb, s));
     if (grads->weight_params)
         WSR_CUDA(cudaMemcpyAsync(grads->weight_params, hdr->gw, 6 * sizeof(float), cudaMemcpyDeviceToDevice, s));
     return WSR_OK;
@@ -402,7 +426,7 @@ wsr_status wsr_render_bwd(const wsr_gaussians* g, const float* records, const ui
     }
     WSR_TRY(wsr_render_bwd_tiles(records, g->n, tile_offsets, tile_list, cams, n_cams, tiles, w, out_rgb, out_den,
                                  grad_rgb, grad_records, workspace, workspace_bytes, stream));
-    return wsr_project_bwd(g, cams, n_cams, w, grad_records, grads, workspace, workspace_bytes, stream);
+    return wsr_project_bwd(g, cams, n_cams, tiles, w, grad_records, grads, workspace, workspace_bytes, stream);
 }
 
 wsr_status wsr_count_pairs(const float* records, int64_t n, const uint32_t* tile_offsets, const uint32_t* tile_list,

@@ -304,6 +304,41 @@ __global__ void __launch_bounds__(256) k_order_scatter(const unsigned* __restric
     }
 }
 
+// Deterministic mode: each tile's list sorted by record index, so that the
+// per-pixel sums of the forward and the chunks of the backward do not depend
+// on the order of the scatter's atomics.  A bitonic sort in shared memory over
+// the segment padded to a power of two; a segment longer than kDetMaxSegment
+// is left as it is and reported.
+__global__ void __launch_bounds__(512) k_sort_segments(const unsigned* __restrict__ offsets,
+                                                       unsigned* __restrict__ list, WsHeader* hdr) {
+    __shared__ unsigned key[kDetMaxSegment];
+    const unsigned a = offsets[blockIdx.x], len = offsets[blockIdx.x + 1] - a;
+    if (len <= 1u) return;                                   // the whole block returns together
+    if (len > (unsigned)kDetMaxSegment) {
+        if (threadIdx.x == 0) set_error(hdr, WSR_ERR_UNSUPPORTED);
+        return;
+    }
+    unsigned p = 2;
+    while (p < len) p <<= 1;
+    for (unsigned i = threadIdx.x; i < p; i += blockDim.x) key[i] = i < len ? list[a + i] : 0xffffffffu;
+    __syncthreads();
+    for (unsigned k = 2; k <= p; k <<= 1)
+        for (unsigned j = k >> 1; j > 0; j >>= 1) {
+            for (unsigned i = threadIdx.x; i < p; i += blockDim.x) {
+                const unsigned l = i ^ j;                    // each element is in one pair of the stage
+                if (l > i) {
+                    const unsigned x = key[i], y = key[l];
+                    if ((x > y) == ((i & k) == 0)) {
+                        key[i] = y;
+                        key[l] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (unsigned i = threadIdx.x; i < len; i += blockDim.x) list[a + i] = key[i];
+}
+
 }  // namespace
 
 cudaError_t launch_tile_order(const Views& vs, const unsigned* offsets, unsigned* buckets, unsigned* order,
@@ -344,6 +379,13 @@ cudaError_t launch_bin_scatter(const float* records, long long n, const Views& v
     if (n == 0) return cudaSuccess;
     dim3 grid((unsigned)((n + 255) / 256), (unsigned)vs.n);
     k_bin<true><<<grid, 256, 0, s>>>(reinterpret_cast<const float4*>(records), n, vs, cursor, list, capacity, hdr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort_segments(const Views& vs, const unsigned* offsets, unsigned* list, WsHeader* hdr,
+                                 cudaStream_t s) {
+    if (vs.total_tiles == 0) return cudaSuccess;
+    k_sort_segments<<<(unsigned)vs.total_tiles, 512, 0, s>>>(offsets, list, hdr);
     return cudaGetLastError();
 }
 

@@ -237,11 +237,13 @@ __device__ __forceinline__ void store_n(float* __restrict__ p, const float* v) {
 // fewer: three blocks of 128 per SM instead of two).
 template <int DEG, bool VD, bool RED, bool ONE>
 __global__ void __launch_bounds__(128, ONE ? 3 : 1) k_project_bwd(const GaussPtrs g, const Views vs, const WeightDev wd,
-                                                     const float* __restrict__ grec, const wsr_grads out) {
+                                                     const float* __restrict__ grec, const wsr_grads out,
+                                                     float* __restrict__ det_sb) {
     constexpr int K = (DEG + 1) * (DEG + 1);
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     float gsig = 0.0f, gbeta = 0.0f;
-    if (i < g.n) {
+    // det_sb != nullptr: deterministic mode (fixed-point records, a bounded grid striding over the
+    // Gaussians, sigma/beta summed per block in a fixed order into det_sb)
+    auto body = [&](const long long i) {
         Params<DEG, VD, RED> P;
         load_params<DEG, VD, RED>(g, i, wd.kind, P);
         const float sigma = __ldg(wd.params + 0), beta = __ldg(wd.params + 1);
@@ -263,13 +265,32 @@ __global__ void __launch_bounds__(128, ONE ? 3 : 1) k_project_bwd(const GaussPtr
         const int nv = ONE ? 1 : vs.n;
         for (int v = 0; v < nv; ++v) {
             const View& V = vs.v[v];
-            const float* gr = grec + WSR_GRAD_RECORD_FLOATS * ((long long)v * g.n + i);
             float g9[9];
             bool any = false;
+            if (det_sb == nullptr) {
+                const float* gr = grec + WSR_GRAD_RECORD_FLOATS * ((long long)v * g.n + i);
 #pragma unroll
-            for (int e = 0; e < 9; ++e) {
-                g9[e] = __ldg(gr + e);
-                any |= (g9[e] != 0.0f);
+                for (int e = 0; e < 9; ++e) {
+                    g9[e] = __ldg(gr + e);
+                    any |= (g9[e] != 0.0f);
+                }
+            } else {
+                // 9 int64 sums with kDetBits bits below the magnitude 2^e of their largest partial
+                const float* gr = grec + kDetRecordFloats * ((long long)v * g.n + i);
+                const long long* sums = reinterpret_cast<const long long*>(gr);
+                const int* mag = reinterpret_cast<const int*>(gr + 18);
+#pragma unroll
+                for (int c = 0; c < 9; ++c) {
+                    const float m = __int_as_float(__ldg(mag + c));
+                    float val = 0.0f;
+                    if (m > 0.0f) {
+                        int e;
+                        frexpf(m, &e);
+                        val = (float)ldexp((double)__ldg(sums + c), e - kDetBits);
+                    }
+                    g9[c] = val;
+                    any |= (val != 0.0f);
+                }
             }
             if (!any) continue;
             const float tz0 = V.R[6] * P.p[0] + V.R[7] * P.p[1] + V.R[8] * P.p[2] + V.T[2];
@@ -471,18 +492,55 @@ __global__ void __launch_bounds__(128, ONE ? 3 : 1) k_project_bwd(const GaussPtr
             }
         }
         if (out.lc_v) out.lc_v[i] = glcv;
+    };
+    if (det_sb == nullptr) {
+        const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        if (i < g.n) body(i);
+    } else {
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.n;
+             i += (long long)gridDim.x * blockDim.x)
+            body(i);
     }
-    // global weight parameters: warp reduce, one atomic per warp
-    if (out.weight_params && wd.kind != WSR_WEIGHT_DIR) {
+    // global weight parameters: warp reduce, then one atomic per warp, or (deterministic) the block's sums
+    // in warp order
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            gsig += __shfl_xor_sync(0xffffffffu, gsig, off);
-            gbeta += __shfl_xor_sync(0xffffffffu, gbeta, off);
-        }
+    for (int off = 16; off > 0; off >>= 1) {
+        gsig += __shfl_xor_sync(0xffffffffu, gsig, off);
+        gbeta += __shfl_xor_sync(0xffffffffu, gbeta, off);
+    }
+    if (det_sb != nullptr) {
+        __shared__ float swb[2][4];
         if ((threadIdx.x & 31) == 0) {
-            if (gsig != 0.0f) atomicAdd(out.weight_params + 0, gsig);
-            if (gbeta != 0.0f) atomicAdd(out.weight_params + 1, gbeta);
+            swb[0][threadIdx.x >> 5] = gsig;
+            swb[1][threadIdx.x >> 5] = gbeta;
         }
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            float t = 0.0f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += swb[threadIdx.x][w];
+            det_sb[2 * blockIdx.x + threadIdx.x] = t;
+        }
+    } else if (out.weight_params && wd.kind != WSR_WEIGHT_DIR && (threadIdx.x & 31) == 0) {
+        if (gsig != 0.0f) atomicAdd(out.weight_params + 0, gsig);
+        if (gbeta != 0.0f) atomicAdd(out.weight_params + 1, gbeta);
+    }
+}
+
+// Deterministic mode: the blocks' sigma/beta sums added in block order.
+__global__ void __launch_bounds__(256) k_det_sb_reduce(const float* __restrict__ sb, int nb, float* __restrict__ gw) {
+    __shared__ float part[2][256];
+    float a0 = 0.0f, a1 = 0.0f;
+    for (int b = threadIdx.x; b < nb; b += 256) {
+        a0 += sb[2 * b];
+        a1 += sb[2 * b + 1];
+    }
+    part[0][threadIdx.x] = a0;
+    part[1][threadIdx.x] = a1;
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        float t = 0.0f;
+        for (int k = 0; k < 256; ++k) t += part[threadIdx.x][k];
+        gw[threadIdx.x] = t;
     }
 }
 
@@ -496,11 +554,17 @@ cudaError_t project_t(const GaussPtrs& g, const Views& vs, WeightDev w, float* r
 
 template <int DEG, bool VD, bool RED>
 cudaError_t project_bwd_t(const GaussPtrs& g, const Views& vs, WeightDev w, const float* grec,
-                          const wsr_grads& out, cudaStream_t s) {
+                          const wsr_grads& out, float* det_sb, cudaStream_t s) {
     const int bs = 128;
-    const long long nb = (g.n + bs - 1) / bs;
-    if (vs.n == 1) k_project_bwd<DEG, VD, RED, true><<<(unsigned)nb, bs, 0, s>>>(g, vs, w, grec, out);
-    else k_project_bwd<DEG, VD, RED, false><<<(unsigned)nb, bs, 0, s>>>(g, vs, w, grec, out);
+    long long nb = (g.n + bs - 1) / bs;
+    if (det_sb && nb > kDetSBBlocks) nb = kDetSBBlocks;    // one sigma/beta slot per block
+    if (vs.n == 1) k_project_bwd<DEG, VD, RED, true><<<(unsigned)nb, bs, 0, s>>>(g, vs, w, grec, out, det_sb);
+    else k_project_bwd<DEG, VD, RED, false><<<(unsigned)nb, bs, 0, s>>>(g, vs, w, grec, out, det_sb);
+    if (det_sb) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_det_sb_reduce<<<1, 256, 0, s>>>(det_sb, (int)nb, out.weight_params);
+    }
     return cudaGetLastError();
 }
 
@@ -516,12 +580,12 @@ cudaError_t project_deg(const GaussPtrs& g, const Views& vs, WeightDev w, float*
 
 template <bool VD, bool RED>
 cudaError_t project_bwd_deg(const GaussPtrs& g, const Views& vs, WeightDev w, const float* grec,
-                            const wsr_grads& out, cudaStream_t s) {
+                            const wsr_grads& out, float* det_sb, cudaStream_t s) {
     switch (g.deg) {
-        case 0: return project_bwd_t<0, VD, RED>(g, vs, w, grec, out, s);
-        case 1: return project_bwd_t<1, VD, RED>(g, vs, w, grec, out, s);
-        case 2: return project_bwd_t<2, VD, RED>(g, vs, w, grec, out, s);
-        default: return project_bwd_t<3, VD, RED>(g, vs, w, grec, out, s);
+        case 0: return project_bwd_t<0, VD, RED>(g, vs, w, grec, out, det_sb, s);
+        case 1: return project_bwd_t<1, VD, RED>(g, vs, w, grec, out, det_sb, s);
+        case 2: return project_bwd_t<2, VD, RED>(g, vs, w, grec, out, det_sb, s);
+        default: return project_bwd_t<3, VD, RED>(g, vs, w, grec, out, det_sb, s);
     }
 }
 
@@ -534,13 +598,13 @@ cudaError_t launch_project(const GaussPtrs& g, const Views& vs, WeightDev w, flo
 }
 
 cudaError_t launch_project_bwd(const GaussPtrs& g, const Views& vs, WeightDev w, const float* grec,
-                               const wsr_grads& out, cudaStream_t s) {
+                               const wsr_grads& out, float* det_sb, cudaStream_t s) {
     if (g.n == 0) return cudaSuccess;
     if (g.vd)
-        return g.red ? project_bwd_deg<true, true>(g, vs, w, grec, out, s)
-                     : project_bwd_deg<true, false>(g, vs, w, grec, out, s);
-    return g.red ? project_bwd_deg<false, true>(g, vs, w, grec, out, s)
-                 : project_bwd_deg<false, false>(g, vs, w, grec, out, s);
+        return g.red ? project_bwd_deg<true, true>(g, vs, w, grec, out, det_sb, s)
+                     : project_bwd_deg<true, false>(g, vs, w, grec, out, det_sb, s);
+    return g.red ? project_bwd_deg<false, true>(g, vs, w, grec, out, det_sb, s)
+                 : project_bwd_deg<false, false>(g, vs, w, grec, out, det_sb, s);
 }
 
 }  // namespace wsr

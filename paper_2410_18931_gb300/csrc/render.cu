@@ -274,7 +274,7 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                                          const Views& vs, const float* __restrict__ wparams,
                                          const float* __restrict__ out_rgb, const float* __restrict__ out_den,
                                          const float* __restrict__ grad_rgb, float* __restrict__ grec,
-                                         float* __restrict__ gw) {
+                                         float* __restrict__ gw, const int pass, float* __restrict__ bg_tiles) {
     constexpr int NT = 2 * CH;
     constexpr int NW = NT / 32;
     constexpr int PW = TW + 1;                          // pixel-table row pitch: one zero column
@@ -558,17 +558,46 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 vc += sslot[t][4].x;
             }
             // record: sum gq r, sum gq dx, sum gq r^2, sum gq r dx, sum gq dx^2, d/d(u w), d/d(c u w)
-            float4* o = reinterpret_cast<float4*>(grec + (size_t)WSR_GRAD_RECORD_FLOATS * sidx[tid]);
-            atomicAdd(o, make_float4(vm.x, vm.y, vrx.x, vc));
-            atomicAdd(o + 1, make_float4(vrx.y, v23.y, v01.x, v01.y));
-            atomicAdd(reinterpret_cast<float*>(o + 2), v23.x);
+            if (pass == 0) {
+                float4* o = reinterpret_cast<float4*>(grec + (size_t)WSR_GRAD_RECORD_FLOATS * sidx[tid]);
+                atomicAdd(o, make_float4(vm.x, vm.y, vrx.x, vc));
+                atomicAdd(o + 1, make_float4(vrx.y, v23.y, v01.x, v01.y));
+                atomicAdd(reinterpret_cast<float*>(o + 2), v23.x);
+            } else {
+                // deterministic mode: a 128-byte record holds 9 int64 sums, then 9 magnitudes (float bits)
+                const float vals[9] = {vm.x, vm.y, vrx.x, vc, vrx.y, v23.y, v01.x, v01.y, v23.x};
+                float* o = grec + (size_t)kDetRecordFloats * sidx[tid];
+                int* mag = reinterpret_cast<int*>(o + 18);
+                if (pass == 1) {
+                    // the largest |partial| of each term (non-negative floats order as their bit patterns)
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) atomicMax(mag + c, __float_as_int(fabsf(vals[c])));
+                } else {
+                    // each partial as fixed point with kDetBits bits below that magnitude: exact integer sums
+                    unsigned long long* sum = reinterpret_cast<unsigned long long*>(o);
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) {
+                        const float m = __int_as_float(mag[c]);
+                        if (m > 0.0f) {
+                            int e;
+                            frexpf(m, &e);                  // m < 2^e
+                            const long long q = __double2ll_rn(ldexp((double)vals[c], kDetBits - e));
+                            atomicAdd(sum + c, (unsigned long long)q);
+                        }
+                    }
+                }
+            }
         }
     }
     __syncthreads();
     if (tid < 4) {
         float t = 0.0f;
         for (int w = 0; w < NW; ++w) t += sbg[tid][w];
-        if (t != 0.0f) atomicAdd(gw + 2 + tid, t);
+        if (pass == 0) {
+            if (t != 0.0f) atomicAdd(gw + 2 + tid, t);
+        } else if (pass == 2) {
+            bg_tiles[4 * (size_t)tile + tid] = t;      // summed in tile order afterwards
+        }
     }
 }
 
@@ -578,10 +607,30 @@ __global__ void __launch_bounds__(2 * CH, 512 / CH)
                  const unsigned* __restrict__ list, const Views vs, const float* __restrict__ wparams,
                  const float* __restrict__ out_rgb, const float* __restrict__ out_den,
                  const float* __restrict__ grad_rgb, float* __restrict__ grec, float* __restrict__ gw,
-                 const unsigned* __restrict__ order, unsigned* __restrict__ counter) {
+                 const int pass, float* __restrict__ bg_tiles, const unsigned* __restrict__ order,
+                 unsigned* __restrict__ counter) {
     for_each_tile(order, counter, vs.total_tiles, [&](int tile) {
-        bwd_tile<TW, TH, CH>(tile, rec, offsets, list, vs, wparams, out_rgb, out_den, grad_rgb, grec, gw);
+        bwd_tile<TW, TH, CH>(tile, rec, offsets, list, vs, wparams, out_rgb, out_den, grad_rgb, grec, gw, pass,
+                             bg_tiles);
     });
+}
+
+// Deterministic mode: the tiles' background terms summed in a fixed order.
+__global__ void __launch_bounds__(256) k_det_bg_reduce(const float* __restrict__ bg, int n_tiles,
+                                                       float* __restrict__ gw) {
+    __shared__ float part[4][256];
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int t = threadIdx.x; t < n_tiles; t += 256)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] += bg[4 * (size_t)t + c];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) part[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        float sum = 0.0f;
+        for (int k = 0; k < 256; ++k) sum += part[threadIdx.x][k];
+        gw[2 + threadIdx.x] = sum;
+    }
 }
 
 // Grid of a launch: one block per tile, or, persistent, as many blocks as
@@ -612,24 +661,26 @@ cudaError_t fwd_t(const float* rec, const unsigned* off, const unsigned* list, c
 
 template <int TW, int TH, int CH>
 cudaError_t bwd_chunk(const float* rec, const unsigned* off, const unsigned* list, const Views& vs, WeightDev w,
-                      const float* rgb, const float* den, const float* grgb, float* grec, float* gw, Sched sched,
-                      cudaStream_t s) {
+                      const float* rgb, const float* den, const float* grgb, float* grec, float* gw, int pass,
+                      float* bg_tiles, Sched sched, cudaStream_t s) {
     const unsigned grid = grid_for(k_render_bwd<TW, TH, CH>, 2 * CH, vs, sched);
     if (sched.order) {
         cudaError_t e = cudaMemsetAsync(sched.counter, 0, sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
     }
     k_render_bwd<TW, TH, CH><<<grid, 2 * CH, 0, s>>>(reinterpret_cast<const float4*>(rec), off, list, vs, w.params,
-                                                     rgb, den, grgb, grec, gw, sched.order, sched.counter);
+                                                     rgb, den, grgb, grec, gw, pass, bg_tiles, sched.order,
+                                                     sched.counter);
     return cudaGetLastError();
 }
 
 template <int TW, int TH>
 cudaError_t bwd_t(const float* rec, const unsigned* off, const unsigned* list, const Views& vs, WeightDev w,
-                  const float* rgb, const float* den, const float* grgb, float* grec, float* gw, Sched sched,
-                  cudaStream_t s) {
-    if (vs.chunk == 64) return bwd_chunk<TW, TH, 64>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, sched, s);
-    return bwd_chunk<TW, TH, 128>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, sched, s);
+                  const float* rgb, const float* den, const float* grgb, float* grec, float* gw, int pass,
+                  float* bg_tiles, Sched sched, cudaStream_t s) {
+    if (vs.chunk == 64)
+        return bwd_chunk<TW, TH, 64>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sched, s);
+    return bwd_chunk<TW, TH, 128>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sched, s);
 }
 
 // Diagnostic: (pixel, Gaussian) pairs inside the cutoff, i.e. the
@@ -729,13 +780,22 @@ cudaError_t launch_render_fwd(const float* rec, const unsigned* off, const unsig
 
 cudaError_t launch_render_bwd(const float* rec, const unsigned* off, const unsigned* list, const Views& vs,
                               WeightDev w, const float* rgb, const float* den, const float* grgb, float* grec,
-                              float* gw, Sched sc, cudaStream_t s) {
+                              float* gw, int pass, float* bg_tiles, Sched sc, cudaStream_t s) {
     if (vs.total_tiles == 0) return cudaSuccess;
-    if (vs.tile_w == 16 && vs.tile_h == 16) return bwd_t<16, 16>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, sc, s);
-    if (vs.tile_w == 8 && vs.tile_h == 8) return bwd_t<8, 8>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, sc, s);
-    if (vs.tile_w == 32 && vs.tile_h == 8) return bwd_t<32, 8>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, sc, s);
-    if (vs.tile_w == 16 && vs.tile_h == 8) return bwd_t<16, 8>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, sc, s);
+    if (vs.tile_w == 16 && vs.tile_h == 16)
+        return bwd_t<16, 16>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sc, s);
+    if (vs.tile_w == 8 && vs.tile_h == 8)
+        return bwd_t<8, 8>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sc, s);
+    if (vs.tile_w == 32 && vs.tile_h == 8)
+        return bwd_t<32, 8>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sc, s);
+    if (vs.tile_w == 16 && vs.tile_h == 8)
+        return bwd_t<16, 8>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sc, s);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_det_bg_reduce(const float* bg_tiles, int n_tiles, float* gw, cudaStream_t s) {
+    k_det_bg_reduce<<<1, 256, 0, s>>>(bg_tiles, n_tiles, gw);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_count_pairs(const float* rec, const unsigned* off, const unsigned* list, const Views& vs,

@@ -41,11 +41,15 @@ struct Views {
     long long total_pix;
     int schedule;         // WSR_SCHEDULE_*
     int chunk;            // Gaussians per block of the backward (64 or 128)
+    int det;              // deterministic mode (wsr_tiles.deterministic)
     View v[WSR_MAX_VIEWS];
 };
 
-// Workspace layout: [header 256 B][cursor: total_tiles + 1 u32][block sums]
+// Workspace layout: [header 8 KB][cursor: total_tiles + 1 u32][block sums]
 //                   [tile order: total_tiles u32][order buckets: 64 u32]
+//                   [deterministic mode: background terms per tile, 4 floats]
+// The header's first 256 bytes are the struct below; in deterministic mode the
+// projection backward keeps its per-block sigma/beta sums after it.
 struct WsHeader {
     int err;                   // first device-side error (wsr_status), 0 if none
     int pad0;
@@ -54,7 +58,15 @@ struct WsHeader {
     unsigned int work[4];      // persistent-schedule counters: [0] forward, [1] backward
 };
 
-constexpr size_t kWsHeader = 256;
+constexpr size_t kWsHeader = 8192;
+constexpr size_t kWsDetSB = 256;       // deterministic mode: sigma/beta per projection-backward block
+constexpr int kDetSBBlocks = (int)((kWsHeader - kWsDetSB) / (2 * sizeof(float)));   // 992
+// Deterministic mode: a record term is added as 64-bit fixed point with kDetBits
+// bits below the largest magnitude of its partials, so up to 2^(62 - kDetBits)
+// partials per record sum without overflow.
+constexpr int kDetBits = 37;
+constexpr int kDetRecordFloats = WSR_GRAD_RECORD_FLOATS_DET;
+constexpr int kDetMaxSegment = WSR_DET_MAX_SEGMENT;
 constexpr int kScanBlock = 1024;       // threads of a scan block
 constexpr int kScanItems = 4;          // elements per scan thread
 constexpr int kScanTile = kScanBlock * kScanItems;

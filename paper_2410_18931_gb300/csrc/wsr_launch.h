@@ -27,8 +27,10 @@ struct WeightDev {
 
 cudaError_t launch_project(const GaussPtrs& g, const Views& vs, WeightDev w, float* records,
                            cudaStream_t s);
+// det_sb: nullptr, or (deterministic mode) room for kDetSBBlocks pairs of sigma/beta block sums; the
+// records are then WSR_GRAD_RECORD_FLOATS_DET floats of fixed-point sums and their scales
 cudaError_t launch_project_bwd(const GaussPtrs& g, const Views& vs, WeightDev w,
-                               const float* grad_records, const wsr_grads& out, cudaStream_t s);
+                               const float* grad_records, const wsr_grads& out, float* det_sb, cudaStream_t s);
 
 cudaError_t launch_bin_count(const float* records, long long n, const Views& vs,
                              unsigned* cursor, cudaStream_t s);
@@ -41,6 +43,9 @@ cudaError_t launch_bin_scatter(const float* records, long long n, const Views& v
 
 cudaError_t launch_tile_order(const Views& vs, const unsigned* tile_offsets, unsigned* buckets,
                               unsigned* order, cudaStream_t s);
+// deterministic mode: each tile's list sorted by record index
+cudaError_t launch_sort_segments(const Views& vs, const unsigned* tile_offsets, unsigned* tile_list,
+                                 WsHeader* hdr, cudaStream_t s);
 
 // Work distribution of a render launch: order == nullptr means one block per
 // tile; otherwise a persistent grid takes tiles order[0..total) via *counter
@@ -53,10 +58,16 @@ struct Sched {
 cudaError_t launch_render_fwd(const float* records, const unsigned* tile_offsets,
                               const unsigned* tile_list, const Views& vs, WeightDev w,
                               float* out_rgb, float* out_den, Sched sched, cudaStream_t s);
+// pass 0: float atomics into WSR_GRAD_RECORD_FLOATS records and grad_wparams.  Deterministic mode
+// (WSR_GRAD_RECORD_FLOATS_DET records): pass 1 takes each record term's largest magnitude, pass 2
+// adds the terms as fixed point and stores each tile's background terms in bg_tiles[4 tile + c].
 cudaError_t launch_render_bwd(const float* records, const unsigned* tile_offsets,
                               const unsigned* tile_list, const Views& vs, WeightDev w,
                               const float* out_rgb, const float* out_den, const float* grad_rgb,
-                              float* grad_records, float* grad_wparams, Sched sched, cudaStream_t s);
+                              float* grad_records, float* grad_wparams, int pass, float* bg_tiles, Sched sched,
+                              cudaStream_t s);
+// deterministic mode: grad_wparams[2..5] = the tiles' background terms summed in tile order
+cudaError_t launch_det_bg_reduce(const float* bg_tiles, int n_tiles, float* grad_wparams, cudaStream_t s);
 
 cudaError_t launch_count_pairs(const float* records, const unsigned* tile_offsets, const unsigned* tile_list,
                                const Views& vs, unsigned long long* count, cudaStream_t s);

@@ -76,14 +76,17 @@ class Renderer:
     """Renders a fixed set of views at a fixed tile shape."""
 
     def __init__(self, cams, tile=(16, 16), device="cuda", headroom: float = 1.25, persistent: bool = False,
-                 chunk: int = 0):
+                 chunk: int = 0, deterministic: bool = False):
         self.lib = A.load()
         self.device = torch.device(device)
         self.cams = list(cams)
         self.cams_c, self.n_cams = A.make_cameras(self.cams)
         self.persistent = bool(persistent)
+        self.deterministic = bool(deterministic)
         self.tiles_c = A.tiles(*tile, A.WSR_SCHEDULE_PERSISTENT if persistent else A.WSR_SCHEDULE_TILE_BLOCKS,
-                               chunk)
+                               chunk, int(self.deterministic))
+        # floats per gradient record of the render backward (wider in the deterministic mode)
+        self.record_floats = A.WSR_GRAD_RECORD_FLOATS_DET if self.deterministic else A.WSR_GRAD_RECORD_FLOATS
         self.chunk = int(chunk)
         self.tile = tuple(tile)
         self.num_tiles = int(self.lib.wsr_num_tiles(self.cams_c, self.n_cams, ctypes.byref(self.tiles_c)))
@@ -145,8 +148,8 @@ class Renderer:
     def wsr_project_bwd(self, g, kind, wparams, grad_records, grads: A.wsr_grads, stream=None):
         w = A.wsr_weight(kind, wparams.data_ptr())
         A.check("wsr_project_bwd", self.lib.wsr_project_bwd(
-            ctypes.byref(g.c_struct()), self.cams_c, self.n_cams, ctypes.byref(w), _ptr(grad_records),
-            ctypes.byref(grads), _ptr(self.workspace), self.workspace.numel(), _stream(stream)))
+            ctypes.byref(g.c_struct()), self.cams_c, self.n_cams, ctypes.byref(self.tiles_c), ctypes.byref(w),
+            _ptr(grad_records), ctypes.byref(grads), _ptr(self.workspace), self.workspace.numel(), _stream(stream)))
 
     def wsr_count_pairs(self, st: FrameState, stream=None) -> int:
         cnt = torch.zeros(1, dtype=torch.int64, device=self.device)
@@ -209,7 +212,7 @@ class Renderer:
                        opacity=torch.empty((n, K) if g.view_dependent else (n,), device=dev),
                        lc_v=torch.empty(n, device=dev), weight_params=torch.empty(6, device=dev))
         if grad_records is None:
-            grad_records = torch.empty(self.n_cams * n * A.WSR_GRAD_RECORD_FLOATS, device=dev)
+            grad_records = torch.empty(self.n_cams * n * self.record_floats, device=dev)
         grads = A.wsr_grads(*[out[k].data_ptr() if out.get(k) is not None else None
                               for k in ("means", "log_scales", "quats", "sh", "opacity", "lc_v", "weight_params")])
         self.wsr_render_bwd(g, st.records, st.tile_offsets, st.tile_list, kind, wparams, st.rgb, st.den,

@@ -142,10 +142,11 @@ class TrainStep:
 
     def __init__(self, flat: FlatParams, sh_degree: int, view_dependent: bool, cams, kind: int,
                  target: torch.Tensor, lr: dict | None = None, lam: float = DSSIM_LAMBDA, tile=(16, 16),
-                 persistent: bool = False, headroom: float = 1.5, capture: bool = True, chunk: int = 0):
+                 persistent: bool = False, headroom: float = 1.5, capture: bool = True, chunk: int = 0,
+                 deterministic: bool = False):
         self.flat, self.kind, self.lam = flat, kind, float(lam)
         self.cams, self.tile, self.persistent, self.headroom = list(cams), tile, persistent, headroom
-        self.chunk = int(chunk)
+        self.chunk, self.deterministic = int(chunk), bool(deterministic)
         self.g = flat.gaussians(sh_degree, view_dependent)
         self.wparams = flat.param["weight_params"]
         self.target = target.reshape(-1, 3).contiguous().float()
@@ -160,10 +161,10 @@ class TrainStep:
     def _build(self, capture: bool):
         dev = self.flat.device
         self.r = Renderer(self.cams, tile=self.tile, persistent=self.persistent, headroom=self.headroom,
-                          chunk=self.chunk)
+                          chunk=self.chunk, deterministic=self.deterministic)
         self.st = self.r.forward(self.g, self.kind, self.wparams)
         self.grad_rgb = torch.empty_like(self.st.rgb)
-        self.grad_records = torch.empty(self.r.n_cams * self.g.n * A.WSR_GRAD_RECORD_FLOATS, device=dev)
+        self.grad_records = torch.empty(self.r.n_cams * self.g.n * self.r.record_floats, device=dev)
         self.graph = None
         if capture:
             snap = self.opt.snapshot()
@@ -197,8 +198,9 @@ class TrainStep:
 
     @property
     def kernels_per_step(self) -> int:
-        # project 1, bin 5 (+3 tile-order kernels when persistent), fwd 1, loss 1, bwd 1, project bwd 1, Adam 2
-        return 12 + (3 if self.persistent else 0)
+        # project 1, bin 5 (+3 tile-order kernels when persistent), fwd 1, loss 1, bwd 1, project bwd 1, Adam 2;
+        # deterministic: + the list sort, a second backward pass and two ordered reductions
+        return 12 + (3 if self.persistent else 0) + (4 if self.deterministic else 0)
 
     def train(self, steps: int, check_every: int = 10) -> torch.Tensor:
         """Make ``steps`` Adam updates; returns the loss triples {L, L1, SSIM}

@@ -186,3 +186,21 @@ def test_bench_uses_a_fixed_launch_configuration_as_given():
     assert bench.launch_config(args, None, None, None, None) == ((16, 8), True, 64, None)
     args = argparse.Namespace(tile="32x8", schedule="per-tile", chunk="128")
     assert bench.launch_config(args, None, None, None, None) == ((32, 8), False, 128, None)
+
+
+def test_deterministic_flag_is_validated(lib):
+    """wsr_tiles.deterministic: 0 or 1; the deterministic workspace holds the
+    per-tile background terms as well; wsr_project_bwd checks the flag too."""
+    from paper_2410_18931_gb300 import _abi as A
+    cams, n = _cam(64, 48)
+    base = lib.wsr_workspace_size(cams, n, ctypes.byref(A.tiles(16, 16)))
+    det = lib.wsr_workspace_size(cams, n, ctypes.byref(A.tiles(16, 16, 0, 0, 1)))
+    assert det > base > 0
+    assert lib.wsr_workspace_size(cams, n, ctypes.byref(A.tiles(16, 16, 0, 0, 2))) == 0
+    assert lib.wsr_workspace_size(cams, n, ctypes.byref(A.tiles(16, 16, 0, 0, -1))) == 0
+    fake = 1 << 20   # never dereferenced: validation fails first
+    g = A.wsr_gaussians()
+    w = A.wsr_weight(0, fake)
+    grads = A.wsr_grads()
+    assert lib.wsr_project_bwd(ctypes.byref(g), cams, n, ctypes.byref(A.tiles(16, 16, 0, 0, 3)), ctypes.byref(w),
+                               fake, ctypes.byref(grads), fake, 1 << 16, None) == A.WSR_ERR_INVALID_ARG

@@ -1,0 +1,92 @@
+"""Deterministic mode (wsr_tiles.deterministic = 1): every output bit for bit
+the same from run to run, the tile lists sorted by record index and holding
+the same pairs as the default binning, the images and gradients within the
+usual tolerances of the FP64 oracle and within rounding of the default mode,
+and a tile beyond the sort's bound reported."""
+import numpy as np
+import pytest
+
+import oracle
+import wsr_scenes as ws
+from tests.gpu_util import AMB_TAU, FWD_TOL, GRAD_TOL, add_envelopes, compare_image, grad_envelope, grad_excess
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("means", "log_scales", "quats", "sh", "opacity", "lc_v", "weight_params")
+
+
+def _run(sc, cams, w, G, tile, persistent, chunk, deterministic):
+    import torch
+    from paper_2410_18931_gb300 import Gaussians, Renderer
+    g = Gaussians.from_scene(sc)
+    wpar = torch.tensor(w.as_array(), device="cuda")
+    r = Renderer(cams, tile=tile, persistent=persistent, chunk=chunk, deterministic=deterministic)
+    st = r.forward(g, w.kind, wpar)
+    out = r.backward(g, w.kind, wpar, st, G)
+    torch.cuda.synchronize()
+    res = {k: out[k].clone() for k in KEYS}
+    res["rgb"], res["den"] = st.rgb.clone(), st.den.clone()
+    total = int(st.tile_offsets[-1])
+    res["offsets"], res["list"] = st.tile_offsets.clone(), st.tile_list[:total].clone()
+    return res
+
+
+@pytest.mark.parametrize("tile,persistent,chunk", [((16, 16), True, 64), ((8, 8), False, 128), ((32, 8), True, 128)])
+def test_deterministic_mode_is_bitwise_reproducible_and_matches_the_oracle(tile, persistent, chunk):
+    import torch
+    sc = ws.random_scene(6000, 81, sh_degree=3, vd_opacity=True, clusters=8, box=1.2, log_scale_mu=-3.2)
+    cams = [ws.look_at((0.2, 0.1, -3.5), width=120, height=90).rounded(),
+            ws.look_at((-1.4, 0.5, -3.0), width=77, height=61).rounded()]
+    w = ws.WeightParams(ws.EXP, 0.1, 0.8, 0.7, (0.2, 0.1, 0.3)).rounded()
+    rng = np.random.default_rng(82)
+    Gs = [rng.normal(size=(c.height, c.width, 3)).astype(np.float32) for c in cams]
+    G = torch.tensor(np.concatenate([x.reshape(-1, 3) for x in Gs]), device="cuda")
+    a = _run(sc, cams, w, G, tile, persistent, chunk, True)
+    b = _run(sc, cams, w, G, tile, persistent, chunk, True)
+    for k in a:
+        assert torch.equal(a[k], b[k]), k                       # bit for bit, every output
+    # the lists: the default binning's pairs, each tile's segment in increasing record index
+    d = _run(sc, cams, w, G, tile, persistent, chunk, False)
+    off = a["offsets"].cpu().numpy().astype(np.int64)
+    lst, lst_d = a["list"].cpu().numpy().astype(np.int64), d["list"].cpu().numpy().astype(np.int64)
+    assert np.array_equal(off, d["offsets"].cpu().numpy().astype(np.int64))
+    for t in range(len(off) - 1):
+        seg = lst[off[t]:off[t + 1]]
+        assert np.all(np.diff(seg) > 0), t
+        assert np.array_equal(seg, np.sort(lst_d[off[t]:off[t + 1]])), t
+    # the same results as the default mode up to rounding order
+    for k in ("rgb", "den") + KEYS:
+        x, y = a[k].double(), d[k].double()
+        assert float((x - y).abs().max()) <= 1e-4 * max(float(y.abs().max()), 1e-12), k
+    # and the method itself: images and gradients against the oracle
+    rgb = a["rgb"].cpu().numpy()
+    o, env = 0, None
+    for c, Gv in zip(cams, Gs):
+        m = c.width * c.height
+        ref = oracle.render(sc, c, w, amb_tau=AMB_TAU)
+        excess, raw, n_amb = compare_image(rgb[o:o + m].reshape(c.height, c.width, 3), ref)
+        assert excess <= FWD_TOL, (excess, raw, n_amb)
+        o += m
+        e = grad_envelope(sc, c, w, Gv.astype(np.float64))
+        env = e if env is None else add_envelopes(env, e)
+    for k in ("means", "log_scales", "quats", "sh", "opacity"):
+        assert grad_excess(a[k].cpu().numpy(), env, k) <= GRAD_TOL, k
+
+
+def test_deterministic_mode_reports_a_tile_beyond_its_sort_bound():
+    """20,000 Gaussians stacked where two tiles meet: more instances in a tile
+    than the sort holds, reported as unsupported (nothing is rendered)."""
+    import torch
+    from paper_2410_18931_gb300 import Gaussians, Renderer
+    from paper_2410_18931_gb300 import _abi as A
+    stack = ws.random_scene(20_000, 42, sh_degree=0, vd_opacity=False, box=0.01, log_scale_mu=-5.5,
+                            log_scale_sd=0.2)
+    stack.means[:] += np.array([0.05, 0.05, 0.0], np.float32)
+    cam = ws.look_at((0.0, 0.0, -3.0), width=96, height=80).rounded()
+    w = ws.WeightParams(ws.EXP, 0.1, 0.8, 1.0, (0.0, 0.0, 0.0))
+    g = Gaussians.from_scene(stack)
+    wpar = torch.tensor(w.as_array(), device="cuda")
+    r = Renderer([cam], deterministic=True)
+    with pytest.raises(A.WSRError) as err:
+        r.forward(g, w.kind, wpar)
+    assert err.value.status == A.WSR_ERR_UNSUPPORTED
