@@ -46,6 +46,7 @@ if ROOT not in sys.path:
 FLOPS_PER_PAIR_FWD = 17
 FLOPS_PER_PAIR_BWD = 35
 FP32_LANES_PER_SM = 128
+MUFU_PER_SM = 16         # ex2 / rsqrt / rcp results per SM and clock
 SM_MAX_MHZ = 2070.0
 METRIC = "fwd and fwd+bwd Mpix/s at 1M Gaussians 1080p vs plain FP32 path; max err"
 KERNELS_PER_STEP = 10    # project 1, bin 5 (count, 3 scan, scatter), fwd 1, loss 1, bwd tiles 1, project bwd 1
@@ -316,7 +317,9 @@ def cpu_oracle_leg(scene, cam, weight, target, gpu_rgb, budget_s: float):
             "sample": f"fwd+bwd (Eq. 7 and its gradient, FP64) on bands of {r1} and {r2} rows of the same "
                       f"1M-Gaussian 1080p view ({tw + t1 + t2:.1f} s with a first, untimed call); whole view "
                       f"extrapolated as {fixed:.2f} s per call + {per_row * 1e3:.1f} ms per row"}
+    mse = float(np.mean(err ** 2))
     maxerr = {"max_abs_err": float(err.max()), "max_abs_err_beyond_tie_bound": float(max(excess.max(), 0.0)),
+              "psnr_db_vs_oracle": round(10.0 * np.log10(1.0 / mse), 2) if mse > 0 else None,
               "pixels_checked": int(r2 * cam.width), "tolerance": 1e-4}
     return base, maxerr
 
@@ -494,6 +497,9 @@ def run_ours(args):
                 "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": profile_traffic(kern),
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 (FMA) x {SM_MAX_MHZ:.0f} MHz",
                 "work": f"{pairs} pairs with q <= 9 x {fl} FP32 flops"}
+        if clk.get("sm_mhz"):
+            # the same work against the peak at the SM clock measured under load
+            roof["frac_at_measured_clock"] = round(ach / (peak * float(clk["sm_mhz"]) / SM_MAX_MHZ), 4)
         if kern == "k_render_bwd":
             # what bounds it (from the kernel's ncu capture): not FP32 throughput
             roof["note"] = ("limited by the shared-memory pipe (~0.84 wavefronts per SM-cycle of 1, about half "
@@ -512,9 +518,17 @@ def run_ours(args):
     K = (S.g.sh_degree + 1) ** 2
     param_bytes = S.g.n * (12 + 12 + 16 + K * 12 + (K * 4 if S.g.view_dependent else 4) + 4)
     stages = {n: round(float(v), 4) for n, v in zip(names, stage_ms)}
+    clk_hz = SM_MAX_MHZ * 1e6
+    # binning's algorithmic bytes: the records read once, a 4-byte index per instance, the offsets
+    bin_bytes = S.g.n * 48 + 4 * instances + 4 * (S.r.num_tiles + 1)
     extra_out = {
         "fwd_mpix_s": round(fwd_value, 2),
+        "ms_per_step_median": round(float(np.median(step_ms)), 4),
         "stage_ms": stages,
+        # the forward against the FP32 lanes (17 flops per pair) and the MUFU (one ex2 per pair)
+        "render_fwd_alu_frac": round(pairs * FLOPS_PER_PAIR_FWD / (stage_ms[2] * 1e-3) / (peak * 1e12), 4),
+        "render_fwd_mufu_frac": round(pairs / (stage_ms[2] * 1e-3) / (sms * MUFU_PER_SM * clk_hz), 4),
+        "bin_hbm_frac": round(bin_bytes / (stage_ms[1] * 1e-3) / 1e9 / hbm_peak, 4),
         "project_hbm_frac": round((param_bytes + S.g.n * 48) / (stage_ms[0] * 1e-3) / 1e9 / hbm_peak, 4),
         "project_bwd_hbm_frac": round((2 * param_bytes + S.g.n * 36) / (stage_ms[5] * 1e-3) / 1e9 / hbm_peak, 4),
         "pairs_in_cutoff": pairs, "tile_instances": instances,
