@@ -23,6 +23,10 @@
  *   - All data pointers are DEVICE pointers owned by the caller.  The library
  *     allocates no memory; scratch comes from a caller-provided workspace
  *     whose size wsr_workspace_size() returns (256-byte aligned).
+ *   - Alignment: render records and gradient records (read and updated as
+ *     16-byte vectors), the workspace and the parameter arrays 16-byte
+ *     aligned; every other array to its element size.  A misaligned
+ *     pointer is WSR_ERR_INVALID_ARG.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy stream).  All
  *     work is enqueued asynchronously on it; no call synchronises the stream
  *     except wsr_check() and wsr_bin_total().

@@ -20,6 +20,7 @@ bool tiles_ok(const wsr_tiles* t) {
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+bool aligned4(const void* p) { return ((uintptr_t)p & 3u) == 0; }
 
 // Builds the per-view constant table.  Returns WSR_OK or the argument error.
 wsr_status make_views(const wsr_camera* cams, int32_t n_cams, const wsr_tiles* tiles, Views* vs) {
@@ -274,6 +275,7 @@ wsr_status wsr_bin_count(const float* records, int64_t n, const wsr_camera* cams
     WSR_TRY(make_views(cams, n_cams, tiles, &vs));
     WSR_TRY(check_ws(vs, workspace, workspace_bytes));
     if (n < 0 || (n > 0 && (!records || !aligned16(records))) || !tile_offsets) return WSR_ERR_INVALID_ARG;
+    if (!aligned4(tile_offsets)) return WSR_ERR_INVALID_ARG;
     if ((unsigned long long)n * (unsigned long long)n_cams > 0xffffffffull) return WSR_ERR_INVALID_ARG;
     return bin_count_impl(records, n, vs, tile_offsets, ~0ull, workspace, (cudaStream_t)stream);
 }
@@ -287,6 +289,7 @@ wsr_status wsr_bin(const float* records, int64_t n, const wsr_camera* cams, int3
     WSR_TRY(check_ws(vs, workspace, workspace_bytes));
     if (n < 0 || (n > 0 && (!records || !aligned16(records))) || !tile_offsets) return WSR_ERR_INVALID_ARG;
     if (list_capacity > 0 && !tile_list) return WSR_ERR_INVALID_ARG;
+    if (!aligned4(tile_offsets) || !aligned4(tile_list)) return WSR_ERR_INVALID_ARG;
     if ((unsigned long long)n * (unsigned long long)n_cams > 0xffffffffull) return WSR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     WSR_TRY(bin_count_impl(records, n, vs, tile_offsets, list_capacity, workspace, s));
@@ -308,6 +311,7 @@ wsr_status wsr_bin_static(const float* records, int64_t n, const wsr_camera* cam
     if (vs.schedule != WSR_SCHEDULE_TILE_BLOCKS) return WSR_ERR_UNSUPPORTED;
     if (n < 0 || (n > 0 && (!records || !aligned16(records))) || !tile_offsets) return WSR_ERR_INVALID_ARG;
     if (list_capacity > 0 && !tile_list) return WSR_ERR_INVALID_ARG;
+    if (!aligned4(tile_offsets) || !aligned4(tile_list)) return WSR_ERR_INVALID_ARG;
     if ((unsigned long long)n * (unsigned long long)n_cams > 0xffffffffull) return WSR_ERR_INVALID_ARG;
     void* scratch = nullptr;
     WSR_TRY(static_scratch(&scratch));
@@ -347,6 +351,10 @@ wsr_status wsr_render_fwd(const float* records, int64_t n, const uint32_t* tile_
     WSR_TRY(check_ws(vs, workspace, workspace_bytes));
     if (n < 0 || !tile_offsets || !out_rgb || !out_den) return WSR_ERR_INVALID_ARG;
     if (n > 0 && (!records || !tile_list)) return WSR_ERR_INVALID_ARG;
+    // the records are read as float4; every other array as 32-bit words
+    if (!aligned16(records) || !aligned4(tile_list) || !aligned4(tile_offsets) || !aligned4(out_rgb) ||
+        !aligned4(out_den))
+        return WSR_ERR_INVALID_ARG;
     return cuda_status(launch_render_fwd(records, tile_offsets, tile_list, vs, wd, out_rgb, out_den,
                                          sched_of(vs, workspace, 0), (cudaStream_t)stream));
 }
@@ -364,6 +372,10 @@ wsr_status wsr_render_bwd_tiles(const float* records, int64_t n, const uint32_t*
     WSR_TRY(check_ws(vs, workspace, workspace_bytes));
     if (n < 0 || !tile_offsets || !out_rgb || !out_den || !grad_rgb) return WSR_ERR_INVALID_ARG;
     if (n > 0 && (!records || !tile_list || !grad_records)) return WSR_ERR_INVALID_ARG;
+    // records are read and gradient records added to as float4 (as 64-bit integers in the deterministic mode)
+    if (!aligned16(records) || !aligned16(grad_records) || !aligned4(tile_list) || !aligned4(tile_offsets) ||
+        !aligned4(out_rgb) || !aligned4(out_den) || !aligned4(grad_rgb))
+        return WSR_ERR_INVALID_ARG;
     if ((unsigned long long)n * (unsigned long long)n_cams > 0xffffffffull) return WSR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     WsHeader* hdr = (WsHeader*)workspace;
@@ -397,7 +409,7 @@ wsr_status wsr_project_bwd(const wsr_gaussians* g, const wsr_camera* cams, int32
     WSR_TRY(check_weight(w, &wd));
     WSR_TRY(make_views(cams, n_cams, nullptr, &vs));
     WSR_TRY(check_gauss(g, n_cams, wd.kind, &gp));
-    if (gp.n > 0 && !grad_records) return WSR_ERR_INVALID_ARG;
+    if (gp.n > 0 && (!grad_records || !aligned16(grad_records))) return WSR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     WsHeader* hdr = (WsHeader*)workspace;
     wsr_grads inner = *grads;
@@ -435,6 +447,8 @@ wsr_status wsr_count_pairs(const float* records, int64_t n, const uint32_t* tile
     static thread_local Views vs;
     if (!tiles || !count_dev || !tile_offsets || n < 0) return WSR_ERR_INVALID_ARG;
     if (n > 0 && (!records || !tile_list)) return WSR_ERR_INVALID_ARG;
+    if (!aligned16(records) || !aligned4(tile_list) || !aligned4(tile_offsets) || ((uintptr_t)count_dev & 7u))
+        return WSR_ERR_INVALID_ARG;
     WSR_TRY(make_views(cams, n_cams, tiles, &vs));
     return cuda_status(launch_count_pairs(records, tile_offsets, tile_list, vs, (unsigned long long*)count_dev,
                                           (cudaStream_t)stream));

@@ -11,6 +11,20 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "wsr.h")
 
 
+def _cuda_present() -> bool:
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:  # pragma: no cover
+        return False
+
+
+# The argument-error tests pass made-up device addresses that validation must
+# reject before any launch.  They run where no GPU is present, so that a
+# check that goes missing can never hand such an address to a kernel.
+host_validation_only = pytest.mark.skipif(_cuda_present(), reason="fake device pointers: run without a GPU")
+
+
 @pytest.fixture(scope="module")
 def lib():
     import __graft_entry__
@@ -64,6 +78,7 @@ def test_tile_and_pixel_counts(lib):
     assert lib.wsr_num_tiles(cams, 0, ctypes.byref(t16)) == 0
 
 
+@host_validation_only
 def test_argument_errors_are_returned(lib):
     from paper_2410_18931_gb300 import _abi as A
     cams, n = _cam(64, 48)
@@ -116,6 +131,7 @@ def test_argument_errors_are_returned(lib):
     assert lib.wsr_check(None, 0, None) == A.WSR_ERR_INVALID_ARG
 
 
+@host_validation_only
 def test_training_entry_points_reject_bad_arguments(lib):
     from paper_2410_18931_gb300 import _abi as A
     cams, n = _cam(64, 48)
@@ -162,6 +178,7 @@ def test_weight_params_rounded_are_float32_exact():
     assert np.array_equal(r.as_array(), w.as_array())
 
 
+@host_validation_only
 def test_tiles_chunk_is_validated(lib):
     from paper_2410_18931_gb300 import _abi as A
     cams, n = _cam(64, 48)
@@ -188,6 +205,7 @@ def test_bench_uses_a_fixed_launch_configuration_as_given():
     assert bench.launch_config(args, None, None, None, None) == ((32, 8), False, 128, None)
 
 
+@host_validation_only
 def test_deterministic_flag_is_validated(lib):
     """wsr_tiles.deterministic: 0 or 1; the deterministic workspace holds the
     per-tile background terms as well; wsr_project_bwd checks the flag too."""
@@ -204,3 +222,32 @@ def test_deterministic_flag_is_validated(lib):
     grads = A.wsr_grads()
     assert lib.wsr_project_bwd(ctypes.byref(g), cams, n, ctypes.byref(A.tiles(16, 16, 0, 0, 3)), ctypes.byref(w),
                                fake, ctypes.byref(grads), fake, 1 << 16, None) == A.WSR_ERR_INVALID_ARG
+
+
+@host_validation_only
+def test_misaligned_record_buffers_are_rejected(lib):
+    """Render records are read, and gradient records updated, as 16-byte
+    vectors; tile offsets and lists are 32-bit words."""
+    from paper_2410_18931_gb300 import _abi as A
+    cams, n = _cam(64, 48)
+    fake = 1 << 20   # never dereferenced: validation fails first
+    for det in (0, 1):
+        t = A.tiles(16, 16, 0, 0, det)
+        ws = lib.wsr_workspace_size(cams, n, ctypes.byref(t))
+        w = A.wsr_weight(A.WSR_WEIGHT_EXP, fake)
+        fwd = lambda rec, lst: lib.wsr_render_fwd(rec, 10, fake, lst, cams, n, ctypes.byref(t), ctypes.byref(w),
+                                                  fake, fake, fake, ws, None)
+        assert fwd(fake + 8, fake) == A.WSR_ERR_INVALID_ARG
+        assert fwd(fake, fake + 2) == A.WSR_ERR_INVALID_ARG
+        bwd = lambda rec, grec: lib.wsr_render_bwd_tiles(rec, 10, fake, fake, cams, n, ctypes.byref(t),
+                                                         ctypes.byref(w), fake, fake, fake, grec, fake, ws, None)
+        assert bwd(fake + 4, fake) == A.WSR_ERR_INVALID_ARG
+        assert bwd(fake, fake + 8) == A.WSR_ERR_INVALID_ARG
+        g = A.wsr_gaussians(10, 0, A.WSR_OPACITY_LOGIT, A.WSR_F32, A.WSR_F32, fake, fake, fake, fake, fake, None)
+        grads = A.wsr_grads()
+        assert lib.wsr_project_bwd(ctypes.byref(g), cams, n, ctypes.byref(t), ctypes.byref(w), fake + 4,
+                                   ctypes.byref(grads), fake, ws, None) == A.WSR_ERR_INVALID_ARG
+        assert lib.wsr_bin(fake, 10, cams, n, ctypes.byref(t), fake + 1, fake, 100, fake, ws,
+                           None) == A.WSR_ERR_INVALID_ARG
+        assert lib.wsr_count_pairs(fake + 4, 10, fake, fake, cams, n, ctypes.byref(t), fake,
+                                   None) == A.WSR_ERR_INVALID_ARG
