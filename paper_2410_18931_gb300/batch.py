@@ -134,7 +134,10 @@ def autotune(g: Gaussians, cams, kind: int, wparams: torch.Tensor, target: torch
                 table.append(dict(tile=shape, persistent=persistent, chunk=chunk, ms=ms, ok=ok))
                 del step
                 torch.cuda.empty_cache()
-    best = min((t for t in table if t["ok"]), key=lambda t: t["ms"])
+    ran = [t for t in table if t["ok"]]
+    if not ran:
+        raise RuntimeError("autotune: every configuration overflowed its tile list")
+    best = min(ran, key=lambda t: t["ms"])
     res = dict(tile=best["tile"], persistent=best["persistent"], chunk=best["chunk"], ms=best["ms"], table=table)
     _cache[key] = res
     return res
