@@ -324,45 +324,56 @@ def cpu_oracle_leg(scene, cam, weight, target, gpu_rgb, budget_s: float):
     return base, maxerr
 
 
-def cpu_band_rate(scene, cam, weight, budget_s: float, with_grad: bool, what: str) -> dict:
+def cpu_band_rate(scene, cam, weight, budget_s: float, with_grad: bool, what: str, gpu_rgb=None) -> dict:
     """The FP64 oracle, as it stands, on bands of rows of one view (about
     ``budget_s`` seconds on the host cores in all), extrapolated to the whole
     view: a call costs a fixed part (projecting every Gaussian) plus a part
     per row, both fitted from two band heights.  Reported as Mpix/s of the
-    whole view."""
+    whole view.  With ``gpu_rgb`` (the GPU image of that view, [H, W, 3]),
+    the taller band is also compared with it: max error, max error beyond
+    the cutoff-tie bound, and PSNR."""
     import numpy as np
 
     import oracle
     threads = os.cpu_count() or 1
     y0 = cam.height // 2
+    amb = 0.02 if gpu_rgb is not None else None
 
     def one(rows):
         band = (y0 - rows // 2, y0 - rows // 2 + rows)
         t0 = time.perf_counter()
-        out = oracle.render(scene, cam, weight, threads=threads, rows=band)
+        out = oracle.render(scene, cam, weight, threads=threads, rows=band, amb_tau=amb)
         if with_grad:
             G = np.full(out["rgb"].shape, 1.0 / (3.0 * cam.width * cam.height))
             oracle.grad(scene, cam, weight, G, threads=threads, rows=band)
-        return time.perf_counter() - t0
+        return time.perf_counter() - t0, out, band
 
     r1 = 4
     # a first call pays one-time costs (loading the library, first touch of the scene) and is not used
-    t0 = one(r1)
+    t0, _, _ = one(r1)
     # the second band is 128 rows taller (or the whole view), so that the per-row part of its time
     # stands well above the run-to-run noise of the fixed part; more rows if the budget allows
     per_row_max = t0 / r1                       # an upper bound: t0 includes the fixed part
     extra = max(128, int(max(budget_s - 3 * t0, 0.0) / max(per_row_max, 1e-6)))
     r2 = int(min(cam.height, r1 + extra))
-    t2 = one(r2)
-    t1 = one(r1)
+    t2, out2, band2 = one(r2)
+    t1, _, _ = one(r1)
     per_row = max((t2 - t1) / (r2 - r1), 1e-9)
     fixed = max(t1 - r1 * per_row, 0.0)
     frame = fixed + cam.height * per_row
-    return {"value": round(cam.width * cam.height / frame / 1e6, 4), "unit": "Mpix/s", "cores": threads,
-            "kind": "oracle",
-            "sample": f"{'fwd+bwd' if with_grad else 'fwd'} (FP64) on bands of {r1} and {r2} rows of one "
-                      f"{cam.width}x{cam.height} view of {what} ({t0 + t1 + t2:.1f} s with a first, untimed "
-                      f"call); whole view extrapolated as {fixed:.2f} s per call + {per_row * 1e3:.1f} ms per row"}
+    res = {"value": round(cam.width * cam.height / frame / 1e6, 4), "unit": "Mpix/s", "cores": threads,
+           "kind": "oracle",
+           "sample": f"{'fwd+bwd' if with_grad else 'fwd'} (FP64) on bands of {r1} and {r2} rows of one "
+                     f"{cam.width}x{cam.height} view of {what} ({t0 + t1 + t2:.1f} s with a first, untimed "
+                     f"call); whole view extrapolated as {fixed:.2f} s per call + {per_row * 1e3:.1f} ms per row"}
+    if gpu_rgb is not None:
+        err = np.abs(gpu_rgb[band2[0]:band2[1]].astype(np.float64) - out2["rgb"])
+        mse = float(np.mean(err ** 2))
+        res["vs_oracle"] = {"max_abs_err": float(err.max()),
+                            "max_abs_err_beyond_tie_bound": float(max((err - out2["amb"][..., None]).max(), 0.0)),
+                            "psnr_db": round(10.0 * np.log10(1.0 / mse), 2) if mse > 0 else None,
+                            "pixels_checked": int((band2[1] - band2[0]) * cam.width)}
+    return res
 
 
 def run_reference(args):
@@ -736,6 +747,9 @@ def run_batched(reps: int = 5, cpu_leg: bool = True) -> dict:
     ms = time_step(step, reps=reps)
     assert step.check() == 0
     kernels = step.kernels_per_step
+    o2 = sum(c.width * c.height for c in cams[:2])
+    rgb2 = step.st.rgb[o2:o2 + cams[2].width * cams[2].height].reshape(cams[2].height, cams[2].width, 3)
+    rgb2 = rgb2.cpu().numpy() if cpu_leg else None
     del step
     torch.cuda.empty_cache()
     single_ms, o = 0.0, 0
@@ -748,7 +762,8 @@ def run_batched(reps: int = 5, cpu_leg: bool = True) -> dict:
         o += m
         del one
         torch.cuda.empty_cache()
-    cpu = None if not cpu_leg else cpu_band_rate(scene, cams[2], weight, 8.0, True, "the 3M-Gaussian 16-view workload")
+    cpu = None if not cpu_leg else cpu_band_rate(scene, cams[2], weight, 8.0, True, "the 3M-Gaussian 16-view workload",
+                                                  gpu_rgb=rgb2)
     return {"workload": extra["name"], "gaussians": g.n, "views": len(cams), "mpix_per_step": round(npix / 1e6, 3),
             "cpu_baseline": cpu,
             "fwd_bwd_mpix_s": round(npix / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms, 3),
@@ -900,8 +915,9 @@ def run_reduced(reps: int = 3, cpu_leg: bool = True) -> dict:
         del s1, rs
         torch.cuda.empty_cache()
     mse = se / (3 * npix)
+    rgb0 = red_rgb[:cams[0].width * cams[0].height].reshape(cams[0].height, cams[0].width, 3).cpu().numpy()
     cpu = None if not cpu_leg else cpu_band_rate(stored, cams[0], weight, 8.0, False,
-                                                  "the 6M-Gaussian 8-view 4K workload (stored values)")
+                                                  "the 6M-Gaussian 8-view 4K workload (stored values)", gpu_rgb=rgb0)
     return {"workload": extra["name"], "gaussians": g16.n, "views": len(cams), "mpix_per_step": round(npix / 1e6, 3),
             "cpu_baseline": cpu,
             "fwd_mpix_s": round(npix / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms, 3),
