@@ -1,0 +1,44 @@
+"""The bench's CPU legs on a tiny scene, without a GPU: the oracle baseline
+estimators and their comparison with a GPU image (here the oracle's own
+image, and the same image with one pixel moved)."""
+import numpy as np
+
+import oracle
+import wsr_scenes as ws
+
+
+def _tiny():
+    sc = ws.random_scene(300, 5, sh_degree=1, vd_opacity=True, clusters=3, box=1.0, log_scale_mu=-3.0)
+    cam = ws.look_at((0.1, 0.2, -3.0), width=40, height=30).rounded()
+    w = ws.WeightParams(ws.EXP, 0.1, 0.8, 0.9, (0.1, 0.2, 0.3)).rounded()
+    return sc, cam, w
+
+
+def test_cpu_band_rate_compares_the_band_with_the_gpu_image():
+    import bench
+    sc, cam, w = _tiny()
+    ref = oracle.render(sc, cam, w)["rgb"].astype(np.float32)
+    res = bench.cpu_band_rate(sc, cam, w, 0.5, True, "a tiny scene", gpu_rgb=ref)
+    assert res["kind"] == "oracle" and res["value"] > 0 and res["cores"] >= 1
+    v = res["vs_oracle"]
+    assert v["pixels_checked"] == cam.width * cam.height     # the taller band is the whole 30-row view
+    assert v["max_abs_err"] < 1e-6                            # float32 rounding of the oracle's own image
+    assert v["max_abs_err_beyond_tie_bound"] < 1e-6
+    moved = ref.copy()
+    moved[15, 20, 1] += 0.25
+    v2 = bench.cpu_band_rate(sc, cam, w, 0.5, False, "a tiny scene", gpu_rgb=moved)["vs_oracle"]
+    assert abs(v2["max_abs_err"] - 0.25) < 1e-6
+    # one channel of one pixel off by 0.25: mse = 0.25^2 / (3 * 1200)
+    assert abs(v2["psnr_db"] - 10 * np.log10(3 * 1200 / 0.0625)) <= 0.005     # reported to 0.01 dB
+    assert "vs_oracle" not in bench.cpu_band_rate(sc, cam, w, 0.5, False, "a tiny scene")
+
+
+def test_cpu_oracle_leg_reports_the_whole_view_and_its_error():
+    import bench
+    sc, cam, w = _tiny()
+    target = ws.target_image(3, cam.height, cam.width)
+    ref = oracle.render(sc, cam, w)["rgb"].astype(np.float32)
+    base, err = bench.cpu_oracle_leg(sc, cam, w, target, ref, 0.5)
+    assert base["kind"] == "oracle" and base["unit"] == "Mpix/s" and base["value"] > 0
+    assert err["max_abs_err"] < 1e-6 and err["max_abs_err_beyond_tie_bound"] < 1e-6
+    assert err["pixels_checked"] <= cam.width * cam.height
