@@ -21,6 +21,7 @@ WSR_RECORD_FLOATS = 12
 WSR_GRAD_RECORD_FLOATS = 12
 WSR_GRAD_RECORD_FLOATS_DET = 32      # deterministic mode: 9 int64 sums and 9 magnitudes per record
 WSR_DET_MAX_SEGMENT = 8192
+WSR_BIN_STATIC_MAX_TILES = 65536     # tiles over all views that wsr_bin_static handles
 
 _c_void_p = ctypes.c_void_p
 

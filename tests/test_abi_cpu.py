@@ -251,3 +251,46 @@ def test_misaligned_record_buffers_are_rejected(lib):
                            None) == A.WSR_ERR_INVALID_ARG
         assert lib.wsr_count_pairs(fake + 4, 10, fake, fake, cams, n, ctypes.byref(t), fake,
                                    None) == A.WSR_ERR_INVALID_ARG
+
+
+def test_binding_constants_match_the_header():
+    """Every numeric #define and enum constant of include/wsr.h has the same
+    value in the Python binding."""
+    from paper_2410_18931_gb300 import _abi as A
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    consts = {k: int(v) for k, v in re.findall(r"^#define\s+(WSR_\w+)\s+(\d+)\s*$", text, flags=re.M)}
+    for body in re.findall(r"enum\s*\{(.*?)\}", text, flags=re.S):
+        consts.update({k: int(v) for k, v in re.findall(r"(WSR_\w+)\s*=\s*(\d+)", body)})
+    assert len(consts) >= 20
+    for k, v in consts.items():
+        assert getattr(A, k) == v, k
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every struct crossing the ABI has the same size and field offsets in
+    C (compiled with the host compiler from include/wsr.h) and in ctypes."""
+    import shutil
+    import subprocess
+    from paper_2410_18931_gb300 import _abi as A
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = ["wsr_camera", "wsr_gaussians", "wsr_weight", "wsr_tiles", "wsr_grads", "wsr_adam_group",
+               "wsr_adam_hparams", "wsr_adam_state"]
+    lines = ['#include <stdio.h>', '#include "wsr.h"', "int main(void) {"]
+    for s in structs:
+        lines.append(f'printf("{s} size %zu\\n", sizeof({s}));')
+        for name, _ in getattr(A, s)._fields_:
+            lines.append(f'printf("{s} {name} %zu\\n", offsetof({s}, {name}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c_layout = {(a, b): int(c) for a, b, c in (ln.split() for ln in out if ln.strip())}
+    for s in structs:
+        cls = getattr(A, s)
+        assert c_layout[(s, "size")] == ctypes.sizeof(cls), s
+        for name, _ in cls._fields_:
+            assert c_layout[(s, name)] == getattr(cls, name).offset, (s, name)

@@ -104,7 +104,7 @@ def test_bin_static_rejects_too_many_tiles():
     lib = A.load()
     cams, n = A.make_cameras([ws.look_at((0, 0, -5), width=4096, height=2160)])
     t8 = A.tiles(8, 8)      # 512 x 270 = 138,240 tiles > WSR_BIN_STATIC_MAX_TILES
-    assert lib.wsr_num_tiles(cams, n, ctypes.byref(t8)) > 65536
+    assert lib.wsr_num_tiles(cams, n, ctypes.byref(t8)) > A.WSR_BIN_STATIC_MAX_TILES
     dummy = torch.empty(16, dtype=torch.float32, device="cuda")
     p = ctypes.c_void_p(dummy.data_ptr())
     status = lib.wsr_bin_static(p, 1, cams, n, ctypes.byref(t8), p, p, 4, None, None)
