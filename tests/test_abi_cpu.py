@@ -294,3 +294,38 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert c_layout[(s, "size")] == ctypes.sizeof(cls), s
         for name, _ in cls._fields_:
             assert c_layout[(s, name)] == getattr(cls, name).offset, (s, name)
+
+
+def test_binding_signatures_match_the_header_prototypes():
+    """Each prototype of include/wsr.h and its ctypes signature agree on the
+    return type and, argument by argument, on the C type."""
+    from paper_2410_18931_gb300 import _abi as A
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    protos = re.findall(r"^\s*(const\s+)?(\w+)\s*(\*?)\s*(wsr_\w+)\s*\(([^)]*)\)\s*;", text, flags=re.M)
+    assert len(protos) == len(A._SIGS)
+    scalars = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64,
+               "size_t": ctypes.c_size_t, "float": ctypes.c_float, "wsr_status": ctypes.c_int}
+    device_structs = {"wsr_adam_state"}      # lives in device memory: a plain device pointer in the binding
+
+    def ctype_of(decl):
+        decl = decl.replace("const ", "").strip()
+        if "*" in decl:
+            base = decl.split("*")[0].strip()
+            if base.startswith("wsr_") and base not in device_structs:
+                return ctypes.POINTER(getattr(A, base))
+            return ("ptr", base)
+        return scalars[decl]
+
+    for const, ret, star, name, params in protos:
+        res, args = A._SIGS[name]
+        want_ret = ctypes.c_char_p if star else scalars[ret]
+        assert res is want_ret, name
+        plist = [] if params.strip() in ("", "void") else [p.strip() for p in params.split(",")]
+        assert len(plist) == len(args), name
+        for p, a in zip(plist, args):
+            decl = re.sub(r"\s*\w+$", "", p)            # drop the parameter name
+            t = ctype_of(decl)
+            if isinstance(t, tuple):                    # a plain data pointer: void* in the binding
+                assert a in (ctypes.c_void_p, A._c_void_p) or t[1] == "uint64_t", (name, p)
+            else:
+                assert a is t, (name, p)
