@@ -949,8 +949,22 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--training-only", action="store_true",
                     help="only the training-step measurement (one JSON object), e.g. for profiling its kernels")
+    ap.add_argument("--deterministic-only", action="store_true",
+                    help="only the deterministic-mode measurement (one JSON object), e.g. for profiling its kernels")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.deterministic_only:
+        import torch
+        torch.cuda.set_device(0)
+        tile = (16, 16) if args.tile == "auto" else tuple(int(v) for v in args.tile.split("x"))
+        persistent = args.schedule != "per-tile"
+        chunk = 64 if args.chunk == "auto" else int(args.chunk)
+        scene, cam, weight, extra, target = build_workload(args, 0, 1)
+        S = Step(scene, cam, weight, tile, target, persistent, chunk)
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        print(json.dumps(run_deterministic(S, scene, cam, weight, target, tile, persistent, chunk, flush,
+                                           reps=args.steps)), flush=True)
+        return
     if args.training_only:
         import torch
         torch.cuda.set_device(0)
