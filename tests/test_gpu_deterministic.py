@@ -15,10 +15,10 @@ pytestmark = pytest.mark.gpu
 KEYS = ("means", "log_scales", "quats", "sh", "opacity", "lc_v", "weight_params")
 
 
-def _run(sc, cams, w, G, tile, persistent, chunk, deterministic):
+def _run(sc, cams, w, G, tile, persistent, chunk, deterministic, reduced=False):
     import torch
     from paper_2410_18931_gb300 import Gaussians, Renderer
-    g = Gaussians.from_scene(sc)
+    g = Gaussians.from_scene(sc, reduced=reduced)
     wpar = torch.tensor(w.as_array(), device="cuda")
     r = Renderer(cams, tile=tile, persistent=persistent, chunk=chunk, deterministic=deterministic)
     st = r.forward(g, w.kind, wpar)
@@ -71,6 +71,34 @@ def test_deterministic_mode_is_bitwise_reproducible_and_matches_the_oracle(tile,
         env = e if env is None else add_envelopes(env, e)
     for k in ("means", "log_scales", "quats", "sh", "opacity"):
         assert grad_excess(a[k].cpu().numpy(), env, k) <= GRAD_TOL, k
+
+
+@pytest.mark.parametrize("kind,deg,vd,reduced", [(ws.LC, 3, True, True), (ws.DIR, 1, False, False),
+                                                  (ws.LC, 2, False, True), (ws.EXP, 0, True, False)])
+def test_deterministic_mode_across_weights_storage_and_opacity(kind, deg, vd, reduced):
+    """Each weight function, SH degrees 0-3, both opacity modes, FP32 and
+    bf16/f16 storage: two deterministic runs equal bit for bit, and within
+    rounding of the default mode."""
+    import torch
+    sc = ws.random_scene(8000, 90 + deg, sh_degree=deg, vd_opacity=vd, clusters=8, box=1.3, log_scale_mu=-3.3)
+    cams = [ws.look_at((0.3, -0.1, -3.4), width=100, height=70).rounded(),
+            ws.look_at((1.1, 0.6, -3.1), width=64, height=48).rounded()]
+    if kind == ws.DIR:
+        w = ws.WeightParams(kind, 0.0, 0.0, 0.7, (0.2, 0.1, 0.3))
+    elif kind == ws.LC:
+        w = ws.WeightParams(kind, 4.5, 0.0, 0.7, (0.2, 0.1, 0.3)).rounded()
+    else:
+        w = ws.WeightParams(kind, 0.1, 0.8, 0.7, (0.2, 0.1, 0.3)).rounded()
+    rng = np.random.default_rng(91 + deg)
+    G = torch.tensor(rng.normal(size=(sum(c.width * c.height for c in cams), 3)).astype(np.float32), device="cuda")
+    a = _run(sc, cams, w, G, (16, 16), True, 64, True, reduced)
+    b = _run(sc, cams, w, G, (16, 16), True, 64, True, reduced)
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+    d = _run(sc, cams, w, G, (16, 16), True, 64, False, reduced)
+    for k in ("rgb", "den") + KEYS:
+        x, y = a[k].double(), d[k].double()
+        assert float((x - y).abs().max()) <= 1e-4 * max(float(y.abs().max()), 1e-12), k
 
 
 def test_deterministic_mode_reports_a_tile_beyond_its_sort_bound():
