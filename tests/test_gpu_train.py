@@ -239,6 +239,29 @@ def test_graph_replay_matches_eager_steps():
     assert a.opt.read_state()["step"] == b.opt.read_state()["step"] == 4
 
 
+def test_deterministic_training_is_bitwise_reproducible():
+    """Six graph-replayed Adam steps over two views in the deterministic mode,
+    twice from the same scene: the parameters and both Adam moments end equal
+    bit for bit (the loss kernel forms each pixel's gradient from its own
+    halo; only the reported loss value is summed with atomics)."""
+    import torch
+    from paper_2410_18931_gb300 import FlatParams, TrainStep
+    _, init, cams, w, targets = _train_problem(n=2000, views=2, kind=ws.LC, deg=2, vd=True)
+    tgt = torch.from_numpy(np.concatenate([t.reshape(-1, 3) for t in targets])).cuda()
+    runs = []
+    for _ in range(2):
+        flat = FlatParams.from_scene(init, w.as_array())
+        step = TrainStep(flat, init.sh_degree, True, cams, w.kind, tgt, persistent=True, chunk=64, capture=True,
+                         deterministic=True)
+        step.train(6, check_every=3)
+        torch.cuda.synchronize()
+        assert step.opt.read_state() == dict(step=6, skipped=0)
+        runs.append((flat.data.clone(), step.opt.exp_avg.clone(), step.opt.exp_avg_sq.clone()))
+    for a, b in zip(*runs):
+        assert torch.equal(a, b)
+    assert not torch.equal(runs[0][0], FlatParams.from_scene(init, w.as_array()).data)
+
+
 def test_overflowed_step_is_skipped_then_redone():
     import torch
     from paper_2410_18931_gb300 import FlatParams, TrainStep
