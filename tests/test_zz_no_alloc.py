@@ -21,7 +21,7 @@ import wsr_scenes as ws
 pytestmark = pytest.mark.gpu
 
 
-def _case(seed, n, width, height, tile):
+def _case(seed, n, width, height, tile, deterministic=False):
     import torch
 
     from paper_2410_18931_gb300 import Gaussians, Renderer
@@ -30,7 +30,7 @@ def _case(seed, n, width, height, tile):
     w = ws.default_weight(ws.LC)
     g = Gaussians.from_scene(sc)
     wpar = torch.tensor(w.as_array(), device="cuda")
-    r = Renderer([cam], tile=tile)
+    r = Renderer([cam], tile=tile, deterministic=deterministic)
     st = r.alloc_state(g.n)
     r.wsr_project(g, w.kind, wpar, st.records)
     r.wsr_bin_count(st.records, g.n, st.tile_offsets)
@@ -109,3 +109,19 @@ def test_bin_static_rejects_too_many_tiles():
     p = ctypes.c_void_p(dummy.data_ptr())
     status = lib.wsr_bin_static(p, 1, cams, n, ctypes.byref(t8), p, p, 4, None, None)
     assert status == A.WSR_ERR_UNSUPPORTED
+
+
+def test_bin_static_in_the_deterministic_mode_gives_the_sorted_lists():
+    """With wsr_tiles.deterministic = 1, wsr_bin_static sorts each tile's list
+    by record index, exactly as wsr_bin does with a workspace: offsets and
+    lists equal element by element."""
+    import torch
+    r, g, w, wpar, st, total = _case(37, 20_000, 200, 150, (16, 16), deterministic=True)
+    status, offsets, tile_list, tot = _bin_static(r, st, total + 64)
+    assert status == 0 and tot == total
+    assert torch.equal(offsets, st.tile_offsets)
+    assert torch.equal(tile_list[:total], st.tile_list[:total])
+    off = offsets.cpu().numpy().astype(np.int64)
+    lst = tile_list.cpu().numpy().astype(np.int64)
+    for t in range(len(off) - 1):
+        assert np.all(np.diff(lst[off[t]:off[t + 1]]) > 0), t
