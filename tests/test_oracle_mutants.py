@@ -1,0 +1,114 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of ``oracle/wsr_oracle.c`` (an exact
+substring replacement: a dropped term, a wrong sign, a swapped operand, a
+misread constant), builds the copy with the oracle's own compiler flags,
+points the oracle's front end at it and runs every pin of
+``test_oracle_pins.py``: at least one must fail.  A copy built without any
+change must pass them all, so the harness itself cannot be what fails.
+The oracle's source file is never modified.
+"""
+import inspect
+import os
+import subprocess
+
+import pytest
+
+import oracle
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "wsr_oracle.c")
+
+# name -> (text in the oracle, planted replacement); each text occurs exactly once
+MUTANTS = {
+    # projection and footprint (Eqs. 3, 5; 3DGS pre-processing)
+    "no_dilation": ("#define ORC_DILATION 0.3", "#define ORC_DILATION 0.0"),
+    "rotation_sign": ("R[1] = 2 * (x * y - w * z);", "R[1] = 2 * (x * y + w * z);"),
+    "fx_fy_swapped_in_jacobian": (
+        "const double J[6] = {cam->fx / tz, 0, -cam->fx * rxc / tz, 0, cam->fy / tz, -cam->fy * ryc / tz};",
+        "const double J[6] = {cam->fy / tz, 0, -cam->fy * rxc / tz, 0, cam->fx / tz, -cam->fx * ryc / tz};"),
+    "y_clamped_with_x_limit": ("const double ryc = clampd(ty / tz, -ORC_CLAMP * tany, ORC_CLAMP * tany);",
+                               "const double ryc = clampd(ty / tz, -ORC_CLAMP * tanx, ORC_CLAMP * tanx);"),
+    "no_near_plane": ("if (!(o->t[2] > cam->znear))", "if (!(o->t[2] > 0.0))"),
+    "scale_not_exponentiated": ("for (int k = 0; k < 3; ++k) s[k] = exp(S->log_scales[3 * i + k]);\n    for (int r",
+                                "for (int k = 0; k < 3; ++k) s[k] = S->log_scales[3 * i + k];\n    for (int r"),
+    # colour and opacity (Eqs. 4, 11)
+    "no_condon_shortley_phase": ("pref = Kl * sqrt(2.0) * ipow(-1.0, am);", "pref = Kl * sqrt(2.0);"),
+    "no_colour_offset": ("o->color[ch] = r + 0.5 > 0 ? r + 0.5 : 0.0;", "o->color[ch] = r > 0 ? r : 0.0;"),
+    "sigmoid_sign": ("o->u = 1.0 / (1.0 + exp(-S->opac[i]));", "o->u = 1.0 / (1.0 + exp(S->opac[i]));"),
+    # weights (Eqs. 8-10) and the weighted sum (Eq. 7)
+    "depth_as_distance": ("o->d = o->t[2];",
+                          "o->d = sqrt(o->t[0] * o->t[0] + o->t[1] * o->t[1] + o->t[2] * o->t[2]);"),
+    "lc_not_clamped": ("o->w = (lin > 0 ? lin : 0.0) * S->lc_v[i];", "o->w = lin * S->lc_v[i];"),
+    "exp_weight_sign": ("o->w = exp(-wt->sigma * pow(d, wt->beta));", "o->w = exp(wt->sigma * pow(d, wt->beta));"),
+    "gaussian_without_half": ("const double a = o->u * o->w * g;            /* alpha_i w(d_i) */",
+                              "const double a = o->u * o->w * g * g;            /* alpha_i w(d_i) */"),
+    "no_background_colour": ("out_rgb[3 * p + ch] = (wt.c_bg[ch] * wt.w_bg + num[3 * p + ch]) / D;",
+                             "out_rgb[3 * p + ch] = num[3 * p + ch] / D;"),
+    "cutoff_misread": ("#define ORC_CUTOFF 9.0", "#define ORC_CUTOFF 8.0"),
+    # gradient
+    "beta_derivative_without_log": ("gbeta += dL_dw * (-wt->sigma * db * log(d)) * o->w;",
+                                    "gbeta += dL_dw * (-wt->sigma * db) * o->w;"),
+    "conic_offdiagonal_counted_once": ("g2[3] += dLdq * 2.0 * dx * dy;", "g2[3] += dLdq * dx * dy;"),
+    "mean_gradient_sign": ("g2[1] += dLdq * (-2.0) * (o->conic[1] * dx + o->conic[2] * dy);",
+                           "g2[1] += dLdq * (2.0) * (o->conic[1] * dx + o->conic[2] * dy);"),
+    "projection_depth_term_sign": (
+        "g_t[2] += -g2[0] * cam->fx * tx / (tz * tz) - g2[1] * cam->fy * ty / (tz * tz);",
+        "g_t[2] += -g2[0] * cam->fx * tx / (tz * tz) + g2[1] * cam->fy * ty / (tz * tz);"),
+    "background_weight_gradient_sign": ("g_wpar[2] += grad_rgb[3 * p + ch] * (wt.c_bg[ch] - rgb[3 * p + ch]) / D;",
+                                        "g_wpar[2] += grad_rgb[3 * p + ch] * (rgb[3 * p + ch] - wt.c_bg[ch]) / D;"),
+    "covariance_chain_factor": ("for (int e = 0; e < 6; ++e) GT[e] *= 2.0;", "for (int e = 0; e < 6; ++e) GT[e] *= 1.0;"),
+    "sigmoid_derivative": ("c->g_opac[i] = dL_du * o->u * (1.0 - o->u);", "c->g_opac[i] = dL_du * o->u;"),
+    "quaternion_not_projected": ("c->g_quats[4 * i + k] = (gqn[k] - q[k] * dot) / qn;",
+                                 "c->g_quats[4 * i + k] = gqn[k] / qn;"),
+}
+
+
+def _build(text: str, path) -> str:
+    # the flags of oracle.build(): portable, no FMA contraction
+    src = path / "mutant.c"
+    src.write_text(text)
+    so = path / "libmutant.so"
+    subprocess.run(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+                    str(src), "-o", str(so), "-lm", "-lpthread"], check=True)
+    return str(so)
+
+
+def _run_pins():
+    """Every pin of test_oracle_pins.py with each of its parameter sets;
+    returns the (pin, parameters) that failed."""
+    from tests import test_oracle_pins as P
+    failed = []
+    for name, fn in inspect.getmembers(P, inspect.isfunction):
+        if not name.startswith("test_") or fn.__module__ != P.__name__:
+            continue
+        combos = [{}]
+        for m in reversed(getattr(fn, "pytestmark", [])):
+            if m.name != "parametrize":
+                continue
+            names = [s.strip() for s in m.args[0].split(",")]
+            combos = [{**c, **dict(zip(names, v if len(names) > 1 else (v,)))} for c in combos for v in m.args[1]]
+        for kw in combos:
+            try:
+                fn(**kw)
+            except Exception:       # an assertion, or a non-finite result caught by numpy
+                failed.append((name, kw))
+    return failed
+
+
+def _with_library(monkeypatch, so):
+    monkeypatch.setattr(oracle, "_lib", None)
+    monkeypatch.setattr(oracle, "build", lambda force=False: so)
+
+
+def test_an_unchanged_copy_passes_every_pin(tmp_path, monkeypatch):
+    _with_library(monkeypatch, _build(open(SRC).read(), tmp_path))
+    assert _run_pins() == []
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_a_planted_mistake_fails_a_pin(name, tmp_path, monkeypatch):
+    old, new = MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, "the planted text must name one place in the oracle"
+    _with_library(monkeypatch, _build(text.replace(old, new), tmp_path))
+    assert _run_pins(), f"no pin fails with the mistake '{name}' planted"

@@ -30,16 +30,19 @@ def _scene(means, log_scales, quats, sh, opacity, lc_v, deg, vd):
 
 def tiny_scene(seed, deg, vd, n=40, box=1.2, ls=-2.2):
     """Small random scene plus Gaussians that exercise the edge cases: one
-    behind the near plane, one far off-screen to the side with a footprint that
-    reaches into the image (Jacobian clamp), one huge and close."""
+    behind the camera, one in front of it but inside the near plane (culled),
+    one far off-screen to the side with a footprint that reaches into the
+    image (Jacobian clamp), one huge and close."""
     sc = ws.random_scene(n, seed, sh_degree=deg, vd_opacity=vd, clusters=0, box=box,
                          log_scale_mu=ls, log_scale_sd=0.4)
     K = (deg + 1) ** 2
-    extra_means = np.array([[0.1, 0.0, -3.1],    # behind / at the camera (camera at z=-3)
+    extra_means = np.array([[0.05, -0.05, -2.9],  # t_z = 0.1: in front, inside the near plane 0.2
+                            [0.1, 0.0, -3.1],    # behind / at the camera (camera at z=-3)
                             [0.3, -2.2, -0.6],   # above the image: t_y/t_z beyond the clamp
                             [2.6, 0.2, -0.5],    # off to the side: t_x/t_z beyond the clamp
                             [-0.1, 0.1, -2.2]])  # close to the camera: large footprint
-    extra_ls = np.array([[-2.0, -2.0, -2.0], [-0.9, -0.6, -0.8], [-0.6, -1.0, -0.8], [-2.5, -2.2, -2.4]])
+    extra_ls = np.array([[-2.3, -2.4, -2.2], [-2.0, -2.0, -2.0], [-0.9, -0.6, -0.8], [-0.6, -1.0, -0.8],
+                         [-2.5, -2.2, -2.4]])
     m = extra_means.shape[0]
     rng = np.random.default_rng(seed + 100)
     q = rng.normal(size=(m, 4))
@@ -367,7 +370,8 @@ def test_gradient_matches_finite_differences(wi, deg, vd):
         assert e < 2e-6, (name, e, worst)
     # the clamped off-screen Gaussian and the culled one are part of the test
     P = oracle.project(sc, cam, WEIGHTS[wi])
-    assert not P["visible"][-4]
+    assert not P["visible"][-4] and not P["visible"][-5]
+    assert 0.0 < P["t"][-5, 2] <= cam.znear           # in front of the camera, inside the near plane
     lx, ly = 1.3 * 0.5 * cam.width / cam.fx, 1.3 * 0.5 * cam.height / cam.fy
     t = P["t"]
     assert abs(t[-3, 1] / t[-3, 2]) > ly and abs(t[-2, 0] / t[-2, 2]) > lx
