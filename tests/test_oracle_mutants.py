@@ -1,13 +1,16 @@
 """The oracle's pins catch plausible mistakes.
 
-Each case plants one mistake in a copy of ``oracle/wsr_oracle.c`` (an exact
-substring replacement: a dropped term, a wrong sign, a swapped operand, a
-misread constant), builds the copy with the oracle's own compiler flags,
-points the oracle's front end at it and runs every pin of
-``test_oracle_pins.py``: at least one must fail.  A copy built without any
-change must pass them all, so the harness itself cannot be what fails.
-The oracle's source file is never modified.
+Each case plants one mistake in a copy of the oracle (an exact substring
+replacement: a dropped term, a wrong sign, a swapped operand, a misread
+constant) and runs every pin of the oracle's pin file against the copy: at
+least one must fail.  A copy without any change must pass them all, so the
+harness itself cannot be what fails.  The renderer's oracle
+(``oracle/wsr_oracle.c``) is copied, built with the oracle's own compiler
+flags and loaded in place of the real library; the training-step oracle
+(``oracle/train.py``) is copied and imported as a separate module in place
+of the real one.  The oracle's own files are never modified.
 """
+import importlib.util
 import inspect
 import os
 import subprocess
@@ -17,6 +20,7 @@ import pytest
 import oracle
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "wsr_oracle.c")
+TRAIN_SRC = os.path.join(os.path.dirname(oracle.__file__), "train.py")
 
 # name -> (text in the oracle, planted replacement); each text occurs exactly once
 MUTANTS = {
@@ -73,10 +77,11 @@ def _build(text: str, path) -> str:
     return str(so)
 
 
-def _run_pins():
-    """Every pin of test_oracle_pins.py with each of its parameter sets;
-    returns the (pin, parameters) that failed."""
-    from tests import test_oracle_pins as P
+def _run_pins(P=None):
+    """Every pin of a pin module (test_oracle_pins.py by default) with each
+    of its parameter sets; returns the (pin, parameters) that failed."""
+    if P is None:
+        from tests import test_oracle_pins as P
     failed = []
     for name, fn in inspect.getmembers(P, inspect.isfunction):
         if not name.startswith("test_") or fn.__module__ != P.__name__:
@@ -112,3 +117,51 @@ def test_a_planted_mistake_fails_a_pin(name, tmp_path, monkeypatch):
     assert text.count(old) == 1, "the planted text must name one place in the oracle"
     _with_library(monkeypatch, _build(text.replace(old, new), tmp_path))
     assert _run_pins(), f"no pin fails with the mistake '{name}' planted"
+
+
+# the training-step oracle (Sec. 4.4 loss, Adam): name -> (text, planted replacement)
+TRAIN_MUTANTS = {
+    "ssim_c1_misread": ("SSIM_C1 = 0.01 ** 2", "SSIM_C1 = 0.03 ** 2"),
+    "ssim_c2_misread": ("SSIM_C2 = 0.03 ** 2", "SSIM_C2 = 0.01 ** 2"),
+    "window_sigma_misread": ("SSIM_SIGMA = 1.5", "SSIM_SIGMA = 1.0"),
+    "window_not_normalised": ("    g /= g.sum()\n    return np.outer(g, g)", "    return np.outer(g, g)"),
+    "filter_is_a_convolution": ("out += win[a, b] * pad[a:a + H, b:b + W]",
+                                "out += win[-1 - a, -1 - b] * pad[a:a + H, b:b + W]"),
+    "adjoint_with_transposed_window": ("acc[a:a + H, b:b + W] += win[a, b] * g", "acc[a:a + H, b:b + W] += win[b, a] * g"),
+    "ssim_mean_gradient_sign": ("/ (b1 * b2) - s * (2.0 * mx / b1 - 2.0 * mx / b2)",
+                                "/ (b1 * b2) + s * (2.0 * mx / b1 - 2.0 * mx / b2)"),
+    "ssim_second_moment_gradient_sign": ("d_exx = -s / b2", "d_exx = s / b2"),
+    "ssim_cross_moment_gradient_factor": ("d_exy = 2.0 * a1 / (b1 * b2)", "d_exy = a1 / (b1 * b2)"),
+    "dssim_gradient_sign": ("gs = np.full(a.shape[:2], -lam / count)", "gs = np.full(a.shape[:2], lam / count)"),
+    "l1_gradient_sign": ("ga += (1.0 - lam) * np.sign(a - b) / count", "ga += (1.0 - lam) * np.sign(b - a) / count"),
+    "lambda_on_the_wrong_term": ("loss=(1.0 - lam) * l1 + lam * (1.0 - ssim)", "loss=lam * l1 + (1.0 - lam) * (1.0 - ssim)"),
+    "adam_v_not_bias_corrected": ("v_hat = v / (1.0 - beta2 ** t)", "v_hat = v"),
+    "adam_m_corrected_with_beta2": ("m_hat = m / (1.0 - beta1 ** t)", "m_hat = m / (1.0 - beta2 ** t)"),
+    "adam_eps_inside_the_root": ("(np.sqrt(v_hat) + eps)", "np.sqrt(v_hat + eps)"),
+    "adam_second_moment_of_g": ("(1.0 - beta2) * g * g", "(1.0 - beta2) * np.abs(g)"),
+}
+
+
+def _with_train_module(monkeypatch, text, path):
+    src = path / "train_mutant.py"
+    src.write_text(text)
+    spec = importlib.util.spec_from_file_location("oracle_train_mutant", str(src))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    from tests import test_train_oracle_pins as P
+    monkeypatch.setattr(P, "T", mod)
+    return P
+
+
+def test_an_unchanged_copy_of_the_training_oracle_passes_every_pin(tmp_path, monkeypatch):
+    P = _with_train_module(monkeypatch, open(TRAIN_SRC).read(), tmp_path)
+    assert _run_pins(P) == []
+
+
+@pytest.mark.parametrize("name", sorted(TRAIN_MUTANTS))
+def test_a_planted_mistake_in_the_training_oracle_fails_a_pin(name, tmp_path, monkeypatch):
+    old, new = TRAIN_MUTANTS[name]
+    text = open(TRAIN_SRC).read()
+    assert text.count(old) == 1, "the planted text must name one place in the oracle"
+    P = _with_train_module(monkeypatch, text.replace(old, new), tmp_path)
+    assert _run_pins(P), f"no pin fails with the mistake '{name}' planted"
