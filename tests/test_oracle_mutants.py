@@ -64,6 +64,24 @@ MUTANTS = {
     "sigmoid_derivative": ("c->g_opac[i] = dL_du * o->u * (1.0 - o->u);", "c->g_opac[i] = dL_du * o->u;"),
     "quaternion_not_projected": ("c->g_quats[4 * i + k] = (gqn[k] - q[k] * dot) / qn;",
                                  "c->g_quats[4 * i + k] = gqn[k] / qn;"),
+    "legendre_normalisation_inverted": ("const double norm = sqrt(fact(l - am) / fact(l + am));",
+                                        "const double norm = sqrt(fact(l + am) / fact(l - am));"),
+    "sh_index_order": ("const int idx = l * l + l + m;", "const int idx = l * l + l - m;"),
+    "rotation_derivative_entry": ("{0, 0, -4 * y, -4 * z},", "{0, 0, -4 * y, 4 * z},"),
+    "direction_gradient_not_tangential": ("g_p[e] += (g_dir[e] - o->dir[e] * dd) / o->vnorm;",
+                                          "g_p[e] += g_dir[e] / o->vnorm;"),
+    "lc_sigma_derivative_sign": ("gsig += dL_dw * v * d / (wt->sigma * wt->sigma);",
+                                 "gsig -= dL_dw * v * d / (wt->sigma * wt->sigma);"),
+    "clamped_x_moves_with_t": ("const int freex = (tx / tz >= -limx && tx / tz <= limx);", "const int freex = 1;"),
+    "camera_centre_from_rows": (
+        "f[k] = -(cam->R[k] * cam->T[0] + cam->R[3 + k] * cam->T[1] + cam->R[6 + k] * cam->T[2]);",
+        "f[k] = -(cam->R[3 * k] * cam->T[0] + cam->R[3 * k + 1] * cam->T[1] + cam->R[3 * k + 2] * cam->T[2]);"),
+    "principal_point_swapped": ("o->mean2d[0] = cam->fx * tx / tz + cam->cx;", "o->mean2d[0] = cam->fx * tx / tz + cam->cy;"),
+    "colour_gradient_without_opacity": ("g2[6 + ch] += c->G[3 * p + ch] * a / D;            /* dL/dc */",
+                                        "g2[6 + ch] += c->G[3 * p + ch] * g / D;            /* dL/dc */"),
+    "exp_depth_derivative_power": ("dL_dd = dL_dw * (-wt->sigma * wt->beta * pow(d, wt->beta - 1.0)) * o->w;",
+                                   "dL_dd = dL_dw * (-wt->sigma * wt->beta * pow(d, wt->beta)) * o->w;"),
+    "opacity_sh_gradient_basis": ("gHa[k] = dL_du * Y[k];", "gHa[k] = dL_du;"),
 }
 
 

@@ -140,6 +140,30 @@ def test_projection_matches_brute_force(deg, vd):
         assert np.abs(a - b).max() <= 1e-11 * scale, key
 
 
+@pytest.mark.parametrize("deg,vd", [(3, True), (2, False)])
+def test_off_axis_camera_matches_brute_force(deg, vd):
+    """A camera off every axis, so its rotation is not symmetric: the camera
+    centre -R^t T, the view directions of the SH and the world-to-camera
+    transform all differ from their transposed forms."""
+    sc = tiny_scene(60 + deg, deg, vd, n=60)
+    cam = ws.look_at((1.3, -0.9, -2.5), width=36, height=28)
+    cam.fy = cam.fx * 1.1
+    R = np.asarray(cam.R, np.float64).reshape(3, 3)
+    assert np.abs(R - R.T).max() > 0.1
+    w = WEIGHTS[1]
+    P = oracle.project(sc, cam, w)
+    B = bf.project(sc, cam, w)
+    assert (P["visible"] == B["visible"]).all()
+    v = P["visible"]
+    for key in ("mean2d", "cov2d", "conic", "color", "u", "w"):
+        a, b = P[key][v], B[key][v]
+        assert np.abs(a - b).max() <= 1e-11 * max(1.0, np.abs(b).max()), key
+    o = oracle.render(sc, cam, w, threads=2)
+    b = bf.render(sc, cam, w)
+    assert np.abs(o["rgb"] - b["rgb"]).max() < 1e-12
+    assert o["pairs"] > 300
+
+
 @pytest.mark.parametrize("wi", [0, 1, 2])
 @pytest.mark.parametrize("deg,vd", [(0, False), (3, True), (1, False)])
 def test_render_matches_brute_force(wi, deg, vd):
