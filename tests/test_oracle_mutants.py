@@ -82,6 +82,17 @@ MUTANTS = {
     "exp_depth_derivative_power": ("dL_dd = dL_dw * (-wt->sigma * wt->beta * pow(d, wt->beta - 1.0)) * o->w;",
                                    "dL_dd = dL_dw * (-wt->sigma * wt->beta * pow(d, wt->beta)) * o->w;"),
     "opacity_sh_gradient_basis": ("gHa[k] = dL_du * Y[k];", "gHa[k] = dL_du;"),
+    "footprint_extent_two_sigma": ("o->rx = 3.0 * sqrt(a);", "o->rx = 2.0 * sqrt(a);"),
+    "jacobian_clamp_misread": ("#define ORC_CLAMP 1.3", "#define ORC_CLAMP 1.2"),
+    # (the +1 is slack only: 3 sqrt(a) is the exact x-extent of q <= 9, so the range one column
+    # short of the exact bound is the smallest mistake a pin can see)
+    "pixel_range_one_column_short": ("*x1 = (int)ceil(o->mean2d[0] + rx - 0.5) + 1;",
+                                     "*x1 = (int)ceil(o->mean2d[0] + rx - 0.5) - 2;"),
+    "row_bands_overlap": ("jobs[t].lo = n * t / nthreads;", "jobs[t].lo = n * t / nthreads - (t > 0);"),
+    "pixel_list_bound_too_tight": ("if (fabs(dx) > o->rx + 1.0 || fabs(dy) > o->ry + 1.0) continue;",
+                                   "if (fabs(dx) > 0.5 * o->rx || fabs(dy) > 0.5 * o->ry) continue;"),
+    "background_colour_gradient": ("g_wpar[3 + ch] += grad_rgb[3 * p + ch] * wt.w_bg / D;",
+                                   "g_wpar[3 + ch] += grad_rgb[3 * p + ch] / D;"),
 }
 
 
