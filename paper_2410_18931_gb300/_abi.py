@@ -9,6 +9,8 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libwsr.so")
 
@@ -152,8 +154,8 @@ def make_cameras(cams) -> tuple:
     cx, cy, width, height and znear attributes."""
     arr = (wsr_camera * len(cams))()
     for k, c in enumerate(cams):
-        R = [float(v) for v in __import__("numpy").asarray(c.R, dtype="float64").reshape(9)]
-        T = [float(v) for v in __import__("numpy").asarray(c.T, dtype="float64").reshape(3)]
+        R = [float(v) for v in np.asarray(c.R, dtype=np.float64).reshape(9)]
+        T = [float(v) for v in np.asarray(c.T, dtype=np.float64).reshape(3)]
         arr[k].R[:] = R
         arr[k].T[:] = T
         arr[k].fx, arr[k].fy, arr[k].cx, arr[k].cy = float(c.fx), float(c.fy), float(c.cx), float(c.cy)
