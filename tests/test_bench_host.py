@@ -42,3 +42,51 @@ def test_cpu_oracle_leg_reports_the_whole_view_and_its_error():
     assert base["kind"] == "oracle" and base["unit"] == "Mpix/s" and base["value"] > 0
     assert err["max_abs_err"] < 1e-6 and err["max_abs_err_beyond_tie_bound"] < 1e-6
     assert err["pixels_checked"] <= cam.width * cam.height
+
+
+def _fake_nvidia_smi(tmp_path, lines):
+    script = tmp_path / "nvidia-smi"
+    body = "".join(f"printf '%s\\n' '{ln}'\n" for ln in lines)
+    script.write_text("#!/bin/sh\n" + body + "exec sleep 30\n")
+    script.chmod(0o755)
+
+
+def test_clock_sampler_reads_clocks_and_throttle_reasons(tmp_path, monkeypatch):
+    """The clocks record of the bench line from nvidia-smi's CSV samples: the
+    median SM clock under load (idle samples below half the peak dropped),
+    the maximum clock, and every throttle reason seen active."""
+    import os
+
+    import bench
+    _fake_nvidia_smi(tmp_path, [
+        "0, 345, 2070, 150.1, 0x0000000000000001, Not Active, Not Active, Not Active, Not Active",
+        "0, 2070, 2070, 1010.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "malformed line"])
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ["PATH"])
+    c = bench.ClockSampler(0)
+    c.start()
+    rec = c.stop()
+    assert rec["sm_mhz"] == 2070.0 and rec["sm_max_mhz"] == 2070.0
+    assert rec["reasons"] == ["sw_power_cap"] and rec["samples"] == 4
+
+
+def test_clock_sampler_reports_slowdowns_and_a_missing_tool(tmp_path, monkeypatch):
+    import os
+
+    import bench
+    _fake_nvidia_smi(tmp_path, [
+        "0, 1500, 2070, 1300.0, 0x0000000000000008, Active, Not Active, Not Active, Not Active",
+        "0, 1450, 2070, 1300.0, 0x0000000000000008, Active, Active, Not Active, Not Active"])
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ["PATH"])
+    c = bench.ClockSampler(0)
+    c.start()
+    rec = c.stop()
+    assert rec["sm_mhz"] == 1475.0 and rec["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
+    empty = tmp_path / "empty"
+    empty.mkdir()
+    monkeypatch.setenv("PATH", str(empty))
+    c = bench.ClockSampler(0)
+    c.start()
+    assert c.stop()["reasons"] == ["unavailable"]
