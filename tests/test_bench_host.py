@@ -90,3 +90,24 @@ def test_clock_sampler_reports_slowdowns_and_a_missing_tool(tmp_path, monkeypatc
     c = bench.ClockSampler(0)
     c.start()
     assert c.stop()["reasons"] == ["unavailable"]
+
+
+def test_profile_traffic_is_dropped_when_the_kernel_source_changed(tmp_path, monkeypatch):
+    """roofline.traffic comes from a committed ncu summary only while the
+    render source it was captured from is unchanged (its sha256 recorded in
+    the summary); after any change it is reported as null."""
+    import hashlib
+
+    import bench
+    (tmp_path / "profiles").mkdir()
+    src = tmp_path / "paper_2410_18931_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "render.cu").write_text("// kernel source\n")
+    sha = hashlib.sha256((src / "render.cu").read_bytes()).hexdigest()
+    (tmp_path / "profiles" / "k_render_bwd.md").write_text(
+        f"# summary\n\ntraffic_bytes_per_launch: 264801792\nsource_sha256: {sha}\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profile_traffic("k_render_bwd") == 264801792.0
+    assert bench.profile_traffic("k_render_fwd") is None              # no summary
+    (src / "render.cu").write_text("// kernel source, edited\n")
+    assert bench.profile_traffic("k_render_bwd") is None
