@@ -111,3 +111,28 @@ def test_profile_traffic_is_dropped_when_the_kernel_source_changed(tmp_path, mon
     assert bench.profile_traffic("k_render_fwd") is None              # no summary
     (src / "render.cu").write_text("// kernel source, edited\n")
     assert bench.profile_traffic("k_render_bwd") is None
+
+
+def test_launch_counts_claimed_per_step_match_the_profiled_launch_lists():
+    """The bench's gpu_launches claim is kernels per step x steps; the kernels
+    per step of each measured step (plain, deterministic, training; the
+    persistent schedule) equal the launches of one step in its committed ncu
+    launch list."""
+    import os
+    import re
+
+    import __graft_entry__
+    import bench
+    __graft_entry__._build_module().build()       # the package loads its library on import
+    from paper_2410_18931_gb300.train import TrainStep
+
+    def profiled(name):
+        text = open(os.path.join(bench.ROOT, "profiles", name)).read()
+        return len(re.findall(r"^\| `k_\w+", text, flags=re.M))
+
+    plain = bench.KERNELS_PER_STEP + bench.ORDER_KERNELS
+    assert profiled("launches_1M_1080p.md") == plain
+    assert profiled("launches_det_1M_1080p.md") == plain + 4
+    step = TrainStep.__new__(TrainStep)            # the count only: no device state
+    step.persistent, step.deterministic = True, False
+    assert profiled("launches_train_1M_1080p.md") == step.kernels_per_step
