@@ -1,0 +1,52 @@
+"""The comparison helpers the GPU parity tests rely on, checked on the CPU
+with the oracle standing in for the GPU: an exact copy passes, a planted
+error beyond the tolerance fails, and only errors inside the cutoff-tie
+allowance are forgiven."""
+import numpy as np
+
+import oracle
+import wsr_scenes as ws
+from tests.gpu_util import AMB_TAU, FWD_TOL, GRAD_TOL, compare_image, grad_envelope, grad_excess, rel_err
+
+
+def _small():
+    sc = ws.random_scene(400, 21, sh_degree=1, vd_opacity=True, clusters=4, box=1.0, log_scale_mu=-2.8)
+    cam = ws.look_at((0.2, -0.1, -3.0), width=48, height=36).rounded()
+    w = ws.WeightParams(ws.EXP, 0.1, 0.8, 0.7, (0.2, 0.1, 0.3)).rounded()
+    return sc, cam, w
+
+
+def test_compare_image_forgives_only_the_tie_allowance():
+    sc, cam, w = _small()
+    ref = oracle.render(sc, cam, w, amb_tau=AMB_TAU)
+    exact = ref["rgb"].astype(np.float32)
+    excess, raw, n_amb = compare_image(exact, ref)
+    assert excess <= 1e-6 and raw <= 1e-6 and n_amb > 0
+    # an error of 3x the tolerance on a pixel with no tie allowance is caught
+    free = np.argwhere(ref["amb"] == 0)
+    y, x = free[len(free) // 2]
+    bad = exact.copy()
+    bad[y, x, 0] += 3 * FWD_TOL
+    assert compare_image(bad, ref)[0] > FWD_TOL
+    # the same error on a pixel whose tie allowance covers it is forgiven
+    tied = np.argwhere(ref["amb"] > 4 * FWD_TOL)
+    assert len(tied) > 0                               # the scene has such pixels
+    y, x = tied[0]
+    ok = exact.copy()
+    ok[y, x, 1] += 3 * FWD_TOL
+    assert compare_image(ok, ref)[0] <= FWD_TOL
+
+
+def test_grad_excess_measures_the_distance_outside_the_envelope():
+    sc, cam, w = _small()
+    G = np.random.default_rng(3).normal(size=(cam.height, cam.width, 3))
+    env = grad_envelope(sc, cam, w, G)
+    mid = env[1]
+    for key in ("means", "log_scales", "quats", "sh", "opacity"):
+        assert grad_excess(mid[key], env, key) == 0.0, key
+        scale = np.abs(mid[key]).max()
+        bad = mid[key].copy().reshape(-1)
+        j = int(np.argmax(np.abs(bad)))
+        bad[j] += 3 * GRAD_TOL * scale                 # 3x the bar on the largest entry
+        assert grad_excess(bad, env, key) > GRAD_TOL, key
+    assert rel_err(mid["means"], mid["means"]) == 0.0
