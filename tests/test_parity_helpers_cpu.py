@@ -50,3 +50,29 @@ def test_grad_excess_measures_the_distance_outside_the_envelope():
         bad[j] += 3 * GRAD_TOL * scale                 # 3x the bar on the largest entry
         assert grad_excess(bad, env, key) > GRAD_TOL, key
     assert rel_err(mid["means"], mid["means"]) == 0.0
+
+
+def test_binning_acceptance_helpers():
+    """The binning test's helpers: every required (Gaussian, tile) pair is also
+    an allowed one, and a tile well away from a footprint is not allowed."""
+    from tests.test_gpu_bin import _allowed, _truth
+    sc, cam, w = _small()
+    P = oracle.project(sc, cam, w)
+    for tw, th in ((16, 16), (8, 8), (32, 8)):
+        must, allowed = _truth(P, cam.width, cam.height, tw, th)
+        assert sum(len(s) for s in must.values()) > 50
+        for i, s in must.items():
+            for ty, tx in s:
+                assert _allowed(allowed[i], ty, tx, cam.width, cam.height, tw, th), (i, ty, tx)
+        # a Gaussian whose footprint lies in one tile: the tiles two away are not allowed
+        tiles_x, tiles_y = -(-cam.width // tw), -(-cam.height // th)
+        checked = 0
+        for i, s in must.items():
+            if len(s) != 1:
+                continue
+            ty, tx = next(iter(s))
+            for dy, dx in ((2, 0), (-2, 0), (0, 2), (0, -2)):
+                if 0 <= ty + dy < tiles_y and 0 <= tx + dx < tiles_x:
+                    assert not _allowed(allowed[i], ty + dy, tx + dx, cam.width, cam.height, tw, th)
+                    checked += 1
+        assert checked > 0
