@@ -11,6 +11,7 @@ numbers as the GPU.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -52,14 +53,18 @@ def _load():
             lib.wsro_project.argtypes = common + [dp]
             lib.wsro_render.argtypes = common + [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp,
                                                  ctypes.c_double, ctypes.POINTER(ctypes.c_longlong),
-                                                 ctypes.c_double]
+                                                 ctypes.c_double, dp]
             lib.wsro_render_pixels.argtypes = common + [ctypes.c_int, ctypes.c_long,
                                                         ctypes.POINTER(ctypes.c_int), dp, dp, dp,
                                                         ctypes.c_double]
-            lib.wsro_grad.argtypes = common + [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp] + [dp] * 8 + [ctypes.c_double]
+            lib.wsro_grad.argtypes = (common + [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp] + [dp] * 8
+                                      + [ctypes.c_double, ctypes.c_double] + [dp] * 8)
+            lib.wsro_tie_width.argtypes = common + [ctypes.c_long, ctypes.POINTER(ctypes.c_long), dp, dp, dp, dp]
             lib.wsro_sh_basis.argtypes = [ctypes.c_long, ctypes.c_int, dp, dp, dp]
+            lib.wsro_set_tie_flips.argtypes = [ctypes.c_uint, ctypes.c_uint, ctypes.c_double]
+            lib.wsro_set_tie_flips.restype = None
             for f in (lib.wsro_project, lib.wsro_render, lib.wsro_render_pixels, lib.wsro_grad,
-                      lib.wsro_sh_basis):
+                      lib.wsro_tie_width, lib.wsro_sh_basis):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -112,14 +117,31 @@ def project(scene, cam, weight) -> dict:
                 depth=out[:, 17], rx=out[:, 18], ry=out[:, 19])
 
 
-def render(scene, cam, weight, *, threads: int | None = None, amb_tau: float | None = None, rows=None,
+def _tie_arg(tie) -> float:
+    """Window argument of the C functions: "fp32" (each pair's window from
+    the FP32 rounding model, ``tie_width``) is passed as -1."""
+    if tie is None:
+        return 0.0
+    if isinstance(tie, str):
+        if tie != "fp32":
+            raise ValueError(f"unknown tie window {tie!r}")
+        return -1.0
+    if not tie > 0:
+        raise ValueError("a fixed tie window must be positive")
+    return float(tie)
+
+
+def render(scene, cam, weight, *, threads: int | None = None, amb_tau=None, rows=None,
            cutoff: float = 9.0):
     """WSR forward (Eq. 7) over the whole image, or over image rows
     ``rows = (y_lo, y_hi)`` of the same camera.
 
     Returns dict(rgb [h, W, 3], den [h, W] = w_B + sum a_i, pairs, amb [h, W]
-    or None).  ``amb`` bounds how far a pixel can move if the pairs within
-    ``amb_tau`` of the q <= 9 cutoff were decided the other way.
+    or None, tie_mass [h, W] or None).  ``amb`` bounds how far a pixel can
+    move if the pairs within the tie window of the q <= 9 cutoff were decided
+    the other way, and ``tie_mass`` is the sum of |a_i| over those pairs.
+    The window is ``amb_tau``: a number (|q - 9| <= amb_tau for every pair)
+    or "fp32" (each pair's bound on an FP32 renderer's rounding of q).
     """
     lib = _load()
     a = _Args(scene, cam, weight)
@@ -128,13 +150,14 @@ def render(scene, cam, weight, *, threads: int | None = None, amb_tau: float | N
     rgb = np.zeros((H, W, 3), np.float64)
     den = np.zeros((H, W), np.float64)
     amb = np.zeros((H, W), np.float64) if amb_tau is not None else None
+    mass = np.zeros((H, W), np.float64) if amb_tau is not None else None
     pairs = ctypes.c_longlong(0)
     rc = lib.wsro_render(*a.args, ctypes.c_int(threads or default_threads()), ctypes.c_int(y_lo),
-                         ctypes.c_int(y_hi), _ptr(rgb), _ptr(den), _ptr(amb), ctypes.c_double(amb_tau or 0.0),
-                         ctypes.byref(pairs), ctypes.c_double(cutoff))
+                         ctypes.c_int(y_hi), _ptr(rgb), _ptr(den), _ptr(amb), ctypes.c_double(_tie_arg(amb_tau)),
+                         ctypes.byref(pairs), ctypes.c_double(cutoff), _ptr(mass))
     if rc:
         raise RuntimeError(f"wsro_render failed ({rc})")
-    return dict(rgb=rgb, den=den, pairs=int(pairs.value), amb=amb)
+    return dict(rgb=rgb, den=den, pairs=int(pairs.value), amb=amb, tie_mass=mass)
 
 
 def render_pixels(scene, cam, weight, xy, *, threads: int | None = None, amb_tau: float = 0.0):
@@ -155,26 +178,60 @@ def render_pixels(scene, cam, weight, xy, *, threads: int | None = None, amb_tau
     return dict(rgb=rgb, den=den, amb=amb)
 
 
-def grad(scene, cam, weight, grad_rgb, *, threads: int | None = None, rows=None, cutoff: float = 9.0) -> dict:
+def grad(scene, cam, weight, grad_rgb, *, threads: int | None = None, rows=None, cutoff: float = 9.0,
+         tie=None) -> dict:
     """Analytic gradient of <grad_rgb, C> with respect to every parameter;
     with ``rows = (y_lo, y_hi)``, grad_rgb covers only those image rows.
-    ``cutoff`` is the footprint bound on q (9 for Eq. 7 as read here)."""
+    ``cutoff`` is the footprint bound on q (9 for Eq. 7 as read here).
+
+    With ``tie`` (a fixed window, or "fp32" as in ``render``), the result
+    also holds ``tie``: per entry of every output, a first-order bound on how
+    far it moves if the pairs within the window are decided the other way,
+    by the backward's own sum or through the forward's C and D."""
     lib = _load()
     a = _Args(scene, cam, weight)
     n, K = scene.n, a.K
     y_lo, y_hi = rows if rows is not None else (0, cam.height)
     G = _d(grad_rgb).reshape(y_hi - y_lo, cam.width, 3)
-    out = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
-               sh=np.zeros((n, K, 3)), opacity=np.zeros((n, K)) if a.vd else np.zeros(n),
-               lc_v=np.zeros(n), wpar=np.zeros(6), g2d=np.zeros((n, 9)))
+
+    def shapes():
+        return dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
+                    sh=np.zeros((n, K, 3)), opacity=np.zeros((n, K)) if a.vd else np.zeros(n),
+                    lc_v=np.zeros(n), wpar=np.zeros(6), g2d=np.zeros((n, 9)))
+
+    keys = ("means", "log_scales", "quats", "sh", "opacity", "lc_v", "wpar", "g2d")
+    out = shapes()
+    t = _tie_arg(tie)
+    bnd = shapes() if t else None
     rc = lib.wsro_grad(*a.args, ctypes.c_int(threads or default_threads()), ctypes.c_int(y_lo),
-                       ctypes.c_int(y_hi), _ptr(G),
-                       _ptr(out["means"]), _ptr(out["log_scales"]), _ptr(out["quats"]),
-                       _ptr(out["sh"]), _ptr(out["opacity"]), _ptr(out["lc_v"]),
-                       _ptr(out["wpar"]), _ptr(out["g2d"]), ctypes.c_double(cutoff))
+                       ctypes.c_int(y_hi), _ptr(G), *[_ptr(out[k]) for k in keys], ctypes.c_double(cutoff),
+                       ctypes.c_double(t), *[_ptr(bnd[k]) if bnd else None for k in keys])
     if rc:
         raise RuntimeError(f"wsro_grad failed ({rc})")
+    if bnd is not None:
+        out["tie"] = bnd
     return out
+
+
+TIE_TERMS = ("mean", "rows", "sums", "record", "threshold", "evaluation")
+
+
+def tie_width(scene, cam, weight, idx, xy) -> dict:
+    """The FP32 rounding model's tie window at listed points: Gaussian
+    ``idx[k]`` at the image position ``xy[k]`` (pixel units, any point).
+    Returns dict(q [M] exact, tau [M] the window, terms [M, 6] its parts in
+    the order of ``TIE_TERMS``); -1 for culled Gaussians."""
+    lib = _load()
+    a = _Args(scene, cam, weight)
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+    pts = _d(xy).reshape(-1, 2)
+    m = idx.shape[0]
+    q, tau, terms = np.zeros(m), np.zeros(m), np.zeros((m, 6))
+    rc = lib.wsro_tie_width(*a.args, ctypes.c_long(m), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                            _ptr(pts), _ptr(q), _ptr(tau), _ptr(terms))
+    if rc:
+        raise RuntimeError(f"wsro_tie_width failed ({rc})")
+    return dict(q=q, tau=tau, terms=terms)
 
 
 def sh_basis(dirs, deg: int, with_grad: bool = False):
@@ -188,3 +245,20 @@ def sh_basis(dirs, deg: int, with_grad: bool = False):
     if rc:
         raise RuntimeError("wsro_sh_basis failed")
     return (Y, dY) if with_grad else Y
+
+
+@contextlib.contextmanager
+def tie_flips(fwd_seed: int, grad_seed: int, tau: float):
+    """Within the block, pairs with |q - 9| <= tau are counted or not by a
+    seeded hash of (seed, Gaussian, pixel), in the forward sums (``fwd_seed``)
+    and in the gradient's sums (``grad_seed``); 0 keeps q <= 9.  It stands in
+    for a renderer that decides cutoff ties either way (tests of the tie
+    bounds only)."""
+    lib = _load()
+    with _lock:
+        lib.wsro_set_tie_flips(int(fwd_seed), int(grad_seed), float(tau))
+    try:
+        yield
+    finally:
+        with _lock:
+            lib.wsro_set_tie_flips(0, 0, 0.0)

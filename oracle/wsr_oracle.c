@@ -300,6 +300,199 @@ static double quad_form(const double conic[3], double dx, double dy)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Cutoff ties: how far an FP32 renderer's q can lie from q.                 */
+/*                                                                          */
+/* Eq. 7 sums the pairs with q <= 9.  A renderer that works in FP32 decides  */
+/* that test from a record rounded to FP32 (the projected mean, and the     */
+/* conic held as the sum of squares q = (qs dy + qw dx)^2 + qd dx^2 of      */
+/* Sigma_2D = T T^t + 0.3 I, T = J W R S formed in FP32), so a pair whose q */
+/* lies within that rounding of 9 may be decided the other way there.  The  */
+/* comparison of such a renderer with this oracle forgives exactly those    */
+/* pairs; tie_width() bounds |q_FP32 - q| for one pair, to first order in   */
+/* the FP32 unit roundoff u = 2^-24 (IEEE operations; exp within 2 ulp),    */
+/* term by term (v = Sigma^-1 d, d the pixel's offset from the mean):       */
+/*   mean    2 (|v_x| e_x + |v_y| e_y), e the bound on the FP32 mean's      */
+/*           error: t = W p + T, then fx t_x / t_z + c_x;                   */
+/*   rows    2 |T^t v| |(|dT|^t |v|)|, dT the bound on the FP32 error of    */
+/*           each entry of T (from R of the normalised quaternion, exp of   */
+/*           the log-scales, W R S, and J at the FP32 t);                    */
+/*   sums    |v|^t E |v|, E the rounding of a, b, c from the rows, the FP32 */
+/*           constant 0.3, and the determinant |r0 x r1|^2 + 0.3 (a0 + c0)  */
+/*           + 0.09 rounded (an error in it acts as one in c); none of it   */
+/*           when the conic is formed in FP64 (det < 1e-3 a c);             */
+/*   record  the rounding of qd, qs and qw themselves;                      */
+/*   test    evaluating q at the pixel (any order of a dozen FMAs, offsets  */
+/*           of up to 62 pixels from a tile origin) and the FP32 threshold; */
+/* and doubles the sum for the second-order terms.  It is test              */
+/* infrastructure: no part of Eq. 7 depends on it.                          */
+/* ------------------------------------------------------------------------ */
+#define ORC_U (1.0 / 16777216.0)    /* FP32 unit roundoff, 2^-24 */
+#define ORC_TIE_CAP 1.0             /* widest tie window the pixel ranges cover */
+
+static double gam(int n) { return n * ORC_U / (1.0 - n * ORC_U); }
+
+typedef struct {
+    double ex, ey;          /* bound on the FP32 mean's error (pixels) */
+    double T[6], eT[6];     /* rows of T = J W R S, and bounds on their FP32 errors */
+    double E[3];            /* rounding of Sigma's a, b, c (the determinant's folded into c) */
+    double eta_d, eta_s, eta_w;  /* relative rounding of qd, qs, qw */
+    double qs, qw, qd;      /* Sigma^-1 as the sum of squares (q units) */
+} otie;
+
+static void tie_model(const oscene* S, long i, const ocam* cam, const oproj* o, otie* m)
+{
+    const double u = ORC_U;
+    memset(m, 0, sizeof *m);
+    if (!o->visible) return;
+    const double* p = S->means + 3 * i;
+    /* t = W p + T: three products, three sums per entry */
+    double et[3];
+    for (int r = 0; r < 3; ++r)
+        et[r] = gam(4) * (fabs(cam->R[3 * r] * p[0]) + fabs(cam->R[3 * r + 1] * p[1]) +
+                          fabs(cam->R[3 * r + 2] * p[2]) + fabs(cam->T[r]));
+    const double tz = o->t[2], ux = o->t[0] / tz, uy = o->t[1] / tz;
+    /* mean fx t_x / t_z + c_x: the error of t, then a product, a quotient and a sum */
+    m->ex = cam->fx * (et[0] + fabs(ux) * et[2]) / tz + 2 * u * cam->fx * fabs(ux) + u * fabs(o->mean2d[0]);
+    m->ey = cam->fy * (et[1] + fabs(uy) * et[2]) / tz + 2 * u * cam->fy * fabs(uy) + u * fabs(o->mean2d[1]);
+    /* R of the normalised quaternion: every entry within 32 u (|q| = 1 and a few roundings
+     * each); exp within 2 ulp (4 u); M = W R S with its 3-term sums */
+    const double* qr = S->quats + 4 * i;
+    const double ql = sqrt(qr[0] * qr[0] + qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]);
+    const double qu[4] = {qr[0] / ql, qr[1] / ql, qr[2] / ql, qr[3] / ql};
+    double Rq[9], M[9], eM[9], sc[3];
+    quat_to_rot(qu, Rq);
+    for (int k = 0; k < 3; ++k) sc[k] = exp(S->log_scales[3 * i + k]);
+    for (int r = 0; r < 3; ++r)
+        for (int cc = 0; cc < 3; ++cc) {
+            double v = 0, av = 0, aw = 0;
+            for (int k = 0; k < 3; ++k) {
+                v += cam->R[3 * r + k] * Rq[3 * k + cc];
+                av += fabs(cam->R[3 * r + k] * Rq[3 * k + cc]);
+                aw += fabs(cam->R[3 * r + k]);
+            }
+            M[3 * r + cc] = v * sc[cc];
+            eM[3 * r + cc] = sc[cc] * (gam(3) * av + 32 * u * aw) + 5 * u * fabs(M[3 * r + cc]);
+        }
+    /* J at the clamped x/z, y/z of the FP32 t; the FP32 clamp limit differs by u */
+    const double eiz = u + et[2] / tz;
+    const double limx = ORC_CLAMP * 0.5 * cam->W / cam->fx, limy = ORC_CLAMP * 0.5 * cam->H / cam->fy;
+    const double cxz = clampd(ux, -limx, limx), cyz = clampd(uy, -limy, limy);
+    const double ecx = et[0] / tz + fabs(ux) * (eiz + u) + u * limx;
+    const double ecy = et[1] / tz + fabs(uy) * (eiz + u) + u * limy;
+    const double J00 = cam->fx / tz, J02 = -cam->fx * cxz / tz, J11 = cam->fy / tz, J12 = -cam->fy * cyz / tz;
+    const double eJ00 = J00 * (eiz + u), eJ11 = J11 * (eiz + u);
+    const double eJ02 = cam->fx / tz * (ecx + fabs(cxz) * (eiz + 2 * u));
+    const double eJ12 = cam->fy / tz * (ecy + fabs(cyz) * (eiz + 2 * u));
+    for (int k = 0; k < 3; ++k) {
+        m->T[k] = J00 * M[k] + J02 * M[6 + k];
+        m->T[3 + k] = J11 * M[3 + k] + J12 * M[6 + k];
+        m->eT[k] = eJ00 * fabs(M[k]) + J00 * eM[k] + eJ02 * fabs(M[6 + k]) + fabs(J02) * eM[6 + k] +
+                   gam(2) * (fabs(J00 * M[k]) + fabs(J02 * M[6 + k]));
+        m->eT[3 + k] = eJ11 * fabs(M[3 + k]) + J11 * eM[3 + k] + eJ12 * fabs(M[6 + k]) + fabs(J12) * eM[6 + k] +
+                       gam(2) * (fabs(J11 * M[3 + k]) + fabs(J12 * M[6 + k]));
+    }
+    const double a = o->cov2d[0], b = o->cov2d[1], c = o->cov2d[2], det = a * c - b * b;
+    m->qd = 1.0 / a;
+    m->qs = sqrt(a / det);
+    m->qw = -(b / a) * m->qs;
+    if (det < 0.999e-3 * a * c) {
+        /* formed in FP64 from the FP32 rows: only the final rounding of qd, qs, qw */
+        m->eta_d = m->eta_s = m->eta_w = u;
+        return;
+    }
+    const double* r0 = m->T;
+    const double* r1 = m->T + 3;
+    double a0 = 0, c0 = 0, babs = 0, x2 = 0, edet = 0;
+    for (int k = 0; k < 3; ++k) {
+        a0 += r0[k] * r0[k];
+        c0 += r1[k] * r1[k];
+        babs += fabs(r0[k] * r1[k]);
+        const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+        const double x = r0[k1] * r1[k2] - r0[k2] * r1[k1];
+        x2 += x * x;
+        edet += 2 * fabs(x) * gam(2) * (fabs(r0[k1] * r1[k2]) + fabs(r0[k2] * r1[k1]));
+    }
+    const double d03 = fabs(0.3 - (double)0.3f);
+    const double ea = gam(3) * a0 + u * a, eb = gam(3) * babs;
+    edet += gam(3) * x2 + 2 * u * 0.3 * (a0 + c0) + u * 0.09 + 2 * u * det;
+    m->E[0] = ea + d03;
+    m->E[1] = eb;
+    m->E[2] = gam(3) * c0 + u * c + d03 + (edet + 2 * fabs(b) * eb + c * ea) / a;
+    m->eta_d = 2 * u;
+    m->eta_s = 3 * u;
+    m->eta_w = 2 * u;
+}
+
+/* The tie window of one pair (pixel offset dx, dy from the mean; q its exact
+ * value); terms[6], if given, gets its six parts (mean, rows, sums, record,
+ * threshold, evaluation), each doubled as in the window. */
+static double tie_width(const otie* m, double dx, double dy, double q, double* terms)
+{
+    const double u = ORC_U;
+    const double r = m->qs * dy + m->qw * dx;
+    const double vx = m->qw * r + m->qd * dx, vy = m->qs * r;     /* v = Sigma^-1 d = grad(q) / 2 */
+    const double t_mean = 2.0 * (fabs(vx) * m->ex + fabs(vy) * m->ey);
+    double tv2 = 0, ev2 = 0;
+    for (int k = 0; k < 3; ++k) {
+        const double tk = m->T[k] * vx + m->T[3 + k] * vy;
+        const double ek = m->eT[k] * fabs(vx) + m->eT[3 + k] * fabs(vy);
+        tv2 += tk * tk;
+        ev2 += ek * ek;
+    }
+    const double t_rows = 2.0 * sqrt(tv2 * ev2);
+    const double t_sums = m->E[0] * vx * vx + 2 * m->E[1] * fabs(vx * vy) + m->E[2] * vy * vy;
+    const double t_rec = 2 * m->eta_s * r * r + 2 * m->eta_w * fabs(r * m->qw * dx) + m->eta_d * m->qd * dx * dx;
+    const double t_cut = 18 * u;                 /* 9 k with k = log2(e) / 2, each rounded to FP32 */
+    const double X = fabs(dx) + 62.0, Y = fabs(dy) + 62.0;
+    const double t_eval = 12 * u * fabs(r) * (m->qs * Y + fabs(m->qw) * X) + 6 * u * m->qd * X * X + u * q;
+    if (terms) {
+        terms[0] = 2.0 * t_mean;
+        terms[1] = 2.0 * t_rows;
+        terms[2] = 2.0 * t_sums;
+        terms[3] = 2.0 * t_rec;
+        terms[4] = 2.0 * t_cut;
+        terms[5] = 2.0 * t_eval;
+    }
+    return 2.0 * (t_mean + t_rows + t_sums + t_rec + t_cut + t_eval);
+}
+
+/* Test hook: with a nonzero seed, a pair within orc_flip_tau of the cutoff is
+ * counted or not by a hash of (seed, Gaussian, pixel) instead of q <= 9, in
+ * the forward sums (which = 0) or in the gradient's sums (which = 1).  It
+ * stands in for a renderer that decides ties either way, so that tests can
+ * check the tie bounds against arbitrary decisions. */
+static unsigned orc_flip_seed[2];
+static double orc_flip_tau;
+
+void wsro_set_tie_flips(unsigned fwd_seed, unsigned grad_seed, double tau)
+{
+    orc_flip_seed[0] = fwd_seed;
+    orc_flip_seed[1] = grad_seed;
+    orc_flip_tau = tau;
+}
+
+static int counted(double q, double cutoff, long i, int x, int y, int which)
+{
+    const unsigned seed = orc_flip_seed[which];
+    if (seed && fabs(q - ORC_CUTOFF) <= orc_flip_tau) {
+        uint64_t h = ((uint64_t)seed << 32) ^ ((uint64_t)i * 0x9E3779B97F4A7C15ull) ^
+                     ((uint64_t)(unsigned)x << 20) ^ (uint64_t)(unsigned)y;
+        h ^= h >> 33; h *= 0xFF51AFD7ED558CCDull; h ^= h >> 33; h *= 0xC4CEB9FE1A85EC53ull; h ^= h >> 33;
+        return (int)(h & 1u);
+    }
+    return q <= cutoff;
+}
+
+/* Models of every Gaussian (malloc'ed). */
+static otie* tie_all(const oscene* S, const ocam* cam, const oproj* P)
+{
+    otie* m = (otie*)malloc(sizeof(otie) * (S->n > 0 ? S->n : 1));
+    if (!m) return NULL;
+    for (long i = 0; i < S->n; ++i) tie_model(S, i, cam, P + i, m + i);
+    return m;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Thread helper                                                             */
 /* ------------------------------------------------------------------------ */
 typedef struct { void (*fn)(void*, long, long, int); void* arg; long lo, hi; int tid; } ojob;
@@ -386,6 +579,9 @@ typedef struct {
     double* amb;             /* [H*W] or NULL: filled in a second pass */
     const double* rgb;       /* final colours, for the second pass */
     const double* dent;      /* total denominators, for the second pass */
+    const otie* tie;         /* per-pair windows from the FP32 model (NULL: amb_tau for every pair) */
+    double* mass;            /* [H*W] or NULL: sum of |a| over the pixel's tie pairs */
+    int* wide;               /* per thread: a pair's window exceeded ORC_TIE_CAP */
 } render_ctx;
 
 static void render_rows(void* arg, long r0, long r1, int tid)
@@ -395,7 +591,8 @@ static void render_rows(void* arg, long r0, long r1, int tid)
     r1 += c->y_lo;
     const int W = c->cam->W;
     long long pairs = 0;
-    const double grow = sqrt((c->cutoff + (c->amb ? c->amb_tau : 0.0)) / ORC_CUTOFF);
+    const double widest = c->amb ? (c->tie ? ORC_TIE_CAP : c->amb_tau) : 0.0;
+    const double grow = sqrt((c->cutoff + widest + (orc_flip_seed[0] ? orc_flip_tau : 0.0)) / ORC_CUTOFF);
     for (long i = 0; i < c->n; ++i) {
         const oproj* o = c->P + i;
         if (!o->visible) continue;
@@ -410,7 +607,9 @@ static void render_rows(void* arg, long r0, long r1, int tid)
                 const long p = (long)(y - c->y_lo) * W + x;
                 if (c->amb) {
                     /* second pass: bound of what a near-cutoff pair can change */
-                    if (fabs(q - c->cutoff) <= c->amb_tau) {
+                    const double tau = c->tie ? tie_width(c->tie + i, dx, dy, q, NULL) : c->amb_tau;
+                    if (tau > widest) c->wide[tid] = 1;
+                    if (fabs(q - c->cutoff) <= tau) {
                         const double g = exp(-0.5 * q);
                         const double a = o->u * o->w * g;
                         double m = 0;
@@ -418,11 +617,12 @@ static void render_rows(void* arg, long r0, long r1, int tid)
                             const double e = fabs(o->color[ch] - c->rgb[3 * p + ch]);
                             if (e > m) m = e;
                         }
-                        c->amb[p] += fabs(a) * m / fabs(c->dent[p]);
+                        c->amb[p] += fabs(a) * m;          /* divided by the least |D| afterwards */
+                        c->mass[p] += fabs(a);
                     }
                     continue;
                 }
-                if (q > c->cutoff) continue;
+                if (!counted(q, c->cutoff, i, x, y, 0)) continue;
                 const double g = exp(-0.5 * q);
                 const double a = o->u * o->w * g;            /* alpha_i w(d_i) */
                 for (int ch = 0; ch < 3; ++ch) c->num[3 * p + ch] += o->color[ch] * a;
@@ -448,14 +648,18 @@ static oproj* project_all(const oscene* S, const ocam* cam, const owt* wt)
  * that bracket pairs whose q is within rounding of 9.
  * out_rgb [rows*W*3]: C per pixel (Eq. 7); out_den [rows*W]: w_B + sum a_i.
  * amb [H*W] (optional): for pixels having Gaussians with |q - 9| <= amb_tau,
- * a bound on how far C can move if those pairs were decided the other way.
+ * a bound on how far C can move if those pairs were decided the other way;
+ * amb_tau < 0 takes each pair's window from the FP32 rounding model above.
+ * tie_mass [H*W] (optional, with amb): the sum of |a| over those pairs.
  * n_pairs (optional): number of (pixel, Gaussian) pairs with q <= 9.
+ * Returns 3 if a model window exceeded ORC_TIE_CAP (the pixel ranges would
+ * then miss pairs).
  */
 int wsro_render(long n, int deg, int vd, const double* means, const double* log_scales,
                 const double* quats, const double* sh, const double* opac, const double* lc_v,
                 const double* cam16, int W, int H, double znear, int wkind, const double* wpar,
                 int nthreads, int y_lo, int y_hi, double* out_rgb, double* out_den, double* amb,
-                double amb_tau, long long* n_pairs, double cutoff)
+                double amb_tau, long long* n_pairs, double cutoff, double* tie_mass)
 {
     if (deg < 0 || deg > 3 || n < 0 || W <= 0 || H <= 0) return 1;
     if (y_lo < 0 || y_hi > H || y_lo >= y_hi) return 1;
@@ -470,7 +674,7 @@ int wsro_render(long n, int deg, int vd, const double* means, const double* log_
     double* num = (double*)calloc(np * 3, sizeof(double));
     double* den = (double*)calloc(np, sizeof(double));
     long long pairs[256] = {0};
-    render_ctx c = {P, n, &cam, &wt, cutoff, y_lo, num, den, pairs, amb_tau, NULL, NULL, NULL};
+    render_ctx c = {P, n, &cam, &wt, cutoff, y_lo, num, den, pairs, amb_tau, NULL, NULL, NULL, NULL, NULL, NULL};
     if (nthreads > rows) nthreads = rows;
     run_parallel(render_rows, &c, rows, nthreads);
     long long tot = 0;
@@ -481,14 +685,32 @@ int wsro_render(long n, int deg, int vd, const double* means, const double* log_
         out_den[p] = D;
         for (int ch = 0; ch < 3; ++ch) out_rgb[3 * p + ch] = (wt.c_bg[ch] * wt.w_bg + num[3 * p + ch]) / D;
     }
+    int rc = 0;
     if (amb) {
-        memset(amb, 0, np * sizeof(double));
-        render_ctx c2 = {P, n, &cam, &wt, cutoff, y_lo, NULL, NULL, pairs, amb_tau, amb, out_rgb, out_den};
-        run_parallel(render_rows, &c2, rows, nthreads);
-        for (long p = 0; p < np; ++p) amb[p] *= 1.05;
+        /* a pixel's tie pairs move C by sum |a| |c - C| / |D'| at most, D' the denominator
+         * after the other decisions: |D'| >= |D| - sum |a| (infinite if D' can vanish) */
+        double* mass = tie_mass ? tie_mass : (double*)malloc(np * sizeof(double));
+        otie* tm = amb_tau < 0 ? tie_all(&S, &cam, P) : NULL;
+        int wide[256] = {0};
+        if (!mass || (amb_tau < 0 && !tm)) {
+            rc = 2;
+        } else {
+            memset(amb, 0, np * sizeof(double));
+            memset(mass, 0, np * sizeof(double));
+            render_ctx c2 = {P, n, &cam, &wt, cutoff, y_lo, NULL, NULL, pairs, amb_tau, amb, out_rgb, out_den,
+                             tm, mass, wide};
+            run_parallel(render_rows, &c2, rows, nthreads);
+            for (long p = 0; p < np; ++p) {
+                const double dlo = fabs(out_den[p]) - mass[p];
+                if (amb[p] > 0) amb[p] = dlo > 0 ? amb[p] / dlo : HUGE_VAL;
+            }
+            for (int t = 0; t < 256; ++t) if (wide[t]) rc = 3;
+        }
+        if (!tie_mass) free(mass);
+        free(tm);
     }
     free(num); free(den); free(P);
-    return 0;
+    return rc;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -520,7 +742,7 @@ static void render_pixels(void* arg, long lo, long hi, int tid)
         const double D = c->wt->w_bg + den;
         double C[3];
         for (int ch = 0; ch < 3; ++ch) C[ch] = (c->wt->c_bg[ch] * c->wt->w_bg + num[ch]) / D;
-        double am = 0;
+        double am = 0, mass = 0;
         if (c->amb) {
             const double grow = sqrt((ORC_CUTOFF + c->amb_tau) / ORC_CUTOFF);
             for (long i = 0; i < c->n; ++i) {
@@ -533,9 +755,11 @@ static void render_pixels(void* arg, long lo, long hi, int tid)
                 const double a = o->u * o->w * exp(-0.5 * q);
                 double m = 0;
                 for (int ch = 0; ch < 3; ++ch) { const double e = fabs(o->color[ch] - C[ch]); if (e > m) m = e; }
-                am += fabs(a) * m / fabs(D);
+                am += fabs(a) * m;
+                mass += fabs(a);
             }
-            c->amb[k] = 1.05 * am;
+            /* divided by the least |D| the tie decisions allow */
+            c->amb[k] = am > 0 ? (fabs(D) > mass ? am / (fabs(D) - mass) : HUGE_VAL) : 0.0;
         }
         for (int ch = 0; ch < 3; ++ch) c->rgb[3 * k + ch] = C[ch];
         c->den[k] = D;
@@ -582,6 +806,17 @@ int wsro_render_pixels(long n, int deg, int vd, const double* means, const doubl
 /* g_sh[n*K*3], g_opac[n or n*K], g_lc_v[n], g_wpar[6] (sigma, beta, w_B,    */
 /* c_B), g2d[n*9]: per-Gaussian dL/d(mean2d x, y), dL/d(conic A, B, C),      */
 /* dL/d(u w), dL/dc (3).  B is the off-diagonal conic entry, counted once.   */
+/*                                                                          */
+/* Tie bounds (optional, test infrastructure): an FP32 renderer may decide  */
+/* pairs within rounding of the cutoff the other way (see tie_width), both  */
+/* in its backward (which terms it sums) and in its forward (the C and D    */
+/* the terms read).  To first order each gradient entry then moves by at    */
+/* most                                                                     */
+/*   B = sum over the Gaussian's tie pairs of |its term|                    */
+/*     + sum over its other pairs at pixels holding ties of the term's      */
+/*       change when C moves by amb and D by the tie mass m = sum |a|,      */
+/* per g2d component, and each parameter entry by sum_k |chain_k| B_k, the  */
+/* chain being linear in g2d; the background terms likewise per pixel.      */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     const oscene* S; const oproj* P; const ocam* cam; const owt* wt;
@@ -590,24 +825,214 @@ typedef struct {
     const double *rgb, *den, *G;
     double *g_means, *g_log_scales, *g_quats, *g_sh, *g_opac, *g_lc_v, *g2d;
     double gw[256][2];     /* per-thread partial sums: sigma, beta */
+    /* tie bounds (NULL b_g2d: none) */
+    const otie* tie;         /* per-pair windows from the FP32 model, or NULL for tie_tau */
+    double tie_tau;
+    const double *amb, *mass;   /* per pixel: the forward's tie allowance and tie mass */
+    double *b_means, *b_log_scales, *b_quats, *b_sh, *b_opac, *b_lc_v, *b_g2d;
+    double bw[256][2];
+    int wide[256];
 } grad_ctx;
+
+/* One Gaussian's parameter gradients as the chain forms them from g2d. */
+typedef struct {
+    double means[3], log_scales[3], quats[4], sh[ORC_MAX_K * 3], opac[ORC_MAX_K], lc_v, sig, beta;
+} ochain;
+
+static void chain_one(const grad_ctx* c, long i, const double* g2, ochain* out)
+{
+    const oscene* S = c->S;
+    const oproj* o = c->P + i;
+    const ocam* cam = c->cam;
+    const owt* wt = c->wt;
+    const int K = S->K;
+    memset(out, 0, sizeof *out);
+    double gsig = 0, gbeta = 0;
+    double g_t[3] = {0, 0, 0};      /* dL/dt (camera space) */
+    double g_dir[3] = {0, 0, 0};    /* dL/d(unit direction) */
+    double g_p[3] = {0, 0, 0};      /* dL/dp (world), direct terms */
+    const double dL_duw = g2[5];
+    const double dL_du = dL_duw * o->w, dL_dw = dL_duw * o->u;
+
+    /* colour: c = max(0, Y.H + 0.5) */
+    double Y[ORC_MAX_K], dY[ORC_MAX_K][3];
+    sh_basis(S->deg, o->dir, Y, dY);
+    const double* H = S->sh + (long)i * K * 3;
+    double* gH = out->sh;
+    for (int ch = 0; ch < 3; ++ch) {
+        const double graw = (o->raw[ch] + 0.5 > 0) ? g2[6 + ch] : 0.0;
+        for (int k = 0; k < K; ++k) {
+            gH[3 * k + ch] = graw * Y[k];
+            for (int e = 0; e < 3; ++e) g_dir[e] += graw * H[3 * k + ch] * dY[k][e];
+        }
+    }
+    /* opacity */
+    if (S->vd) {
+        const double* Ha = S->opac + (long)i * K;
+        double* gHa = out->opac;
+        for (int k = 0; k < K; ++k) {
+            gHa[k] = dL_du * Y[k];
+            for (int e = 0; e < 3; ++e) g_dir[e] += dL_du * Ha[k] * dY[k][e];
+        }
+    } else {
+        out->opac[0] = dL_du * o->u * (1.0 - o->u);
+    }
+    /* depth weight; d = t_z */
+    const double d = o->d;
+    double dL_dd = 0;
+    if (wt->kind == 1) {
+        const double db = pow(d, wt->beta);
+        gsig += dL_dw * (-db) * o->w;
+        gbeta += dL_dw * (-wt->sigma * db * log(d)) * o->w;
+        dL_dd = dL_dw * (-wt->sigma * wt->beta * pow(d, wt->beta - 1.0)) * o->w;
+    } else if (wt->kind == 2) {
+        const double lin = 1.0 - d / wt->sigma;
+        if (lin > 0) {
+            const double v = S->lc_v[i];
+            out->lc_v = dL_dw * lin;
+            gsig += dL_dw * v * d / (wt->sigma * wt->sigma);
+            dL_dd = dL_dw * (-v / wt->sigma);
+        }
+    }
+    g_t[2] += dL_dd;
+    /* direction: dir = v / |v| */
+    {
+        double dd = 0;
+        for (int e = 0; e < 3; ++e) dd += o->dir[e] * g_dir[e];
+        for (int e = 0; e < 3; ++e) g_p[e] += (g_dir[e] - o->dir[e] * dd) / o->vnorm;
+    }
+    /* projected mean */
+    const double tx = o->t[0], ty = o->t[1], tz = o->t[2];
+    g_t[0] += g2[0] * cam->fx / tz;
+    g_t[1] += g2[1] * cam->fy / tz;
+    g_t[2] += -g2[0] * cam->fx * tx / (tz * tz) - g2[1] * cam->fy * ty / (tz * tz);
+
+    /* conic = Sigma_2D^{-1}:  dL/dSigma = -K Gk K with Gk the symmetric
+     * matrix gradient [[gA, gB/2], [gB/2, gC]] */
+    const double Kc[4] = {o->conic[0], o->conic[1], o->conic[1], o->conic[2]};
+    const double Gk[4] = {g2[2], 0.5 * g2[3], 0.5 * g2[3], g2[4]};
+    double t1[4], GS[4];
+    mat_mul(Kc, Gk, t1, 2, 2, 2);
+    mat_mul(t1, Kc, GS, 2, 2, 2);
+    for (int e = 0; e < 4; ++e) GS[e] = -GS[e];
+    /* Sigma_2D = T Sigma_3D T^t + 0.3 I,  T = J W */
+    const double tanx = 0.5 * cam->W / cam->fx, tany = 0.5 * cam->H / cam->fy;
+    const double limx = ORC_CLAMP * tanx, limy = ORC_CLAMP * tany;
+    const double rx = clampd(tx / tz, -limx, limx), ry = clampd(ty / tz, -limy, limy);
+    const int freex = (tx / tz >= -limx && tx / tz <= limx);
+    const int freey = (ty / tz >= -limy && ty / tz <= limy);
+    const double J[6] = {cam->fx / tz, 0, -cam->fx * rx / tz, 0, cam->fy / tz, -cam->fy * ry / tz};
+    double T[6], Tt[6], Sig3[9], M[9], Mt[9], Rg[9];
+    mat_mul(J, cam->R, T, 2, 3, 3);
+    transpose(T, Tt, 2, 3);
+    const double* qr = S->quats + 4 * i;
+    const double qn = sqrt(qr[0] * qr[0] + qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]);
+    const double q[4] = {qr[0] / qn, qr[1] / qn, qr[2] / qn, qr[3] / qn};
+    quat_to_rot(q, Rg);
+    double s[3];
+    for (int k = 0; k < 3; ++k) s[k] = exp(S->log_scales[3 * i + k]);
+    for (int r = 0; r < 3; ++r)
+        for (int cc = 0; cc < 3; ++cc) M[3 * r + cc] = Rg[3 * r + cc] * s[cc];
+    transpose(M, Mt, 3, 3);
+    mat_mul(M, Mt, Sig3, 3, 3, 3);
+    /* dL/dSigma_3D = T^t GS T ;  dL/dT = 2 GS T Sigma_3D */
+    double t2[6], GSig3[9], GT[6], t3[6];
+    mat_mul(GS, T, t2, 2, 2, 3);
+    mat_mul(Tt, t2, GSig3, 3, 2, 3);
+    mat_mul(GS, T, t3, 2, 2, 3);
+    mat_mul(t3, Sig3, GT, 2, 3, 3);
+    for (int e = 0; e < 6; ++e) GT[e] *= 2.0;
+    /* dL/dJ = dL/dT W^t */
+    double Wt[9], GJ[6];
+    transpose(cam->R, Wt, 3, 3);
+    mat_mul(GT, Wt, GJ, 2, 3, 3);
+    /* J00 = fx/tz, J02 = -fx rx/tz, J11 = fy/tz, J12 = -fy ry/tz,
+     * rx = clamp(tx/tz) (moves with t only when not clamped) */
+    g_t[2] += GJ[0] * (-cam->fx / (tz * tz)) + GJ[4] * (-cam->fy / (tz * tz));
+    g_t[2] += GJ[2] * (cam->fx * rx / (tz * tz)) + GJ[5] * (cam->fy * ry / (tz * tz));
+    if (freex) {
+        g_t[0] += GJ[2] * (-cam->fx / (tz * tz));
+        g_t[2] += GJ[2] * (-cam->fx / tz) * (-tx / (tz * tz));
+    }
+    if (freey) {
+        g_t[1] += GJ[5] * (-cam->fy / (tz * tz));
+        g_t[2] += GJ[5] * (-cam->fy / tz) * (-ty / (tz * tz));
+    }
+    /* t = W p + T  =>  dL/dp += W^t dL/dt */
+    for (int e = 0; e < 3; ++e)
+        g_p[e] += cam->R[e] * g_t[0] + cam->R[3 + e] * g_t[1] + cam->R[6 + e] * g_t[2];
+    for (int e = 0; e < 3; ++e) out->means[e] = g_p[e];
+
+    /* Sigma_3D = M M^t, M = R diag(s):  dL/dM = 2 dL/dSigma_3D M */
+    double GM[9];
+    mat_mul(GSig3, M, GM, 3, 3, 3);
+    for (int e = 0; e < 9; ++e) GM[e] *= 2.0;
+    double gs[3] = {0, 0, 0}, GR[9];
+    for (int r = 0; r < 3; ++r)
+        for (int cc = 0; cc < 3; ++cc) {
+            GR[3 * r + cc] = GM[3 * r + cc] * s[cc];
+            gs[cc] += GM[3 * r + cc] * Rg[3 * r + cc];
+        }
+    for (int k = 0; k < 3; ++k) out->log_scales[k] = gs[k] * s[k];
+    /* rotation from the normalised quaternion */
+    double dR[9][4], gqn[4] = {0, 0, 0, 0};
+    quat_to_rot_grad(q, dR);
+    for (int e = 0; e < 9; ++e)
+        for (int k = 0; k < 4; ++k) gqn[k] += GR[e] * dR[e][k];
+    double dot = 0;
+    for (int k = 0; k < 4; ++k) dot += gqn[k] * q[k];
+    for (int k = 0; k < 4; ++k) out->quats[k] = (gqn[k] - q[k] * dot) / qn;
+    out->sig = gsig;
+    out->beta = gbeta;
+}
+
+/* out (+)= s * |x| over n entries (s = 0: plain copy of x) */
+static void put(double* out, const double* x, int n, double s)
+{
+    for (int k = 0; k < n; ++k) out[k] = s > 0 ? out[k] + s * fabs(x[k]) : x[k];
+}
 
 static void grad_gaussians(void* arg, long lo, long hi, int tid)
 {
     grad_ctx* c = (grad_ctx*)arg;
     const oscene* S = c->S;
     const ocam* cam = c->cam;
-    const owt* wt = c->wt;
     const int K = S->K, W = cam->W;
-    double gsig = 0, gbeta = 0;
+    const int nop = S->vd ? K : 1;
+    const int bnd = c->b_g2d != NULL;
+    double gsig = 0, gbeta = 0, bsig = 0, bbeta = 0;
+    const double widest = c->tie ? ORC_TIE_CAP : c->tie_tau;
     for (long i = lo; i < hi; ++i) {
         const oproj* o = c->P + i;
         double* g2 = c->g2d + 9 * i;
+        double B[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         memset(g2, 0, 9 * sizeof(double));
-        if (!o->visible) continue;
+        if (!o->visible) {
+            /* culled (behind the near plane): no gradient */
+            ochain none;
+            memset(&none, 0, sizeof none);
+            put(c->g_means + 3 * i, none.means, 3, 0);
+            put(c->g_log_scales + 3 * i, none.log_scales, 3, 0);
+            put(c->g_quats + 4 * i, none.quats, 4, 0);
+            put(c->g_sh + (long)i * K * 3, none.sh, K * 3, 0);
+            put(c->g_opac + (long)i * nop, none.opac, nop, 0);
+            c->g_lc_v[i] = 0;
+            if (bnd) {
+                put(c->b_means + 3 * i, none.means, 3, 0);
+                put(c->b_log_scales + 3 * i, none.log_scales, 3, 0);
+                put(c->b_quats + 4 * i, none.quats, 4, 0);
+                put(c->b_sh + (long)i * K * 3, none.sh, K * 3, 0);
+                put(c->b_opac + (long)i * nop, none.opac, nop, 0);
+                c->b_lc_v[i] = 0;
+                memset(c->b_g2d + 9 * i, 0, 9 * sizeof(double));
+            }
+            continue;
+        }
         /* ---- per-pixel part: Eq. 7 and the Gaussian footprint ---- */
         int x0, x1, y0, y1;
-        pixel_range(o, cam, sqrt(c->cutoff / ORC_CUTOFF), &x0, &x1, &y0, &y1);
+        double reach = bnd && ORC_CUTOFF + widest > c->cutoff ? ORC_CUTOFF + widest : c->cutoff;
+        if (orc_flip_seed[1] && ORC_CUTOFF + orc_flip_tau > reach) reach = ORC_CUTOFF + orc_flip_tau;
+        pixel_range(o, cam, sqrt(reach / ORC_CUTOFF), &x0, &x1, &y0, &y1);
         if (y0 < c->y_lo) y0 = c->y_lo;
         if (y1 > c->y_hi - 1) y1 = c->y_hi - 1;
         const double uw = o->u * o->w;
@@ -615,176 +1040,122 @@ static void grad_gaussians(void* arg, long lo, long hi, int tid)
             for (int x = x0; x <= x1; ++x) {
                 const double dx = x + 0.5 - o->mean2d[0], dy = y + 0.5 - o->mean2d[1];
                 const double q = quad_form(o->conic, dx, dy);
-                if (q > c->cutoff) continue;
+                const int in = counted(q, c->cutoff, i, x, y, 1);
+                int tie = 0;
+                if (bnd) {
+                    const double tau = c->tie ? tie_width(c->tie + i, dx, dy, q, NULL) : c->tie_tau;
+                    if (tau > widest) c->wide[tid] = 1;
+                    tie = fabs(q - ORC_CUTOFF) <= tau;
+                }
+                if (!in && !tie) continue;
                 const long p = (long)(y - c->y_lo) * W + x;
                 const double g = exp(-0.5 * q);
                 const double a = uw * g;
                 const double D = c->den[p];
-                double dLda = 0;
+                double dLda = 0, t[9];
                 for (int ch = 0; ch < 3; ++ch) {
                     dLda += c->G[3 * p + ch] * (o->color[ch] - c->rgb[3 * p + ch]) / D;
-                    g2[6 + ch] += c->G[3 * p + ch] * a / D;            /* dL/dc */
+                    t[6 + ch] = c->G[3 * p + ch] * a / D;                   /* dL/dc */
                 }
-                g2[5] += dLda * g;                                     /* dL/d(uw) */
+                t[5] = dLda * g;                                           /* dL/d(uw) */
                 const double dLdq = dLda * uw * (-0.5 * g);
-                g2[2] += dLdq * dx * dx;                               /* dL/dA */
-                g2[3] += dLdq * 2.0 * dx * dy;                         /* dL/dB */
-                g2[4] += dLdq * dy * dy;                               /* dL/dC */
+                t[2] = dLdq * dx * dx;                                     /* dL/dA */
+                t[3] = dLdq * 2.0 * dx * dy;                               /* dL/dB */
+                t[4] = dLdq * dy * dy;                                     /* dL/dC */
                 /* q depends on the mean through dx = px - mu */
-                g2[0] += dLdq * (-2.0) * (o->conic[0] * dx + o->conic[1] * dy);
-                g2[1] += dLdq * (-2.0) * (o->conic[1] * dx + o->conic[2] * dy);
+                t[0] = dLdq * (-2.0) * (o->conic[0] * dx + o->conic[1] * dy);
+                t[1] = dLdq * (-2.0) * (o->conic[1] * dx + o->conic[2] * dy);
+                if (in)
+                    for (int k = 0; k < 9; ++k) g2[k] += t[k];
+                if (bnd && (tie || c->mass[p] > 0)) {
+                    /* the forward's tie decisions move this pixel's C by at most amb and its D by at
+                     * most the tie mass m, so |D'| >= dlo = |D| - m.  A tie pair's own term is at
+                     * most its value at the worst such C and D; a counted pair's term moves by at
+                     * most its change between (C, D) and the worst (C', D'). */
+                    const double dlo = fabs(D) - c->mass[p];
+                    double dla = 0, cw[3];
+                    for (int ch = 0; ch < 3; ++ch) {
+                        const double Gc = fabs(c->G[3 * p + ch]), e = fabs(o->color[ch] - c->rgb[3 * p + ch]);
+                        if (tie) {
+                            dla += Gc * (e + c->amb[p]) / dlo;
+                            cw[ch] = Gc * fabs(a) / dlo;
+                        } else {
+                            dla += Gc * (c->amb[p] + e * c->mass[p] / fabs(D)) / dlo;
+                            cw[ch] = Gc * fabs(a) * c->mass[p] / (fabs(D) * dlo);
+                        }
+                    }
+                    if (!(dlo > 0)) dla = HUGE_VAL;
+                    const double sq = fabs(uw) * 0.5 * g * dla;
+                    B[5] += g * dla;
+                    B[2] += sq * dx * dx;
+                    B[3] += sq * 2.0 * fabs(dx * dy);
+                    B[4] += sq * dy * dy;
+                    B[0] += sq * 2.0 * fabs(o->conic[0] * dx + o->conic[1] * dy);
+                    B[1] += sq * 2.0 * fabs(o->conic[1] * dx + o->conic[2] * dy);
+                    for (int ch = 0; ch < 3; ++ch) B[6 + ch] += dlo > 0 ? cw[ch] : HUGE_VAL;
+                }
             }
 
         /* ---- per-Gaussian chain ---- */
-        double g_t[3] = {0, 0, 0};      /* dL/dt (camera space) */
-        double g_dir[3] = {0, 0, 0};    /* dL/d(unit direction) */
-        double g_p[3] = {0, 0, 0};      /* dL/dp (world), direct terms */
-        const double dL_duw = g2[5];
-        const double dL_du = dL_duw * o->w, dL_dw = dL_duw * o->u;
-
-        /* colour: c = max(0, Y.H + 0.5) */
-        double Y[ORC_MAX_K], dY[ORC_MAX_K][3];
-        sh_basis(S->deg, o->dir, Y, dY);
-        const double* H = S->sh + (long)i * K * 3;
-        double* gH = c->g_sh + (long)i * K * 3;
-        for (int ch = 0; ch < 3; ++ch) {
-            const double graw = (o->raw[ch] + 0.5 > 0) ? g2[6 + ch] : 0.0;
-            for (int k = 0; k < K; ++k) {
-                gH[3 * k + ch] = graw * Y[k];
-                for (int e = 0; e < 3; ++e) g_dir[e] += graw * H[3 * k + ch] * dY[k][e];
-            }
+        ochain ch;
+        chain_one(c, i, g2, &ch);
+        put(c->g_means + 3 * i, ch.means, 3, 0);
+        put(c->g_log_scales + 3 * i, ch.log_scales, 3, 0);
+        put(c->g_quats + 4 * i, ch.quats, 4, 0);
+        put(c->g_sh + (long)i * K * 3, ch.sh, K * 3, 0);
+        put(c->g_opac + (long)i * nop, ch.opac, nop, 0);
+        c->g_lc_v[i] = ch.lc_v;
+        gsig += ch.sig;
+        gbeta += ch.beta;
+        if (!bnd) continue;
+        memcpy(c->b_g2d + 9 * i, B, sizeof B);
+        memset(c->b_means + 3 * i, 0, 3 * sizeof(double));
+        memset(c->b_log_scales + 3 * i, 0, 3 * sizeof(double));
+        memset(c->b_quats + 4 * i, 0, 4 * sizeof(double));
+        memset(c->b_sh + (long)i * K * 3, 0, (size_t)K * 3 * sizeof(double));
+        memset(c->b_opac + (long)i * nop, 0, (size_t)nop * sizeof(double));
+        c->b_lc_v[i] = 0;
+        for (int k = 0; k < 9; ++k) {
+            if (!(B[k] > 0)) continue;
+            double e[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            e[k] = 1.0;
+            ochain ck;
+            chain_one(c, i, e, &ck);
+            put(c->b_means + 3 * i, ck.means, 3, B[k]);
+            put(c->b_log_scales + 3 * i, ck.log_scales, 3, B[k]);
+            put(c->b_quats + 4 * i, ck.quats, 4, B[k]);
+            put(c->b_sh + (long)i * K * 3, ck.sh, K * 3, B[k]);
+            put(c->b_opac + (long)i * nop, ck.opac, nop, B[k]);
+            c->b_lc_v[i] += fabs(ck.lc_v) * B[k];
+            bsig += fabs(ck.sig) * B[k];
+            bbeta += fabs(ck.beta) * B[k];
         }
-        /* opacity */
-        if (S->vd) {
-            const double* Ha = S->opac + (long)i * K;
-            double* gHa = c->g_opac + (long)i * K;
-            for (int k = 0; k < K; ++k) {
-                gHa[k] = dL_du * Y[k];
-                for (int e = 0; e < 3; ++e) g_dir[e] += dL_du * Ha[k] * dY[k][e];
-            }
-        } else {
-            c->g_opac[i] = dL_du * o->u * (1.0 - o->u);
-        }
-        /* depth weight; d = t_z */
-        const double d = o->d;
-        double dL_dd = 0;
-        c->g_lc_v[i] = 0;
-        if (wt->kind == 1) {
-            const double db = pow(d, wt->beta);
-            gsig += dL_dw * (-db) * o->w;
-            gbeta += dL_dw * (-wt->sigma * db * log(d)) * o->w;
-            dL_dd = dL_dw * (-wt->sigma * wt->beta * pow(d, wt->beta - 1.0)) * o->w;
-        } else if (wt->kind == 2) {
-            const double lin = 1.0 - d / wt->sigma;
-            if (lin > 0) {
-                const double v = S->lc_v[i];
-                c->g_lc_v[i] = dL_dw * lin;
-                gsig += dL_dw * v * d / (wt->sigma * wt->sigma);
-                dL_dd = dL_dw * (-v / wt->sigma);
-            }
-        }
-        g_t[2] += dL_dd;
-        /* direction: dir = v / |v| */
-        {
-            double dd = 0;
-            for (int e = 0; e < 3; ++e) dd += o->dir[e] * g_dir[e];
-            for (int e = 0; e < 3; ++e) g_p[e] += (g_dir[e] - o->dir[e] * dd) / o->vnorm;
-        }
-        /* projected mean */
-        const double tx = o->t[0], ty = o->t[1], tz = o->t[2];
-        g_t[0] += g2[0] * cam->fx / tz;
-        g_t[1] += g2[1] * cam->fy / tz;
-        g_t[2] += -g2[0] * cam->fx * tx / (tz * tz) - g2[1] * cam->fy * ty / (tz * tz);
-
-        /* conic = Sigma_2D^{-1}:  dL/dSigma = -K Gk K with Gk the symmetric
-         * matrix gradient [[gA, gB/2], [gB/2, gC]] */
-        const double Kc[4] = {o->conic[0], o->conic[1], o->conic[1], o->conic[2]};
-        const double Gk[4] = {g2[2], 0.5 * g2[3], 0.5 * g2[3], g2[4]};
-        double t1[4], GS[4];
-        mat_mul(Kc, Gk, t1, 2, 2, 2);
-        mat_mul(t1, Kc, GS, 2, 2, 2);
-        for (int e = 0; e < 4; ++e) GS[e] = -GS[e];
-        /* Sigma_2D = T Sigma_3D T^t + 0.3 I,  T = J W */
-        const double tanx = 0.5 * cam->W / cam->fx, tany = 0.5 * cam->H / cam->fy;
-        const double limx = ORC_CLAMP * tanx, limy = ORC_CLAMP * tany;
-        const double rx = clampd(tx / tz, -limx, limx), ry = clampd(ty / tz, -limy, limy);
-        const int freex = (tx / tz >= -limx && tx / tz <= limx);
-        const int freey = (ty / tz >= -limy && ty / tz <= limy);
-        const double J[6] = {cam->fx / tz, 0, -cam->fx * rx / tz, 0, cam->fy / tz, -cam->fy * ry / tz};
-        double T[6], Tt[6], Sig3[9], M[9], Mt[9], Rg[9];
-        mat_mul(J, cam->R, T, 2, 3, 3);
-        transpose(T, Tt, 2, 3);
-        const double* qr = S->quats + 4 * i;
-        const double qn = sqrt(qr[0] * qr[0] + qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]);
-        const double q[4] = {qr[0] / qn, qr[1] / qn, qr[2] / qn, qr[3] / qn};
-        quat_to_rot(q, Rg);
-        double s[3];
-        for (int k = 0; k < 3; ++k) s[k] = exp(S->log_scales[3 * i + k]);
-        for (int r = 0; r < 3; ++r)
-            for (int cc = 0; cc < 3; ++cc) M[3 * r + cc] = Rg[3 * r + cc] * s[cc];
-        transpose(M, Mt, 3, 3);
-        mat_mul(M, Mt, Sig3, 3, 3, 3);
-        /* dL/dSigma_3D = T^t GS T ;  dL/dT = 2 GS T Sigma_3D */
-        double t2[6], GSig3[9], GT[6], t3[6];
-        mat_mul(GS, T, t2, 2, 2, 3);
-        mat_mul(Tt, t2, GSig3, 3, 2, 3);
-        mat_mul(GS, T, t3, 2, 2, 3);
-        mat_mul(t3, Sig3, GT, 2, 3, 3);
-        for (int e = 0; e < 6; ++e) GT[e] *= 2.0;
-        /* dL/dJ = dL/dT W^t */
-        double Wt[9], GJ[6];
-        transpose(cam->R, Wt, 3, 3);
-        mat_mul(GT, Wt, GJ, 2, 3, 3);
-        /* J00 = fx/tz, J02 = -fx rx/tz, J11 = fy/tz, J12 = -fy ry/tz,
-         * rx = clamp(tx/tz) (moves with t only when not clamped) */
-        g_t[2] += GJ[0] * (-cam->fx / (tz * tz)) + GJ[4] * (-cam->fy / (tz * tz));
-        g_t[2] += GJ[2] * (cam->fx * rx / (tz * tz)) + GJ[5] * (cam->fy * ry / (tz * tz));
-        if (freex) {
-            g_t[0] += GJ[2] * (-cam->fx / (tz * tz));
-            g_t[2] += GJ[2] * (-cam->fx / tz) * (-tx / (tz * tz));
-        }
-        if (freey) {
-            g_t[1] += GJ[5] * (-cam->fy / (tz * tz));
-            g_t[2] += GJ[5] * (-cam->fy / tz) * (-ty / (tz * tz));
-        }
-        /* t = W p + T  =>  dL/dp += W^t dL/dt */
-        for (int e = 0; e < 3; ++e)
-            g_p[e] += cam->R[e] * g_t[0] + cam->R[3 + e] * g_t[1] + cam->R[6 + e] * g_t[2];
-        for (int e = 0; e < 3; ++e) c->g_means[3 * i + e] = g_p[e];
-
-        /* Sigma_3D = M M^t, M = R diag(s):  dL/dM = 2 dL/dSigma_3D M */
-        double GM[9];
-        mat_mul(GSig3, M, GM, 3, 3, 3);
-        for (int e = 0; e < 9; ++e) GM[e] *= 2.0;
-        double gs[3] = {0, 0, 0}, GR[9];
-        for (int r = 0; r < 3; ++r)
-            for (int cc = 0; cc < 3; ++cc) {
-                GR[3 * r + cc] = GM[3 * r + cc] * s[cc];
-                gs[cc] += GM[3 * r + cc] * Rg[3 * r + cc];
-            }
-        for (int k = 0; k < 3; ++k) c->g_log_scales[3 * i + k] = gs[k] * s[k];
-        /* rotation from the normalised quaternion */
-        double dR[9][4], gqn[4] = {0, 0, 0, 0};
-        quat_to_rot_grad(q, dR);
-        for (int e = 0; e < 9; ++e)
-            for (int k = 0; k < 4; ++k) gqn[k] += GR[e] * dR[e][k];
-        double dot = 0;
-        for (int k = 0; k < 4; ++k) dot += gqn[k] * q[k];
-        for (int k = 0; k < 4; ++k) c->g_quats[4 * i + k] = (gqn[k] - q[k] * dot) / qn;
     }
     c->gw[tid][0] = gsig;
     c->gw[tid][1] = gbeta;
+    c->bw[tid][0] = bsig;
+    c->bw[tid][1] = bbeta;
 }
 
+/*
+ * tie_tau: 0 for no tie bounds; > 0 for the window |q - 9| <= tie_tau for
+ * every pair; < 0 for each pair's window from the FP32 rounding model.  With
+ * tie bounds, b_* receive the bounds of the same shapes as g_* (b_wpar[6]).
+ * Returns 3 if a model window exceeded ORC_TIE_CAP.
+ */
 int wsro_grad(long n, int deg, int vd, const double* means, const double* log_scales,
               const double* quats, const double* sh, const double* opac, const double* lc_v,
               const double* cam16, int W, int H, double znear, int wkind, const double* wpar,
               int nthreads, int y_lo, int y_hi, const double* grad_rgb,
               double* g_means, double* g_log_scales, double* g_quats, double* g_sh,
-              double* g_opac, double* g_lc_v, double* g_wpar, double* g2d, double cutoff)
+              double* g_opac, double* g_lc_v, double* g_wpar, double* g2d, double cutoff,
+              double tie_tau, double* b_means, double* b_log_scales, double* b_quats, double* b_sh,
+              double* b_opac, double* b_lc_v, double* b_wpar, double* b_g2d)
 {
     if (deg < 0 || deg > 3 || n < 0 || W <= 0 || H <= 0) return 1;
     if (y_lo < 0 || y_hi > H || y_lo >= y_hi) return 1;
+    const int bnd = tie_tau != 0.0;
+    if (bnd && !(b_means && b_log_scales && b_quats && b_sh && b_opac && b_lc_v && b_wpar && b_g2d)) return 1;
     oscene S; ocam cam; owt wt;
     fill_scene(&S, n, deg, vd, means, log_scales, quats, sh, opac, lc_v);
     make_cam(&cam, cam16, W, H, znear);
@@ -792,40 +1163,88 @@ int wsro_grad(long n, int deg, int vd, const double* means, const double* log_sc
     const long np = (long)W * (y_hi - y_lo);
     double* rgb = (double*)malloc(np * 3 * sizeof(double));
     double* den = (double*)malloc(np * sizeof(double));
-    if (!rgb || !den) { free(rgb); free(den); return 2; }
+    double* amb = bnd ? (double*)malloc(np * sizeof(double)) : NULL;
+    double* mass = bnd ? (double*)malloc(np * sizeof(double)) : NULL;
+    if (!rgb || !den || (bnd && (!amb || !mass))) { free(rgb); free(den); free(amb); free(mass); return 2; }
     int rc = wsro_render(n, deg, vd, means, log_scales, quats, sh, opac, lc_v, cam16, W, H, znear,
-                         wkind, wpar, nthreads, y_lo, y_hi, rgb, den, NULL, 0.0, NULL, cutoff);
-    if (rc) { free(rgb); free(den); return rc; }
+                         wkind, wpar, nthreads, y_lo, y_hi, rgb, den, amb, tie_tau, NULL, cutoff, mass);
+    if (rc) { free(rgb); free(den); free(amb); free(mass); return rc; }
     oproj* P = project_all(&S, &cam, &wt);
-    if (!P) { free(rgb); free(den); return 2; }
     grad_ctx* c = (grad_ctx*)calloc(1, sizeof(grad_ctx));
+    otie* tm = (bnd && tie_tau < 0 && P) ? tie_all(&S, &cam, P) : NULL;
+    if (!P || !c || (bnd && tie_tau < 0 && !tm)) {
+        free(P); free(c); free(tm); free(rgb); free(den); free(amb); free(mass);
+        return 2;
+    }
     c->S = &S; c->P = P; c->cam = &cam; c->wt = &wt; c->y_lo = y_lo; c->y_hi = y_hi; c->cutoff = cutoff;
     c->rgb = rgb; c->den = den; c->G = grad_rgb;
     c->g_means = g_means; c->g_log_scales = g_log_scales; c->g_quats = g_quats; c->g_sh = g_sh;
     c->g_opac = g_opac; c->g_lc_v = g_lc_v; c->g2d = g2d;
-    if (S.vd) memset(g_opac, 0, (size_t)n * S.K * sizeof(double));
+    if (bnd) {
+        c->tie = tm; c->tie_tau = tie_tau; c->amb = amb; c->mass = mass;
+        c->b_means = b_means; c->b_log_scales = b_log_scales; c->b_quats = b_quats; c->b_sh = b_sh;
+        c->b_opac = b_opac; c->b_lc_v = b_lc_v; c->b_g2d = b_g2d;
+    }
     run_parallel(grad_gaussians, c, n, nthreads);
     for (int k = 0; k < 6; ++k) g_wpar[k] = 0;
     for (int t = 0; t < 256; ++t) { g_wpar[0] += c->gw[t][0]; g_wpar[1] += c->gw[t][1]; }
+    if (bnd) {
+        for (int k = 0; k < 6; ++k) b_wpar[k] = 0;
+        for (int t = 0; t < 256; ++t) {
+            b_wpar[0] += c->bw[t][0];
+            b_wpar[1] += c->bw[t][1];
+            if (c->wide[t]) rc = 3;
+        }
+    }
     /* background terms of Eq. 7 */
     for (long p = 0; p < np; ++p) {
         const double D = den[p];
         for (int ch = 0; ch < 3; ++ch) {
             g_wpar[2] += grad_rgb[3 * p + ch] * (wt.c_bg[ch] - rgb[3 * p + ch]) / D;
             g_wpar[3 + ch] += grad_rgb[3 * p + ch] * wt.w_bg / D;
+            if (bnd && mass[p] > 0) {
+                const double Gc = fabs(grad_rgb[3 * p + ch]), dlo = fabs(D) - mass[p];
+                b_wpar[2] += dlo > 0 ? Gc * (amb[p] + fabs(wt.c_bg[ch] - rgb[3 * p + ch]) * mass[p] / fabs(D)) / dlo
+                                     : HUGE_VAL;
+                b_wpar[3 + ch] += dlo > 0 ? Gc * fabs(wt.w_bg) * mass[p] / (fabs(D) * dlo) : HUGE_VAL;
+            }
         }
     }
-    /* invisible Gaussians: zero gradients */
-    for (long i = 0; i < n; ++i)
-        if (!P[i].visible) {
-            memset(g_means + 3 * i, 0, 3 * sizeof(double));
-            memset(g_log_scales + 3 * i, 0, 3 * sizeof(double));
-            memset(g_quats + 4 * i, 0, 4 * sizeof(double));
-            memset(g_sh + (long)i * S.K * 3, 0, (size_t)S.K * 3 * sizeof(double));
-            if (S.vd) memset(g_opac + (long)i * S.K, 0, (size_t)S.K * sizeof(double));
-            else g_opac[i] = 0;
-            g_lc_v[i] = 0;
+    free(c); free(P); free(tm); free(rgb); free(den); free(amb); free(mass);
+    return rc;
+}
+
+/*
+ * The tie window of listed pairs (test infrastructure): for each k, the
+ * Gaussian idx[k] at the pixel position (xy[2k], xy[2k+1]) (pixel units, not
+ * a pixel index: any point).  Outputs: q[k] (exact), tau[k] (the window,
+ * tie_width) and terms[6k .. 6k+5] (its parts: mean, rows, sums, record,
+ * threshold, evaluation).
+ */
+int wsro_tie_width(long n, int deg, int vd, const double* means, const double* log_scales,
+                   const double* quats, const double* sh, const double* opac, const double* lc_v,
+                   const double* cam16, int W, int H, double znear, int wkind, const double* wpar,
+                   long npts, const long* idx, const double* xy, double* q, double* tau, double* terms)
+{
+    if (deg < 0 || deg > 3 || n < 0) return 1;
+    oscene S; ocam cam; owt wt;
+    fill_scene(&S, n, deg, vd, means, log_scales, quats, sh, opac, lc_v);
+    make_cam(&cam, cam16, W, H, znear);
+    make_wt(&wt, wkind, wpar);
+    for (long k = 0; k < npts; ++k) {
+        if (idx[k] < 0 || idx[k] >= n) return 1;
+        oproj o;
+        otie m;
+        project_one(&S, idx[k], &cam, &wt, &o);
+        tie_model(&S, idx[k], &cam, &o, &m);
+        if (!o.visible) {
+            q[k] = tau[k] = -1.0;
+            for (int j = 0; j < 6; ++j) terms[6 * k + j] = -1.0;
+            continue;
         }
-    free(c); free(P); free(rgb); free(den);
+        const double dx = xy[2 * k] - o.mean2d[0], dy = xy[2 * k + 1] - o.mean2d[1];
+        q[k] = quad_form(o.conic, dx, dy);
+        tau[k] = tie_width(&m, dx, dy, q[k], terms + 6 * k);
+    }
     return 0;
 }

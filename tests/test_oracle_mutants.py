@@ -33,8 +33,9 @@ MUTANTS = {
     "y_clamped_with_x_limit": ("const double ryc = clampd(ty / tz, -ORC_CLAMP * tany, ORC_CLAMP * tany);",
                                "const double ryc = clampd(ty / tz, -ORC_CLAMP * tanx, ORC_CLAMP * tanx);"),
     "no_near_plane": ("if (!(o->t[2] > cam->znear))", "if (!(o->t[2] > 0.0))"),
-    "scale_not_exponentiated": ("for (int k = 0; k < 3; ++k) s[k] = exp(S->log_scales[3 * i + k]);\n    for (int r",
-                                "for (int k = 0; k < 3; ++k) s[k] = S->log_scales[3 * i + k];\n    for (int r"),
+    "scale_not_exponentiated": (
+        "s[k] = exp(S->log_scales[3 * i + k]);\n    for (int r = 0; r < 3; ++r)\n        for (int c = 0; c < 3; ++c) M",
+        "s[k] = S->log_scales[3 * i + k];\n    for (int r = 0; r < 3; ++r)\n        for (int c = 0; c < 3; ++c) M"),
     # colour and opacity (Eqs. 4, 11)
     "no_condon_shortley_phase": ("pref = Kl * sqrt(2.0) * ipow(-1.0, am);", "pref = Kl * sqrt(2.0);"),
     "no_colour_offset": ("o->color[ch] = r + 0.5 > 0 ? r + 0.5 : 0.0;", "o->color[ch] = r > 0 ? r : 0.0;"),
@@ -52,18 +53,18 @@ MUTANTS = {
     # gradient
     "beta_derivative_without_log": ("gbeta += dL_dw * (-wt->sigma * db * log(d)) * o->w;",
                                     "gbeta += dL_dw * (-wt->sigma * db) * o->w;"),
-    "conic_offdiagonal_counted_once": ("g2[3] += dLdq * 2.0 * dx * dy;", "g2[3] += dLdq * dx * dy;"),
-    "mean_gradient_sign": ("g2[1] += dLdq * (-2.0) * (o->conic[1] * dx + o->conic[2] * dy);",
-                           "g2[1] += dLdq * (2.0) * (o->conic[1] * dx + o->conic[2] * dy);"),
+    "conic_offdiagonal_counted_once": ("t[3] = dLdq * 2.0 * dx * dy;", "t[3] = dLdq * dx * dy;"),
+    "mean_gradient_sign": ("t[1] = dLdq * (-2.0) * (o->conic[1] * dx + o->conic[2] * dy);",
+                           "t[1] = dLdq * (2.0) * (o->conic[1] * dx + o->conic[2] * dy);"),
     "projection_depth_term_sign": (
         "g_t[2] += -g2[0] * cam->fx * tx / (tz * tz) - g2[1] * cam->fy * ty / (tz * tz);",
         "g_t[2] += -g2[0] * cam->fx * tx / (tz * tz) + g2[1] * cam->fy * ty / (tz * tz);"),
     "background_weight_gradient_sign": ("g_wpar[2] += grad_rgb[3 * p + ch] * (wt.c_bg[ch] - rgb[3 * p + ch]) / D;",
                                         "g_wpar[2] += grad_rgb[3 * p + ch] * (rgb[3 * p + ch] - wt.c_bg[ch]) / D;"),
     "covariance_chain_factor": ("for (int e = 0; e < 6; ++e) GT[e] *= 2.0;", "for (int e = 0; e < 6; ++e) GT[e] *= 1.0;"),
-    "sigmoid_derivative": ("c->g_opac[i] = dL_du * o->u * (1.0 - o->u);", "c->g_opac[i] = dL_du * o->u;"),
-    "quaternion_not_projected": ("c->g_quats[4 * i + k] = (gqn[k] - q[k] * dot) / qn;",
-                                 "c->g_quats[4 * i + k] = gqn[k] / qn;"),
+    "sigmoid_derivative": ("out->opac[0] = dL_du * o->u * (1.0 - o->u);", "out->opac[0] = dL_du * o->u;"),
+    "quaternion_not_projected": ("out->quats[k] = (gqn[k] - q[k] * dot) / qn;",
+                                 "out->quats[k] = gqn[k] / qn;"),
     "legendre_normalisation_inverted": ("const double norm = sqrt(fact(l - am) / fact(l + am));",
                                         "const double norm = sqrt(fact(l + am) / fact(l - am));"),
     "sh_index_order": ("const int idx = l * l + l + m;", "const int idx = l * l + l - m;"),
@@ -77,8 +78,8 @@ MUTANTS = {
         "f[k] = -(cam->R[k] * cam->T[0] + cam->R[3 + k] * cam->T[1] + cam->R[6 + k] * cam->T[2]);",
         "f[k] = -(cam->R[3 * k] * cam->T[0] + cam->R[3 * k + 1] * cam->T[1] + cam->R[3 * k + 2] * cam->T[2]);"),
     "principal_point_swapped": ("o->mean2d[0] = cam->fx * tx / tz + cam->cx;", "o->mean2d[0] = cam->fx * tx / tz + cam->cy;"),
-    "colour_gradient_without_opacity": ("g2[6 + ch] += c->G[3 * p + ch] * a / D;            /* dL/dc */",
-                                        "g2[6 + ch] += c->G[3 * p + ch] * g / D;            /* dL/dc */"),
+    "colour_gradient_without_opacity": ("t[6 + ch] = c->G[3 * p + ch] * a / D;                   /* dL/dc */",
+                                        "t[6 + ch] = c->G[3 * p + ch] * g / D;                   /* dL/dc */"),
     "exp_depth_derivative_power": ("dL_dd = dL_dw * (-wt->sigma * wt->beta * pow(d, wt->beta - 1.0)) * o->w;",
                                    "dL_dd = dL_dw * (-wt->sigma * wt->beta * pow(d, wt->beta)) * o->w;"),
     "opacity_sh_gradient_basis": ("gHa[k] = dL_du * Y[k];", "gHa[k] = dL_du;"),
@@ -93,6 +94,26 @@ MUTANTS = {
                                    "if (fabs(dx) > 0.5 * o->rx || fabs(dy) > 0.5 * o->ry) continue;"),
     "background_colour_gradient": ("g_wpar[3 + ch] += grad_rgb[3 * p + ch] * wt.w_bg / D;",
                                    "g_wpar[3 + ch] += grad_rgb[3 * p + ch] / D;"),
+    # cutoff ties: the FP32 rounding model behind the windows, and the bounds built on them
+    "tie_model_without_the_mean": ("const double t_mean = 2.0 * (fabs(vx) * m->ex + fabs(vy) * m->ey);",
+                                   "const double t_mean = 0.0;"),
+    "tie_model_without_the_rows": ("const double t_rows = 2.0 * sqrt(tv2 * ev2);", "const double t_rows = 0.0;"),
+    "tie_model_without_the_evaluation": ("return 2.0 * (t_mean + t_rows + t_sums + t_rec + t_cut + t_eval);",
+                                         "return 2.0 * (t_mean + t_rows + t_sums + t_rec + t_cut);"),
+    "tie_window_a_twentieth": ("return 2.0 * (t_mean + t_rows + t_sums + t_rec + t_cut + t_eval);",
+                               "return 0.1 * (t_mean + t_rows + t_sums + t_rec + t_cut + t_eval);"),
+    "tie_allowance_over_the_unmoved_denominator": (
+        "if (amb[p] > 0) amb[p] = dlo > 0 ? amb[p] / dlo : HUGE_VAL;",
+        "if (amb[p] > 0) amb[p] = amb[p] / fabs(out_den[p]);"),
+    "tie_bound_ignores_the_colour_shift": ("dla += Gc * (c->amb[p] + e * c->mass[p] / fabs(D)) / dlo;",
+                                           "dla += Gc * (e * c->mass[p] / fabs(D)) / dlo;"),
+    "tie_bound_chain_with_signs": ("out[k] = s > 0 ? out[k] + s * fabs(x[k]) : x[k];",
+                                   "out[k] = s > 0 ? out[k] + s * x[k] : x[k];"),
+    "tie_bound_background_weight_ignores_the_colour_shift": (
+        "b_wpar[2] += dlo > 0 ? Gc * (amb[p] + fabs(wt.c_bg[ch] - rgb[3 * p + ch]) * mass[p] / fabs(D)) / dlo",
+        "b_wpar[2] += dlo > 0 ? Gc * (fabs(wt.c_bg[ch] - rgb[3 * p + ch]) * mass[p] / fabs(D)) / dlo"),
+    "tie_bound_conic_terms_halved": ("const double sq = fabs(uw) * 0.5 * g * dla;",
+                                     "const double sq = fabs(uw) * 0.25 * g * dla;"),
 }
 
 

@@ -425,6 +425,32 @@ def test_gradient_2d_records_match_finite_differences_of_projection_outputs():
         assert abs(fd - an["g2d"][i, 5]) < 1e-6 * max(1.0, abs(fd))
 
 
+def test_lc_weight_at_zero_v_keeps_its_gradient():
+    """LC (Eq. 10) with v_i = 0 exactly, in front of sigma: w_i = 0, so the
+    Gaussian adds nothing to Eq. 7, but dL/dv_i = max(0, 1 - d/sigma) dL/dw is
+    not zero; the analytic gradient equals central finite differences in v_i
+    (C is linear in v_i around 0 through a_i = u w g)."""
+    sc = tiny_scene(51, 1, True, n=12)
+    cam = tiny_cam(32, 24)
+    w = WEIGHTS[2]
+    P = oracle.project(sc, cam, w)
+    zero = np.nonzero(P["visible"] & (P["depth"] < w.sigma))[0][:3]
+    assert len(zero) == 3
+    sc.lc_v[zero] = 0.0
+    R = np.random.default_rng(4).normal(size=(cam.height, cam.width, 3))
+    an = oracle.grad(sc, cam, w, R)
+    for i in zero:
+        h = 1e-6
+        sc.lc_v[i] = h
+        lp, _ = _loss_and_pairs(sc, cam, w, R)
+        sc.lc_v[i] = -h
+        lm, _ = _loss_and_pairs(sc, cam, w, R)
+        sc.lc_v[i] = 0.0
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd) > 1e-6, fd
+        assert abs(fd - an["lc_v"][i]) < 1e-6 * max(1.0, abs(fd)), (i, fd, an["lc_v"][i])
+
+
 def test_row_window_equals_rows_of_the_full_image():
     """A window of rows of the same camera (the same Jacobian clamp) is the
     corresponding rows of the full image, and its gradient is the gradient
@@ -459,3 +485,128 @@ def test_tie_bound_covers_a_shifted_cutoff():
                 moved = oracle.render(sc, cam, w, cutoff=cut)
                 d = np.abs(moved["rgb"] - base["rgb"]).max(axis=2)
                 assert np.all(d <= base["amb"] + 1e-12), (w.kind, tau, cut)
+
+
+# --------------------------------------------------------------------------
+# cutoff ties: the bounds used when an FP32 renderer is compared with Eq. 7
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("wi,deg,vd", [(0, 0, False), (1, 3, True), (2, 1, False), (2, 3, True)])
+def test_tie_bounds_cover_any_decision_of_the_ties(wi, deg, vd):
+    """Pairs within tau of q = 9 decided at random (a seeded hash per pair),
+    independently in the forward sums and in the gradient's sums: every pixel
+    stays within its allowance, and every gradient entry (each parameter
+    tensor, sigma, beta, w_B, c_B, the 2D records) within its tie bound."""
+    sc = tiny_scene(3 + wi, deg, vd, n=300, ls=-2.6)
+    cam = tiny_cam(64, 48)
+    w = WEIGHTS[wi]
+    tau = 0.05
+    G = np.random.default_rng(1 + wi).normal(size=(cam.height, cam.width, 3))
+    base = oracle.render(sc, cam, w, amb_tau=tau)
+    ref = oracle.grad(sc, cam, w, G, tie=tau)
+    assert (base["amb"] > 0).sum() > 50
+    for sf, sg in [(1, 2), (3, 0), (0, 4), (5, 5), (11, 13)]:
+        with oracle.tie_flips(sf, sg, tau):
+            r = oracle.render(sc, cam, w)
+            g = oracle.grad(sc, cam, w, G)
+        d = np.abs(r["rgb"] - base["rgb"]).max(axis=2)
+        assert np.all(d <= base["amb"] * (1 + 1e-9) + 1e-13), (sf, (d - base["amb"]).max())
+        for k in ("means", "log_scales", "quats", "sh", "opacity", "lc_v", "wpar", "g2d"):
+            ex = np.abs(g[k] - ref[k]) - ref["tie"][k] * (1 + 1e-9)
+            assert ex.max() <= 1e-12 * max(1.0, np.abs(ref[k]).max()), (sf, sg, k, ex.max())
+
+
+def test_tie_bound_is_zero_without_ties():
+    """A window that holds no pair gives no allowance and no gradient bound."""
+    sc = tiny_scene(62, 2, True, n=40)
+    cam = tiny_cam()
+    w = WEIGHTS[1]
+    G = np.random.default_rng(3).normal(size=(cam.height, cam.width, 3))
+    r = oracle.render(sc, cam, w, amb_tau=1e-13)
+    g = oracle.grad(sc, cam, w, G, tie=1e-13)
+    assert np.all(r["amb"] == 0) and np.all(r["tie_mass"] == 0)
+    for k, b in g["tie"].items():
+        assert np.all(b == 0), k
+
+
+def _ellipse_pixels(P, idx_all, nang):
+    """Pixel centres nearest to nang points on each Gaussian's q = 9 ellipse."""
+    a, b, c = (P["cov2d"][idx_all, k] for k in range(3))
+    l00 = np.sqrt(a)
+    l10 = b / l00
+    l11 = np.sqrt(c - l10 * l10)
+    th = np.linspace(0.0, 2.0 * np.pi, nang, endpoint=False)
+    ct, st = np.cos(th)[None, :], np.sin(th)[None, :]
+    dx = 3.0 * l00[:, None] * ct
+    dy = 3.0 * (l10[:, None] * ct + l11[:, None] * st)
+    x = np.floor(P["mean2d"][idx_all, 0][:, None] + dx) + 0.5
+    y = np.floor(P["mean2d"][idx_all, 1][:, None] + dy) + 0.5
+    return np.repeat(idx_all, nang), np.stack([x.reshape(-1), y.reshape(-1)], axis=1)
+
+
+def _restated_ratios(sc, cam, w, tile, nang=12):
+    """Each rounding source of the FP32 test in isolation, against the part
+    of the window that bounds it, and the whole test against the window."""
+    from tests import fp32_restatement as R32
+    P = oracle.project(sc, cam, w)
+    vis32, rec, rows = R32.records(sc, cam)
+    vis = np.nonzero(P["visible"] & vis32)[0]
+    idx, xy = _ellipse_pixels(P, vis, nang)
+    t = oracle.tie_width(sc, cam, w, idx, xy)
+    T = dict(zip(oracle.TIE_TERMS, t["terms"].T))
+    assert np.all(t["tau"] > 0) and np.allclose(t["terms"].sum(1), t["tau"], rtol=1e-12)
+    px, py = xy[:, 0], xy[:, 1]
+    q = t["q"]
+    # the mean alone: the exact conic at the float32 mean
+    mu = rec[idx, :2].astype(np.float64)
+    A, B, C = (P["conic"][idx, k] for k in range(3))
+    dxm, dym = px - mu[:, 0], py - mu[:, 1]
+    q_mean = A * dxm * dxm + 2 * B * dxm * dym + C * dym * dym
+    # the rows alone: Sigma = T T^t + 0.3 I formed exactly from the float32 rows, at the exact mean
+    r = rows[idx].astype(np.float64)
+    a = (r[:, :3] ** 2).sum(1) + 0.3
+    c = (r[:, 3:] ** 2).sum(1) + 0.3
+    b = (r[:, :3] * r[:, 3:]).sum(1)
+    dx, dy = px - P["mean2d"][idx, 0], py - P["mean2d"][idx, 1]
+    q_rows = (c * dx * dx - 2 * b * dx * dy + a * dy * dy) / (a * c - b * b)
+    # the rest of the record (sums, qs/qw/qd, threshold): the float32 record's form at the exact mean
+    rec_exact_mu = rec[idx].astype(np.float64)
+    rec_exact_mu[:, :2] = P["mean2d"][idx]
+    q_form = R32.q_record(rec_exact_mu, px, py)
+    # the evaluation alone: the float32 test against the same record evaluated exactly
+    q_eval = R32.q_at(rec[idx], px, py, tile)
+    q_rec = R32.q_record(rec[idx].astype(np.float64), px, py)
+    with np.errstate(divide="ignore", invalid="ignore"):      # a zero term gives inf (the check fails)
+        return dict(mean=np.abs(q_mean - q) / T["mean"],
+                    rows=np.abs(q_rows - q) / T["rows"],
+                    record=np.abs(q_form - q_rows) / (T["sums"] + T["record"] + T["threshold"]),
+                    evaluation=np.abs(q_eval - q_rec) / T["evaluation"],
+                    total=np.abs(q_eval - q) / t["tau"])
+
+
+def test_tie_model_covers_an_fp32_restatement():
+    """The FP32 rounding model behind the tie windows against a float32
+    restatement of the record and the per-pixel test (every operation
+    rounded to float32), at pixel centres next to each Gaussian's q = 9
+    ellipse: each rounding source alone (the mean; the rows of T; the sums,
+    qs, qw, qd and the threshold; the evaluation at the pixel) stays within
+    the part of the window that bounds it, and the whole test within the
+    window, on scenes with Gaussians inside the near plane, beyond the
+    Jacobian clamp and close to the camera, a slice of the 1M-Gaussian 1080p
+    workload, and needles (some formed in FP64).  The window is not vacuous:
+    the worst rounding seen reaches a twentieth of it."""
+    worst = 0.0
+    cases = [(tiny_scene(3, 0, False, n=400, ls=-2.6), tiny_cam(64, 48), WEIGHTS[0], 16),
+             (tiny_scene(4, 3, True, n=400, ls=-2.6), tiny_cam(64, 48), WEIGHTS[1], 32)]
+    scene, cams, w3, _ = ws.workload(3)
+    cases.append((scene.subset(np.arange(6000)), cams[0].rounded(), w3, 16))
+    nd = ws.random_scene(2000, 5, sh_degree=0, vd_opacity=False, clusters=0, box=1.0, log_scale_mu=-3.0,
+                         log_scale_sd=0.3)
+    nd.log_scales[:, 0] = -0.5
+    cases.append((nd, ws.look_at((0.3, 0.2, -3.0), width=320, height=240).rounded(), ws.default_weight(ws.DIR), 16))
+    for sc, cam, w, tile in cases:
+        ratios = _restated_ratios(sc, cam, w, tile)
+        for k, v in ratios.items():
+            assert np.all(np.isfinite(v)) and v.max() <= 1.0, (k, v.max())
+        worst = max(worst, float(ratios["total"].max()))
+    assert worst >= 0.05, worst
