@@ -6,8 +6,7 @@ import pytest
 
 import oracle
 import wsr_scenes as ws
-from tests.gpu_util import (AMB_TAU, FWD_TOL, GRAD_TOL, add_envelopes, compare_image, grad_envelope, grad_excess,
-                            rel_err)
+from tests.gpu_util import TIE, GRAD_TOL, add_envelopes, assert_image_parity, grad_envelope, grad_excess, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -34,9 +33,8 @@ def test_persistent_schedule_matches_oracle_and_tile_blocks(tile):
     o = 0
     for cam in cams:
         m = cam.width * cam.height
-        ref = oracle.render(sc, cam, w, amb_tau=AMB_TAU)
-        excess, raw, n_amb = compare_image(rgb[o:o + m].reshape(cam.height, cam.width, 3), ref)
-        assert excess <= FWD_TOL, (cam.width, cam.height, excess)
+        ref = oracle.render(sc, cam, w, amb_tau=TIE)
+        assert_image_parity(rgb[o:o + m].reshape(cam.height, cam.width, 3), ref, what=(cam.width, cam.height))
         o += m
 
 

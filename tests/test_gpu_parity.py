@@ -1,17 +1,19 @@
 """CUDA path against the FP64 oracle, element by element (needs a GPU).
 
-Tolerances: forward max abs pixel error 1e-4 (plus, for pixels that hold a
-Gaussian within |q - 9| <= 0.02 of the cutoff, the oracle's bound on what
-deciding that tie the other way changes); gradients max error / max
-magnitude 1e-3 per tensor.
+Tolerances: forward max abs pixel error 1e-4 plus, for pixels holding a
+Gaussian within its FP32 rounding window of the cutoff q = 9 (the oracle's
+per-pair bound), the oracle's bound on what deciding those ties the other
+way changes; in images of 10,000 pixels or more, at most 0.1% of the pixels
+over 1e-4 before that allowance.  Gradients: max error / max magnitude 1e-3
+per tensor plus each entry's tie bound.
 """
 import numpy as np
 import pytest
 
 import oracle
 import wsr_scenes as ws
-from tests.gpu_util import (AMB_TAU, FWD_TOL, GRAD_TOL, add_envelopes, compare_image, gpu_render, grad_envelope,
-                            grad_excess, rel_err)
+from tests.gpu_util import (FWD_TOL, GRAD_TOL, TIE, add_envelopes, assert_image_parity, compare_image, gpu_render,
+                            grad_envelope, grad_excess, rel_err)
 
 pytestmark = pytest.mark.gpu
 
@@ -19,7 +21,7 @@ TILES = [(16, 16), (8, 8), (32, 8), (16, 8)]
 
 
 def _oracle(scene, cam, weight):
-    return oracle.render(scene, cam, weight, amb_tau=AMB_TAU)
+    return oracle.render(scene, cam, weight, amb_tau=TIE)
 
 
 @pytest.mark.parametrize("tile", TILES)
@@ -29,8 +31,7 @@ def test_workload1_forward_all_tiles(tile):
     cam = cams[0].rounded()
     (rgb, den), = gpu_render(scene, [cam], weight, tile=tile)
     ref = _oracle(scene, cam, weight)
-    excess, raw, n_amb = compare_image(rgb, ref)
-    assert excess <= FWD_TOL, (excess, raw, n_amb)
+    assert_image_parity(rgb, ref, what=tile)
     assert np.abs(den - ref["den"]).max() <= 1e-3 * max(1.0, np.abs(ref["den"]).max())
 
 
@@ -48,8 +49,7 @@ def test_ragged_image_each_weight(kind, deg, vd):
     ref = _oracle(sc, cam, w)
     for tile in [(16, 16), (32, 8)]:
         (rgb, _), = gpu_render(sc, [cam], w, tile=tile)
-        excess, raw, n_amb = compare_image(rgb, ref)
-        assert excess <= FWD_TOL, (tile, excess, raw, n_amb)
+        assert_image_parity(rgb, ref, what=tile)
 
 
 @pytest.mark.parametrize("kind", [ws.DIR, ws.EXP, ws.LC])
@@ -60,22 +60,19 @@ def test_workload2_full_size_forward(kind):
     cam = cams[0].rounded()
     (rgb, _), = gpu_render(scene, [cam], weight)
     ref = _oracle(scene, cam, weight)
-    excess, raw, n_amb = compare_image(rgb, ref)
-    assert excess <= FWD_TOL, (excess, raw, n_amb)
-    # ties at the cutoff are rarely decided differently: almost every pixel
-    # meets the plain tolerance without the allowance
-    n_off = int((np.abs(rgb - ref["rgb"]).max(axis=2) > FWD_TOL).sum())
-    assert n_off <= 1e-3 * cam.width * cam.height, (n_off, n_amb)
+    assert_image_parity(rgb, ref, what=kind)
 
 
 def test_workload3_full_size_forward():
-    """1M Gaussians, 64 clusters, SH degree 3, VD opacity, LC, 1920x1080."""
+    """1M Gaussians, 64 clusters, SH degree 3, VD opacity, LC, 1920x1080:
+    every pixel within 1e-4 plus its tie allowance, and at most 0.1% of the
+    2,073,600 pixels over 1e-4 before it."""
     scene, cams, weight, _ = ws.workload(3)
     cam = cams[0].rounded()
     (rgb, _), = gpu_render(scene, [cam], weight)
     ref = _oracle(scene, cam, weight)
-    excess, raw, n_amb = compare_image(rgb, ref)
-    assert excess <= FWD_TOL, (excess, raw, n_amb)
+    st = assert_image_parity(rgb, ref, what="1M x 1080p")
+    assert st["pixels"] == 1920 * 1080
 
 
 def test_multiview_uneven_sizes():
@@ -86,8 +83,7 @@ def test_multiview_uneven_sizes():
     views = gpu_render(sc, cams, w)
     for cam, (rgb, _) in zip(cams, views):
         ref = _oracle(sc, cam, w)
-        excess, raw, n_amb = compare_image(rgb, ref)
-        assert excess <= FWD_TOL, (cam.width, cam.height, excess, raw, n_amb)
+        assert_image_parity(rgb, ref, what=(cam.width, cam.height))
 
 
 def test_reduced_precision_storage_matches_oracle_on_stored_values():
@@ -99,8 +95,7 @@ def test_reduced_precision_storage_matches_oracle_on_stored_values():
     w = ws.default_weight(ws.LC)
     (rgb, _), = gpu_render(q, [cam], w, reduced=True)
     ref = _oracle(q, cam, w)
-    excess, raw, n_amb = compare_image(rgb, ref)
-    assert excess <= FWD_TOL, (excess, raw, n_amb)
+    assert_image_parity(rgb, ref, what="reduced")
 
 
 @pytest.mark.parametrize("n_views", [1, 3])
@@ -151,6 +146,7 @@ def test_gradients_match_oracle(kind, deg, vd):
     w = ws.WeightParams(kind, 0.1 if kind == ws.EXP else 4.8, 0.8, 0.6, (0.3, 0.2, 0.1))
     out, env = _grad_case(sc, cam, w)
     ref = env[1]
+    tie_w = env[2]["wpar"] - ref["wpar"]
     for k in ("means", "log_scales", "quats", "sh", "opacity"):
         e = grad_excess(out[k].cpu().numpy(), env, k)
         assert e <= GRAD_TOL, (k, e)
@@ -160,7 +156,27 @@ def test_gradients_match_oracle(kind, deg, vd):
     for k in range(6):
         if (kind == ws.DIR and k < 2) or (kind == ws.LC and k == 1):
             continue
-        assert abs(gw[k] - ref["wpar"][k]) <= GRAD_TOL * max(abs(ref["wpar"][k]), 1e-3), (k, gw[k], ref["wpar"][k])
+        assert abs(gw[k] - ref["wpar"][k]) <= GRAD_TOL * max(abs(ref["wpar"][k]), 1e-3) + tie_w[k], \
+            (k, gw[k], ref["wpar"][k], tie_w[k])
+
+
+def test_lc_weight_at_zero_v_keeps_its_gradient():
+    """LC (Eq. 10) with v_i = 0 exactly for a fifth of the Gaussians: they add
+    nothing to Eq. 7 (w_i = 0) but are not culled, since dL/dv_i =
+    max(0, 1 - d/sigma) dL/dw is not zero; every gradient tensor, lc_v's
+    entries at v_i = 0 included, against the oracle."""
+    sc = ws.random_scene(3_000, 27, sh_degree=2, vd_opacity=True, clusters=6, box=1.2,
+                         log_scale_mu=-3.2, log_scale_sd=0.5)
+    sc.lc_v[::5] = 0.0
+    cam = ws.look_at((0.2, 0.1, -3.5), width=96, height=72).rounded()
+    w = ws.WeightParams(ws.LC, 4.8, 0.8, 0.6, (0.3, 0.2, 0.1))
+    out, env = _grad_case(sc, cam, w)
+    for k in ("means", "log_scales", "quats", "sh", "opacity", "lc_v"):
+        e = grad_excess(out[k].cpu().numpy(), env, k)
+        assert e <= GRAD_TOL, (k, e)
+    g0 = out["lc_v"].cpu().numpy()[::5]
+    assert (np.abs(env[1]["lc_v"][::5]) > 0).sum() > 100
+    assert (np.abs(g0) > 0).sum() > 100
 
 
 def test_gradient_records_match_oracle():
@@ -196,17 +212,20 @@ def test_gradient_records_match_oracle():
     # dL/dSigma = -K G K, G = [[dA, dB/2], [dB/2, dC]]
     A, B, C = (P["conic"][:, k] for k in range(3))
 
-    def to_sigma(g):
+    def to_sigma(g, A, B, C, sign=-1.0):
         g = g.copy()
         dA, dB, dC = g[:, 2], 0.5 * g[:, 3], g[:, 4]
         p00, p01 = A * dA + B * dB, A * dB + B * dC
         p10, p11 = B * dA + C * dB, B * dB + C * dC
-        g[:, 2] = -(p00 * A + p01 * B)
-        g[:, 3] = -(p00 * B + p01 * C) - (p10 * A + p11 * B)
-        g[:, 4] = -(p10 * B + p11 * C)
+        g[:, 2] = sign * (p00 * A + p01 * B)
+        g[:, 3] = sign * ((p00 * B + p01 * C) + (p10 * A + p11 * B))
+        g[:, 4] = sign * (p10 * B + p11 * C)
         return g
 
-    env_s = tuple({"g2d": to_sigma(e["g2d"])} for e in env)
+    # the map is linear in g: the mid value maps as is, the tie bound through |K| . |G| . |K|
+    mid = to_sigma(env[1]["g2d"], A, B, C)
+    bound = to_sigma(env[2]["g2d"] - env[1]["g2d"], np.abs(A), np.abs(B), np.abs(C), sign=1.0)
+    env_s = ({"g2d": mid - bound}, {"g2d": mid}, {"g2d": mid + bound})
     for c, name in [((0, 2), "mean"), ((2, 5), "Sigma_2D"), ((5, 6), "uw"), ((6, 9), "color")]:
         part = tuple({"g2d": e["g2d"][:, c[0]:c[1]]} for e in env_s)
         err = grad_excess(conv[:, c[0]:c[1]], part, "g2d")
@@ -274,8 +293,7 @@ def test_single_gaussian_straddling_the_border():
     w = ws.default_weight(ws.EXP)
     (rgb, _), = gpu_render(sc, [cam], w)
     ref = _oracle(sc, cam, w)
-    excess, _, _ = compare_image(rgb, ref)
-    assert excess <= FWD_TOL
+    assert_image_parity(rgb, ref)
     assert (np.abs(rgb - 0.0).max(axis=2) > 1e-3).sum() > 20      # it does reach the image
 
 
@@ -323,8 +341,8 @@ def test_capacity_overflow_is_reported_and_recovered(persistent):
     r2.capacity = total // 3
     st2 = r2.forward(g, w.kind, wpar)
     ref = _oracle(sc, cam, w)
-    excess, _, _ = compare_image(st2.rgb.cpu().numpy().reshape(cam.height, cam.width, 3), ref)
-    assert excess <= FWD_TOL and r2.capacity >= total
+    assert_image_parity(st2.rgb.cpu().numpy().reshape(cam.height, cam.width, 3), ref)
+    assert r2.capacity >= total
 
 
 def test_autograd_function_matches_raw_backward():
@@ -378,7 +396,7 @@ def test_workload3_subset_gradients_match_fp64_finite_differences():
     of the FP64 oracle's forward, for sampled entries of every parameter
     tensor and for sigma, w_B and c_B.  An entry is skipped when the set of
     pairs with q <= 9 changes between +h and -h; the tolerance is 1e-3 of the
-    tensor's largest GPU gradient plus the oracle's tie envelope at that entry."""
+    tensor's largest GPU gradient plus the oracle's tie bound at that entry."""
     import torch
     from paper_2410_18931_gb300 import Gaussians, Renderer
     scene, cams, w, _ = ws.workload(3)
@@ -394,7 +412,7 @@ def test_workload3_subset_gradients_match_fp64_finite_differences():
     st = r.forward(g, w.kind, wpar)
     out = r.backward(g, w.kind, wpar, st, torch.from_numpy(R.reshape(-1, 3)).cuda())
     torch.cuda.synchronize()
-    lo, _, hi = grad_envelope(sc, cam, w, R.astype(np.float64))
+    lo, mid, hi = grad_envelope(sc, cam, w, R.astype(np.float64))
     Rd = R.astype(np.float64)
 
     def loss_pairs(s, wp):
@@ -407,7 +425,7 @@ def test_workload3_subset_gradients_match_fp64_finite_differences():
     steps = dict(means=1e-5, log_scales=1e-4, quats=1e-4, sh=1e-3, opacity=1e-3, lc_v=1e-3)
     for name, hstep in steps.items():
         gpu = out[name].cpu().numpy().astype(np.float64).reshape(-1)
-        slack = np.abs(np.asarray(hi[name]) - np.asarray(lo[name])).reshape(-1)
+        slack = (np.asarray(hi[name]) - np.asarray(mid[name])).reshape(-1)      # the entry's tie bound
         scale = np.abs(gpu).max()
         flat = getattr(sc, name).reshape(-1)
         for k in rng.choice(flat.size, 12, replace=False):
@@ -435,7 +453,7 @@ def test_workload3_subset_gradients_match_fp64_finite_differences():
         if pp != pm:
             continue
         fd = (lp - lm) / (2 * h)
-        tie = abs(hi["wpar"][k] - lo["wpar"][k])
+        tie = hi["wpar"][k] - mid["wpar"][k]
         assert abs(gw[k] - fd) <= 1e-3 * max(abs(fd), 1e-3) + tie, (k, gw[k], fd)
         checked += 1
     assert checked >= 50

@@ -6,7 +6,8 @@ import numpy as np
 
 import oracle
 import wsr_scenes as ws
-from tests.gpu_util import AMB_TAU, FWD_TOL, GRAD_TOL, compare_image, grad_envelope, grad_excess, rel_err
+from tests.gpu_util import (FWD_TOL, GRAD_TOL, TIE, assert_image_parity, compare_image, grad_envelope, grad_excess,
+                            image_stats, rel_err)
 
 
 def _small():
@@ -18,7 +19,7 @@ def _small():
 
 def test_compare_image_forgives_only_the_tie_allowance():
     sc, cam, w = _small()
-    ref = oracle.render(sc, cam, w, amb_tau=AMB_TAU)
+    ref = oracle.render(sc, cam, w, amb_tau=TIE)
     exact = ref["rgb"].astype(np.float32)
     excess, raw, n_amb = compare_image(exact, ref)
     assert excess <= 1e-6 and raw <= 1e-6 and n_amb > 0
@@ -76,3 +77,27 @@ def test_binning_acceptance_helpers():
                     assert not _allowed(allowed[i], ty + dy, tx + dx, cam.width, cam.height, tw, th)
                     checked += 1
         assert checked > 0
+
+
+def test_raw_rule_counts_pixels_that_need_the_allowance():
+    """In an image of 12,000 pixels, 12 pixels (0.1%) over the tolerance
+    before their allowance pass and 13 fail, even though every one of them
+    lies within its allowance; images under 10,000 pixels are held to the
+    allowance alone."""
+    import pytest
+    ref = {"rgb": np.zeros((120, 100, 3)), "amb": np.full((120, 100), 1e-3)}
+    gpu = np.zeros((120, 100, 3), np.float32)
+    flat = gpu.reshape(-1, 3)
+    flat[:12, 0] = 5e-4
+    st = assert_image_parity(gpu, ref)
+    assert st["pixels_over_tol_raw"] == 12 and st["pixels_using_allowance"] == 12
+    flat[12, 1] = 5e-4
+    with pytest.raises(AssertionError):
+        assert_image_parity(gpu, ref)
+    small = {"rgb": ref["rgb"][:50], "amb": ref["amb"][:50]}
+    assert image_stats(gpu[:50], small)["pixels_over_tol_raw"] == 13
+    assert_image_parity(gpu[:50], small)
+    # beyond the allowance fails whatever the size
+    flat[0, 2] = 2e-3
+    with pytest.raises(AssertionError):
+        assert_image_parity(gpu[:50], small)
