@@ -146,9 +146,12 @@ __device__ __forceinline__ void rot_scale(const float* qr, const float* ls, floa
     for (int k = 0; k < 3; ++k) s[k] = expf(ls[k]);
 }
 
-__device__ __forceinline__ float depth_weight(int kind, float d, float sigma, float beta, float v) {
+// The depth factor of the weight (Eqs. 8-10): w = factor for DIR and EXP, w = factor * v_i for LC.
+// A Gaussian is culled only where the factor is 0 (LC beyond sigma, EXP underflow): there neither
+// Eq. 7 nor its gradient depends on it.  Where only v_i is 0, w = 0 but dw/dv_i is not, so it stays.
+__device__ __forceinline__ float depth_factor(int kind, float d, float sigma, float beta) {
     if (kind == WSR_WEIGHT_EXP) return expf(-sigma * powf(d, beta));
-    if (kind == WSR_WEIGHT_LC) return fmaxf(0.0f, 1.0f - d / sigma) * v;
+    if (kind == WSR_WEIGHT_LC) return fmaxf(0.0f, 1.0f - d / sigma);
     return 1.0f;
 }
 
@@ -168,16 +171,17 @@ __global__ void __launch_bounds__(256) k_project(const GaussPtrs g, const Views 
         const View& V = vs.v[v];
         float4* o = rec + 3 * ((long long)v * g.n + i);
         const float tz = V.R[6] * P.p[0] + V.R[7] * P.p[1] + V.R[8] * P.p[2] + V.T[2];
-        float w = 0.0f;
-        if (tz > V.znear) w = depth_weight(wd.kind, tz, sigma, beta, P.lcv);
-        if (!(tz > V.znear) || w == 0.0f) {
-            // culled: behind the near plane (App. C), or zero depth weight
+        float wf = 0.0f;
+        if (tz > V.znear) wf = depth_factor(wd.kind, tz, sigma, beta);
+        if (!(tz > V.znear) || wf == 0.0f) {
+            // culled: behind the near plane (App. C), or a zero depth factor
             // (LC beyond sigma), which contributes nothing to Eq. 7 or its gradient
             o[0] = make_float4(0.f, 0.f, 0.f, 0.f);
             o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
             o[2] = make_float4(0.f, -1.f, -1.f, tz);
             continue;
         }
+        const float w = (wd.kind == WSR_WEIGHT_LC) ? wf * P.lcv : wf;
         Geom G;
         geometry(V, Rg, s, P.p[0], P.p[1], P.p[2], G);
         const float mx = V.fx * G.tx / G.tz + V.cx;
@@ -295,8 +299,9 @@ __global__ void __launch_bounds__(128, ONE ? 3 : 1) k_project_bwd(const GaussPtr
             if (!any) continue;
             const float tz0 = V.R[6] * P.p[0] + V.R[7] * P.p[1] + V.R[8] * P.p[2] + V.T[2];
             if (!(tz0 > V.znear)) continue;
-            const float w = depth_weight(wd.kind, tz0, sigma, beta, P.lcv);
-            if (w == 0.0f) continue;
+            const float wf = depth_factor(wd.kind, tz0, sigma, beta);
+            if (wf == 0.0f) continue;
+            const float w = (wd.kind == WSR_WEIGHT_LC) ? wf * P.lcv : wf;
             Geom G;
             geometry(V, Rg, s, P.p[0], P.p[1], P.p[2], G);
             const float tx = G.tx, ty = G.ty, tz = G.tz;
