@@ -230,10 +230,15 @@ wsr_status wsr_project(const wsr_gaussians* g, const wsr_camera* cams, int32_t n
  * list_capacity (so the render calls stay in bounds, with incomplete tiles),
  * the workspace records WSR_ERR_CAPACITY (see wsr_check) and the true total
  * (wsr_bin_total); the caller grows the list and runs the frame again.
+ *   total_dev      [1] uint64 device output, may be NULL: the true instance
+ *                  count of this call, written on `stream` after the scan (a
+ *                  captured graph learns from it how far to grow the list
+ *                  without a host read inside the graph)
  */
 wsr_status wsr_bin(const float* records, int64_t n, const wsr_camera* cams, int32_t n_cams,
                    const wsr_tiles* tiles, uint32_t* tile_offsets, uint32_t* tile_list,
-                   uint64_t list_capacity, void* workspace, size_t workspace_bytes, void* stream);
+                   uint64_t list_capacity, uint64_t* total_dev, void* workspace, size_t workspace_bytes,
+                   void* stream);
 
 /*
  * wsr_bin_count — first half of wsr_bin (count + scan only), for callers that
@@ -405,28 +410,40 @@ wsr_status wsr_adam_step(float* params, const float* grads, float* exp_avg, floa
  * the whole device and stall the frame), or a plug-in that is handed only its
  * input and output buffers by its host.  This entry point needs no workspace:
  * its scratch (per-tile counters, scan partial sums, a small header) lives in
- * one fixed device array inside this library, about 257 KB, which every GPU
- * that loads the library holds until the process exits.  The paper has no
- * counterpart; this is an integration entry point, not part of the method.
+ * one fixed device array inside this library, WSR_BIN_STATIC_BYTES =
+ * 270,848 bytes (264.5 KiB), which every GPU that loads the library holds
+ * until the process exits.  The paper has no counterpart; this is an
+ * integration entry point, not part of the method.
  *
  * Arguments and results are those of wsr_bin, except:
  *   - there is no workspace: at most WSR_BIN_STATIC_MAX_TILES tiles over all
- *     views; more returns WSR_ERR_UNSUPPORTED before anything is enqueued;
+ *     views, and only the per-tile schedule (WSR_SCHEDULE_TILE_BLOCKS); other
+ *     calls return WSR_ERR_UNSUPPORTED before anything is enqueued;
  *   - total_dev [1] uint64 device output (may be NULL): the true number of tile
  *     instances.  When it exceeds list_capacity the list is incomplete and the
- *     offsets are clamped to list_capacity, as in wsr_bin.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call shares the one array, and the array keeps the last
- * call's contents (each call clears what it needs cleared): calls that overlap
- * on the GPU (on different streams, or from different threads) race on it.
- * The call allocates nothing: no cudaMalloc, no cudaFree, no allocating
- * library routine.
+ *     offsets are clamped to list_capacity, as in wsr_bin;
+ *   - status_dev [1] int32 device output (may be NULL): the device-side status
+ *     of this call, written on `stream` after its last kernel: WSR_OK,
+ *     WSR_ERR_CAPACITY (the list was too small: see total_dev), or, in the
+ *     deterministic mode, WSR_ERR_UNSUPPORTED (a tile holds more than
+ *     WSR_DET_MAX_SEGMENT instances and its list was left unsorted).  It is
+ *     the only place such errors surface, since wsr_check reads a workspace.
+ * The array's device address is looked up (cudaGetSymbolAddress, which
+ * allocates nothing) on every call made outside stream capture, with the
+ * calling thread's current device; a call inside a capture reuses the address
+ * the last call outside capture found on that device, so make one call on a
+ * device before capturing it (and again after a cudaDeviceReset); a first
+ * call inside a capture returns WSR_ERR_UNSUPPORTED.  Every call shares the
+ * one array, and the array keeps the last call's contents (each call clears
+ * what it needs cleared): calls that overlap on the GPU (on different
+ * streams, or from different threads) race on it.  The call allocates
+ * nothing: no cudaMalloc, no cudaFree, no allocating library routine.
  */
 #define WSR_BIN_STATIC_MAX_TILES 65536
+#define WSR_BIN_STATIC_BYTES 270848
 wsr_status wsr_bin_static(const float* records, int64_t n, const wsr_camera* cams, int32_t n_cams,
                           const wsr_tiles* tiles, uint32_t* tile_offsets, uint32_t* tile_list,
-                          uint64_t list_capacity, uint64_t* total_dev, void* stream);
+                          uint64_t list_capacity, uint64_t* total_dev, int32_t* status_dev, void* stream);
 
 /*
  * wsr_count_pairs — diagnostic: the number of (pixel, Gaussian) pairs with

@@ -327,7 +327,12 @@ static double quad_form(const double conic[3], double dx, double dy)
 /* infrastructure: no part of Eq. 7 depends on it.                          */
 /* ------------------------------------------------------------------------ */
 #define ORC_U (1.0 / 16777216.0)    /* FP32 unit roundoff, 2^-24 */
-#define ORC_TIE_CAP 1.0             /* widest tie window the pixel ranges cover */
+/* Widest tie window the pixel ranges cover: they reach q = 9 + ORC_TIE_CAP.
+ * Every term of the window grows at most linearly in q, so if each pair
+ * within ORC_TIE_CAP of the cutoff has a window under ORC_TIE_CAP / 2, no pair
+ * beyond the ranges (q > 9 + ORC_TIE_CAP) can be a tie; callers report a
+ * window that breaks this (too_wide). */
+#define ORC_TIE_CAP 1.0
 
 static double gam(int n) { return n * ORC_U / (1.0 - n * ORC_U); }
 
@@ -483,6 +488,8 @@ static int counted(double q, double cutoff, long i, int x, int y, int which)
     return q <= cutoff;
 }
 
+static int too_wide(double q, double tau) { return fabs(q - ORC_CUTOFF) <= ORC_TIE_CAP && tau > 0.5 * ORC_TIE_CAP; }
+
 /* Models of every Gaussian (malloc'ed). */
 static otie* tie_all(const oscene* S, const ocam* cam, const oproj* P)
 {
@@ -581,7 +588,7 @@ typedef struct {
     const double* dent;      /* total denominators, for the second pass */
     const otie* tie;         /* per-pair windows from the FP32 model (NULL: amb_tau for every pair) */
     double* mass;            /* [H*W] or NULL: sum of |a| over the pixel's tie pairs */
-    int* wide;               /* per thread: a pair's window exceeded ORC_TIE_CAP */
+    int* wide;               /* per thread: a model window broke the ORC_TIE_CAP rule (too_wide) */
 } render_ctx;
 
 static void render_rows(void* arg, long r0, long r1, int tid)
@@ -608,7 +615,7 @@ static void render_rows(void* arg, long r0, long r1, int tid)
                 if (c->amb) {
                     /* second pass: bound of what a near-cutoff pair can change */
                     const double tau = c->tie ? tie_width(c->tie + i, dx, dy, q, NULL) : c->amb_tau;
-                    if (tau > widest) c->wide[tid] = 1;
+                    if (c->tie ? too_wide(q, tau) : tau > widest) c->wide[tid] = 1;
                     if (fabs(q - c->cutoff) <= tau) {
                         const double g = exp(-0.5 * q);
                         const double a = o->u * o->w * g;
@@ -652,7 +659,7 @@ static oproj* project_all(const oscene* S, const ocam* cam, const owt* wt)
  * amb_tau < 0 takes each pair's window from the FP32 rounding model above.
  * tie_mass [H*W] (optional, with amb): the sum of |a| over those pairs.
  * n_pairs (optional): number of (pixel, Gaussian) pairs with q <= 9.
- * Returns 3 if a model window exceeded ORC_TIE_CAP (the pixel ranges would
+ * Returns 3 if a model window broke the ORC_TIE_CAP rule (the pixel ranges would
  * then miss pairs).
  */
 int wsro_render(long n, int deg, int vd, const double* means, const double* log_scales,
@@ -1044,7 +1051,7 @@ static void grad_gaussians(void* arg, long lo, long hi, int tid)
                 int tie = 0;
                 if (bnd) {
                     const double tau = c->tie ? tie_width(c->tie + i, dx, dy, q, NULL) : c->tie_tau;
-                    if (tau > widest) c->wide[tid] = 1;
+                    if (c->tie ? too_wide(q, tau) : tau > widest) c->wide[tid] = 1;
                     tie = fabs(q - ORC_CUTOFF) <= tau;
                 }
                 if (!in && !tie) continue;
@@ -1141,7 +1148,7 @@ static void grad_gaussians(void* arg, long lo, long hi, int tid)
  * tie_tau: 0 for no tie bounds; > 0 for the window |q - 9| <= tie_tau for
  * every pair; < 0 for each pair's window from the FP32 rounding model.  With
  * tie bounds, b_* receive the bounds of the same shapes as g_* (b_wpar[6]).
- * Returns 3 if a model window exceeded ORC_TIE_CAP.
+ * Returns 3 if a model window broke the ORC_TIE_CAP rule (too_wide).
  */
 int wsro_grad(long n, int deg, int vd, const double* means, const double* log_scales,
               const double* quats, const double* sh, const double* opac, const double* lc_v,

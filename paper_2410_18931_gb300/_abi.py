@@ -24,6 +24,7 @@ WSR_GRAD_RECORD_FLOATS = 12
 WSR_GRAD_RECORD_FLOATS_DET = 32      # deterministic mode: 9 int64 sums and 9 magnitudes per record
 WSR_DET_MAX_SEGMENT = 8192
 WSR_BIN_STATIC_MAX_TILES = 65536     # tiles over all views that wsr_bin_static handles
+WSR_BIN_STATIC_BYTES = 270848        # its fixed scratch array, held by every GPU that loads the library
 
 _c_void_p = ctypes.c_void_p
 
@@ -83,7 +84,8 @@ _SIGS = {
     "wsr_project": (ctypes.c_int, [_P(wsr_gaussians), _P(wsr_camera), ctypes.c_int32, _P(wsr_weight),
                                    _c_void_p, _c_void_p]),
     "wsr_bin": (ctypes.c_int, [_c_void_p, ctypes.c_int64, _P(wsr_camera), ctypes.c_int32, _P(wsr_tiles),
-                               _c_void_p, _c_void_p, ctypes.c_uint64, _c_void_p, ctypes.c_size_t, _c_void_p]),
+                               _c_void_p, _c_void_p, ctypes.c_uint64, _c_void_p, _c_void_p, ctypes.c_size_t,
+                               _c_void_p]),
     "wsr_bin_count": (ctypes.c_int, [_c_void_p, ctypes.c_int64, _P(wsr_camera), ctypes.c_int32,
                                      _P(wsr_tiles), _c_void_p, _c_void_p, ctypes.c_size_t, _c_void_p]),
     "wsr_bin_total": (ctypes.c_int, [_c_void_p, ctypes.c_size_t, _P(ctypes.c_uint64), _c_void_p]),
@@ -101,7 +103,7 @@ _SIGS = {
                                        _P(wsr_weight), _c_void_p, _P(wsr_grads), _c_void_p, ctypes.c_size_t,
                                        _c_void_p]),
     "wsr_bin_static": (ctypes.c_int, [_c_void_p, ctypes.c_int64, _P(wsr_camera), ctypes.c_int32, _P(wsr_tiles),
-                                      _c_void_p, _c_void_p, ctypes.c_uint64, _c_void_p, _c_void_p]),
+                                      _c_void_p, _c_void_p, ctypes.c_uint64, _c_void_p, _c_void_p, _c_void_p]),
     "wsr_count_pairs": (ctypes.c_int, [_c_void_p, ctypes.c_int64, _c_void_p, _c_void_p, _P(wsr_camera),
                                        ctypes.c_int32, _P(wsr_tiles), _c_void_p, _c_void_p]),
     "wsr_loss_l1": (ctypes.c_int, [_c_void_p, _c_void_p, ctypes.c_int64, _c_void_p, _c_void_p, _c_void_p]),

@@ -21,6 +21,7 @@ bool tiles_ok(const wsr_tiles* t) {
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 bool aligned4(const void* p) { return ((uintptr_t)p & 3u) == 0; }
+bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
 
 // Builds the per-view constant table.  Returns WSR_OK or the argument error.
 wsr_status make_views(const wsr_camera* cams, int32_t n_cams, const wsr_tiles* tiles, Views* vs) {
@@ -182,23 +183,32 @@ constexpr size_t kStaticTiles = WSR_BIN_STATIC_MAX_TILES;
 constexpr size_t kStaticBytes = kWsHeader + align256c(sizeof(unsigned) * (kStaticTiles + 1)) +
                                 align256c(sizeof(unsigned long long) * ((kStaticTiles + kScanTile - 1) / kScanTile + 1));
 
+static_assert(kStaticBytes == WSR_BIN_STATIC_BYTES, "the header states the scratch array's size");
+
 static __device__ __align__(256) unsigned char g_bin_static_scratch[kStaticBytes];
 
 constexpr int kMaxDevices = 128;
 std::mutex g_static_mu;
 void* g_static_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (host code cannot use the symbol itself as a device address).
-wsr_status static_scratch(void** out) {
+// Device address of the scratch array on the current device (host code cannot
+// use the symbol itself as a device address).  Looked up afresh on every call
+// outside stream capture, so that a device reset in between leaves no stale
+// address behind; inside a capture the last address found on the device is
+// reused (the lookup is not made while a stream captures).
+wsr_status static_scratch(cudaStream_t s, void** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return WSR_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return WSR_ERR_UNSUPPORTED;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return WSR_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_bin_static_scratch) != cudaSuccess || !p) return WSR_ERR_CUDA;
         g_static_addr[dev] = p;
+    } else if (!g_static_addr[dev]) {
+        return WSR_ERR_UNSUPPORTED;
     }
     *out = g_static_addr[dev];
     return WSR_OK;
@@ -281,15 +291,15 @@ wsr_status wsr_bin_count(const float* records, int64_t n, const wsr_camera* cams
 }
 
 wsr_status wsr_bin(const float* records, int64_t n, const wsr_camera* cams, int32_t n_cams, const wsr_tiles* tiles,
-                   uint32_t* tile_offsets, uint32_t* tile_list, uint64_t list_capacity, void* workspace,
-                   size_t workspace_bytes, void* stream) {
+                   uint32_t* tile_offsets, uint32_t* tile_list, uint64_t list_capacity, uint64_t* total_dev,
+                   void* workspace, size_t workspace_bytes, void* stream) {
     static thread_local Views vs;
     if (!tiles) return WSR_ERR_INVALID_ARG;
     WSR_TRY(make_views(cams, n_cams, tiles, &vs));
     WSR_TRY(check_ws(vs, workspace, workspace_bytes));
     if (n < 0 || (n > 0 && (!records || !aligned16(records))) || !tile_offsets) return WSR_ERR_INVALID_ARG;
     if (list_capacity > 0 && !tile_list) return WSR_ERR_INVALID_ARG;
-    if (!aligned4(tile_offsets) || !aligned4(tile_list)) return WSR_ERR_INVALID_ARG;
+    if (!aligned4(tile_offsets) || !aligned4(tile_list) || !aligned8(total_dev)) return WSR_ERR_INVALID_ARG;
     if ((unsigned long long)n * (unsigned long long)n_cams > 0xffffffffull) return WSR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     WSR_TRY(bin_count_impl(records, n, vs, tile_offsets, list_capacity, workspace, s));
@@ -298,12 +308,14 @@ wsr_status wsr_bin(const float* records, int64_t n, const wsr_camera* cams, int3
     WSR_CUDA(launch_bin_scatter(records, n, vs, (unsigned*)(ws + L.cursor), tile_list, list_capacity,
                                 (WsHeader*)ws, s));
     if (vs.det) WSR_CUDA(launch_sort_segments(vs, tile_offsets, tile_list, (WsHeader*)ws, s));
+    if (total_dev)
+        WSR_CUDA(cudaMemcpyAsync(total_dev, &((WsHeader*)ws)->total, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
     return WSR_OK;
 }
 
 wsr_status wsr_bin_static(const float* records, int64_t n, const wsr_camera* cams, int32_t n_cams,
                           const wsr_tiles* tiles, uint32_t* tile_offsets, uint32_t* tile_list, uint64_t list_capacity,
-                          uint64_t* total_dev, void* stream) {
+                          uint64_t* total_dev, int32_t* status_dev, void* stream) {
     static thread_local Views vs;
     if (!tiles) return WSR_ERR_INVALID_ARG;
     WSR_TRY(make_views(cams, n_cams, tiles, &vs));
@@ -311,14 +323,15 @@ wsr_status wsr_bin_static(const float* records, int64_t n, const wsr_camera* cam
     if (vs.schedule != WSR_SCHEDULE_TILE_BLOCKS) return WSR_ERR_UNSUPPORTED;
     if (n < 0 || (n > 0 && (!records || !aligned16(records))) || !tile_offsets) return WSR_ERR_INVALID_ARG;
     if (list_capacity > 0 && !tile_list) return WSR_ERR_INVALID_ARG;
-    if (!aligned4(tile_offsets) || !aligned4(tile_list)) return WSR_ERR_INVALID_ARG;
+    if (!aligned4(tile_offsets) || !aligned4(tile_list) || !aligned8(total_dev) || !aligned4(status_dev))
+        return WSR_ERR_INVALID_ARG;
     if ((unsigned long long)n * (unsigned long long)n_cams > 0xffffffffull) return WSR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
     void* scratch = nullptr;
-    WSR_TRY(static_scratch(&scratch));
+    WSR_TRY(static_scratch(s, &scratch));
     Views vb = vs;                 // the binning's part of the layout (no backward regions)
     vb.det = 0;
     if (ws_layout(vb).total > kStaticBytes) return WSR_ERR_UNSUPPORTED;
-    cudaStream_t s = (cudaStream_t)stream;
     WSR_TRY(bin_count_impl(records, n, vs, tile_offsets, list_capacity, scratch, s));
     const WsLayout L = ws_layout(vs);
     char* ws = (char*)scratch;
@@ -327,6 +340,8 @@ wsr_status wsr_bin_static(const float* records, int64_t n, const wsr_camera* cam
     if (vs.det) WSR_CUDA(launch_sort_segments(vs, tile_offsets, tile_list, (WsHeader*)ws, s));
     if (total_dev)
         WSR_CUDA(cudaMemcpyAsync(total_dev, &((WsHeader*)ws)->total, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    if (status_dev)
+        WSR_CUDA(cudaMemcpyAsync(status_dev, &((WsHeader*)ws)->err, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     return WSR_OK;
 }
 

@@ -105,9 +105,11 @@ class Renderer:
         A.check("wsr_project", self.lib.wsr_project(ctypes.byref(g.c_struct()), self.cams_c, self.n_cams,
                                                     ctypes.byref(w), _ptr(records), _stream(stream)))
 
-    def wsr_bin(self, records, n, offsets, tile_list, stream=None):
+    def wsr_bin(self, records, n, offsets, tile_list, stream=None, total_dev=None):
+        """``total_dev``: optional [1] int64 device tensor that receives the true instance count."""
         A.check("wsr_bin", self.lib.wsr_bin(_ptr(records), n, self.cams_c, self.n_cams, ctypes.byref(self.tiles_c),
                                             _ptr(offsets), _ptr(tile_list), tile_list.numel(),
+                                            _ptr(total_dev) if total_dev is not None else None,
                                             _ptr(self.workspace), self.workspace.numel(), _stream(stream)))
 
     def wsr_bin_count(self, records, n, offsets, stream=None):

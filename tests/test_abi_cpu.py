@@ -112,11 +112,18 @@ def test_argument_errors_are_returned(lib):
     assert lib.wsr_workspace_size(zc, 1, ctypes.byref(t16)) == 0
     # workspace too small
     ws = lib.wsr_workspace_size(cams, n, ctypes.byref(t16))
-    assert lib.wsr_bin(fake, 10, cams, n, ctypes.byref(t16), fake, fake, 100, fake, ws - 16,
+    assert lib.wsr_bin(fake, 10, cams, n, ctypes.byref(t16), fake, fake, 100, None, fake, ws - 16,
                        None) == A.WSR_ERR_INVALID_ARG
     # unsupported tile shape
-    assert lib.wsr_bin(fake, 10, cams, n, ctypes.byref(A.tiles(24, 24)), fake, fake, 100, fake, ws,
+    assert lib.wsr_bin(fake, 10, cams, n, ctypes.byref(A.tiles(24, 24)), fake, fake, 100, None, fake, ws,
                        None) == A.WSR_ERR_UNSUPPORTED
+    # a misaligned device total (uint64), and the static entry's misaligned total and status (int32)
+    assert lib.wsr_bin(fake, 10, cams, n, ctypes.byref(t16), fake, fake, 100, fake + 4, fake, ws,
+                       None) == A.WSR_ERR_INVALID_ARG
+    assert lib.wsr_bin_static(fake, 10, cams, n, ctypes.byref(t16), fake, fake, 100, fake + 4, None,
+                              None) == A.WSR_ERR_INVALID_ARG
+    assert lib.wsr_bin_static(fake, 10, cams, n, ctypes.byref(t16), fake, fake, 100, None, fake + 2,
+                              None) == A.WSR_ERR_INVALID_ARG
     # null outputs of the renderer
     assert lib.wsr_render_fwd(fake, 10, fake, fake, cams, n, ctypes.byref(t16), ctypes.byref(w), None, fake,
                               fake, ws, None) == A.WSR_ERR_INVALID_ARG
@@ -247,7 +254,7 @@ def test_misaligned_record_buffers_are_rejected(lib):
         grads = A.wsr_grads()
         assert lib.wsr_project_bwd(ctypes.byref(g), cams, n, ctypes.byref(t), ctypes.byref(w), fake + 4,
                                    ctypes.byref(grads), fake, ws, None) == A.WSR_ERR_INVALID_ARG
-        assert lib.wsr_bin(fake, 10, cams, n, ctypes.byref(t), fake + 1, fake, 100, fake, ws,
+        assert lib.wsr_bin(fake, 10, cams, n, ctypes.byref(t), fake + 1, fake, 100, None, fake, ws,
                            None) == A.WSR_ERR_INVALID_ARG
         assert lib.wsr_count_pairs(fake + 4, 10, fake, fake, cams, n, ctypes.byref(t), fake,
                                    None) == A.WSR_ERR_INVALID_ARG
