@@ -155,3 +155,52 @@ def test_tile_lists_of_several_uneven_views_in_one_call():
         assert extra <= 0.03 * n_must, (v, extra, n_must)
         t0 += tiles_x * tiles_y
     assert t0 == len(off) - 1
+
+
+def test_device_total_inside_a_captured_graph():
+    """wsr_bin's device total (total_dev) inside a captured CUDA graph: each
+    replay writes the true instance count of that replay's records, with no
+    host read in the graph, including a replay whose list overflows (the
+    total then exceeds the capacity and tells the caller how far to grow)."""
+    import torch
+
+    from paper_2410_18931_gb300 import Gaussians, Renderer
+    from paper_2410_18931_gb300 import _abi as A
+    sc = _scene()
+    cam = ws.look_at((0.1, -0.2, -3.0), width=200, height=150).rounded()
+    w = ws.default_weight(ws.EXP)
+    g = Gaussians.from_scene(sc)
+    wpar = torch.tensor(w.as_array(), device="cuda")
+    r = Renderer([cam], tile=(16, 16))
+    st = r.alloc_state(g.n)
+    r.wsr_project(g, w.kind, wpar, st.records)
+    r.wsr_bin_count(st.records, g.n, st.tile_offsets)
+    total = r.wsr_bin_total()
+    tile_list = torch.empty(total + 16, dtype=torch.int32, device="cuda")
+    total_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
+    records = st.records.clone()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):                     # warm-up call outside the capture
+        r.wsr_bin(records, g.n, st.tile_offsets, tile_list, stream=side, total_dev=total_dev)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        r.wsr_bin(records, g.n, st.tile_offsets, tile_list, total_dev=total_dev)
+    total_dev.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert int(total_dev.item()) == total
+    # the same graph on records with every Gaussian doubled in place: half the Gaussians moved onto
+    # the other half's positions are binned twice as often where they overlap
+    half = g.n // 2
+    records.view(-1, 12)[half:2 * half] = records.view(-1, 12)[:half]
+    total_dev.zero_()
+    graph.replay()
+    err = r.wsr_check()                               # read before the recount below clears it
+    got = int(total_dev.item())
+    r.wsr_bin_count(records, g.n, st.tile_offsets)
+    expect = r.wsr_bin_total()
+    assert got == expect and expect != total
+    assert (err == A.WSR_ERR_CAPACITY) == (expect > tile_list.numel())
