@@ -44,6 +44,7 @@ if ROOT not in sys.path:
 # d/d(c u w), d/d(u w) sums 8; dL/dq' = e (P . cw) 8; g r, g dx 2; the five
 # moments (three FMAs, two adds) 8 -> 35.
 FLOPS_PER_PAIR_FWD = 17
+FLOPS_PER_SLOT_TEST_FWD = 9   # of those, the q test every evaluated slot pays (dx, dy, r, q')
 FLOPS_PER_PAIR_BWD = 35
 FP32_LANES_PER_SM = 128
 MUFU_PER_SM = 16         # ex2 / rsqrt / rcp results per SM and clock
@@ -470,7 +471,7 @@ def run_ours(args):
     # pair statistics (outside timing): algorithmic pairs and tile instances
     S.run()
     torch.cuda.synchronize()
-    pairs = S.r.wsr_count_pairs(S.st)
+    pairs, fwd_slots, bwd_pixels = S.r.wsr_count_pairs(S.st)
     instances = S.r.wsr_bin_total()
     A.check("wsr_bin", S.r.wsr_check())
 
@@ -558,6 +559,17 @@ def run_ours(args):
         "project_bwd_hbm_frac": round((2 * param_bytes + S.g.n * 36) / (stage_ms[5] * 1e-3) / 1e9 / hbm_peak, 4),
         "pairs_in_cutoff": pairs, "tile_instances": instances,
         "bbox_overhead": round(instances * tile[0] * tile[1] / max(pairs, 1), 3),
+        # the work the render kernels actually do (wsr_count_pairs): the forward tests q at every pixel
+        # of each warp whose region a footprint reaches (9 flops: dx, dy, r, q') and accumulates the
+        # pairs inside the cutoff (8 flops); the backward walks every pixel of its units (35 flops)
+        "fwd_slots_evaluated": fwd_slots,
+        "fwd_slots_per_pair": round(fwd_slots / max(pairs, 1), 3),
+        "render_fwd_alu_frac_evaluated": round((fwd_slots * FLOPS_PER_SLOT_TEST_FWD + pairs * (
+            FLOPS_PER_PAIR_FWD - FLOPS_PER_SLOT_TEST_FWD)) / (stage_ms[2] * 1e-3) / (peak * 1e12), 4),
+        "bwd_pixels_walked": bwd_pixels,
+        "bwd_pixels_per_pair": round(bwd_pixels / max(pairs, 1), 3),
+        "render_bwd_alu_frac_evaluated": round(bwd_pixels * FLOPS_PER_PAIR_BWD / (stage_ms[4] * 1e-3) / (peak * 1e12),
+                                               4),
     }
 
     line = {"metric": METRIC, "value": round(value, 2),

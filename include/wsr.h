@@ -446,10 +446,16 @@ wsr_status wsr_bin_static(const float* records, int64_t n, const wsr_camera* cam
                           uint64_t list_capacity, uint64_t* total_dev, int32_t* status_dev, void* stream);
 
 /*
- * wsr_count_pairs — diagnostic: the number of (pixel, Gaussian) pairs with
- * q <= 9 over all views, i.e. the terms of the sums of Eq. 7 that the render
- * kernels evaluate (their algorithmic work), written to *count_dev (device
- * uint64, overwritten).  Arguments as for wsr_render_fwd.
+ * wsr_count_pairs — diagnostic: the work of the render kernels over all views,
+ * written to count_dev [3] (device uint64, overwritten, 8-byte aligned):
+ *   [0] (pixel, Gaussian) pairs with q <= 9, i.e. the terms of the sums of
+ *       Eq. 7 (the algorithmic work of both render kernels);
+ *   [1] (pixel, Gaussian) slots wsr_render_fwd evaluates: for each Gaussian of
+ *       a tile, the pixels of every warp whose region of the tile its footprint
+ *       reaches (the forward tests q at each of them);
+ *   [2] pixels the backward walks: each footprint row's span within a tile,
+ *       padded to an even length.
+ * Arguments as for wsr_render_fwd.  Not part of a timed step.
  */
 wsr_status wsr_count_pairs(const float* records, int64_t n, const uint32_t* tile_offsets,
                            const uint32_t* tile_list, const wsr_camera* cams, int32_t n_cams,

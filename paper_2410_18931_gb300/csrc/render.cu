@@ -52,6 +52,43 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
+// The backward's pixel spans of one record on the rows of a tile: on row y the
+// footprint q' <= QM is mu_x + c(dy) +- h(dy) with the conic entries
+// A' = qw^2 + qd, B' = qs qw, C' = qs^2, det' = A' C' - B'^2 = qd qs^2:
+// c = -B' dy / A', h = sqrt(A' QM - det' dy^2) / A' (no cancellation anywhere),
+// widened by 0.02 pixel.  `row` gives the span of a local row as
+// (first column) | (units << 8), a unit being two horizontally adjacent
+// pixels (the second a padding pixel when the span's length is odd).
+struct RowSpans {
+    float Ap, hb, det, ia, ext;
+    __device__ __forceinline__ RowSpans(const float4 a, const float qd, const float QM) {
+        Ap = fmaf(a.w, a.w, qd);
+        hb = a.z * a.w;
+        det = qd * a.z * a.z;
+        ia = rcp_approx(Ap);
+        // rows the footprint can reach: |dy| <= sqrt(A' QM / det'), with a pixel of slack
+        ext = fminf(sqrt_approx(fmaxf(Ap * QM * rcp_approx(det), 0.0f)), 1e6f) + 1.0f;
+    }
+    // local rows [lo, hi] of the block [first, first + count) that the footprint can reach
+    __device__ __forceinline__ void rows(const float4 a, int y_org, int first, int count, int& lo, int& hi) const {
+        lo = max(first, (int)floorf(a.y - ext - 0.5f) - y_org);
+        hi = min(first + count - 1, (int)ceilf(a.y + ext - 0.5f) - y_org);
+    }
+    __device__ __forceinline__ unsigned short row(const float4 a, const float QM, int x_org, int y_org, int x_lim,
+                                                  int ly) const {
+        const float dy = (float)(y_org + ly) + 0.5f - a.y;
+        const float d4 = fmaf(-det * dy, dy, Ap * QM);
+        if (d4 < 0.0f) return 0;
+        const float h = sqrt_approx(d4) * ia;
+        const float cx = a.x - hb * dy * ia;
+        const float fx0 = fmaxf(ceilf(cx - h - 0.52f), (float)x_org);
+        const float fx1 = fminf(floorf(cx + h - 0.48f), (float)(x_org + x_lim - 1));
+        if (!(fx0 <= fx1)) return 0;
+        const int xs = (int)fx0 - x_org, len = (int)fx1 - (int)fx0 + 1;
+        return (unsigned short)(xs | (((len + 1) >> 1) << 8));    // start, units
+    }
+};
+
 // Pixel-per-thread layout of the pair-count diagnostic.
 template <int TW, int TH, int PPT>
 struct TileShape {
@@ -352,36 +389,15 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 s2[gj] = f2(cb, b.y);
                 sidx[gj] = r;
             }
-            // row y: the footprint is mu_x + c(dy) +- h(dy) with the conic entries
-            // A' = qw^2 + qd, B' = qs qw, C' = qs^2, det' = A' C' - B'^2 = qd qs^2:
-            // c = -B' dy / A', h = sqrt(A' QM - det' dy^2) / A' (no cancellation anywhere)
-            const float Ap = fmaf(a.w, a.w, b.x);
-            const float hb = a.z * a.w;
-            const float det = b.x * a.z * a.z;
-            const float ia = rcp_approx(Ap);
-            // rows the footprint can reach: |dy| <= sqrt(A' QM / det'), with a pixel of slack
-            const float ext = fminf(sqrt_approx(fmaxf(Ap * QM * rcp_approx(det), 0.0f)), 1e6f) + 1.0f;
-            const int ly_lo = max(half * HR, (int)floorf(a.y - ext - 0.5f) - y_org);
-            const int ly_hi = min(min(y_lim, half * HR + HR) - 1, (int)ceilf(a.y + ext - 0.5f) - y_org);
+            const RowSpans rs(a, b.x, QM);
+            int ly_lo, ly_hi;
+            rs.rows(a, y_org, half * HR, min(HR, y_lim - half * HR), ly_lo, ly_hi);
 #pragma unroll
             for (int k = 0; k < HR; ++k) {
                 const int ly = half * HR + k;
                 unsigned short sp = 0;
-                if (ly >= ly_lo && ly <= ly_hi) {
-                    const float dy = (float)(y_org + ly) + 0.5f - a.y;
-                    const float d4 = fmaf(-det * dy, dy, Ap * QM);
-                    if (d4 >= 0.0f) {
-                        const float h = sqrt_approx(d4) * ia;
-                        const float cx = a.x - hb * dy * ia;
-                        const float fx0 = fmaxf(ceilf(cx - h - 0.52f), (float)x_org);
-                        const float fx1 = fminf(floorf(cx + h - 0.48f), (float)(x_org + x_lim - 1));
-                        if (fx0 <= fx1) {
-                            const int xs = (int)fx0 - x_org, len = (int)fx1 - (int)fx0 + 1;
-                            sp = (unsigned short)(xs | (((len + 1) >> 1) << 8));   // start, units
-                            nunits += (unsigned)((len + 1) >> 1);
-                        }
-                    }
-                }
+                if (ly >= ly_lo && ly <= ly_hi) sp = rs.row(a, QM, x_org, y_org, x_lim, ly);
+                nunits += (unsigned)(sp >> 8);
                 span[k] = sp;
             }
         }
@@ -683,14 +699,21 @@ cudaError_t bwd_t(const float* rec, const unsigned* off, const unsigned* list, c
     return bwd_chunk<TW, TH, 128>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sched, s);
 }
 
-// Diagnostic: (pixel, Gaussian) pairs inside the cutoff, i.e. the
-// algorithmic work of the render kernels (q' from each pixel's own dx, dy; the
-// renderers may decide pairs within rounding of the cutoff differently).
-template <int TW, int TH, int PPT>
+// Diagnostic: the work of the render kernels, three counts added to count[0..2]:
+//   [0] (pixel, Gaussian) pairs inside the cutoff, i.e. the algorithmic work
+//       (q' from each pixel's own dx, dy; the renderers may decide pairs
+//       within rounding of the cutoff differently);
+//   [1] the (pixel, Gaussian) slots the forward evaluates: for every Gaussian
+//       of a tile, the pixels of each warp whose region its footprint reaches
+//       (the forward's per-warp test; all the tile's pixel slots with one warp);
+//   [2] the pixels of the backward's units (each footprint row's span, padded
+//       to an even length), from the backward's own span arithmetic.
+template <int TW, int TH, int PPT, int PX>
 __global__ void __launch_bounds__(TileShape<TW, TH, PPT>::NT)
     k_count_pairs(const float4* __restrict__ rec, const unsigned* __restrict__ offsets,
                   const unsigned* __restrict__ list, const Views vs, unsigned long long* __restrict__ count) {
     using S = TileShape<TW, TH, PPT>;
+    using F = FwdShape<TW, TH, PX>;
     constexpr int NT = S::NT;
     __shared__ float4 s0[NT];
     __shared__ float s1[NT];
@@ -702,15 +725,37 @@ __global__ void __launch_bounds__(TileShape<TW, TH, PPT>::NT)
     const int x = tc.tx * TW + lx;
     const int y0 = tc.ty * TH + ly * PPT;
     const float px = (float)x + 0.5f;
-    unsigned long long cnt_pairs = 0;
+    const int x_org = tc.tx * TW, y_org = tc.ty * TH;
+    const int x_lim = min(TW, V.W - x_org), y_lim = min(TH, V.H - y_org);
+    const float QM = kQMax * 1.0001f + 1e-4f;
+    unsigned long long cnt_pairs = 0, cnt_fwd = 0, cnt_bwd = 0;
     const unsigned start = offsets[tile], end = offsets[tile + 1];
     for (unsigned base = start; base < end; base += NT) {
         const int cnt = (int)min((unsigned)NT, end - base);
         __syncthreads();
         if (tid < cnt) {
             const float4* p = rec + 3ull * list[base + tid];
-            s0[tid] = __ldg(p);
-            s1[tid] = __ldg(reinterpret_cast<const float*>(p + 1));
+            const float4 a = __ldg(p);
+            const float qd = __ldg(reinterpret_cast<const float*>(p + 1));
+            s0[tid] = a;
+            s1[tid] = qd;
+            // the forward's slots: 32 threads x PX x 2 pixels per warp whose rows the footprint reaches
+            if constexpr (F::NW > 1) {
+                const float xl = (float)x_org + 0.5f, xh = xl + (float)(TW - 1);
+#pragma unroll
+                for (int w = 0; w < F::NW; ++w) {
+                    const float yl = (float)(y_org + F::row_lo(w)) + 0.5f;
+                    const float yh = (float)(y_org + F::row_hi(w)) + 0.5f;
+                    if (footprint_hits(a.x, a.y, a.z, a.w, qd, xl, xh, yl, yh)) cnt_fwd += 32ull * PX * 2;
+                }
+            } else {
+                cnt_fwd += (unsigned long long)F::NT * PX * 2;
+            }
+            // the backward's unit pixels
+            const RowSpans rs(a, qd, QM);
+            int lo, hi;
+            rs.rows(a, y_org, 0, y_lim, lo, hi);
+            for (int r = lo; r <= hi; ++r) cnt_bwd += 2ull * (rs.row(a, QM, x_org, y_org, x_lim, r) >> 8);
         }
         __syncthreads();
         if (x >= V.W) continue;
@@ -729,8 +774,16 @@ __global__ void __launch_bounds__(TileShape<TW, TH, PPT>::NT)
         }
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) cnt_pairs += __shfl_xor_sync(0xffffffffu, cnt_pairs, off);
-    if ((tid & 31) == 0 && cnt_pairs) atomicAdd(count, cnt_pairs);
+    for (int off = 16; off > 0; off >>= 1) {
+        cnt_pairs += __shfl_xor_sync(0xffffffffu, cnt_pairs, off);
+        cnt_fwd += __shfl_xor_sync(0xffffffffu, cnt_fwd, off);
+        cnt_bwd += __shfl_xor_sync(0xffffffffu, cnt_bwd, off);
+    }
+    if ((tid & 31) == 0) {
+        if (cnt_pairs) atomicAdd(count, cnt_pairs);
+        if (cnt_fwd) atomicAdd(count + 1, cnt_fwd);
+        if (cnt_bwd) atomicAdd(count + 2, cnt_bwd);
+    }
 }
 
 // Mean absolute error and its gradient: float4 loads and stores (the arrays are 16-byte aligned;
@@ -800,13 +853,14 @@ cudaError_t launch_det_bg_reduce(const float* bg_tiles, int n_tiles, float* gw, 
 
 cudaError_t launch_count_pairs(const float* rec, const unsigned* off, const unsigned* list, const Views& vs,
                                unsigned long long* count, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), s);
+    cudaError_t e = cudaMemsetAsync(count, 0, 3 * sizeof(unsigned long long), s);
     if (e != cudaSuccess || vs.total_tiles == 0) return e;
     const float4* r = reinterpret_cast<const float4*>(rec);
-    if (vs.tile_w == 16 && vs.tile_h == 16) k_count_pairs<16, 16, 2><<<vs.total_tiles, 128, 0, s>>>(r, off, list, vs, count);
-    else if (vs.tile_w == 8 && vs.tile_h == 8) k_count_pairs<8, 8, 2><<<vs.total_tiles, 32, 0, s>>>(r, off, list, vs, count);
-    else if (vs.tile_w == 32 && vs.tile_h == 8) k_count_pairs<32, 8, 2><<<vs.total_tiles, 128, 0, s>>>(r, off, list, vs, count);
-    else if (vs.tile_w == 16 && vs.tile_h == 8) k_count_pairs<16, 8, 2><<<vs.total_tiles, 64, 0, s>>>(r, off, list, vs, count);
+    // the forward's pixels per thread (PX) as launch_render_fwd picks them
+    if (vs.tile_w == 16 && vs.tile_h == 16) k_count_pairs<16, 16, 2, 2><<<vs.total_tiles, 128, 0, s>>>(r, off, list, vs, count);
+    else if (vs.tile_w == 8 && vs.tile_h == 8) k_count_pairs<8, 8, 2, 1><<<vs.total_tiles, 32, 0, s>>>(r, off, list, vs, count);
+    else if (vs.tile_w == 32 && vs.tile_h == 8) k_count_pairs<32, 8, 2, 2><<<vs.total_tiles, 128, 0, s>>>(r, off, list, vs, count);
+    else if (vs.tile_w == 16 && vs.tile_h == 8) k_count_pairs<16, 8, 2, 2><<<vs.total_tiles, 64, 0, s>>>(r, off, list, vs, count);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }

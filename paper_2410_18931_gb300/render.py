@@ -153,12 +153,13 @@ class Renderer:
             ctypes.byref(g.c_struct()), self.cams_c, self.n_cams, ctypes.byref(self.tiles_c), ctypes.byref(w),
             _ptr(grad_records), ctypes.byref(grads), _ptr(self.workspace), self.workspace.numel(), _stream(stream)))
 
-    def wsr_count_pairs(self, st: FrameState, stream=None) -> int:
-        cnt = torch.zeros(1, dtype=torch.int64, device=self.device)
+    def wsr_count_pairs(self, st: FrameState, stream=None) -> tuple:
+        """(pairs with q <= 9, slots the forward evaluates, pixels the backward walks)."""
+        cnt = torch.zeros(3, dtype=torch.int64, device=self.device)
         A.check("wsr_count_pairs", self.lib.wsr_count_pairs(
             _ptr(st.records), st.n, _ptr(st.tile_offsets), _ptr(st.tile_list), self.cams_c, self.n_cams,
             ctypes.byref(self.tiles_c), _ptr(cnt), _stream(stream)))
-        return int(cnt.item())
+        return tuple(int(v) for v in cnt.cpu().tolist())
 
     def wsr_check(self, stream=None) -> int:
         return int(self.lib.wsr_check(_ptr(self.workspace), self.workspace.numel(), _stream(stream)))

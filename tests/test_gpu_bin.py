@@ -204,3 +204,30 @@ def test_device_total_inside_a_captured_graph():
     expect = r.wsr_bin_total()
     assert got == expect and expect != total
     assert (err == A.WSR_ERR_CAPACITY) == (expect > tile_list.numel())
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8), (16, 8)])
+def test_work_counts_of_the_render_kernels(tile):
+    """wsr_count_pairs: the pairs with q <= 9 agree with the oracle's count (up
+    to ties decided differently in FP32, far fewer than 0.1%); the forward's
+    evaluated slots and the backward's walked pixels hold every pair and fit
+    in the tile instances' pixels; the forward's slots come in whole warps
+    (32 threads of PX x 2 pixels) and the backward's pixels in whole units."""
+    import torch
+
+    from paper_2410_18931_gb300 import Gaussians, Renderer
+    sc = _scene()
+    cam = ws.look_at((0.1, -0.2, -3.0), width=200, height=150).rounded()
+    w = ws.default_weight(ws.EXP)
+    g = Gaussians.from_scene(sc)
+    r = Renderer([cam], tile=tile)
+    st = r.forward(g, w.kind, torch.tensor(w.as_array(), device="cuda"))
+    pairs, fwd_slots, bwd_pixels = r.wsr_count_pairs(st)
+    instances = r.wsr_bin_total()
+    ref = oracle.render(sc, cam, w)["pairs"]
+    assert abs(pairs - ref) <= 1e-3 * ref, (pairs, ref)
+    cap = instances * tile[0] * tile[1]
+    assert pairs <= fwd_slots <= cap and pairs <= bwd_pixels <= cap
+    px = 1 if tile == (8, 8) else 2
+    assert fwd_slots % (32 * px * 2 if tile != (8, 8) else 64) == 0
+    assert bwd_pixels % 2 == 0
