@@ -149,8 +149,7 @@ __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ rec, lon
         s_wend[warp][lane] = winc;
         s_run[warp][lane] = make_int2(row + ta, lo);
         __syncwarp();
-        // tile j of the batch: its counter and the lane (Gaussian) that owns it
-        auto locate = [&](int j, unsigned*& cur, int& owner) {
+        for (int j = lane; j < nt; j += 32) {
             int sl = 0, sh = 31;    // segment: first lane whose inclusive end exceeds j
             while (sl < sh) {
                 const int mid = (sl + sh) >> 1;
@@ -158,33 +157,14 @@ __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ rec, lon
                 else sl = mid + 1;
             }
             const int2 run = s_run[warp][sl];
-            cur = cursor + run.x + (j - (sl ? s_wend[warp][sl - 1] : 0));
-            owner = run.y;
-        };
-        const long long rid0 = (long long)v * n + (long long)blockIdx.x * blockDim.x + warp * 32;
-        if constexpr (SCATTER) {
-            // two tiles per lane and step: both slot claims are in flight before either store waits
-            for (int j = lane; j < nt; j += 64) {
-                unsigned *ca, *cb = nullptr;
-                int oa, ob = 0;
-                locate(j, ca, oa);
-                const bool two = j + 32 < nt;
-                if (two) locate(j + 32, cb, ob);
-                const unsigned sa = atomicAdd(ca, 1u);
-                const unsigned sb = two ? atomicAdd(cb, 1u) : 0u;
-                if (sa < capacity) list[sa] = (unsigned)(rid0 + oa);
+            unsigned* cur = cursor + run.x + (j - (sl ? s_wend[warp][sl - 1] : 0));
+            if constexpr (SCATTER) {
+                const unsigned slot = atomicAdd(cur, 1u);
+                const long long rid = (long long)v * n + (long long)blockIdx.x * blockDim.x + warp * 32 + run.y;
+                if (slot < capacity) list[slot] = (unsigned)rid;
                 else set_error(hdr, WSR_ERR_CAPACITY);
-                if (two) {
-                    if (sb < capacity) list[sb] = (unsigned)(rid0 + ob);
-                    else set_error(hdr, WSR_ERR_CAPACITY);
-                }
-            }
-        } else {
-            for (int j = lane; j < nt; j += 32) {
-                unsigned* c;
-                int o;
-                locate(j, c, o);
-                atomicAdd(c, 1u);
+            } else {
+                atomicAdd(cur, 1u);
             }
         }
         __syncwarp();
