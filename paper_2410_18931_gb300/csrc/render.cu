@@ -132,7 +132,8 @@ __device__ __forceinline__ void fwd_tile(const int tile, const float4* __restric
     const int tid = threadIdx.x;
     const int x0 = tc.tx * TW + (tid % S::BX) * PX;
     const int y0 = tc.ty * TH + (tid / S::BX) * S::PY;
-    // offsets of the block's pixels from the tile's first pixel (a second column is ignored when PX == 1)
+    // offsets of the block's pixels from the tile's first pixel (PX == 1: the first column only, its two
+    // rows paired instead)
     const float2 ox = f2((float)(x0 - tc.tx * TW), (float)(x0 - tc.tx * TW + 1));
     const float oy0 = (float)(y0 - tc.ty * TH), oy1 = oy0 + 1.0f;
 
@@ -197,6 +198,24 @@ __device__ __forceinline__ void fwd_tile(const int tile, const float4* __restric
             const float2 crg = f2(b.z, b.w);
             // q' = r^2 + qd dx^2 with dx = g_x + o_x: qd dx^2 = qd g_x^2 + o_x (2 qd g_x + o_x qd) and
             // r = r_0 + qs o_y + qw o_x from the values at the tile's first pixel centre
+            if constexpr (PX == 1) {
+                // one column, its two rows paired: the same dx, so the same qd dx^2
+                const float P1 = fmaf(ox.x, fmaf(ox.x, t.w, t.z), t.y);
+                const float base = fmaf(a.w, ox.x, t.x);
+                const float2 rr = __ffma2_rn(f2(a.z, a.z), f2(oy0, oy1), f2(base, base));
+                const float2 q = __ffma2_rn(rr, rr, f2(P1, P1));
+                if (q.x <= kQMax) {
+                    const float e = ex2_approx(-q.x);
+                    rg[0][0] = __ffma2_rn(crg, f2(e, e), rg[0][0]);
+                    bd[0][0] = __ffma2_rn(cbuw, f2(e, e), bd[0][0]);
+                }
+                if (q.y <= kQMax) {
+                    const float e = ex2_approx(-q.y);
+                    rg[1][0] = __ffma2_rn(crg, f2(e, e), rg[1][0]);
+                    bd[1][0] = __ffma2_rn(cbuw, f2(e, e), bd[1][0]);
+                }
+                continue;
+            }
             const float2 P = __ffma2_rn(ox, __ffma2_rn(ox, f2(t.w, t.w), f2(t.z, t.z)), f2(t.y, t.y));
             const float rys[2] = {fmaf(a.z, oy0, t.x), fmaf(a.z, oy1, t.x)};
 #pragma unroll
@@ -208,7 +227,7 @@ __device__ __forceinline__ void fwd_tile(const int tile, const float4* __restric
                     rg[r][0] = __ffma2_rn(crg, f2(e, e), rg[r][0]);
                     bd[r][0] = __ffma2_rn(cbuw, f2(e, e), bd[r][0]);
                 }
-                if (PX == 2 && q.y <= kQMax) {
+                if (q.y <= kQMax) {
                     const float e = ex2_approx(-q.y);
                     rg[r][1] = __ffma2_rn(crg, f2(e, e), rg[r][1]);
                     bd[r][1] = __ffma2_rn(cbuw, f2(e, e), bd[r][1]);
