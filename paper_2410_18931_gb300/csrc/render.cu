@@ -291,39 +291,37 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// Backward, one block per tile, balanced over (pixel, Gaussian) pairs.
+// Backward, one block per tile, a group of lanes per Gaussian.
 //
-// For each chunk of up to CH Gaussians of the tile:
+// The tile's pixel terms P = (G/D, -(G.C)/D) sit in shared memory with one
+// zero column past the tile's right edge.  For each chunk of CH Gaussians of
+// the tile:
 //   A. two threads per Gaussian compute, for their half of the tile's rows,
-//      the span of pixels whose centre can lie inside the footprint (the
-//      roots of the quadratic q(dx) = 9 on that row, widened slightly);
-//   B. every span is padded to an even length and cut into units of two
-//      horizontally adjacent pixels; a block scan lays the units of all
-//      Gaussians end to end (Gaussian-major) and each thread writes one byte
-//      per unit (row and column of its first pixel).  A padding pixel lies
-//      outside the footprint or in a zero column of the pixel table, so it
-//      adds nothing;
-//   C. every thread takes an equal slice of the units and walks it two units
-//      (four pixels, one paired FP32 op per quantity and unit) per step,
-//      accumulating the nine record terms of the current Gaussian in
-//      registers; when the Gaussian changes, or at the end of its slice, it
-//      stores them in a (thread, Gaussian) slot.  The only branch in the walk
-//      is that change;
-//   D. thread j sums Gaussian j's slots and adds them to its global record.
+//      the span of pixels whose centre can lie inside the footprint (the roots
+//      of q(dx) = 9 on each row, widened slightly, padded to an even length:
+//      a padding pixel lies in the zero column or outside the footprint), and
+//      the first and last rows with a span;
+//   B. the chunk's Gaussians are ordered by their number of rows, longest
+//      first (a counting sort), and each warp takes the next 32 / L of that
+//      order whenever it is free (a shared counter), so that the groups of a
+//      warp walk for the same number of steps and the warps stay busy;
+//   C. a group of L = TW / 4 consecutive lanes takes one Gaussian at a time and
+//      walks its rows one per step; lane k takes columns start + k + m L
+//      (m = 0..3) of the row, so the lanes of a group read consecutive pixels
+//      of the table (no bank conflicts), four pixels per step from one decode
+//      of the row's span, one paired FP32 op per quantity and two pixels.  The
+//      nine record terms stay in registers until the Gaussian's last row; then
+//      log2(L) shuffle steps sum them over the group and its first lane adds
+//      them to the Gaussian's global record (in the deterministic mode: its
+//      magnitude, then its fixed-point value).  A Gaussian's sums over a tile
+//      are thus formed in one fixed order, whichever group takes it.
 // Every pair is tested against the forward's cutoff (q' <= kQMax, FP32, from
 // the same record values).  The forward forms q' from values at the tile's
 // first pixel centre, the walk from each pixel's own offsets, so a pair
 // within rounding of the cutoff (a tie: its term is e^-4.5 of the
-// Gaussian's peak there) may be counted by one and not the other; making
-// the walk repeat the forward's operations exactly cost 2% of its time.
-// Gaussians per chunk (CH, a template parameter: 128 by default, or 64) and
-// threads per block (2 CH).
-
-template <int TW> struct UnitCode;                    // bits of the column in a unit byte
-template <> struct UnitCode<8> { static constexpr int XB = 3; };
-template <> struct UnitCode<16> { static constexpr int XB = 4; };
-template <> struct UnitCode<32> { static constexpr int XB = 5; };
-
+// Gaussian's peak there) may be counted by one and not the other.
+// Gaussians per chunk (CH, a template parameter: 128 or 64) and threads per
+// block (2 CH).
 template <int TW, int TH, int CH>
 __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restrict__ rec,
                                          const unsigned* __restrict__ offsets, const unsigned* __restrict__ list,
@@ -334,24 +332,21 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
     constexpr int NT = 2 * CH;
     constexpr int NW = NT / 32;
     constexpr int PW = TW + 1;                          // pixel-table row pitch: one zero column
-    constexpr int XB = UnitCode<TW>::XB;
     constexpr int HR = TH / 2;                          // rows per thread in step A
-    constexpr int MAXU = CH * TH * (TW / 2);            // units when every span covers its whole row
-    constexpr int NSLOT = NT + CH;                      // slices touch at most NT + CH (thread, Gaussian) pairs
-    static_assert(NT == 2 * CH && TH % 2 == 0 && ((TH - 1) << XB) < 256 && CH <= 256, "unit encoding");
+    constexpr int L = TW / 4;                           // lanes per Gaussian in step C
+    constexpr int NB = TH + 1;                          // row counts 0 .. TH
+    static_assert(NT == 2 * CH && TH % 2 == 0 && TW % 4 == 0 && 32 % L == 0 && CH <= 256 && TW <= 64, "layout");
     __shared__ float4 spix[PW * TH + 1];        // per pixel: G/D (3), -(G.C)/D; zero column and pad entry
     __shared__ float4 s0[CH];                   // mu_x, mu_y, qs, qw
     __shared__ float4 s1[CH];                   // qd, u w, c_r u w, c_g u w
     __shared__ float2 s2[CH];                   // c_b u w, u w
     __shared__ unsigned sidx[CH];
-    __shared__ unsigned soff[CH + 1];           // first unit of each Gaussian
-    __shared__ unsigned char sunit[MAXU];       // unit: row << XB | column of its first pixel
-    __shared__ float2 sslot[NSLOT][5];          // partial sums per (thread, Gaussian), paired as accumulated
-    __shared__ unsigned char sslotj[NSLOT];     // the Gaussian of each slot (slots are sorted by it)
-    __shared__ unsigned short sfirst[CH];       // first slot of each Gaussian with units
-    __shared__ unsigned short ssbase[NT];
-    __shared__ unsigned swarp[NW];
-    __shared__ unsigned stot[2];                // units and slots of the chunk
+    __shared__ unsigned short sspan[CH][TH];    // per row: first column | units << 8 (a unit: two pixels)
+    __shared__ unsigned char sfirst[CH];        // first row with a span
+    __shared__ unsigned char snst[CH];          // rows from there to the last row with a span
+    __shared__ unsigned char sord[CH];          // the chunk's Gaussians, most rows first
+    __shared__ unsigned shist[NB];
+    __shared__ unsigned snext;                  // the next position of the order a warp takes
     __shared__ float sbg[4][NW];
 
     const TileCoord tc = tile_coord(vs, tile);
@@ -388,14 +383,15 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
     }
 
     const float QM = kQMax * 1.0001f + 1e-4f;
+    const int grp = tid / L, gk = tid % L;             // group and lane within the group
     const unsigned start = offsets[tile], end = offsets[tile + 1];
     for (unsigned base = start; base < end; base += CH) {
         const int cnt = (int)min((unsigned)CH, end - base);
-        __syncthreads();
-        // ---- A: record and the spans of half the rows of Gaussian tid / 2 ----
+        __syncthreads();                                // the previous chunk is done with shared memory
+        if (tid < NB) shist[tid] = 0u;
+        // ---- A: record, spans of half the rows of Gaussian tid / 2, first and last rows ----
         const int gj = tid >> 1, half = tid & 1;
-        unsigned short span[HR];
-        unsigned nunits = 0;
+        int row_lo = TH, row_hi = -1;
         if (gj < cnt) {
             const unsigned r = list[base + gj];
             const float4* pr = rec + 3ull * r;
@@ -416,208 +412,133 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 const int ly = half * HR + k;
                 unsigned short sp = 0;
                 if (ly >= ly_lo && ly <= ly_hi) sp = rs.row(a, QM, x_org, y_org, x_lim, ly);
-                nunits += (unsigned)(sp >> 8);
-                span[k] = sp;
+                sspan[gj][ly] = sp;
+                if (sp >> 8) {
+                    row_lo = min(row_lo, ly);
+                    row_hi = max(row_hi, ly);
+                }
             }
         }
-        // ---- B: block scan of the units (thread order = Gaussian, then half); unit bytes ----
-        unsigned inc = nunits;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const unsigned y = __shfl_up_sync(0xffffffffu, inc, off);
-            if (lane >= off) inc += y;
-        }
-        if (lane == 31) swarp[warp] = inc;
+        row_lo = min(row_lo, __shfl_xor_sync(0xffffffffu, row_lo, 1));      // the two halves of a Gaussian
+        row_hi = max(row_hi, __shfl_xor_sync(0xffffffffu, row_hi, 1));
+        const int nst = row_hi >= row_lo ? row_hi - row_lo + 1 : 0;
         __syncthreads();
-        unsigned wbase = 0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) wbase += (w < warp) ? swarp[w] : 0u;
-        const unsigned ex = wbase + inc - nunits;
-        if (gj < cnt) {
-            if (half == 0) soff[gj] = ex;
-            unsigned k = ex;
-#pragma unroll
-            for (int r = 0; r < HR; ++r) {
-                const unsigned sp = span[r];
-                const unsigned code = ((unsigned)(half * HR + r) << XB) | (sp & 0xffu);
-                for (unsigned u = 0; u < (sp >> 8); ++u) sunit[k++] = (unsigned char)(code + 2u * u);
-            }
+        // ---- B: the chunk's order, most rows first (rank within the bucket from the count) ----
+        unsigned rank = 0;
+        if (gj < cnt && half == 0) {
+            sfirst[gj] = (unsigned char)max(row_lo, 0);
+            snst[gj] = (unsigned char)nst;
+            rank = atomicAdd(&shist[nst], 1u);
         }
-        if (tid == NT - 1) {
-            soff[cnt] = wbase + inc;
-            stot[0] = wbase + inc;
+        if (tid == 0) snext = 0u;
+        __syncthreads();
+        if (gj < cnt && half == 0) {
+            unsigned at = rank;
+#pragma unroll
+            for (int c = NB - 1; c > 0; --c) at += c > nst ? shist[c] : 0u;
+            sord[at] = (unsigned char)gj;
         }
         __syncthreads();
-        // ---- C: an equal slice of the units per thread ----
-        const unsigned total = stot[0];
-        const unsigned u0 = (unsigned)(((unsigned long long)tid * total) / NT);
-        const unsigned u1 = (unsigned)(((unsigned long long)(tid + 1) * total) / NT);
-        // owner(u): the last Gaussian whose first unit is <= u
-        auto owner = [&](unsigned u) {
-            int lo = 0, hi = cnt - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (soff[mid] <= u) lo = mid;
-                else hi = mid - 1;
-            }
-            return lo;
-        };
-        int j = 0, jlast = -1;
-        if (u0 < u1) {
-            j = owner(u0);
-            jlast = owner(u1 - 1);
-        }
-        {
-            // slots: a block scan of the number of Gaussians each slice touches
-            const unsigned nslot = (unsigned)(jlast - j + 1);
-            unsigned sinc = nslot;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const unsigned y = __shfl_up_sync(0xffffffffu, sinc, off);
-                if (lane >= off) sinc += y;
-            }
-            if (lane == 31) swarp[warp] = sinc;      // step B's reads of swarp ended at the last barrier
-            __syncthreads();
-            unsigned sb = 0;
-#pragma unroll
-            for (int w = 0; w < NW; ++w) sb += (w < warp) ? swarp[w] : 0u;
-            const unsigned b0 = sb + sinc - nslot;
-            ssbase[tid] = (unsigned short)b0;
-            for (unsigned k = 0; k < nslot; ++k) sslotj[b0 + k] = (unsigned char)(j + (int)k);
-            // a Gaussian's first slot belongs to the slice holding its first unit
-            if (nslot > 0u) {
-                if (soff[j] == u0) sfirst[j] = (unsigned short)b0;
-                for (unsigned k = 1; k < nslot; ++k) sfirst[j + (int)k] = (unsigned short)(b0 + k);
-            }
-            if (tid == NT - 1) stot[1] = sb + sinc;
-        }
-        if (u0 < u1) {
-            int slot = ssbase[tid];
-            // per-Gaussian constants as float2 pairs (refreshed when the Gaussian changes)
-            float2 nmx, qs2, qw2, qd2, cw0, cw1;
-            float gy0;
-            unsigned uend = 0;
-            auto load_gaussian = [&](int jj) {
-                const float4 a = s0[jj], b = s1[jj];
-                const float2 c2 = s2[jj];
-                const float gx0 = (float)x_org + 0.5f - a.x;            // dx of column 0
-                nmx = f2(gx0, gx0 + 1.0f);
-                gy0 = (float)y_org + 0.5f - a.y;                        // dy of row 0
-                qs2 = f2(a.z, a.z);
-                qw2 = f2(a.w, a.w);
-                qd2 = f2(b.x, b.x);
-                cw0 = f2(-kLn2 * b.z, -kLn2 * b.w);    // -ln2 (c u w, u w): dL/dq' = e * (P . cw)
-                cw1 = f2(-kLn2 * c2.x, -kLn2 * c2.y);
-                uend = soff[jj + 1];
-            };
-            load_gaussian(j);
-            // accumulators, paired: (cuw_r, cuw_g), (cuw_b, uw); and, over the two pixels of a unit, the
+        // ---- C: a group per Gaussian; each warp takes the next 32 / L Gaussians of the order ----
+        constexpr int GW = 32 / L;                      // groups per warp
+        for (;;) {
+            unsigned at0 = 0;
+            if (lane == 0) at0 = atomicAdd(&snext, (unsigned)GW);
+            at0 = __shfl_sync(0xffffffffu, at0, 0);
+            if (at0 >= (unsigned)cnt) break;
+            const int so = (int)at0 + (grp % GW);
+            const bool act = so < cnt;
+            const int j = act ? (int)sord[so] : 0;
+            const int steps = act ? (int)snst[j] : 0;
+            const int r0 = act ? (int)sfirst[j] : 0;
+            const float4 a = s0[j], b = s1[j];
+            const float2 c2 = s2[j];
+            const float gx0 = (float)x_org + 0.5f - a.x;                 // dx of column 0
+            const float gy0 = (float)y_org + 0.5f - a.y;                 // dy of row 0
+            const float2 qs2 = f2(a.z, a.z), qw2 = f2(a.w, a.w), qd2 = f2(b.x, b.x), gx2 = f2(gx0, gx0);
+            const float2 cw0 = f2(-kLn2 * b.z, -kLn2 * b.w);     // -ln2 (c u w, u w): dL/dq' = e * (P . cw)
+            const float2 cw1 = f2(-kLn2 * c2.x, -kLn2 * c2.y);
+            // accumulators, paired: (cuw_r, cuw_g), (cuw_b, uw); and, over the two columns of a row, the
             // moments of gq = dL/dq' in the record's own frame (r = qs dy + qw dx, dx):
             // sum gq r^2, sum gq r dx, sum gq dx^2, sum gq r, sum gq dx.  Kept apart, a thin
             // footprint's small along-axis terms (dx) are not rounded away under its large r terms.
             float2 g01 = f2(0.f, 0.f), g23 = f2(0.f, 0.f);
             float2 srr = f2(0.f, 0.f), srx = srr, sxx = srr, sr = srr, sx = srr;
-            auto store_slot = [&](int sl) {
-                sslot[sl][0] = g01;
-                sslot[sl][1] = g23;
-                sslot[sl][2] = f2(srr.x + srr.y, sxx.x + sxx.y);
-                sslot[sl][3] = f2(sr.x + sr.y, sx.x + sx.y);
-                sslot[sl][4] = f2(srx.x + srx.y, 0.f);
-            };
-            // one or two units per step: two independent chains overlap their latencies; the second
-            // unit is masked out (e = 0) when it lies past the slice or the current Gaussian
-            auto unit_terms = [&](unsigned d, bool valid) {
-                const int x = (int)(d & ((1u << XB) - 1u)), ly = (int)(d >> XB);
-                const int pi = ly * PW + x;
-                const float4 P0 = spix[pi];
-                const float4 P1 = spix[pi + 1];
-                const float xf = (float)x, dy = (float)ly + gy0;
-                const float2 dx = __fadd2_rn(f2(xf, xf), nmx);
-                const float2 dy2 = f2(dy, dy);
-                const float2 rr = __ffma2_rn(qs2, dy2, __fmul2_rn(qw2, dx));        // the forward's arithmetic
-                const float2 q = __ffma2_rn(rr, rr, __fmul2_rn(__fmul2_rn(qd2, dx), dx));
-                const float e0 = ex2_approx((valid && q.x <= kQMax) ? -q.x : -256.0f);  // 2^-256 flushes to 0
-                const float e1 = ex2_approx((valid && q.y <= kQMax) ? -q.y : -256.0f);
-                // d/d(c u w) and d/d(u w) at fixed c u w
-                g01 = __ffma2_rn(f2(P0.x, P0.y), f2(e0, e0), g01);
-                g23 = __ffma2_rn(f2(P0.z, P0.w), f2(e0, e0), g23);
-                g01 = __ffma2_rn(f2(P1.x, P1.y), f2(e1, e1), g01);
-                g23 = __ffma2_rn(f2(P1.z, P1.w), f2(e1, e1), g23);
-                // dL/dq' per pixel: e * (P . cw)
-                const float2 m0 = __ffma2_rn(f2(P0.z, P0.w), cw1, __fmul2_rn(f2(P0.x, P0.y), cw0));
-                const float2 m1 = __ffma2_rn(f2(P1.z, P1.w), cw1, __fmul2_rn(f2(P1.x, P1.y), cw0));
-                const float2 gq = __fmul2_rn(f2(e0, e1), f2(m0.x + m0.y, m1.x + m1.y));
-                const float2 tr = __fmul2_rn(gq, rr), tx = __fmul2_rn(gq, dx);
-                srr = __ffma2_rn(tr, rr, srr);
-                srx = __ffma2_rn(tr, dx, srx);
-                sxx = __ffma2_rn(tx, dx, sxx);
-                sr = __fadd2_rn(sr, tr);
-                sx = __fadd2_rn(sx, tx);
-            };
-            for (unsigned u = u0; u < u1;) {
-                if (u == uend) {
-                    // the next Gaussian with units: store this one's sums, zero slots for any between
-                    store_slot(slot++);
-                    g01 = g23 = srr = srx = sxx = sr = sx = f2(0.f, 0.f);
-                    ++j;
-                    while (soff[j + 1] <= u) {
+            // dx of this lane's four offsets in a span (k + m L) from the span's first column, less that column
+            const float2 gxo[2] = {__fadd2_rn(f2((float)gk, (float)(gk + L)), gx2),
+                                   __fadd2_rn(f2((float)(gk + 2 * L), (float)(gk + 3 * L)), gx2)};
+            for (int st = 0; st < steps; ++st) {
+                const int ly = r0 + st;
+                const unsigned sp = sspan[j][ly];
+                const int xs = (int)(sp & 0xffu);
+                const int rowb = ly * PW, cb = rowb + xs, ce = rowb + TW;
+                const float xsf = (float)xs;
+                const float dyf = (float)ly + gy0;
+                const float2 dy2 = f2(dyf, dyf);
 #pragma unroll
-                        for (int c = 0; c < 5; ++c) sslot[slot][c] = f2(0.f, 0.f);
-                        ++slot;
-                        ++j;
-                    }
-                    load_gaussian(j);
+                for (int m = 0; m < 2; ++m) {
+                    // Columns past the span evaluate q > 9 (the span holds every pixel centre of the row with
+                    // q' <= kQMax, with a margin), so the cutoff test zeroes them; columns past the tile read
+                    // the zero column.  No per-pixel validity mask is needed.
+                    const float4 P0 = spix[min(cb + gk + 2 * m * L, ce)];
+                    const float4 P1 = spix[min(cb + gk + (2 * m + 1) * L, ce)];
+                    const float2 dx = __fadd2_rn(f2(xsf, xsf), gxo[m]);
+                    const float2 rr = __ffma2_rn(qs2, dy2, __fmul2_rn(qw2, dx));        // the forward's arithmetic
+                    const float2 q = __ffma2_rn(rr, rr, __fmul2_rn(__fmul2_rn(qd2, dx), dx));
+                    const float e0 = ex2_approx(q.x <= kQMax ? -q.x : -256.0f);          // 2^-256 flushes to 0
+                    const float e1 = ex2_approx(q.y <= kQMax ? -q.y : -256.0f);
+                    // d/d(c u w) and d/d(u w) at fixed c u w
+                    g01 = __ffma2_rn(f2(P0.x, P0.y), f2(e0, e0), g01);
+                    g23 = __ffma2_rn(f2(P0.z, P0.w), f2(e0, e0), g23);
+                    g01 = __ffma2_rn(f2(P1.x, P1.y), f2(e1, e1), g01);
+                    g23 = __ffma2_rn(f2(P1.z, P1.w), f2(e1, e1), g23);
+                    // dL/dq' per pixel: e * (P . cw)
+                    const float2 m0 = __ffma2_rn(f2(P0.z, P0.w), cw1, __fmul2_rn(f2(P0.x, P0.y), cw0));
+                    const float2 m1 = __ffma2_rn(f2(P1.z, P1.w), cw1, __fmul2_rn(f2(P1.x, P1.y), cw0));
+                    const float2 gq = __fmul2_rn(f2(e0, e1), f2(m0.x + m0.y, m1.x + m1.y));
+                    const float2 tr = __fmul2_rn(gq, rr), tx = __fmul2_rn(gq, dx);
+                    srr = __ffma2_rn(tr, rr, srr);
+                    srx = __ffma2_rn(tr, dx, srx);
+                    sxx = __ffma2_rn(tx, dx, sxx);
+                    sr = __fadd2_rn(sr, tr);
+                    sx = __fadd2_rn(sx, tx);
                 }
-                const bool two = u + 1 < min(u1, uend);
-                const unsigned d0 = sunit[u];
-                const unsigned d1 = sunit[two ? u + 1 : u];
-                unit_terms(d0, true);
-                unit_terms(d1, two);
-                u += two ? 2u : 1u;
             }
-            store_slot(slot);
-        }
-        __syncthreads();
-        // ---- D: totals of Gaussian tid to its global record ----
-        // the slots are sorted by Gaussian, so Gaussian tid's slots are a run
-        if (tid < cnt && soff[tid + 1] > soff[tid]) {
-            const int nslots = (int)stot[1];
-            const int lo = sfirst[tid];
-            float2 v01 = f2(0.f, 0.f), v23 = f2(0.f, 0.f), vrx = f2(0.f, 0.f), vm = f2(0.f, 0.f);
-            float vc = 0.f;
-            for (int t = lo; t < nslots && (int)sslotj[t] == tid; ++t) {
-                v01 = __fadd2_rn(v01, sslot[t][0]);
-                v23 = __fadd2_rn(v23, sslot[t][1]);
-                vrx = __fadd2_rn(vrx, sslot[t][2]);
-                vm = __fadd2_rn(vm, sslot[t][3]);
-                vc += sslot[t][4].x;
-            }
-            // record: sum gq r, sum gq dx, sum gq r^2, sum gq r dx, sum gq dx^2, d/d(u w), d/d(c u w)
-            if (pass == 0) {
-                float4* o = reinterpret_cast<float4*>(grec + (size_t)WSR_GRAD_RECORD_FLOATS * sidx[tid]);
-                atomicAdd(o, make_float4(vm.x, vm.y, vrx.x, vc));
-                atomicAdd(o + 1, make_float4(vrx.y, v23.y, v01.x, v01.y));
-                atomicAdd(reinterpret_cast<float*>(o + 2), v23.x);
-            } else {
-                // deterministic mode: a 128-byte record holds 9 int64 sums, then 9 magnitudes (float bits)
-                const float vals[9] = {vm.x, vm.y, vrx.x, vc, vrx.y, v23.y, v01.x, v01.y, v23.x};
-                float* o = grec + (size_t)kDetRecordFloats * sidx[tid];
-                int* mag = reinterpret_cast<int*>(o + 18);
-                if (pass == 1) {
-                    // the largest |partial| of each term (non-negative floats order as their bit patterns)
+            // the group's sums: record order sum gq r, sum gq dx, sum gq r^2, sum gq r dx, sum gq dx^2,
+            // d/d(u w), d/d(c u w)
+            float vals[9] = {sr.x + sr.y, sx.x + sx.y, srr.x + srr.y, srx.x + srx.y, sxx.x + sxx.y,
+                             g23.y, g01.x, g01.y, g23.x};
+            __syncwarp();
 #pragma unroll
-                    for (int c = 0; c < 9; ++c) atomicMax(mag + c, __float_as_int(fabsf(vals[c])));
+            for (int off = L / 2; off > 0; off >>= 1)
+#pragma unroll
+                for (int c = 0; c < 9; ++c) vals[c] += __shfl_xor_sync(0xffffffffu, vals[c], off);
+            if (act && gk == 0 && steps > 0) {
+                if (pass == 0) {
+                    float4* o = reinterpret_cast<float4*>(grec + (size_t)WSR_GRAD_RECORD_FLOATS * sidx[j]);
+                    atomicAdd(o, make_float4(vals[0], vals[1], vals[2], vals[3]));
+                    atomicAdd(o + 1, make_float4(vals[4], vals[5], vals[6], vals[7]));
+                    atomicAdd(reinterpret_cast<float*>(o + 2), vals[8]);
                 } else {
-                    // each partial as fixed point with kDetBits bits below that magnitude: exact integer sums
-                    unsigned long long* sum = reinterpret_cast<unsigned long long*>(o);
+                    // deterministic mode: a 128-byte record holds 9 int64 sums, then 9 magnitudes (float bits)
+                    float* o = grec + (size_t)kDetRecordFloats * sidx[j];
+                    int* mag = reinterpret_cast<int*>(o + 18);
+                    if (pass == 1) {
+                        // the largest |partial| of each term (non-negative floats order as their bit patterns)
 #pragma unroll
-                    for (int c = 0; c < 9; ++c) {
-                        const float m = __int_as_float(mag[c]);
-                        if (m > 0.0f) {
-                            int e;
-                            frexpf(m, &e);                  // m < 2^e
-                            const long long q = __double2ll_rn(ldexp((double)vals[c], kDetBits - e));
-                            atomicAdd(sum + c, (unsigned long long)q);
+                        for (int c = 0; c < 9; ++c) atomicMax(mag + c, __float_as_int(fabsf(vals[c])));
+                    } else {
+                        // each partial as fixed point with kDetBits bits below that magnitude: exact integer sums
+                        unsigned long long* sum = reinterpret_cast<unsigned long long*>(o);
+#pragma unroll
+                        for (int c = 0; c < 9; ++c) {
+                            const float m = __int_as_float(mag[c]);
+                            if (m > 0.0f) {
+                                int e;
+                                frexpf(m, &e);                  // m < 2^e
+                                const long long q = __double2ll_rn(ldexp((double)vals[c], kDetBits - e));
+                                atomicAdd(sum + c, (unsigned long long)q);
+                            }
                         }
                     }
                 }
