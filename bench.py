@@ -964,7 +964,7 @@ def main():
     ap.add_argument("--workload", type=int, default=3)
     ap.add_argument("--tile", default="auto", help="WxH (16x16, 8x8, 32x8, 16x8) or auto")
     ap.add_argument("--schedule", default="auto", choices=["auto", "per-tile", "persistent"])
-    ap.add_argument("--chunk", default="auto", choices=["auto", "128", "64"],
+    ap.add_argument("--chunk", default="auto", choices=["auto", "128", "64", "256"],
                     help="Gaussians per block of the backward")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")

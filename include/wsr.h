@@ -135,9 +135,10 @@ enum {
  * that order through a counter in the workspace; the same workspace and tiles
  * must then be passed to wsr_bin and the renderers.  `chunk` is how many of a
  * tile's Gaussians one block of wsr_render_bwd takes at a time (two threads
- * per Gaussian): 0 for the default 128, or 64 (blocks of 128 threads, twice as
- * many resident); other values return WSR_ERR_UNSUPPORTED.  It changes the
- * schedule only, not the result beyond rounding order.
+ * per Gaussian): 0 for the default 128, 64 (blocks of 128 threads, twice as
+ * many resident) or 256 (blocks of 512 threads, half as many); other values
+ * return WSR_ERR_UNSUPPORTED.  It changes the schedule only, not the result
+ * beyond rounding order.
  *
  * `deterministic` = 1 makes every result bitwise reproducible from run to run
  * for the same inputs and tiles (0, the default, lets the order of atomics
@@ -157,7 +158,7 @@ enum {
 typedef struct {
     int32_t tile_w, tile_h;
     int32_t schedule;            /* WSR_SCHEDULE_* */
-    int32_t chunk;               /* Gaussians per backward block: 0 (128) or 64 */
+    int32_t chunk;               /* Gaussians per backward block: 0 (128), 64 or 256 */
     int32_t deterministic;       /* 0, or 1: bitwise-reproducible results */
 } wsr_tiles;
 

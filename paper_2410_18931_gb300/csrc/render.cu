@@ -636,6 +636,8 @@ cudaError_t bwd_t(const float* rec, const unsigned* off, const unsigned* list, c
                   float* bg_tiles, Sched sched, cudaStream_t s) {
     if (vs.chunk == 64)
         return bwd_chunk<TW, TH, 64>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sched, s);
+    if (vs.chunk == 256)
+        return bwd_chunk<TW, TH, 256>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sched, s);
     return bwd_chunk<TW, TH, 128>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sched, s);
 }
 

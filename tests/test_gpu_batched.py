@@ -81,22 +81,23 @@ def test_autotune_returns_a_measured_valid_choice():
     npix = sum(c.width * c.height for c in cams)
     target = torch.rand(npix, 3, device="cuda")
     res = autotune(g, cams, w.kind, wpar, target, reps=2)
-    assert len(res["table"]) == 16 and all(t["ok"] for t in res["table"])      # 4 shapes x 2 schedules x 2 chunks
-    assert res["chunk"] in (64, 128)
+    assert len(res["table"]) == 24 and all(t["ok"] for t in res["table"])      # 4 shapes x 2 schedules x 3 chunks
+    assert res["chunk"] in (64, 128, 256)
     assert res["ms"] == min(t["ms"] for t in res["table"])
     assert autotune(g, cams, w.kind, wpar, target) is res      # cached
 
 
+@pytest.mark.parametrize("chunk", [64, 256])
 @pytest.mark.parametrize("tile,persistent", [((16, 16), False), ((32, 8), True), ((8, 8), True)])
-def test_backward_with_64_gaussians_per_block_matches_oracle(tile, persistent):
+def test_backward_with_64_or_256_gaussians_per_block_matches_oracle(tile, persistent, chunk):
     """The backward's chunk size changes only the schedule: gradients with 64
-    Gaussians per block against the oracle (summed over the views)."""
+    or 256 Gaussians per block against the oracle (summed over the views)."""
     import torch
     from paper_2410_18931_gb300 import Gaussians, Renderer
     sc, cams, w = _scene_and_views()
     g = Gaussians.from_scene(sc)
     wpar = torch.tensor(w.as_array(), device="cuda")
-    r = Renderer(cams, tile=tile, persistent=persistent, chunk=64)
+    r = Renderer(cams, tile=tile, persistent=persistent, chunk=chunk)
     st = r.forward(g, w.kind, wpar)
     rng = np.random.default_rng(9)
     Gs = [rng.normal(size=(c.height, c.width, 3)).astype(np.float32) for c in cams]
