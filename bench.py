@@ -528,8 +528,10 @@ def run_ours(args):
             roof["frac_at_measured_clock"] = round(ach / (peak * float(clk["sm_mhz"]) / SM_MAX_MHZ), 4)
         if kern == "k_render_bwd":
             # what bounds it (from the kernel's ncu capture): not FP32 throughput
-            roof["note"] = ("limited by the shared-memory pipe (~0.84 wavefronts per SM-cycle of 1, about half "
-                            "of them bank conflicts from random per-lane pixel loads) and by issue (~73%)")
+            roof["note"] = ("bound by issue (~66% active) and the FMA pipe (~61% busy) at 32 resident warps per SM "
+                            "(64 registers); about 30% of its pixel slots lie past a row's span (four columns of "
+                            "four lanes per row against spans of ~11 pixels), and 29% of its shared-memory "
+                            "wavefronts are bank conflicts")
     else:
         roof = {"bound": "hbm", "kernel": names[dom], "achieved": None, "peak": None, "unit": "GB/s",
                 "frac": None, "traffic": None}
