@@ -454,8 +454,10 @@ wsr_status wsr_bin_static(const float* records, int64_t n, const wsr_camera* cam
  *   [1] (pixel, Gaussian) slots wsr_render_fwd evaluates: for each Gaussian of
  *       a tile, the pixels of every warp whose region of the tile its footprint
  *       reaches (the forward tests q at each of them);
- *   [2] pixels the backward walks: each footprint row's span within a tile,
- *       padded to an even length.
+ *   [2] (pixel, Gaussian) slots wsr_render_bwd evaluates: for each Gaussian
+ *       of a tile, the rows from its first span to its last, each of tile
+ *       width columns, or of half the tile width when none of its row spans
+ *       is longer than that.
  * Arguments as for wsr_render_fwd.  Not part of a timed step.
  */
 wsr_status wsr_count_pairs(const float* records, int64_t n, const uint32_t* tile_offsets,

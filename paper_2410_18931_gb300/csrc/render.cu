@@ -37,20 +37,11 @@ __device__ __forceinline__ TileCoord tile_coord(const Views& vs, int tile) {
     return t;
 }
 
-__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-
-// Hardware square root and reciprocal (relative error ~2^-22), for the
-// backward's per-row spans: they are widened by 0.02 pixel, far above that.
-__device__ __forceinline__ float sqrt_approx(float x) {
-    float y;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float rcp_approx(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
+// A lane count as a type, to instantiate one walk of the backward per group size.
+template <int N>
+struct Lanes {
+    static constexpr int value = N;
+};
 
 // The backward's pixel spans of one record on the rows of a tile: on row y the
 // footprint q' <= QM is mu_x + c(dy) +- h(dy) with the conic entries
@@ -301,20 +292,23 @@ __device__ __forceinline__ float warp_sum(float v) {
 //      of q(dx) = 9 on each row, widened slightly, padded to an even length:
 //      a padding pixel lies in the zero column or outside the footprint), and
 //      the first and last rows with a span;
-//   B. the chunk's Gaussians are ordered by their number of rows, longest
-//      first (a counting sort), and each warp takes the next 32 / L of that
-//      order whenever it is free (a shared counter), so that the groups of a
-//      warp walk for the same number of steps and the warps stay busy;
-//   C. a group of L = TW / 4 consecutive lanes takes one Gaussian at a time and
-//      walks its rows one per step; lane k takes columns start + k + m L
-//      (m = 0..3) of the row, so the lanes of a group read consecutive pixels
-//      of the table (no bank conflicts), four pixels per step from one decode
-//      of the row's span, one paired FP32 op per quantity and two pixels.  The
-//      nine record terms stay in registers until the Gaussian's last row; then
-//      log2(L) shuffle steps sum them over the group and its first lane adds
-//      them to the Gaussian's global record (in the deterministic mode: its
-//      magnitude, then its fixed-point value).  A Gaussian's sums over a tile
-//      are thus formed in one fixed order, whichever group takes it.
+//   B. the chunk's Gaussians are ordered wide ones first (a row span longer
+//      than TW / 2 pixels), each class by its number of rows, longest first
+//      (a counting sort); each warp takes the next Gaussians of a class
+//      whenever it is free (a shared counter per class), so that the groups
+//      of a warp walk for the same number of steps and the warps stay busy;
+//   C. a group of L consecutive lanes takes one Gaussian at a time and walks
+//      its rows one per step, L = TW / 4 for the wide class and TW / 8 for
+//      the narrow one (whose spans all fit in 4 L columns); lane k takes
+//      columns start + k + m L (m = 0..3) of the row, so the lanes of a group
+//      read consecutive pixels of the table (no bank conflicts), four pixels
+//      per step from one decode of the row's span, one paired FP32 op per
+//      quantity and two pixels.  The nine record terms stay in registers
+//      until the Gaussian's last row; then log2(L) shuffle steps sum them
+//      over the group and its first lane adds them to the Gaussian's global
+//      record (in the deterministic mode: its magnitude, then its fixed-point
+//      value).  A Gaussian's sums over a tile are thus formed in one fixed
+//      order, whichever group takes it.
 // Every pair is tested against the forward's cutoff (q' <= kQMax, FP32, from
 // the same record values).  The forward forms q' from values at the tile's
 // first pixel centre, the walk from each pixel's own offsets, so a pair
@@ -333,9 +327,9 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
     constexpr int NW = NT / 32;
     constexpr int PW = TW + 1;                          // pixel-table row pitch: one zero column
     constexpr int HR = TH / 2;                          // rows per thread in step A
-    constexpr int L = TW / 4;                           // lanes per Gaussian in step C
     constexpr int NB = TH + 1;                          // row counts 0 .. TH
-    static_assert(NT == 2 * CH && TH % 2 == 0 && TW % 4 == 0 && 32 % L == 0 && CH <= 256 && TW <= 64, "layout");
+    constexpr int NK = 2 * NB;                          // sort keys: narrow 0 .. TH, wide NB .. NB + TH
+    static_assert(NT == 2 * CH && TH % 2 == 0 && TW % 8 == 0 && TW <= 64 && CH <= 256 && NK <= NT, "layout");
     __shared__ float4 spix[PW * TH + 1];        // per pixel: G/D (3), -(G.C)/D; zero column and pad entry
     __shared__ float4 s0[CH];                   // mu_x, mu_y, qs, qw
     __shared__ float4 s1[CH];                   // qd, u w, c_r u w, c_g u w
@@ -344,9 +338,10 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
     __shared__ unsigned short sspan[CH][TH];    // per row: first column | units << 8 (a unit: two pixels)
     __shared__ unsigned char sfirst[CH];        // first row with a span
     __shared__ unsigned char snst[CH];          // rows from there to the last row with a span
-    __shared__ unsigned char sord[CH];          // the chunk's Gaussians, most rows first
-    __shared__ unsigned shist[NB];
-    __shared__ unsigned snext;                  // the next position of the order a warp takes
+    __shared__ unsigned char sord[CH];          // the chunk's Gaussians: wide ones first, most rows first
+    __shared__ unsigned shist[NK];
+    __shared__ unsigned snext[2];               // per class: the next position of the order a warp takes
+    __shared__ unsigned snwide;                 // wide Gaussians in the chunk
     __shared__ float sbg[4][NW];
 
     const TileCoord tc = tile_coord(vs, tile);
@@ -383,15 +378,14 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
     }
 
     const float QM = kQMax * 1.0001f + 1e-4f;
-    const int grp = tid / L, gk = tid % L;             // group and lane within the group
     const unsigned start = offsets[tile], end = offsets[tile + 1];
     for (unsigned base = start; base < end; base += CH) {
         const int cnt = (int)min((unsigned)CH, end - base);
         __syncthreads();                                // the previous chunk is done with shared memory
-        if (tid < NB) shist[tid] = 0u;
+        if (tid < NK) shist[tid] = 0u;
         // ---- A: record, spans of half the rows of Gaussian tid / 2, first and last rows ----
         const int gj = tid >> 1, half = tid & 1;
-        int row_lo = TH, row_hi = -1;
+        int row_lo = TH, row_hi = -1, umax = 0;
         if (gj < cnt) {
             const unsigned r = list[base + gj];
             const float4* pr = rec + 3ull * r;
@@ -416,134 +410,150 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 if (sp >> 8) {
                     row_lo = min(row_lo, ly);
                     row_hi = max(row_hi, ly);
+                    umax = max(umax, sp >> 8);
                 }
             }
         }
         row_lo = min(row_lo, __shfl_xor_sync(0xffffffffu, row_lo, 1));      // the two halves of a Gaussian
         row_hi = max(row_hi, __shfl_xor_sync(0xffffffffu, row_hi, 1));
+        umax = max(umax, __shfl_xor_sync(0xffffffffu, umax, 1));
         const int nst = row_hi >= row_lo ? row_hi - row_lo + 1 : 0;
+        const int key = nst + (2 * umax > TW / 2 ? NB : 0);     // wide: a span longer than TW / 2 pixels
         __syncthreads();
-        // ---- B: the chunk's order, most rows first (rank within the bucket from the count) ----
+        // ---- B: the chunk's order, wide first, most rows first (rank within the bucket from the count) ----
         unsigned rank = 0;
         if (gj < cnt && half == 0) {
             sfirst[gj] = (unsigned char)max(row_lo, 0);
             snst[gj] = (unsigned char)nst;
-            rank = atomicAdd(&shist[nst], 1u);
+            rank = atomicAdd(&shist[key], 1u);
         }
-        if (tid == 0) snext = 0u;
+        if (tid < 2) snext[tid] = 0u;
         __syncthreads();
         if (gj < cnt && half == 0) {
             unsigned at = rank;
 #pragma unroll
-            for (int c = NB - 1; c > 0; --c) at += c > nst ? shist[c] : 0u;
+            for (int c = NK - 1; c > 0; --c) at += c > key ? shist[c] : 0u;
             sord[at] = (unsigned char)gj;
         }
+        if (tid == 0) {
+            unsigned nw = 0;
+#pragma unroll
+            for (int c = NB; c < NK; ++c) nw += shist[c];
+            snwide = nw;
+        }
         __syncthreads();
-        // ---- C: a group per Gaussian; each warp takes the next 32 / L Gaussians of the order ----
-        constexpr int GW = 32 / L;                      // groups per warp
-        for (;;) {
-            unsigned at0 = 0;
-            if (lane == 0) at0 = atomicAdd(&snext, (unsigned)GW);
-            at0 = __shfl_sync(0xffffffffu, at0, 0);
-            if (at0 >= (unsigned)cnt) break;
-            const int so = (int)at0 + (grp % GW);
-            const bool act = so < cnt;
-            const int j = act ? (int)sord[so] : 0;
-            const int steps = act ? (int)snst[j] : 0;
-            const int r0 = act ? (int)sfirst[j] : 0;
-            const float4 a = s0[j], b = s1[j];
-            const float2 c2 = s2[j];
-            const float gx0 = (float)x_org + 0.5f - a.x;                 // dx of column 0
-            const float gy0 = (float)y_org + 0.5f - a.y;                 // dy of row 0
-            const float2 qs2 = f2(a.z, a.z), qw2 = f2(a.w, a.w), qd2 = f2(b.x, b.x), gx2 = f2(gx0, gx0);
-            const float2 cw0 = f2(-kLn2 * b.z, -kLn2 * b.w);     // -ln2 (c u w, u w): dL/dq' = e * (P . cw)
-            const float2 cw1 = f2(-kLn2 * c2.x, -kLn2 * c2.y);
-            // accumulators, paired: (cuw_r, cuw_g), (cuw_b, uw); and, over the two columns of a row, the
-            // moments of gq = dL/dq' in the record's own frame (r = qs dy + qw dx, dx):
-            // sum gq r^2, sum gq r dx, sum gq dx^2, sum gq r, sum gq dx.  Kept apart, a thin
-            // footprint's small along-axis terms (dx) are not rounded away under its large r terms.
-            float2 g01 = f2(0.f, 0.f), g23 = f2(0.f, 0.f);
-            float2 srr = f2(0.f, 0.f), srx = srr, sxx = srr, sr = srr, sx = srr;
-            // dx of this lane's four offsets in a span (k + m L) from the span's first column, less that column
-            const float2 gxo[2] = {__fadd2_rn(f2((float)gk, (float)(gk + L)), gx2),
-                                   __fadd2_rn(f2((float)(gk + 2 * L), (float)(gk + 3 * L)), gx2)};
-            for (int st = 0; st < steps; ++st) {
-                const int ly = r0 + st;
-                const unsigned sp = sspan[j][ly];
-                const int xs = (int)(sp & 0xffu);
-                const int rowb = ly * PW, cb = rowb + xs, ce = rowb + TW;
-                const float xsf = (float)xs;
-                const float dyf = (float)ly + gy0;
-                const float2 dy2 = f2(dyf, dyf);
+        // ---- C: a group per Gaussian; each warp takes the next 32 / L Gaussians of a class ----
+        const int nwide = (int)snwide;
+        auto walk = [&](auto lanes, const int lo, const int hi, unsigned* next) {
+            constexpr int L = decltype(lanes)::value;
+            constexpr int GW = 32 / L;                  // groups per warp
+            const int grp = lane / L, gk = lane % L;    // group and lane within the group
+            for (;;) {
+                unsigned at0 = 0;
+                if (lane == 0) at0 = atomicAdd(next, (unsigned)GW);
+                at0 = __shfl_sync(0xffffffffu, at0, 0);
+                if (lo + (int)at0 >= hi) break;
+                const int so = lo + (int)at0 + grp;
+                const bool act = so < hi;
+                const int j = act ? (int)sord[so] : 0;
+                const int steps = act ? (int)snst[j] : 0;
+                const int r0 = act ? (int)sfirst[j] : 0;
+                const float4 a = s0[j], b = s1[j];
+                const float2 c2 = s2[j];
+                const float gx0 = (float)x_org + 0.5f - a.x;                 // dx of column 0
+                const float gy0 = (float)y_org + 0.5f - a.y;                 // dy of row 0
+                const float2 qs2 = f2(a.z, a.z), qw2 = f2(a.w, a.w), qd2 = f2(b.x, b.x), gx2 = f2(gx0, gx0);
+                const float2 cw0 = f2(-kLn2 * b.z, -kLn2 * b.w);     // -ln2 (c u w, u w): dL/dq' = e * (P . cw)
+                const float2 cw1 = f2(-kLn2 * c2.x, -kLn2 * c2.y);
+                // accumulators, paired: (cuw_r, cuw_g), (cuw_b, uw); and, over the two columns of a row, the
+                // moments of gq = dL/dq' in the record's own frame (r = qs dy + qw dx, dx):
+                // sum gq r^2, sum gq r dx, sum gq dx^2, sum gq r, sum gq dx.  Kept apart, a thin
+                // footprint's small along-axis terms (dx) are not rounded away under its large r terms.
+                float2 g01 = f2(0.f, 0.f), g23 = f2(0.f, 0.f);
+                float2 srr = f2(0.f, 0.f), srx = srr, sxx = srr, sr = srr, sx = srr;
+                // dx of this lane's four offsets in a span (k + m L) from the span's first column, less that column
+                const float2 gxo[2] = {__fadd2_rn(f2((float)gk, (float)(gk + L)), gx2),
+                                       __fadd2_rn(f2((float)(gk + 2 * L), (float)(gk + 3 * L)), gx2)};
+                for (int st = 0; st < steps; ++st) {
+                    const int ly = r0 + st;
+                    const unsigned sp = sspan[j][ly];
+                    const int xs = (int)(sp & 0xffu);
+                    const int rowb = ly * PW, cb = rowb + xs, ce = rowb + TW;
+                    const float xsf = (float)xs;
+                    const float dyf = (float)ly + gy0;
+                    const float2 dy2 = f2(dyf, dyf);
 #pragma unroll
-                for (int m = 0; m < 2; ++m) {
-                    // Columns past the span evaluate q > 9 (the span holds every pixel centre of the row with
-                    // q' <= kQMax, with a margin), so the cutoff test zeroes them; columns past the tile read
-                    // the zero column.  No per-pixel validity mask is needed.
-                    const float4 P0 = spix[min(cb + gk + 2 * m * L, ce)];
-                    const float4 P1 = spix[min(cb + gk + (2 * m + 1) * L, ce)];
-                    const float2 dx = __fadd2_rn(f2(xsf, xsf), gxo[m]);
-                    const float2 rr = __ffma2_rn(qs2, dy2, __fmul2_rn(qw2, dx));        // the forward's arithmetic
-                    const float2 q = __ffma2_rn(rr, rr, __fmul2_rn(__fmul2_rn(qd2, dx), dx));
-                    const float e0 = ex2_approx(q.x <= kQMax ? -q.x : -256.0f);          // 2^-256 flushes to 0
-                    const float e1 = ex2_approx(q.y <= kQMax ? -q.y : -256.0f);
-                    // d/d(c u w) and d/d(u w) at fixed c u w
-                    g01 = __ffma2_rn(f2(P0.x, P0.y), f2(e0, e0), g01);
-                    g23 = __ffma2_rn(f2(P0.z, P0.w), f2(e0, e0), g23);
-                    g01 = __ffma2_rn(f2(P1.x, P1.y), f2(e1, e1), g01);
-                    g23 = __ffma2_rn(f2(P1.z, P1.w), f2(e1, e1), g23);
-                    // dL/dq' per pixel: e * (P . cw)
-                    const float2 m0 = __ffma2_rn(f2(P0.z, P0.w), cw1, __fmul2_rn(f2(P0.x, P0.y), cw0));
-                    const float2 m1 = __ffma2_rn(f2(P1.z, P1.w), cw1, __fmul2_rn(f2(P1.x, P1.y), cw0));
-                    const float2 gq = __fmul2_rn(f2(e0, e1), f2(m0.x + m0.y, m1.x + m1.y));
-                    const float2 tr = __fmul2_rn(gq, rr), tx = __fmul2_rn(gq, dx);
-                    srr = __ffma2_rn(tr, rr, srr);
-                    srx = __ffma2_rn(tr, dx, srx);
-                    sxx = __ffma2_rn(tx, dx, sxx);
-                    sr = __fadd2_rn(sr, tr);
-                    sx = __fadd2_rn(sx, tx);
+                    for (int m = 0; m < 2; ++m) {
+                        // Columns past the span evaluate q > 9 (the span holds every pixel centre of the row with
+                        // q' <= kQMax, with a margin), so the cutoff test zeroes them; columns past the tile read
+                        // the zero column.  No per-pixel validity mask is needed.
+                        const float4 P0 = spix[min(cb + gk + 2 * m * L, ce)];
+                        const float4 P1 = spix[min(cb + gk + (2 * m + 1) * L, ce)];
+                        const float2 dx = __fadd2_rn(f2(xsf, xsf), gxo[m]);
+                        const float2 rr = __ffma2_rn(qs2, dy2, __fmul2_rn(qw2, dx));        // the forward's arithmetic
+                        const float2 q = __ffma2_rn(rr, rr, __fmul2_rn(__fmul2_rn(qd2, dx), dx));
+                        const float e0 = ex2_approx(q.x <= kQMax ? -q.x : -256.0f);          // 2^-256 flushes to 0
+                        const float e1 = ex2_approx(q.y <= kQMax ? -q.y : -256.0f);
+                        // d/d(c u w) and d/d(u w) at fixed c u w
+                        g01 = __ffma2_rn(f2(P0.x, P0.y), f2(e0, e0), g01);
+                        g23 = __ffma2_rn(f2(P0.z, P0.w), f2(e0, e0), g23);
+                        g01 = __ffma2_rn(f2(P1.x, P1.y), f2(e1, e1), g01);
+                        g23 = __ffma2_rn(f2(P1.z, P1.w), f2(e1, e1), g23);
+                        // dL/dq' per pixel: e * (P . cw)
+                        const float2 m0 = __ffma2_rn(f2(P0.z, P0.w), cw1, __fmul2_rn(f2(P0.x, P0.y), cw0));
+                        const float2 m1 = __ffma2_rn(f2(P1.z, P1.w), cw1, __fmul2_rn(f2(P1.x, P1.y), cw0));
+                        const float2 gq = __fmul2_rn(f2(e0, e1), f2(m0.x + m0.y, m1.x + m1.y));
+                        const float2 tr = __fmul2_rn(gq, rr), tx = __fmul2_rn(gq, dx);
+                        srr = __ffma2_rn(tr, rr, srr);
+                        srx = __ffma2_rn(tr, dx, srx);
+                        sxx = __ffma2_rn(tx, dx, sxx);
+                        sr = __fadd2_rn(sr, tr);
+                        sx = __fadd2_rn(sx, tx);
+                    }
                 }
-            }
-            // the group's sums: record order sum gq r, sum gq dx, sum gq r^2, sum gq r dx, sum gq dx^2,
-            // d/d(u w), d/d(c u w)
-            float vals[9] = {sr.x + sr.y, sx.x + sx.y, srr.x + srr.y, srx.x + srx.y, sxx.x + sxx.y,
-                             g23.y, g01.x, g01.y, g23.x};
-            __syncwarp();
+                // the group's sums: record order sum gq r, sum gq dx, sum gq r^2, sum gq r dx, sum gq dx^2,
+                // d/d(u w), d/d(c u w)
+                float vals[9] = {sr.x + sr.y, sx.x + sx.y, srr.x + srr.y, srx.x + srx.y, sxx.x + sxx.y,
+                                 g23.y, g01.x, g01.y, g23.x};
+                __syncwarp();
 #pragma unroll
-            for (int off = L / 2; off > 0; off >>= 1)
+                for (int off = L / 2; off > 0; off >>= 1)
 #pragma unroll
-                for (int c = 0; c < 9; ++c) vals[c] += __shfl_xor_sync(0xffffffffu, vals[c], off);
-            if (act && gk == 0 && steps > 0) {
-                if (pass == 0) {
-                    float4* o = reinterpret_cast<float4*>(grec + (size_t)WSR_GRAD_RECORD_FLOATS * sidx[j]);
-                    atomicAdd(o, make_float4(vals[0], vals[1], vals[2], vals[3]));
-                    atomicAdd(o + 1, make_float4(vals[4], vals[5], vals[6], vals[7]));
-                    atomicAdd(reinterpret_cast<float*>(o + 2), vals[8]);
-                } else {
-                    // deterministic mode: a 128-byte record holds 9 int64 sums, then 9 magnitudes (float bits)
-                    float* o = grec + (size_t)kDetRecordFloats * sidx[j];
-                    int* mag = reinterpret_cast<int*>(o + 18);
-                    if (pass == 1) {
-                        // the largest |partial| of each term (non-negative floats order as their bit patterns)
-#pragma unroll
-                        for (int c = 0; c < 9; ++c) atomicMax(mag + c, __float_as_int(fabsf(vals[c])));
+                    for (int c = 0; c < 9; ++c) vals[c] += __shfl_xor_sync(0xffffffffu, vals[c], off);
+                if (act && gk == 0 && steps > 0) {
+                    if (pass == 0) {
+                        float4* o = reinterpret_cast<float4*>(grec + (size_t)WSR_GRAD_RECORD_FLOATS * sidx[j]);
+                        atomicAdd(o, make_float4(vals[0], vals[1], vals[2], vals[3]));
+                        atomicAdd(o + 1, make_float4(vals[4], vals[5], vals[6], vals[7]));
+                        atomicAdd(reinterpret_cast<float*>(o + 2), vals[8]);
                     } else {
-                        // each partial as fixed point with kDetBits bits below that magnitude: exact integer sums
-                        unsigned long long* sum = reinterpret_cast<unsigned long long*>(o);
+                        // deterministic mode: a 128-byte record holds 9 int64 sums, then 9 magnitudes (float bits)
+                        float* o = grec + (size_t)kDetRecordFloats * sidx[j];
+                        int* mag = reinterpret_cast<int*>(o + 18);
+                        if (pass == 1) {
+                            // the largest |partial| of each term (non-negative floats order as their bit patterns)
 #pragma unroll
-                        for (int c = 0; c < 9; ++c) {
-                            const float m = __int_as_float(mag[c]);
-                            if (m > 0.0f) {
-                                int e;
-                                frexpf(m, &e);                  // m < 2^e
-                                const long long q = __double2ll_rn(ldexp((double)vals[c], kDetBits - e));
-                                atomicAdd(sum + c, (unsigned long long)q);
+                            for (int c = 0; c < 9; ++c) atomicMax(mag + c, __float_as_int(fabsf(vals[c])));
+                        } else {
+                            // each partial as fixed point with kDetBits bits below that magnitude: exact integer sums
+                            unsigned long long* sum = reinterpret_cast<unsigned long long*>(o);
+#pragma unroll
+                            for (int c = 0; c < 9; ++c) {
+                                const float m = __int_as_float(mag[c]);
+                                if (m > 0.0f) {
+                                    int e;
+                                    frexpf(m, &e);                  // m < 2^e
+                                    const long long q = __double2ll_rn(ldexp((double)vals[c], kDetBits - e));
+                                    atomicAdd(sum + c, (unsigned long long)q);
+                                }
                             }
                         }
                     }
                 }
             }
-        }
+        };
+        walk(Lanes<TW / 4>(), 0, nwide, &snext[0]);        // the wide class
+        walk(Lanes<TW / 8>(), nwide, cnt, &snext[1]);      // the narrow class
     }
     __syncthreads();
     if (tid < 4) {
@@ -648,8 +658,9 @@ cudaError_t bwd_t(const float* rec, const unsigned* off, const unsigned* list, c
 //   [1] the (pixel, Gaussian) slots the forward evaluates: for every Gaussian
 //       of a tile, the pixels of each warp whose region its footprint reaches
 //       (the forward's per-warp test; all the tile's pixel slots with one warp);
-//   [2] the pixels of the backward's units (each footprint row's span, padded
-//       to an even length), from the backward's own span arithmetic.
+//   [2] the backward's pixel slots (per tile instance, the rows from the first
+//       to the last with a span, TW columns each, or TW / 2 when no span is
+//       longer than TW / 2 pixels), from the backward's own span arithmetic.
 template <int TW, int TH, int PPT, int PX>
 __global__ void __launch_bounds__(TileShape<TW, TH, PPT>::NT)
     k_count_pairs(const float4* __restrict__ rec, const unsigned* __restrict__ offsets,
@@ -693,11 +704,20 @@ __global__ void __launch_bounds__(TileShape<TW, TH, PPT>::NT)
             } else {
                 cnt_fwd += (unsigned long long)F::NT * PX * 2;
             }
-            // the backward's unit pixels
+            // the backward's pixel slots: the rows from its first span to its last, TW columns each, or
+            // TW / 2 when no span is longer than TW / 2 pixels
             const RowSpans rs(a, qd, QM);
-            int lo, hi;
+            int lo, hi, r_lo = TH, r_hi = -1, umax = 0;
             rs.rows(a, y_org, 0, y_lim, lo, hi);
-            for (int r = lo; r <= hi; ++r) cnt_bwd += 2ull * (rs.row(a, QM, x_org, y_org, x_lim, r) >> 8);
+            for (int r = lo; r <= hi; ++r) {
+                const int u = rs.row(a, QM, x_org, y_org, x_lim, r) >> 8;
+                if (u) {
+                    r_lo = min(r_lo, r);
+                    r_hi = max(r_hi, r);
+                    umax = max(umax, u);
+                }
+            }
+            if (r_hi >= r_lo) cnt_bwd += (unsigned long long)(r_hi - r_lo + 1) * (2 * umax > TW / 2 ? TW : TW / 2);
         }
         __syncthreads();
         if (x >= V.W) continue;

@@ -111,6 +111,22 @@ __device__ __forceinline__ bool footprint_hits(float mx, float my, float qs, flo
     return best <= thr;
 }
 
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// Hardware square root and reciprocal (relative error ~2^-22): the backward's
+// per-row spans (widened by 0.02 pixel, far above that) and the SSIM map's
+// two quotients.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

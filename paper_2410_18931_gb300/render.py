@@ -154,7 +154,7 @@ class Renderer:
             _ptr(grad_records), ctypes.byref(grads), _ptr(self.workspace), self.workspace.numel(), _stream(stream)))
 
     def wsr_count_pairs(self, st: FrameState, stream=None) -> tuple:
-        """(pairs with q <= 9, slots the forward evaluates, pixels the backward walks)."""
+        """(pairs with q <= 9, slots the forward evaluates, slots the backward evaluates)."""
         cnt = torch.zeros(3, dtype=torch.int64, device=self.device)
         A.check("wsr_count_pairs", self.lib.wsr_count_pairs(
             _ptr(st.records), st.n, _ptr(st.tile_offsets), _ptr(st.tile_list), self.cams_c, self.n_cams,

@@ -212,7 +212,8 @@ def test_work_counts_of_the_render_kernels(tile):
     to ties decided differently in FP32, far fewer than 0.1%); the forward's
     evaluated slots and the backward's walked pixels hold every pair and fit
     in the tile instances' pixels; the forward's slots come in whole warps
-    (32 threads of PX x 2 pixels) and the backward's pixels in whole units."""
+    (32 threads of PX x 2 pixels) and the backward's in rows of half a tile
+    width or a whole one."""
     import torch
 
     from paper_2410_18931_gb300 import Gaussians, Renderer
@@ -230,4 +231,4 @@ def test_work_counts_of_the_render_kernels(tile):
     assert pairs <= fwd_slots <= cap and pairs <= bwd_pixels <= cap
     px = 1 if tile == (8, 8) else 2
     assert fwd_slots % (32 * px * 2 if tile != (8, 8) else 64) == 0
-    assert bwd_pixels % 2 == 0
+    assert bwd_pixels % (tile[0] // 2) == 0
