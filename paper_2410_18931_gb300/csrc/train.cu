@@ -31,8 +31,10 @@ constexpr int kLT = 32;                     // output tile side
 constexpr int kIn = kLT + 4 * kR;           // staged input side (52)
 constexpr int kSt = kLT + 2 * kR;           // statistics side (42)
 constexpr int kLossThreads = 256;
-// the partials reuse the staged pixels (no longer needed after the statistics), the filtered
-// partials reuse the statistics
+// Shared memory, in floats: the staged (rendered, target) pairs, then the horizontally filtered
+// statistics as (mu_x, mu_y) and (E[x^2], E[y^2]) pairs and E[xy].  The loss partials with
+// respect to (mu_x, E[x^2]) as pairs and E[xy] reuse the staged pixels (no longer needed after
+// the statistics); the filtered partials reuse the statistics.
 constexpr int kLossSmemFloats = 2 * kIn * kIn + 5 * kIn * kSt;
 static_assert(3 * kSt * kSt <= 2 * kIn * kIn, "partials reuse the staged pixels");
 static_assert(3 * kSt * kLT <= 5 * kIn * kSt, "filtered partials reuse the statistics buffer");
@@ -55,15 +57,21 @@ __device__ __forceinline__ float block_sum_to(float x, float* red) {
     return t;   // valid in thread 0
 }
 
-__global__ void __launch_bounds__(kLossThreads) k_loss_3dgs(const float* __restrict__ rgb,
-                                                            const float* __restrict__ tgt, const LossViews L,
-                                                            float* __restrict__ loss, float* __restrict__ grad) {
-    extern __shared__ float sm[];
-    float* sx = sm;                          // [kIn][kIn] rendered
-    float* sy = sx + kIn * kIn;              // [kIn][kIn] target
-    float* hs = sy + kIn * kIn;              // [5][kIn][kSt] horizontally filtered statistics
-    float* mm = sx;                          // [3][kSt][kSt] partials of the loss (reuses sx, sy)
-    float* hm = hs;                          // [3][kSt][kLT] horizontally filtered partials
+// Every filter step runs on two quantities at once where it can (paired FP32 ops on float2):
+// the rendered and target values, their squares, and the first two loss partials; the cross
+// terms E[xy] and its partial go alone.
+__global__ void __launch_bounds__(kLossThreads, 3) k_loss_3dgs(const float* __restrict__ rgb,
+                                                               const float* __restrict__ tgt, const LossViews L,
+                                                               float* __restrict__ loss, float* __restrict__ grad) {
+    extern __shared__ __align__(16) float sm[];
+    float2* sxy = reinterpret_cast<float2*>(sm);                   // [kIn][kIn] (rendered, target)
+    float2* h01 = reinterpret_cast<float2*>(sm + 2 * kIn * kIn);   // [kIn][kSt] filtered (x, y)
+    float2* h23 = h01 + kIn * kSt;                                 // [kIn][kSt] filtered (x^2, y^2)
+    float* h4 = reinterpret_cast<float*>(h23 + kIn * kSt);         // [kIn][kSt] filtered x y
+    float2* m01 = reinterpret_cast<float2*>(sm);                   // [kSt][kSt] partials: mu_x, E[x^2]
+    float* m2 = reinterpret_cast<float*>(m01 + kSt * kSt);         // [kSt][kSt] partial: E[xy]
+    float2* f01 = h01;                                             // [kSt][kLT] horizontally filtered
+    float* f2s = reinterpret_cast<float*>(f01 + kSt * kLT);        // [kSt][kLT]
     __shared__ float red[kLossThreads / 32];
     const int tid = threadIdx.x;
 
@@ -76,68 +84,87 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_3dgs(const float* __restr
     const float gs = -L.lam * L.inv_count;                 // dL / d(SSIM map value)
     const float gl1 = (1.0f - L.lam) * L.inv_count;        // dL / d|x - y|
     float l1 = 0.f, ss = 0.f;
+    float2 g2[2 * kR + 1];                                 // the window's taps, paired
+#pragma unroll
+    for (int k = 0; k < 2 * kR + 1; ++k) g2[k] = f2(L.g[k], L.g[k]);
 
     for (int c = 0; c < 3; ++c) {
         for (int i = tid; i < kIn * kIn; i += kLossThreads) {
             const int iy = i / kIn, ix = i - iy * kIn;
             const int gx = x0 - 2 * kR + ix, gy = y0 - 2 * kR + iy;
-            float a = 0.f, b = 0.f;
+            float2 ab = f2(0.f, 0.f);
             if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
                 const long long p = (base + (long long)gy * W + gx) * 3 + c;
-                a = rgb[p];
-                b = tgt[p];
+                ab = f2(rgb[p], tgt[p]);
             }
-            sx[i] = a;
-            sy[i] = b;
+            sxy[i] = ab;
         }
         __syncthreads();
         // horizontal statistics: three neighbouring columns per item from one window of 13
         for (int it = tid; it < kIn * kH1; it += kLossThreads) {
             const int iy = it / kH1, jx0 = (it - iy * kH1) * 3;
-            const float* rx = sx + iy * kIn + jx0;
-            const float* ry = sy + iy * kIn + jx0;
-            float a[2 * kR + 3], b[2 * kR + 3];
+            const float2* r = sxy + iy * kIn + jx0;
+            float2 ab[2 * kR + 3], sq[2 * kR + 3];
+            float xy[2 * kR + 3];
 #pragma unroll
             for (int k = 0; k < 2 * kR + 3; ++k) {
-                a[k] = rx[k];
-                b[k] = ry[k];
+                ab[k] = r[k];
+                sq[k] = __fmul2_rn(ab[k], ab[k]);
+                xy[k] = ab[k].x * ab[k].y;
             }
 #pragma unroll
             for (int o = 0; o < 3; ++o) {
-                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+                float2 s01 = f2(0.f, 0.f), s23 = f2(0.f, 0.f);
+                float s4 = 0.f;
 #pragma unroll
                 for (int k = 0; k < 2 * kR + 1; ++k) {
-                    const float w = L.g[k], wa = w * a[o + k], wb = w * b[o + k];
-                    s0 += wa;
-                    s1 += wb;
-                    s2 = fmaf(wa, a[o + k], s2);
-                    s3 = fmaf(wb, b[o + k], s3);
-                    s4 = fmaf(wa, b[o + k], s4);
+                    s01 = __ffma2_rn(g2[k], ab[o + k], s01);
+                    s23 = __ffma2_rn(g2[k], sq[o + k], s23);
+                    s4 = fmaf(g2[k].x, xy[o + k], s4);
                 }
                 const int i = iy * kSt + jx0 + o;
-                hs[i] = s0;
-                hs[kIn * kSt + i] = s1;
-                hs[2 * kIn * kSt + i] = s2;
-                hs[3 * kIn * kSt + i] = s3;
-                hs[4 * kIn * kSt + i] = s4;
+                h01[i] = s01;
+                h23[i] = s23;
+                h4[i] = s4;
             }
         }
         __syncthreads();
         // vertical statistics, SSIM map and the loss partials: seven rows per item
         for (int it = tid; it < kSt * kS2; it += kLossThreads) {
             const int strip = it / kSt, jx = it - strip * kSt, jy0 = strip * kV2;
-            float st[5][kV2];
+            float2 st01[kV2], st23[kV2];
+            float st4[kV2];
+            {
+                float2 h[kV2 + 2 * kR];
 #pragma unroll
-            for (int q = 0; q < 5; ++q) {
+                for (int r = 0; r < kV2 + 2 * kR; ++r) h[r] = h01[(jy0 + r) * kSt + jx];
+#pragma unroll
+                for (int o = 0; o < kV2; ++o) {
+                    float2 acc = f2(0.f, 0.f);
+#pragma unroll
+                    for (int k = 0; k < 2 * kR + 1; ++k) acc = __ffma2_rn(g2[k], h[o + k], acc);
+                    st01[o] = acc;
+                }
+#pragma unroll
+                for (int r = 0; r < kV2 + 2 * kR; ++r) h[r] = h23[(jy0 + r) * kSt + jx];
+#pragma unroll
+                for (int o = 0; o < kV2; ++o) {
+                    float2 acc = f2(0.f, 0.f);
+#pragma unroll
+                    for (int k = 0; k < 2 * kR + 1; ++k) acc = __ffma2_rn(g2[k], h[o + k], acc);
+                    st23[o] = acc;
+                }
+            }
+            {
                 float h[kV2 + 2 * kR];
 #pragma unroll
-                for (int r = 0; r < kV2 + 2 * kR; ++r) h[r] = hs[q * kIn * kSt + (jy0 + r) * kSt + jx];
+                for (int r = 0; r < kV2 + 2 * kR; ++r) h[r] = h4[(jy0 + r) * kSt + jx];
 #pragma unroll
                 for (int o = 0; o < kV2; ++o) {
                     float acc = 0.f;
 #pragma unroll
-                    for (int k = 0; k < 2 * kR + 1; ++k) acc = fmaf(L.g[k], h[o + k], acc);
-                    st[q][o] = acc;
+                    for (int k = 0; k < 2 * kR + 1; ++k) acc = fmaf(g2[k].x, h[o + k], acc);
+                    st4[o] = acc;
                 }
             }
             const int gx = x0 - kR + jx;
@@ -146,42 +173,46 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_3dgs(const float* __restr
 #pragma unroll
             for (int o = 0; o < kV2; ++o) {
                 const int jy = jy0 + o, gy = y0 - kR + jy;
-                float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+                float2 p01 = f2(0.f, 0.f);
+                float p2 = 0.f;
                 if (col_in && gy >= 0 && gy < H) {
-                    const float mx = st[0][o], my = st[1][o];
-                    const float sxx = st[2][o] - mx * mx, syy = st[3][o] - my * my, sxy = st[4][o] - mx * my;
-                    const float a1 = 2.f * mx * my + L.c1, a2 = 2.f * sxy + L.c2;
+                    const float mx = st01[o].x, my = st01[o].y;
+                    const float sxx = st23[o].x - mx * mx, syy = st23[o].y - my * my, sxy_ = st4[o] - mx * my;
+                    const float a1 = 2.f * mx * my + L.c1, a2 = 2.f * sxy_ + L.c2;
                     const float b1 = mx * mx + my * my + L.c1, b2 = sxx + syy + L.c2;
-                    const float ib1 = 1.0f / b1, ib2 = 1.0f / b2;
+                    const float ib1 = rcp_approx(b1), ib2 = rcp_approx(b2);
                     const float sv = a1 * a2 * ib1 * ib2;
-                    m0 = gs * (2.f * my * (a2 - a1) * ib1 * ib2 + 2.f * mx * sv * (ib2 - ib1));
-                    m1 = gs * (-sv * ib2);
-                    m2 = gs * (2.f * a1 * ib1 * ib2);
+                    p01 = f2(gs * (2.f * my * (a2 - a1) * ib1 * ib2 + 2.f * mx * sv * (ib2 - ib1)), gs * (-sv * ib2));
+                    p2 = gs * (2.f * a1 * ib1 * ib2);
                     if (col_own && jy >= kR && jy < kR + kLT) ss += sv;
                 }
                 const int i = jy * kSt + jx;
-                mm[i] = m0;
-                mm[kSt * kSt + i] = m1;
-                mm[2 * kSt * kSt + i] = m2;
+                m01[i] = p01;
+                m2[i] = p2;
             }
         }
         __syncthreads();
         // horizontal pass of the partials: four columns per item
         for (int it = tid; it < kSt * kB3; it += kLossThreads) {
             const int jy = it / kB3, ox0 = (it - jy * kB3) * kH3;
+            float2 r[kH3 + 2 * kR];
+            float r2[kH3 + 2 * kR];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const float* row = mm + q * kSt * kSt + jy * kSt + ox0;
-                float r[kH3 + 2 * kR];
+            for (int k = 0; k < kH3 + 2 * kR; ++k) {
+                r[k] = m01[jy * kSt + ox0 + k];
+                r2[k] = m2[jy * kSt + ox0 + k];
+            }
 #pragma unroll
-                for (int k = 0; k < kH3 + 2 * kR; ++k) r[k] = row[k];
+            for (int o = 0; o < kH3; ++o) {
+                float2 acc = f2(0.f, 0.f);
+                float acc2 = 0.f;
 #pragma unroll
-                for (int o = 0; o < kH3; ++o) {
-                    float acc = 0.f;
-#pragma unroll
-                    for (int k = 0; k < 2 * kR + 1; ++k) acc = fmaf(L.g[k], r[o + k], acc);
-                    hm[q * kSt * kLT + jy * kLT + ox0 + o] = acc;
+                for (int k = 0; k < 2 * kR + 1; ++k) {
+                    acc = __ffma2_rn(g2[k], r[o + k], acc);
+                    acc2 = fmaf(g2[k].x, r2[o + k], acc2);
                 }
+                f01[jy * kLT + ox0 + o] = acc;
+                f2s[jy * kLT + ox0 + o] = acc2;
             }
         }
         __syncthreads();
@@ -189,31 +220,38 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_3dgs(const float* __restr
         for (int it = tid; it < kLT * kS4; it += kLossThreads) {
             const int strip = it / kLT, ox = it - strip * kLT, oy0 = strip * kV4;
             const int gx = x0 + ox;
-            float f[3][kV4];
+            float2 cc[kV4 + 2 * kR];
+            float c2[kV4 + 2 * kR];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                float c[kV4 + 2 * kR];
+            for (int r = 0; r < kV4 + 2 * kR; ++r) {
+                cc[r] = f01[(oy0 + r) * kLT + ox];
+                c2[r] = f2s[(oy0 + r) * kLT + ox];
+            }
+            float2 f[kV4];
+            float fx[kV4];
 #pragma unroll
-                for (int r = 0; r < kV4 + 2 * kR; ++r) c[r] = hm[q * kSt * kLT + (oy0 + r) * kLT + ox];
+            for (int o = 0; o < kV4; ++o) {
+                float2 acc = f2(0.f, 0.f);
+                float acc2 = 0.f;
 #pragma unroll
-                for (int o = 0; o < kV4; ++o) {
-                    float acc = 0.f;
-#pragma unroll
-                    for (int k = 0; k < 2 * kR + 1; ++k) acc = fmaf(L.g[k], c[o + k], acc);
-                    f[q][o] = acc;
+                for (int k = 0; k < 2 * kR + 1; ++k) {
+                    acc = __ffma2_rn(g2[k], cc[o + k], acc);
+                    acc2 = fmaf(g2[k].x, c2[o + k], acc2);
                 }
+                f[o] = acc;
+                fx[o] = acc2;
             }
             if (gx >= W) continue;
 #pragma unroll
             for (int o = 0; o < kV4; ++o) {
                 const int oy = oy0 + o, gy = y0 + oy;
                 if (gy >= H) break;
-                    const long long pix = (base + (long long)gy * W + gx) * 3 + c;
+                const long long pix = (base + (long long)gy * W + gx) * 3 + c;
                 const float a = rgb[pix], b = tgt[pix];      // the staged copies are overwritten by now
                 const float d = a - b;
                 l1 += fabsf(d);
                 const float gd = d > 0.f ? gl1 : (d < 0.f ? -gl1 : 0.f);
-                grad[pix] = f[0][o] + 2.f * a * f[1][o] + b * f[2][o] + gd;
+                grad[pix] = f[o].x + 2.f * a * f[o].y + b * fx[o] + gd;
             }
         }
         __syncthreads();
