@@ -634,17 +634,21 @@ def run_deterministic(S, scene, cam, weight, target, tile, persistent, chunk, fl
         outs.append([D.st.rgb.clone()] + [v.clone() for v in D.out.values()])
     S.A.check("deterministic step", D.r.wsr_check())
     same = all(torch.equal(a, b) for a, b in zip(*outs))
-    times = []
+    times, stages = [], []
     for _ in range(reps):
         flush.zero_()
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
         D.run(evs)
         torch.cuda.synchronize()
         times.append(evs[0].elapsed_time(evs[6]))
+        stages.append([evs[k].elapsed_time(evs[k + 1]) for k in range(6)])
     ms = float(np.mean(times))
+    st_ms = np.mean(np.array(stages), axis=0)
+    stage_names = D.stage_names
     del D, outs
     torch.cuda.empty_cache()
     return {"ms_per_step": round(ms, 4), "fwd_bwd_mpix_s": round(cam.width * cam.height / (ms * 1e-3) / 1e6, 2),
+            "stage_ms": {k: round(float(v), 4) for k, v in zip(stage_names, st_ms)},
             "tile": "%dx%d" % tile, "schedule": "persistent" if persistent else "per-tile", "chunk": chunk,
             "longest_tile_list": longest, "bitwise_repeat": bool(same),
             # + the list sort, the backward's magnitude pass and the two ordered reductions
