@@ -970,7 +970,7 @@ def main():
     ap.add_argument("--workload", type=int, default=3)
     ap.add_argument("--tile", default="auto", help="WxH (16x16, 8x8, 32x8, 16x8) or auto")
     ap.add_argument("--schedule", default="auto", choices=["auto", "per-tile", "persistent"])
-    ap.add_argument("--chunk", default="auto", choices=["auto", "128", "64", "256"],
+    ap.add_argument("--chunk", default="auto", choices=["auto", "128", "64", "256", "512"],
                     help="Gaussians per block of the backward")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
@@ -990,7 +990,7 @@ def main():
         torch.cuda.set_device(0)
         tile = (16, 16) if args.tile == "auto" else tuple(int(v) for v in args.tile.split("x"))
         persistent = args.schedule != "per-tile"
-        chunk = 64 if args.chunk == "auto" else int(args.chunk)
+        chunk = 512 if args.chunk == "auto" else int(args.chunk)
         scene, cam, weight, extra, target = build_workload(args, 0, 1)
         S = Step(scene, cam, weight, tile, target, persistent, chunk)
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -1003,7 +1003,7 @@ def main():
         # the launch configuration as given; "auto" takes what the tuner picks for this view on a GB300
         tile = (16, 16) if args.tile == "auto" else tuple(int(v) for v in args.tile.split("x"))
         persistent = args.schedule != "per-tile"
-        chunk = 64 if args.chunk == "auto" else int(args.chunk)
+        chunk = 512 if args.chunk == "auto" else int(args.chunk)
         print(json.dumps(run_training(steps=args.steps, warmup=args.warmup, tile=tile, persistent=persistent,
                                       chunk=chunk)), flush=True)
         return

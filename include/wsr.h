@@ -134,10 +134,10 @@ enum {
  * the render calls launch one block per resident slot that takes tiles from
  * that order through a counter in the workspace; the same workspace and tiles
  * must then be passed to wsr_bin and the renderers.  `chunk` is how many of a
- * tile's Gaussians one block of wsr_render_bwd takes at a time (two threads
- * per Gaussian): 0 for the default 128, 64 (blocks of 128 threads, twice as
- * many resident) or 256 (blocks of 512 threads, half as many); other values
- * return WSR_ERR_UNSUPPORTED.  It changes the schedule only, not the result
+ * tile's Gaussians one block of wsr_render_bwd takes at a time: 0 for the
+ * default 128 (blocks of 256 threads), 64 (blocks of 128 threads, twice as
+ * many resident), 256 or 512 (blocks of 256 threads, fewer barriers per
+ * Gaussian); other values return WSR_ERR_UNSUPPORTED.  It changes the schedule only, not the result
  * beyond rounding order.
  *
  * `deterministic` = 1 makes every result bitwise reproducible from run to run
@@ -158,7 +158,7 @@ enum {
 typedef struct {
     int32_t tile_w, tile_h;
     int32_t schedule;            /* WSR_SCHEDULE_* */
-    int32_t chunk;               /* Gaussians per backward block: 0 (128), 64 or 256 */
+    int32_t chunk;               /* Gaussians per backward block: 0 (128), 64, 256, 512 */
     int32_t deterministic;       /* 0, or 1: bitwise-reproducible results */
 } wsr_tiles;
 

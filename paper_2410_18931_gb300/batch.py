@@ -15,7 +15,7 @@ from . import _abi as A
 from .render import Gaussians, Renderer
 
 DEFAULT_SHAPES = ((8, 8), (16, 8), (16, 16), (32, 8))
-DEFAULT_CHUNKS = (128, 64, 256)   # Gaussians per block of the backward
+DEFAULT_CHUNKS = (128, 64, 256, 512)   # Gaussians per block of the backward
 
 
 class GraphStep:

@@ -33,7 +33,8 @@ wsr_status make_views(const wsr_camera* cams, int32_t n_cams, const wsr_tiles* t
         if (tiles->schedule != WSR_SCHEDULE_TILE_BLOCKS && tiles->schedule != WSR_SCHEDULE_PERSISTENT)
             return WSR_ERR_INVALID_ARG;
         if (!tiles_ok(tiles)) return WSR_ERR_UNSUPPORTED;
-        if (tiles->chunk != 0 && tiles->chunk != 64 && tiles->chunk != 128 && tiles->chunk != 256)
+        if (tiles->chunk != 0 && tiles->chunk != 64 && tiles->chunk != 128 && tiles->chunk != 256 &&
+            tiles->chunk != 512)
             return WSR_ERR_UNSUPPORTED;
         tw = tiles->tile_w;
         th = tiles->tile_h;

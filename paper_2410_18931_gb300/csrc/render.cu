@@ -37,6 +37,12 @@ __device__ __forceinline__ TileCoord tile_coord(const Views& vs, int tile) {
     return t;
 }
 
+// Threads per block of the backward for chunks of CH Gaussians: 2 CH, at most 256.
+template <int CH>
+struct BwdThreads {
+    static constexpr int value = CH < 128 ? 2 * CH : 256;
+};
+
 // A lane count as a type, to instantiate one walk of the backward per group size.
 template <int N>
 struct Lanes {
@@ -314,8 +320,8 @@ __device__ __forceinline__ float warp_sum(float v) {
 // first pixel centre, the walk from each pixel's own offsets, so a pair
 // within rounding of the cutoff (a tie: its term is e^-4.5 of the
 // Gaussian's peak there) may be counted by one and not the other.
-// Gaussians per chunk (CH, a template parameter: 128 or 64) and threads per
-// block (2 CH).
+// Gaussians per chunk: CH, a template parameter (64, 128, 256 or 512); threads
+// per block: BwdThreads<CH> (2 CH up to 256).
 template <int TW, int TH, int CH>
 __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restrict__ rec,
                                          const unsigned* __restrict__ offsets, const unsigned* __restrict__ list,
@@ -323,13 +329,14 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                                          const float* __restrict__ out_rgb, const float* __restrict__ out_den,
                                          const float* __restrict__ grad_rgb, float* __restrict__ grec,
                                          float* __restrict__ gw, const int pass, float* __restrict__ bg_tiles) {
-    constexpr int NT = 2 * CH;
+    constexpr int NT = BwdThreads<CH>::value;
     constexpr int NW = NT / 32;
+    constexpr int PASSES = 2 * CH / NT;                // step A: (Gaussian, half) items per thread
     constexpr int PW = TW + 1;                          // pixel-table row pitch: one zero column
     constexpr int HR = TH / 2;                          // rows per thread in step A
     constexpr int NB = TH + 1;                          // row counts 0 .. TH
     constexpr int NK = 2 * NB;                          // sort keys: narrow 0 .. TH, wide NB .. NB + TH
-    static_assert(NT == 2 * CH && TH % 2 == 0 && TW % 8 == 0 && TW <= 64 && CH <= 256 && NK <= NT, "layout");
+    static_assert(PASSES * NT == 2 * CH && TH % 2 == 0 && TW % 8 == 0 && TW <= 64 && CH <= 512 && NK <= NT, "layout");
     __shared__ float4 spix[PW * TH + 1];        // per pixel: G/D (3), -(G.C)/D; zero column and pad entry
     __shared__ float4 s0[CH];                   // mu_x, mu_y, qs, qw
     __shared__ float4 s1[CH];                   // qd, u w, c_r u w, c_g u w
@@ -338,7 +345,9 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
     __shared__ unsigned short sspan[CH][TH];    // per row: first column | units << 8 (a unit: two pixels)
     __shared__ unsigned char sfirst[CH];        // first row with a span
     __shared__ unsigned char snst[CH];          // rows from there to the last row with a span
-    __shared__ unsigned char sord[CH];          // the chunk's Gaussians: wide ones first, most rows first
+    __shared__ unsigned char skey[CH];          // sort key: rows, plus NB when wide
+    __shared__ unsigned short srank[CH];        // rank among the chunk's Gaussians of the same key
+    __shared__ unsigned short sord[CH];         // the chunk's Gaussians: wide ones first, most rows first
     __shared__ unsigned shist[NK];
     __shared__ unsigned snext[2];               // per class: the next position of the order a warp takes
     __shared__ unsigned snwide;                 // wide Gaussians in the chunk
@@ -379,61 +388,65 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
 
     const float QM = kQMax * 1.0001f + 1e-4f;
     const unsigned start = offsets[tile], end = offsets[tile + 1];
+    if (tid < NK) shist[tid] = 0u;
     for (unsigned base = start; base < end; base += CH) {
         const int cnt = (int)min((unsigned)CH, end - base);
         __syncthreads();                                // the previous chunk is done with shared memory
-        if (tid < NK) shist[tid] = 0u;
-        // ---- A: record, spans of half the rows of Gaussian tid / 2, first and last rows ----
-        const int gj = tid >> 1, half = tid & 1;
-        int row_lo = TH, row_hi = -1, umax = 0;
-        if (gj < cnt) {
-            const unsigned r = list[base + gj];
-            const float4* pr = rec + 3ull * r;
-            const float4 a = __ldg(pr);
-            const float4 b = __ldg(pr + 1);
-            if (half == 0) {
-                const float cb = __ldg(reinterpret_cast<const float*>(pr + 2));
-                s0[gj] = a;
-                s1[gj] = b;
-                s2[gj] = f2(cb, b.y);
-                sidx[gj] = r;
-            }
-            const RowSpans rs(a, b.x, QM);
-            int ly_lo, ly_hi;
-            rs.rows(a, y_org, half * HR, min(HR, y_lim - half * HR), ly_lo, ly_hi);
+        // ---- A: record, spans of half the rows of a Gaussian per item, first and last rows ----
+#pragma unroll 1
+        for (int ps = 0; ps < PASSES; ++ps) {
+            const int u = tid + ps * NT;
+            const int gj = u >> 1, half = u & 1;
+            int row_lo = TH, row_hi = -1, umax = 0;
+            if (gj < cnt) {
+                const unsigned r = list[base + gj];
+                const float4* pr = rec + 3ull * r;
+                const float4 a = __ldg(pr);
+                const float4 b = __ldg(pr + 1);
+                if (half == 0) {
+                    const float cb = __ldg(reinterpret_cast<const float*>(pr + 2));
+                    s0[gj] = a;
+                    s1[gj] = b;
+                    s2[gj] = f2(cb, b.y);
+                    sidx[gj] = r;
+                }
+                const RowSpans rs(a, b.x, QM);
+                int ly_lo, ly_hi;
+                rs.rows(a, y_org, half * HR, min(HR, y_lim - half * HR), ly_lo, ly_hi);
 #pragma unroll
-            for (int k = 0; k < HR; ++k) {
-                const int ly = half * HR + k;
-                unsigned short sp = 0;
-                if (ly >= ly_lo && ly <= ly_hi) sp = rs.row(a, QM, x_org, y_org, x_lim, ly);
-                sspan[gj][ly] = sp;
-                if (sp >> 8) {
-                    row_lo = min(row_lo, ly);
-                    row_hi = max(row_hi, ly);
-                    umax = max(umax, sp >> 8);
+                for (int k = 0; k < HR; ++k) {
+                    const int ly = half * HR + k;
+                    unsigned short sp = 0;
+                    if (ly >= ly_lo && ly <= ly_hi) sp = rs.row(a, QM, x_org, y_org, x_lim, ly);
+                    sspan[gj][ly] = sp;
+                    if (sp >> 8) {
+                        row_lo = min(row_lo, ly);
+                        row_hi = max(row_hi, ly);
+                        umax = max(umax, sp >> 8);
+                    }
                 }
             }
-        }
-        row_lo = min(row_lo, __shfl_xor_sync(0xffffffffu, row_lo, 1));      // the two halves of a Gaussian
-        row_hi = max(row_hi, __shfl_xor_sync(0xffffffffu, row_hi, 1));
-        umax = max(umax, __shfl_xor_sync(0xffffffffu, umax, 1));
-        const int nst = row_hi >= row_lo ? row_hi - row_lo + 1 : 0;
-        const int key = nst + (2 * umax > TW / 2 ? NB : 0);     // wide: a span longer than TW / 2 pixels
-        __syncthreads();
-        // ---- B: the chunk's order, wide first, most rows first (rank within the bucket from the count) ----
-        unsigned rank = 0;
-        if (gj < cnt && half == 0) {
-            sfirst[gj] = (unsigned char)max(row_lo, 0);
-            snst[gj] = (unsigned char)nst;
-            rank = atomicAdd(&shist[key], 1u);
+            row_lo = min(row_lo, __shfl_xor_sync(0xffffffffu, row_lo, 1));      // the two halves of a Gaussian
+            row_hi = max(row_hi, __shfl_xor_sync(0xffffffffu, row_hi, 1));
+            umax = max(umax, __shfl_xor_sync(0xffffffffu, umax, 1));
+            if (gj < cnt && half == 0) {
+                const int nst = row_hi >= row_lo ? row_hi - row_lo + 1 : 0;
+                const int key = nst + (2 * umax > TW / 2 ? NB : 0);     // wide: a span longer than TW / 2 pixels
+                sfirst[gj] = (unsigned char)max(row_lo, 0);
+                snst[gj] = (unsigned char)nst;
+                skey[gj] = (unsigned char)key;
+                srank[gj] = (unsigned short)atomicAdd(&shist[key], 1u);
+            }
         }
         if (tid < 2) snext[tid] = 0u;
         __syncthreads();
-        if (gj < cnt && half == 0) {
-            unsigned at = rank;
+        // ---- B: the chunk's order, wide first, most rows first (rank within the bucket from the count) ----
+        for (int gj = tid; gj < cnt; gj += NT) {
+            const int key = skey[gj];
+            unsigned at = srank[gj];
 #pragma unroll
             for (int c = NK - 1; c > 0; --c) at += c > key ? shist[c] : 0u;
-            sord[at] = (unsigned char)gj;
+            sord[at] = (unsigned short)gj;
         }
         if (tid == 0) {
             unsigned nw = 0;
@@ -442,6 +455,7 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
             snwide = nw;
         }
         __syncthreads();
+        if (tid < NK) shist[tid] = 0u;                  // for the next chunk (step C does not read it)
         // ---- C: a group per Gaussian; each warp takes the next 32 / L Gaussians of a class ----
         const int nwide = (int)snwide;
         auto walk = [&](auto lanes, const int lo, const int hi, unsigned* next) {
@@ -568,7 +582,7 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
 }
 
 template <int TW, int TH, int CH>
-__global__ void __launch_bounds__(2 * CH, 512 / CH)
+__global__ void __launch_bounds__(BwdThreads<CH>::value, 1024 / BwdThreads<CH>::value)
     k_render_bwd(const float4* __restrict__ rec, const unsigned* __restrict__ offsets,
                  const unsigned* __restrict__ list, const Views vs, const float* __restrict__ wparams,
                  const float* __restrict__ out_rgb, const float* __restrict__ out_den,
@@ -629,12 +643,13 @@ template <int TW, int TH, int CH>
 cudaError_t bwd_chunk(const float* rec, const unsigned* off, const unsigned* list, const Views& vs, WeightDev w,
                       const float* rgb, const float* den, const float* grgb, float* grec, float* gw, int pass,
                       float* bg_tiles, Sched sched, cudaStream_t s) {
-    const unsigned grid = grid_for(k_render_bwd<TW, TH, CH>, 2 * CH, vs, sched);
+    constexpr int NT = BwdThreads<CH>::value;
+    const unsigned grid = grid_for(k_render_bwd<TW, TH, CH>, NT, vs, sched);
     if (sched.order) {
         cudaError_t e = cudaMemsetAsync(sched.counter, 0, sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
     }
-    k_render_bwd<TW, TH, CH><<<grid, 2 * CH, 0, s>>>(reinterpret_cast<const float4*>(rec), off, list, vs, w.params,
+    k_render_bwd<TW, TH, CH><<<grid, NT, 0, s>>>(reinterpret_cast<const float4*>(rec), off, list, vs, w.params,
                                                      rgb, den, grgb, grec, gw, pass, bg_tiles, sched.order,
                                                      sched.counter);
     return cudaGetLastError();
@@ -648,6 +663,8 @@ cudaError_t bwd_t(const float* rec, const unsigned* off, const unsigned* list, c
         return bwd_chunk<TW, TH, 64>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sched, s);
     if (vs.chunk == 256)
         return bwd_chunk<TW, TH, 256>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sched, s);
+    if (vs.chunk == 512)
+        return bwd_chunk<TW, TH, 512>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sched, s);
     return bwd_chunk<TW, TH, 128>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sched, s);
 }
 

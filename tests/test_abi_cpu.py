@@ -189,12 +189,12 @@ def test_weight_params_rounded_are_float32_exact():
 def test_tiles_chunk_is_validated(lib):
     from paper_2410_18931_gb300 import _abi as A
     cams, n = _cam(64, 48)
-    for chunk, expect in ((0, True), (64, True), (128, True), (256, True)):
+    for chunk, expect in ((0, True), (64, True), (128, True), (256, True), (512, True)):
         assert (lib.wsr_workspace_size(cams, n, ctypes.byref(A.tiles(16, 16, 0, chunk))) > 0) == expect
     fake = 1 << 20
     ws = lib.wsr_workspace_size(cams, n, ctypes.byref(A.tiles(16, 16)))
     w = A.wsr_weight(A.WSR_WEIGHT_EXP, fake)
-    for chunk, status in ((32, A.WSR_ERR_UNSUPPORTED), (512, A.WSR_ERR_UNSUPPORTED), (-1, A.WSR_ERR_INVALID_ARG)):
+    for chunk, status in ((32, A.WSR_ERR_UNSUPPORTED), (1024, A.WSR_ERR_UNSUPPORTED), (-1, A.WSR_ERR_INVALID_ARG)):
         t = A.tiles(16, 16, 0, chunk)
         assert lib.wsr_render_fwd(fake, 10, fake, fake, cams, n, ctypes.byref(t), ctypes.byref(w), fake, fake,
                                   fake, ws, None) == status
