@@ -273,9 +273,9 @@ static wsr_status bin_count_impl(const float* records, int64_t n, const Views& v
     unsigned* bsum = (unsigned*)(ws + L.block_sums);
     WSR_CUDA(cudaMemsetAsync(&hdr->err, 0, sizeof(int), s));
     WSR_CUDA(launch_bin_count(records, n, vs, cursor, s));
-    WSR_CUDA(launch_scan(vs, cursor, bsum, tile_offsets, capacity, hdr, s));
-    if (vs.schedule == WSR_SCHEDULE_PERSISTENT)
-        WSR_CUDA(launch_tile_order(vs, tile_offsets, (unsigned*)(ws + L.buckets), (unsigned*)(ws + L.order), s));
+    const bool persistent = vs.schedule == WSR_SCHEDULE_PERSISTENT;
+    WSR_CUDA(launch_scan(vs, cursor, bsum, tile_offsets, capacity, hdr, (unsigned*)(ws + L.buckets),
+                         persistent ? (unsigned*)(ws + L.order) : nullptr, s));
     return WSR_OK;
 }
 

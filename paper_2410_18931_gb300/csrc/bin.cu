@@ -7,7 +7,9 @@
 // scatter (a counting sort by tile with arbitrary order inside each tile).
 //
 //   k_bin<false>   count: atomicAdd into every tile the footprint reaches
-//   k_scan_*       exclusive scan of the per-tile counts (three phases)
+//   k_scan_*       exclusive scan of the per-tile counts (three phases; one
+//                  block, with the persistent schedule's tile order, for up
+//                  to kSmallScanTiles tiles)
 //   k_bin<true>    scatter: claim a slot per (Gaussian, tile) and store
 // A tile is listed when a pixel-centre column of it meets the footprint
 // q <= 9 within the tile's band of pixel-centre rows (the ellipse's exact
@@ -274,6 +276,54 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_apply(unsigned* __restrict_
 // largest down; the order inside a bucket is arbitrary.
 __device__ __forceinline__ int cost_bucket(unsigned c) { return c ? 32 - __clz(c) : 0; }   // 0..32
 
+// Exclusive scan over the tiles and, for the persistent schedule, the longest-first
+// tile order (the buckets of k_order_*), in one block: for views of at most
+// kSmallScanTiles tiles.  Thread k takes consecutive tiles [k per, (k + 1) per).
+constexpr int kSmallScanTiles = kScanBlock * 32;
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_order_small(unsigned* __restrict__ cursor, int n,
+                                                                 unsigned* __restrict__ offsets,
+                                                                 unsigned long long capacity, WsHeader* hdr,
+                                                                 unsigned* __restrict__ order) {
+    __shared__ unsigned long long s_warp[33];
+    __shared__ unsigned s_hist[33];
+    const unsigned long long lim = capacity < 0xffffffffull ? capacity : 0xffffffffull;
+    const int per = (n + kScanBlock - 1) / kScanBlock;
+    const int b0 = min((int)threadIdx.x * per, n), b1 = min(b0 + per, n);
+    unsigned long long x = 0;
+    for (int t = b0; t < b1; ++t) x += cursor[t];
+    if (threadIdx.x < 33) s_hist[threadIdx.x] = 0u;
+    unsigned long long tot;
+    unsigned long long run = block_exclusive_scan(x, s_warp, tot);   // ends with a barrier
+    for (int t = b0; t < b1; ++t) {
+        const unsigned c = cursor[t];
+        const unsigned o = (unsigned)(run < lim ? run : lim);
+        offsets[t] = o;
+        cursor[t] = o;                  // the scatter's cursor starts at the tile's offset
+        run += c;
+    }
+    if (threadIdx.x == 0) {
+        offsets[n] = (unsigned)(tot < lim ? tot : lim);
+        hdr->total = tot;
+        if (tot > lim) set_error(hdr, WSR_ERR_CAPACITY);
+    }
+    if (!order) return;
+    __syncthreads();                    // the block's offsets are visible to all its threads
+    for (int t = b0; t < b1; ++t) atomicAdd(&s_hist[cost_bucket(offsets[t + 1] - offsets[t])], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned r = 0;                 // bucket starts, largest bucket first
+        for (int b = 32; b >= 0; --b) {
+            const unsigned h = s_hist[b];
+            s_hist[b] = r;
+            r += h;
+        }
+    }
+    __syncthreads();
+    for (int t = b0; t < b1; ++t)
+        order[atomicAdd(&s_hist[cost_bucket(offsets[t + 1] - offsets[t])], 1u)] = (unsigned)t;
+}
+
 __global__ void __launch_bounds__(256) k_order_hist(const unsigned* __restrict__ offsets, int n,
                                                     unsigned* __restrict__ hist) {
     __shared__ unsigned h[33];
@@ -364,14 +414,21 @@ cudaError_t launch_bin_count(const float* records, long long n, const Views& vs,
 }
 
 cudaError_t launch_scan(const Views& vs, unsigned* cursor, unsigned* block_sums, unsigned* offsets,
-                        unsigned long long capacity, WsHeader* hdr, cudaStream_t s) {
+                        unsigned long long capacity, WsHeader* hdr, unsigned* buckets, unsigned* order,
+                        cudaStream_t s) {
     const int n = vs.total_tiles;
+    if (n <= kSmallScanTiles) {
+        k_scan_order_small<<<1, kScanBlock, 0, s>>>(cursor, n, offsets, capacity, hdr, order);
+        return cudaGetLastError();
+    }
     const int nb = (n + kScanTile - 1) / kScanTile;
     unsigned long long* bsum = reinterpret_cast<unsigned long long*>(block_sums);
     k_scan_reduce<<<nb, kScanBlock, 0, s>>>(cursor, n, bsum);
     k_scan_top<<<1, kScanBlock, 0, s>>>(bsum, nb, offsets, n, capacity, hdr);
     k_scan_apply<<<nb, kScanBlock, 0, s>>>(cursor, n, bsum, offsets, capacity);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !order) return e;
+    return launch_tile_order(vs, offsets, buckets, order, s);
 }
 
 cudaError_t launch_bin_scatter(const float* records, long long n, const Views& vs, unsigned* cursor,

@@ -31,13 +31,17 @@ constexpr int kLT = 32;                     // output tile side
 constexpr int kIn = kLT + 4 * kR;           // staged input side (52)
 constexpr int kSt = kLT + 2 * kR;           // statistics side (42)
 constexpr int kLossThreads = 256;
+constexpr int kStage = (kIn * kIn + kLossThreads - 1) / kLossThreads;   // staged pixels per thread
 // Shared memory, in floats: the staged (rendered, target) pairs, then the horizontally filtered
 // statistics as (mu_x, mu_y) and (E[x^2], E[y^2]) pairs and E[xy].  The loss partials with
 // respect to (mu_x, E[x^2]) as pairs and E[xy] reuse the staged pixels (no longer needed after
-// the statistics); the filtered partials reuse the statistics.
-constexpr int kLossSmemFloats = 2 * kIn * kIn + 5 * kIn * kSt;
-static_assert(3 * kSt * kSt <= 2 * kIn * kIn, "partials reuse the staged pixels");
-static_assert(3 * kSt * kLT <= 5 * kIn * kSt, "filtered partials reuse the statistics buffer");
+// the statistics); the filtered partials reuse the statistics.  The partials' rows are kMP
+// apart and the filtered partials' kFP apart (odd numbers of 8-byte words): the horizontal
+// pass reads them a row per lane, and its lanes then fall on distinct banks.
+constexpr int kMP = kSt + 1, kFP = kLT + 1;
+constexpr int kStatOff = ((3 * kSt * kMP > 2 * kIn * kIn ? 3 * kSt * kMP : 2 * kIn * kIn) + 3) / 4 * 4;
+constexpr int kLossSmemFloats = kStatOff + 5 * kIn * kSt;      // the statistics start at kStatOff
+static_assert(3 * kSt * kFP <= 5 * kIn * kSt, "layout");
 // register blocking of the four filter passes (outputs per item along the filtered axis)
 constexpr int kH1 = kSt / 3;                // horizontal statistics: 3 columns
 constexpr int kV2 = 7, kS2 = kSt / kV2;     // vertical statistics: 7 rows
@@ -65,13 +69,13 @@ __global__ void __launch_bounds__(kLossThreads, 3) k_loss_3dgs(const float* __re
                                                                float* __restrict__ loss, float* __restrict__ grad) {
     extern __shared__ __align__(16) float sm[];
     float2* sxy = reinterpret_cast<float2*>(sm);                   // [kIn][kIn] (rendered, target)
-    float2* h01 = reinterpret_cast<float2*>(sm + 2 * kIn * kIn);   // [kIn][kSt] filtered (x, y)
+    float2* h01 = reinterpret_cast<float2*>(sm + kStatOff);        // [kIn][kSt] filtered (x, y)
     float2* h23 = h01 + kIn * kSt;                                 // [kIn][kSt] filtered (x^2, y^2)
     float* h4 = reinterpret_cast<float*>(h23 + kIn * kSt);         // [kIn][kSt] filtered x y
-    float2* m01 = reinterpret_cast<float2*>(sm);                   // [kSt][kSt] partials: mu_x, E[x^2]
-    float* m2 = reinterpret_cast<float*>(m01 + kSt * kSt);         // [kSt][kSt] partial: E[xy]
-    float2* f01 = h01;                                             // [kSt][kLT] horizontally filtered
-    float* f2s = reinterpret_cast<float*>(f01 + kSt * kLT);        // [kSt][kLT]
+    float2* m01 = reinterpret_cast<float2*>(sm);                   // [kSt][kMP] partials: mu_x, E[x^2]
+    float* m2 = reinterpret_cast<float*>(m01 + kSt * kMP);         // [kSt][kMP] partial: E[xy]
+    float2* f01 = h01;                                             // [kSt][kFP] horizontally filtered
+    float* f2s = reinterpret_cast<float*>(f01 + kSt * kFP);        // [kSt][kFP]
     __shared__ float red[kLossThreads / 32];
     const int tid = threadIdx.x;
 
@@ -89,15 +93,25 @@ __global__ void __launch_bounds__(kLossThreads, 3) k_loss_3dgs(const float* __re
     for (int k = 0; k < 2 * kR + 1; ++k) g2[k] = f2(L.g[k], L.g[k]);
 
     for (int c = 0; c < 3; ++c) {
-        for (int i = tid; i < kIn * kIn; i += kLossThreads) {
-            const int iy = i / kIn, ix = i - iy * kIn;
-            const int gx = x0 - 2 * kR + ix, gy = y0 - 2 * kR + iy;
-            float2 ab = f2(0.f, 0.f);
-            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-                const long long p = (base + (long long)gy * W + gx) * 3 + c;
-                ab = f2(rgb[p], tgt[p]);
+        {
+            // all of a thread's loads first, then the stores: kStage independent loads in flight
+            float2 ab[kStage];
+#pragma unroll
+            for (int k = 0; k < kStage; ++k) {
+                const int i = tid + k * kLossThreads;
+                const int iy = i / kIn, ix = i - iy * kIn;
+                const int gx = x0 - 2 * kR + ix, gy = y0 - 2 * kR + iy;
+                ab[k] = f2(0.f, 0.f);
+                if (i < kIn * kIn && gx >= 0 && gx < W && gy >= 0 && gy < H) {
+                    const long long p = (base + (long long)gy * W + gx) * 3 + c;
+                    ab[k] = f2(__ldg(rgb + p), __ldg(tgt + p));
+                }
             }
-            sxy[i] = ab;
+#pragma unroll
+            for (int k = 0; k < kStage; ++k) {
+                const int i = tid + k * kLossThreads;
+                if (i < kIn * kIn) sxy[i] = ab[k];
+            }
         }
         __syncthreads();
         // horizontal statistics: three neighbouring columns per item from one window of 13
@@ -186,21 +200,21 @@ __global__ void __launch_bounds__(kLossThreads, 3) k_loss_3dgs(const float* __re
                     p2 = gs * (2.f * a1 * ib1 * ib2);
                     if (col_own && jy >= kR && jy < kR + kLT) ss += sv;
                 }
-                const int i = jy * kSt + jx;
+                const int i = jy * kMP + jx;
                 m01[i] = p01;
                 m2[i] = p2;
             }
         }
         __syncthreads();
-        // horizontal pass of the partials: four columns per item
+        // horizontal pass of the partials: four columns per item, consecutive lanes on consecutive rows
         for (int it = tid; it < kSt * kB3; it += kLossThreads) {
-            const int jy = it / kB3, ox0 = (it - jy * kB3) * kH3;
+            const int blk = it / kSt, jy = it - blk * kSt, ox0 = blk * kH3;
             float2 r[kH3 + 2 * kR];
             float r2[kH3 + 2 * kR];
 #pragma unroll
             for (int k = 0; k < kH3 + 2 * kR; ++k) {
-                r[k] = m01[jy * kSt + ox0 + k];
-                r2[k] = m2[jy * kSt + ox0 + k];
+                r[k] = m01[jy * kMP + ox0 + k];
+                r2[k] = m2[jy * kMP + ox0 + k];
             }
 #pragma unroll
             for (int o = 0; o < kH3; ++o) {
@@ -211,8 +225,8 @@ __global__ void __launch_bounds__(kLossThreads, 3) k_loss_3dgs(const float* __re
                     acc = __ffma2_rn(g2[k], r[o + k], acc);
                     acc2 = fmaf(g2[k].x, r2[o + k], acc2);
                 }
-                f01[jy * kLT + ox0 + o] = acc;
-                f2s[jy * kLT + ox0 + o] = acc2;
+                f01[jy * kFP + ox0 + o] = acc;
+                f2s[jy * kFP + ox0 + o] = acc2;
             }
         }
         __syncthreads();
@@ -224,8 +238,19 @@ __global__ void __launch_bounds__(kLossThreads, 3) k_loss_3dgs(const float* __re
             float c2[kV4 + 2 * kR];
 #pragma unroll
             for (int r = 0; r < kV4 + 2 * kR; ++r) {
-                cc[r] = f01[(oy0 + r) * kLT + ox];
-                c2[r] = f2s[(oy0 + r) * kLT + ox];
+                cc[r] = f01[(oy0 + r) * kFP + ox];
+                c2[r] = f2s[(oy0 + r) * kFP + ox];
+            }
+            float av[kV4], bv[kV4];            // the staged copies are overwritten by now: read them again
+#pragma unroll
+            for (int o = 0; o < kV4; ++o) {
+                const int gy = y0 + oy0 + o;
+                av[o] = bv[o] = 0.f;
+                if (gx < W && gy < H) {
+                    const long long pix = (base + (long long)gy * W + gx) * 3 + c;
+                    av[o] = __ldg(rgb + pix);
+                    bv[o] = __ldg(tgt + pix);
+                }
             }
             float2 f[kV4];
             float fx[kV4];
@@ -247,7 +272,7 @@ __global__ void __launch_bounds__(kLossThreads, 3) k_loss_3dgs(const float* __re
                 const int oy = oy0 + o, gy = y0 + oy;
                 if (gy >= H) break;
                 const long long pix = (base + (long long)gy * W + gx) * 3 + c;
-                const float a = rgb[pix], b = tgt[pix];      // the staged copies are overwritten by now
+                const float a = av[o], b = bv[o];
                 const float d = a - b;
                 l1 += fabsf(d);
                 const float gd = d > 0.f ? gl1 : (d < 0.f ? -gl1 : 0.f);

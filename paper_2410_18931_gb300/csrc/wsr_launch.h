@@ -34,15 +34,15 @@ cudaError_t launch_project_bwd(const GaussPtrs& g, const Views& vs, WeightDev w,
 
 cudaError_t launch_bin_count(const float* records, long long n, const Views& vs,
                              unsigned* cursor, cudaStream_t s);
+// the scan of the per-tile counts into offsets (and the scatter's cursors); with `order`, also
+// the persistent schedule's longest-first tile order (`buckets`: 66 words of scratch)
 cudaError_t launch_scan(const Views& vs, unsigned* cursor, unsigned* block_sums,
                         unsigned* tile_offsets, unsigned long long capacity, WsHeader* hdr,
-                        cudaStream_t s);
+                        unsigned* buckets, unsigned* order, cudaStream_t s);
 cudaError_t launch_bin_scatter(const float* records, long long n, const Views& vs,
                                unsigned* cursor, unsigned* tile_list,
                                unsigned long long capacity, WsHeader* hdr, cudaStream_t s);
 
-cudaError_t launch_tile_order(const Views& vs, const unsigned* tile_offsets, unsigned* buckets,
-                              unsigned* order, cudaStream_t s);
 // deterministic mode: each tile's list sorted by record index
 cudaError_t launch_sort_segments(const Views& vs, const unsigned* tile_offsets, unsigned* tile_list,
                                  WsHeader* hdr, cudaStream_t s);

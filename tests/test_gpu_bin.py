@@ -75,23 +75,23 @@ def _allowed(g, ty, tx, W, H, tw, th):
     return bool(np.any((cols >= xl - d) & (cols <= xr + d)))
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8), (16, 8)])
-def test_tile_lists_hold_exactly_the_footprint_tiles(tile):
+def _check_lists(sc, cam, w, tile, persistent=False):
+    """Bins one view and checks its lists against the footprint geometry;
+    returns the rendered image."""
     import torch
     from paper_2410_18931_gb300 import Gaussians, Renderer
-    sc = _scene()
-    cam = ws.look_at((0.3, -0.2, -3.6), width=200, height=150).rounded()
-    w = ws.WeightParams(ws.EXP, 0.1, 0.8, 0.9, (0.1, 0.2, 0.1))
     g = Gaussians.from_scene(sc)
-    r = Renderer([cam], tile=tile)
+    r = Renderer([cam], tile=tile, persistent=persistent)
     st = r.forward(g, w.kind, torch.tensor(w.as_array(), device="cuda"))
     torch.cuda.synchronize()
     off = st.tile_offsets.cpu().numpy().astype(np.int64)
     lst = st.tile_list.cpu().numpy().astype(np.int64)
     tw, th = tile
     tiles_x = -(-cam.width // tw)
+    assert len(off) - 1 == tiles_x * -(-cam.height // th)
+    assert off[0] == 0 and np.all(np.diff(off) >= 0)
     listed = {}
-    for t in range(len(off) - 1):
+    for t in np.flatnonzero(np.diff(off)):
         ids = lst[off[t]:off[t + 1]]
         assert len(np.unique(ids)) == len(ids), t                # no pair twice
         for i in ids.tolist():
@@ -110,6 +110,29 @@ def test_tile_lists_hold_exactly_the_footprint_tiles(tile):
             assert _allowed(allowed[i], ty, tx, cam.width, cam.height, tw, th), (i, ty, tx)
             extra += 1
     assert extra <= 0.03 * n_must, (extra, n_must)
+    return st.rgb.cpu().numpy()
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8), (16, 8)])
+def test_tile_lists_hold_exactly_the_footprint_tiles(tile):
+    cam = ws.look_at((0.3, -0.2, -3.6), width=200, height=150).rounded()
+    w = ws.WeightParams(ws.EXP, 0.1, 0.8, 0.9, (0.1, 0.2, 0.1))
+    _check_lists(_scene(), cam, w, tile)
+
+
+@pytest.mark.parametrize("height", [1024, 1032])
+def test_tile_lists_and_order_around_the_one_block_scan_limit(height):
+    """The scan and the persistent schedule's tile order run in one block up
+    to 32768 tiles and in three passes beyond: 8x8 tiles on 2048 x 1024
+    (32768 tiles) and 2048 x 1032 (33024).  The lists hold the footprint
+    tiles, and the persistent schedule (which walks the tile order) renders
+    the image the one-block-per-tile schedule does."""
+    cam = ws.look_at((0.3, -0.2, -2.2), width=2048, height=height).rounded()
+    w = ws.WeightParams(ws.EXP, 0.1, 0.8, 0.9, (0.1, 0.2, 0.1))
+    sc = _scene()
+    a = _check_lists(sc, cam, w, (8, 8), persistent=True)
+    b = _check_lists(sc, cam, w, (8, 8), persistent=False)
+    assert np.abs(a - b).max() <= 2e-6
 
 
 def test_tile_lists_of_several_uneven_views_in_one_call():
