@@ -58,6 +58,11 @@ def _truth(P, W, H, tw, th):
 
 def _allowed(g, ty, tx, W, H, tw, th):
     mx, my, A, B, C, ex, ey = g
+    # the kernel's footprint is q <= 9 (1 + 1e-4) + 1.4e-4 (it keeps every pixel centre whose FP32 q
+    # reaches the cutoff); taken here as q <= CUT_K.  Near a row where the ellipse is tangent, that
+    # widening moves the x-extent by about sqrt(9e-4 / A), more than a pixel fraction on big footprints.
+    cut_k = CUT * 1.0002 + 5e-4
+    ex, ey = ex * np.sqrt(cut_k / CUT), ey * np.sqrt(cut_k / CUT)
     # the tile's band of pixel-centre rows, inside the footprint's y-extent (the kernel pads
     # the extents by a relative 1e-4 and 0.01 pixel: rows that close are allowed too)
     sy = 1e-3 * ey + 0.02
@@ -67,7 +72,7 @@ def _allowed(g, ty, tx, W, H, tw, th):
         return False
     # x-extent of {q <= 9} over dy in [ya, yb]: for fixed dy, dx = (-B dy +- sqrt(B^2 dy^2 - A (C dy^2 - 9))) / A
     dys = np.linspace(ya, yb, 257)
-    disc = np.maximum(B * B * dys ** 2 - A * (C * dys ** 2 - CUT), 0.0)
+    disc = np.maximum(B * B * dys ** 2 - A * (C * dys ** 2 - cut_k), 0.0)
     xl = np.min((-B * dys - np.sqrt(disc)) / A)
     xr = np.max((-B * dys + np.sqrt(disc)) / A)
     d = 5e-3 * ex + 0.05 + (yb - ya) / 256 * abs(B / A)       # margin plus the sampling step in dy
