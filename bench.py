@@ -50,8 +50,7 @@ FP32_LANES_PER_SM = 128
 MUFU_PER_SM = 16         # ex2 / rsqrt / rcp results per SM and clock
 SM_MAX_MHZ = 2070.0
 METRIC = "fwd and fwd+bwd Mpix/s at 1M Gaussians 1080p vs plain FP32 path; max err"
-KERNELS_PER_STEP = 10    # project 1, bin 5 (count, 3 scan, scatter), fwd 1, loss 1, bwd tiles 1, project bwd 1
-ORDER_KERNELS = 3        # the persistent schedule's tile order (histogram, scan, scatter) inside wsr_bin
+KERNELS_PER_STEP = 5     # project 1, fwd 1, loss 1, bwd tiles 1, project bwd 1; plus wsr_bin's (Renderer.bin_kernels)
 
 
 # --------------------------------------------------------------------------
@@ -463,7 +462,7 @@ def run_ours(args):
     scene, cam, weight, extra, target = build_workload(args, rank, world)
     tile, persistent, chunk, tune_ms = launch_config(args, scene, cam, weight, target)
     S = Step(scene, cam, weight, tile, target, persistent, chunk)
-    kernels_per_step = KERNELS_PER_STEP + (ORDER_KERNELS if persistent else 0)
+    kernels_per_step = KERNELS_PER_STEP + S.r.bin_kernels
     A = S.A
     npix = cam.width * cam.height
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -590,7 +589,9 @@ def run_ours(args):
         line["autotune_ms"] = tune_ms
 
     if world == 1 and not args.no_deterministic:
-        line["deterministic"] = run_deterministic(S, scene, cam, weight, target, tile, persistent, chunk, flush)
+        # the deterministic mode's own launch configuration: 16x16 tiles (fewer instances, so fewer of its
+        # fixed-point atomics and shorter lists to sort), persistent, 512 Gaussians per backward block
+        line["deterministic"] = run_deterministic(S, scene, cam, weight, target, (16, 16), True, 512, flush)
     if world == 1 and not args.no_batched:
         line["batched"] = run_batched(cpu_leg=not args.no_cpu_baseline)
     if world == 1 and not args.no_reduced:
@@ -613,20 +614,22 @@ def run_deterministic(S, scene, cam, weight, target, tile, persistent, chunk, fl
     """The same step in the deterministic mode (tile lists sorted by record
     index, fixed-point gradient sums in two backward passes): its time, and
     whether two runs give the same bits.  The sort holds a bounded number of
-    instances per tile; when the step's tiles hold more, the leg takes 8x8
-    tiles."""
+    instances per tile; when a tile holds more, the leg takes 8x8 tiles."""
     import numpy as np
     import torch
-    off = S.st.tile_offsets.to(torch.int64)
+    D = None
+    for t in (tile, (8, 8)):
+        try:
+            D = Step(scene, cam, weight, t, target, persistent, chunk, deterministic=True)
+            tile = t
+            break
+        except S.A.WSRError as e:
+            if e.status != S.A.WSR_ERR_UNSUPPORTED:
+                raise
+    if D is None:
+        return {"unsupported": f"a tile holds more than {S.A.WSR_DET_MAX_SEGMENT} instances (8x8 tiles)"}
+    off = D.st.tile_offsets.to(torch.int64)
     longest = int((off[1:] - off[:-1]).max())
-    if longest > S.A.WSR_DET_MAX_SEGMENT:
-        tile, chunk = (8, 8), 128
-    try:
-        D = Step(scene, cam, weight, tile, target, persistent, chunk, deterministic=True)
-    except S.A.WSRError as e:
-        if e.status != S.A.WSR_ERR_UNSUPPORTED:
-            raise
-        return {"unsupported": f"a tile holds more than {S.A.WSR_DET_MAX_SEGMENT} instances ({tile[0]}x{tile[1]} tiles)"}
     outs = []
     for _ in range(2):
         D.run()
@@ -644,15 +647,15 @@ def run_deterministic(S, scene, cam, weight, target, tile, persistent, chunk, fl
         stages.append([evs[k].elapsed_time(evs[k + 1]) for k in range(6)])
     ms = float(np.mean(times))
     st_ms = np.mean(np.array(stages), axis=0)
-    stage_names = D.stage_names
+    stage_names, bin_kernels = D.stage_names, D.r.bin_kernels
     del D, outs
     torch.cuda.empty_cache()
     return {"ms_per_step": round(ms, 4), "fwd_bwd_mpix_s": round(cam.width * cam.height / (ms * 1e-3) / 1e6, 2),
             "stage_ms": {k: round(float(v), 4) for k, v in zip(stage_names, st_ms)},
             "tile": "%dx%d" % tile, "schedule": "persistent" if persistent else "per-tile", "chunk": chunk,
             "longest_tile_list": longest, "bitwise_repeat": bool(same),
-            # + the list sort, the backward's magnitude pass and the two ordered reductions
-            "kernels_per_step": KERNELS_PER_STEP + (ORDER_KERNELS if persistent else 0) + 4}
+            # + the backward's magnitude pass and the two ordered reductions (the list sort is in bin_kernels)
+            "kernels_per_step": KERNELS_PER_STEP + bin_kernels + 3}
 
 
 def run_e2e(args, S, scene, weight, target, flush):
@@ -969,8 +972,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", type=int, default=3)
     # the defaults are the autotuner's choice for the 1M-Gaussian 1080p view on a GB300 (16x8 tiles,
-    # persistent schedule, 512 Gaussians per backward block); "auto" runs the tuner before the timed region
-    ap.add_argument("--tile", default="16x8", help="WxH (16x16, 8x8, 32x8, 16x8) or auto")
+    # persistent schedule, 512 Gaussians per backward block; the deterministic mode 16x16 tiles);
+    # "auto" runs the tuner before the timed region
+    ap.add_argument("--tile", default=None, help="WxH (16x16, 8x8, 32x8, 16x8) or auto")
     ap.add_argument("--schedule", default="persistent", choices=["auto", "per-tile", "persistent"])
     ap.add_argument("--chunk", default="512", choices=["auto", "128", "64", "256", "512"],
                     help="Gaussians per block of the backward")
@@ -990,7 +994,7 @@ def main():
     if args.deterministic_only:
         import torch
         torch.cuda.set_device(0)
-        tile = (16, 8) if args.tile == "auto" else tuple(int(v) for v in args.tile.split("x"))
+        tile = (16, 16) if args.tile in (None, "auto") else tuple(int(v) for v in args.tile.split("x"))
         persistent = args.schedule != "per-tile"
         chunk = 512 if args.chunk == "auto" else int(args.chunk)
         scene, cam, weight, extra, target = build_workload(args, 0, 1)
@@ -1003,12 +1007,14 @@ def main():
         import torch
         torch.cuda.set_device(0)
         # the launch configuration as given; "auto" takes what the tuner picks for this view on a GB300
-        tile = (16, 8) if args.tile == "auto" else tuple(int(v) for v in args.tile.split("x"))
+        tile = (16, 8) if args.tile in (None, "auto") else tuple(int(v) for v in args.tile.split("x"))
         persistent = args.schedule != "per-tile"
         chunk = 512 if args.chunk == "auto" else int(args.chunk)
         print(json.dumps(run_training(steps=args.steps, warmup=args.warmup, tile=tile, persistent=persistent,
                                       chunk=chunk)), flush=True)
         return
+    if args.tile is None:
+        args.tile = "16x8"
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -70,6 +70,7 @@ enum { WSR_OPACITY_LOGIT = 0, WSR_OPACITY_SH = 1 };
 #define WSR_GRAD_RECORD_FLOATS 12 /* one 2D gradient record: 48 bytes (9 used) */
 #define WSR_GRAD_RECORD_FLOATS_DET 32 /* one record in deterministic mode: 128 bytes */
 #define WSR_DET_MAX_SEGMENT 8192  /* deterministic mode: most instances one tile may hold */
+#define WSR_SCAN_ONE_BLOCK_TILES 32768  /* wsr_bin scans (and orders) up to this many tiles in one kernel */
 
 /* Pinhole camera (passed by value through host memory). */
 typedef struct {

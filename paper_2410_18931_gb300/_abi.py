@@ -23,6 +23,7 @@ WSR_RECORD_FLOATS = 12
 WSR_GRAD_RECORD_FLOATS = 12
 WSR_GRAD_RECORD_FLOATS_DET = 32      # deterministic mode: 9 int64 sums and 9 magnitudes per record
 WSR_DET_MAX_SEGMENT = 8192
+WSR_SCAN_ONE_BLOCK_TILES = 32768     # wsr_bin scans (and orders) up to this many tiles in one kernel
 WSR_BIN_STATIC_MAX_TILES = 65536     # tiles over all views that wsr_bin_static handles
 WSR_BIN_STATIC_BYTES = 270848        # its fixed scratch array, held by every GPU that loads the library
 

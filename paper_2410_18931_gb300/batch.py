@@ -80,9 +80,9 @@ class GraphStep:
 
     @property
     def kernels_per_step(self) -> int:
-        # project 1, bin 5 (+3 tile-order kernels when persistent), fwd 1, loss 1, bwd 1, project bwd 1;
-        # deterministic: + the list sort, a second backward pass and two ordered reductions
-        return 10 + (3 if self.r.persistent else 0) + (4 if self.r.deterministic else 0)
+        # project 1, bin (Renderer.bin_kernels), fwd 1, loss 1, bwd 1, project bwd 1;
+        # deterministic: + a second backward pass and two ordered reductions
+        return 5 + self.r.bin_kernels + (3 if self.r.deterministic else 0)
 
 
 def time_step(step: GraphStep, reps: int = 5, warmup: int = 2, flush: torch.Tensor | None = None) -> float:

@@ -14,6 +14,8 @@
 // A tile is listed when a pixel-centre column of it meets the footprint
 // q <= 9 within the tile's band of pixel-centre rows (the ellipse's exact
 // extent per tile row), not merely when it meets the bounding box.
+#include <mutex>
+
 #include "wsr_launch.h"
 
 namespace wsr {
@@ -278,38 +280,60 @@ __device__ __forceinline__ int cost_bucket(unsigned c) { return c ? 32 - __clz(c
 
 // Exclusive scan over the tiles and, for the persistent schedule, the longest-first
 // tile order (the buckets of k_order_*), in one block: for views of at most
-// kSmallScanTiles tiles.  Thread k takes consecutive tiles [k per, (k + 1) per).
-constexpr int kSmallScanTiles = kScanBlock * 32;
+// kSmallScanTiles tiles.  The counts pass through shared memory (dynamic, n + 1
+// words) so that every global access is coalesced.  Warp w scans the
+// consecutive tiles [w seg, (w + 1) seg), 32 at a time (lane l on tile 32 i + l
+// of its range: no bank conflicts), after one block scan of the warps' totals.
+constexpr int kSmallScanTiles = WSR_SCAN_ONE_BLOCK_TILES;
+static_assert(kSmallScanTiles % kScanBlock == 0, "whole segments");
 
 __global__ void __launch_bounds__(kScanBlock) k_scan_order_small(unsigned* __restrict__ cursor, int n,
                                                                  unsigned* __restrict__ offsets,
                                                                  unsigned long long capacity, WsHeader* hdr,
                                                                  unsigned* __restrict__ order) {
+    extern __shared__ unsigned s_off[];         // [n + 1]: the counts, then the offsets
     __shared__ unsigned long long s_warp[33];
     __shared__ unsigned s_hist[33];
     const unsigned long long lim = capacity < 0xffffffffull ? capacity : 0xffffffffull;
-    const int per = (n + kScanBlock - 1) / kScanBlock;
-    const int b0 = min((int)threadIdx.x * per, n), b1 = min(b0 + per, n);
-    unsigned long long x = 0;
-    for (int t = b0; t < b1; ++t) x += cursor[t];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = threadIdx.x; t < n; t += kScanBlock) s_off[t] = cursor[t];
     if (threadIdx.x < 33) s_hist[threadIdx.x] = 0u;
+    __syncthreads();
+    const int seg = (n + kScanBlock - 1) / kScanBlock * 32;             // tiles per warp, a multiple of 32
+    const int w0 = min(warp * seg, n), w1 = min(w0 + seg, n);
+    unsigned long long x = 0;
+    for (int t = w0 + lane; t < w1; t += 32) x += s_off[t];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
     unsigned long long tot;
-    unsigned long long run = block_exclusive_scan(x, s_warp, tot);   // ends with a barrier
-    for (int t = b0; t < b1; ++t) {
-        const unsigned c = cursor[t];
-        const unsigned o = (unsigned)(run < lim ? run : lim);
-        offsets[t] = o;
-        cursor[t] = o;                  // the scatter's cursor starts at the tile's offset
-        run += c;
+    unsigned long long carry = block_exclusive_scan(lane == 0 ? x : 0ull, s_warp, tot);   // ends with a barrier
+    carry = __shfl_sync(0xffffffffu, carry, 0);
+    for (int t0 = w0; t0 < w1; t0 += 32) {
+        const int t = t0 + lane;
+        const unsigned c = t < w1 ? s_off[t] : 0u;
+        unsigned long long inc = c;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc += y;
+        }
+        const unsigned long long run = carry + inc - c;
+        if (t < w1) s_off[t] = (unsigned)(run < lim ? run : lim);
+        carry += __shfl_sync(0xffffffffu, inc, 31);
     }
     if (threadIdx.x == 0) {
-        offsets[n] = (unsigned)(tot < lim ? tot : lim);
+        s_off[n] = (unsigned)(tot < lim ? tot : lim);
         hdr->total = tot;
         if (tot > lim) set_error(hdr, WSR_ERR_CAPACITY);
     }
+    __syncthreads();
+    for (int t = threadIdx.x; t <= n; t += kScanBlock) {
+        const unsigned o = s_off[t];
+        offsets[t] = o;
+        if (t < n) cursor[t] = o;       // the scatter's cursor starts at the tile's offset
+    }
     if (!order) return;
-    __syncthreads();                    // the block's offsets are visible to all its threads
-    for (int t = b0; t < b1; ++t) atomicAdd(&s_hist[cost_bucket(offsets[t + 1] - offsets[t])], 1u);
+    for (int t = threadIdx.x; t < n; t += kScanBlock) atomicAdd(&s_hist[cost_bucket(s_off[t + 1] - s_off[t])], 1u);
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned r = 0;                 // bucket starts, largest bucket first
@@ -320,8 +344,8 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_order_small(unsigned* __res
         }
     }
     __syncthreads();
-    for (int t = b0; t < b1; ++t)
-        order[atomicAdd(&s_hist[cost_bucket(offsets[t + 1] - offsets[t])], 1u)] = (unsigned)t;
+    for (int t = threadIdx.x; t < n; t += kScanBlock)
+        order[atomicAdd(&s_hist[cost_bucket(s_off[t + 1] - s_off[t])], 1u)] = (unsigned)t;
 }
 
 __global__ void __launch_bounds__(256) k_order_hist(const unsigned* __restrict__ offsets, int n,
@@ -418,7 +442,22 @@ cudaError_t launch_scan(const Views& vs, unsigned* cursor, unsigned* block_sums,
                         cudaStream_t s) {
     const int n = vs.total_tiles;
     if (n <= kSmallScanTiles) {
-        k_scan_order_small<<<1, kScanBlock, 0, s>>>(cursor, n, offsets, capacity, hdr, order);
+        const size_t smem = sizeof(unsigned) * ((size_t)n + 1);
+        if (smem > 48 * 1024) {
+            // the dynamic shared-memory opt-in is a per-device attribute: set once per device (thread-safe)
+            static std::once_flag once[64];
+            static cudaError_t once_err[64];
+            int dev = 0;
+            cudaError_t e = cudaGetDevice(&dev);
+            if (e != cudaSuccess) return e;
+            if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+            std::call_once(once[dev], [&] {
+                once_err[dev] = cudaFuncSetAttribute(k_scan_order_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)(sizeof(unsigned) * (kSmallScanTiles + 1)));
+            });
+            if (once_err[dev] != cudaSuccess) return once_err[dev];
+        }
+        k_scan_order_small<<<1, kScanBlock, smem, s>>>(cursor, n, offsets, capacity, hdr, order);
         return cudaGetLastError();
     }
     const int nb = (n + kScanTile - 1) / kScanTile;

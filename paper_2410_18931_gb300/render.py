@@ -90,6 +90,14 @@ class Renderer:
         self.chunk = int(chunk)
         self.tile = tuple(tile)
         self.num_tiles = int(self.lib.wsr_num_tiles(self.cams_c, self.n_cams, ctypes.byref(self.tiles_c)))
+        # kernels one wsr_bin launches: the count; the scan, in one kernel (with the persistent schedule's
+        # tile order) up to WSR_SCAN_ONE_BLOCK_TILES tiles, else three (and three for the order); the
+        # scatter; in the deterministic mode the sort of each tile's list
+        if self.num_tiles <= A.WSR_SCAN_ONE_BLOCK_TILES:
+            self.bin_kernels = 3
+        else:
+            self.bin_kernels = 5 + (3 if persistent else 0)
+        self.bin_kernels += 1 if self.deterministic else 0
         self.num_pix = int(self.lib.wsr_num_pixels(self.cams_c, self.n_cams))
         ws = int(self.lib.wsr_workspace_size(self.cams_c, self.n_cams, ctypes.byref(self.tiles_c)))
         if self.num_tiles <= 0 or ws == 0:

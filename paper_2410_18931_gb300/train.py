@@ -198,9 +198,9 @@ class TrainStep:
 
     @property
     def kernels_per_step(self) -> int:
-        # project 1, bin 5 (+3 tile-order kernels when persistent), fwd 1, loss 1, bwd 1, project bwd 1, Adam 2;
-        # deterministic: + the list sort, a second backward pass and two ordered reductions
-        return 12 + (3 if self.persistent else 0) + (4 if self.deterministic else 0)
+        # project 1, bin (Renderer.bin_kernels), fwd 1, loss 1, bwd 1, project bwd 1, Adam 2;
+        # deterministic: + a second backward pass and two ordered reductions
+        return 7 + self.r.bin_kernels + (3 if self.deterministic else 0)
 
     def train(self, steps: int, check_every: int = 10) -> torch.Tensor:
         """Make ``steps`` Adam updates; returns the loss triples {L, L1, SSIM}
