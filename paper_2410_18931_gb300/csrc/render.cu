@@ -54,8 +54,9 @@ struct Lanes {
 // A' = qw^2 + qd, B' = qs qw, C' = qs^2, det' = A' C' - B'^2 = qd qs^2:
 // c = -B' dy / A', h = sqrt(A' QM - det' dy^2) / A' (no cancellation anywhere),
 // widened by 0.02 pixel.  `row` gives the span of a local row as
-// (first column) | (units << 8), a unit being two horizontally adjacent
-// pixels (the second a padding pixel when the span's length is odd).
+// (first column, rounded down to even) | (column pairs << 8): the pairs from
+// that even column that hold the span (a padding pixel at either end lies
+// outside the footprint or in the tile's zero column).
 struct RowSpans {
     float Ap, hb, det, ia, ext;
     __device__ __forceinline__ RowSpans(const float4 a, const float qd, const float QM) {
@@ -81,8 +82,8 @@ struct RowSpans {
         const float fx0 = fmaxf(ceilf(cx - h - 0.52f), (float)x_org);
         const float fx1 = fminf(floorf(cx + h - 0.48f), (float)(x_org + x_lim - 1));
         if (!(fx0 <= fx1)) return 0;
-        const int xs = (int)fx0 - x_org, len = (int)fx1 - (int)fx0 + 1;
-        return (unsigned short)(xs | (((len + 1) >> 1) << 8));    // start, units
+        const int xs = (int)fx0 - x_org, len = (int)fx1 - (int)fx0 + 1, xe = xs & ~1;
+        return (unsigned short)(xe | (((xs - xe + len + 1) >> 1) << 8));    // even start, column pairs
     }
 };
 
@@ -332,17 +333,19 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
     constexpr int NT = BwdThreads<CH>::value;
     constexpr int NW = NT / 32;
     constexpr int PASSES = 2 * CH / NT;                // step A: (Gaussian, half) items per thread
-    constexpr int PW = TW + 1;                          // pixel-table row pitch: one zero column
+    constexpr int PP = TW / 2 + 1;                      // pixel-table row pitch in column pairs: one zero pair
     constexpr int HR = TH / 2;                          // rows per thread in step A
     constexpr int NB = TH + 1;                          // row counts 0 .. TH
     constexpr int NK = 2 * NB;                          // sort keys: narrow 0 .. TH, wide NB .. NB + TH
     static_assert(PASSES * NT == 2 * CH && TH % 2 == 0 && TW % 8 == 0 && TW <= 64 && CH <= 512 && NK <= NT, "layout");
-    __shared__ float4 spix[PW * TH + 1];        // per pixel: G/D (3), -(G.C)/D; zero column and pad entry
+    // per pixel: G/D (3), -(G.C)/D, stored per column pair as (x0, x1, y0, y1) and (z0, z1, w0, w1)
+    __shared__ float4 spA[PP * TH];
+    __shared__ float4 spB[PP * TH];
     __shared__ float4 s0[CH];                   // mu_x, mu_y, qs, qw
     __shared__ float4 s1[CH];                   // qd, u w, c_r u w, c_g u w
     __shared__ float2 s2[CH];                   // c_b u w, u w
     __shared__ unsigned sidx[CH];
-    __shared__ unsigned short sspan[CH][TH];    // per row: first column | units << 8 (a unit: two pixels)
+    __shared__ unsigned short sspan[CH][TH];    // per row: even first column | column pairs << 8
     __shared__ unsigned char sfirst[CH];        // first row with a span
     __shared__ unsigned char snst[CH];          // rows from there to the last row with a span
     __shared__ unsigned char skey[CH];          // sort key: rows, plus NB when wide
@@ -363,8 +366,8 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
     const float cB0 = __ldg(wparams + 3), cB1 = __ldg(wparams + 4), cB2 = __ldg(wparams + 5);
 
     float bg[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int p = tid; p < PW * TH + 1; p += NT) {
-        const int ly = p / PW, lx = p - ly * PW;
+    for (int p = tid; p < 2 * PP * TH; p += NT) {
+        const int ly = p / (2 * PP), lx = p - ly * (2 * PP);
         float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
         if (lx < x_lim && ly < y_lim) {
             const long long pix = V.pix_base + (long long)(y_org + ly) * V.W + x_org + lx;
@@ -378,7 +381,11 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
             bg[2] += f.y * wB;
             bg[3] += f.z * wB;
         }
-        spix[p] = f;
+        const int pi = 4 * (ly * PP + (lx >> 1)) + (lx & 1);
+        reinterpret_cast<float*>(spA)[pi] = f.x;
+        reinterpret_cast<float*>(spA)[pi + 2] = f.y;
+        reinterpret_cast<float*>(spB)[pi] = f.z;
+        reinterpret_cast<float*>(spB)[pi + 2] = f.w;
     }
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -476,47 +483,50 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 const float2 c2 = s2[j];
                 const float gx0 = (float)x_org + 0.5f - a.x;                 // dx of column 0
                 const float gy0 = (float)y_org + 0.5f - a.y;                 // dy of row 0
-                const float2 qs2 = f2(a.z, a.z), qw2 = f2(a.w, a.w), qd2 = f2(b.x, b.x), gx2 = f2(gx0, gx0);
-                const float2 cw0 = f2(-kLn2 * b.z, -kLn2 * b.w);     // -ln2 (c u w, u w): dL/dq' = e * (P . cw)
-                const float2 cw1 = f2(-kLn2 * c2.x, -kLn2 * c2.y);
-                // accumulators, paired: (cuw_r, cuw_g), (cuw_b, uw); and, over the two columns of a row, the
-                // moments of gq = dL/dq' in the record's own frame (r = qs dy + qw dx, dx):
+                const float qs = a.z;
+                const float2 qw2 = f2(a.w, a.w), qd2 = f2(b.x, b.x), gx2 = f2(gx0, gx0);
+                // -ln2 (c u w, u w), each twice: dL/dq' = e * (P . cw) for two pixels at once
+                const float2 cwr = f2(-kLn2 * b.z, -kLn2 * b.z), cwg = f2(-kLn2 * b.w, -kLn2 * b.w);
+                const float2 cwb = f2(-kLn2 * c2.x, -kLn2 * c2.x), cwu = f2(-kLn2 * c2.y, -kLn2 * c2.y);
+                // accumulators, each over the two pixels of a column pair: d/d(c u w) per channel, d/d(u w);
+                // and the moments of gq = dL/dq' in the record's own frame (r = qs dy + qw dx, dx):
                 // sum gq r^2, sum gq r dx, sum gq dx^2, sum gq r, sum gq dx.  Kept apart, a thin
                 // footprint's small along-axis terms (dx) are not rounded away under its large r terms.
-                float2 g01 = f2(0.f, 0.f), g23 = f2(0.f, 0.f);
+                float2 gr = f2(0.f, 0.f), gg = gr, gb = gr, gu = gr;
                 float2 srr = f2(0.f, 0.f), srx = srr, sxx = srr, sr = srr, sx = srr;
-                // dx of this lane's four offsets in a span (k + m L) from the span's first column, less that column
-                const float2 gxo[2] = {__fadd2_rn(f2((float)gk, (float)(gk + L)), gx2),
-                                       __fadd2_rn(f2((float)(gk + 2 * L), (float)(gk + 3 * L)), gx2)};
+                // dx of this lane's two column pairs (2 (k + m L), +1) from the row's even first column, less
+                // that column
+                const float2 gxo[2] = {__fadd2_rn(f2((float)(2 * gk), (float)(2 * gk + 1)), gx2),
+                                       __fadd2_rn(f2((float)(2 * (gk + L)), (float)(2 * (gk + L) + 1)), gx2)};
                 for (int st = 0; st < steps; ++st) {
                     const int ly = r0 + st;
                     const unsigned sp = sspan[j][ly];
-                    const int xs = (int)(sp & 0xffu);
-                    const int rowb = ly * PW, cb = rowb + xs, ce = rowb + TW;
-                    const float xsf = (float)xs;
-                    const float dyf = (float)ly + gy0;
-                    const float2 dy2 = f2(dyf, dyf);
+                    const int xe = (int)(sp & 0xffu);                           // even first column
+                    const int rowb = ly * PP, pb = rowb + (xe >> 1), pe = rowb + TW / 2;
+                    const float xsf = (float)xe;
+                    const float rb = qs * ((float)ly + gy0);                     // qs dy
+                    const float2 rb2 = f2(rb, rb);
 #pragma unroll
                     for (int m = 0; m < 2; ++m) {
-                        // Columns past the span evaluate q > 9 (the span holds every pixel centre of the row with
-                        // q' <= kQMax, with a margin), so the cutoff test zeroes them; columns past the tile read
-                        // the zero column.  No per-pixel validity mask is needed.
-                        const float4 P0 = spix[min(cb + gk + 2 * m * L, ce)];
-                        const float4 P1 = spix[min(cb + gk + (2 * m + 1) * L, ce)];
+                        // Columns outside the span evaluate q > 9 (the span holds every pixel centre of the row
+                        // with q' <= kQMax, with a margin), so the cutoff test zeroes them; pairs past the tile
+                        // read the zero pair.  No per-pixel validity mask is needed.
+                        const int pi = min(pb + gk + m * L, pe);
+                        const float4 A = spA[pi], B = spB[pi];          // (x0, x1, y0, y1), (z0, z1, w0, w1)
                         const float2 dx = __fadd2_rn(f2(xsf, xsf), gxo[m]);
-                        const float2 rr = __ffma2_rn(qs2, dy2, __fmul2_rn(qw2, dx));        // the forward's arithmetic
+                        const float2 rr = __ffma2_rn(qw2, dx, rb2);
                         const float2 q = __ffma2_rn(rr, rr, __fmul2_rn(__fmul2_rn(qd2, dx), dx));
-                        const float e0 = ex2_approx(q.x <= kQMax ? -q.x : -256.0f);          // 2^-256 flushes to 0
-                        const float e1 = ex2_approx(q.y <= kQMax ? -q.y : -256.0f);
+                        const float2 e = f2(ex2_approx(q.x <= kQMax ? -q.x : -256.0f),      // 2^-256 flushes to 0
+                                            ex2_approx(q.y <= kQMax ? -q.y : -256.0f));
                         // d/d(c u w) and d/d(u w) at fixed c u w
-                        g01 = __ffma2_rn(f2(P0.x, P0.y), f2(e0, e0), g01);
-                        g23 = __ffma2_rn(f2(P0.z, P0.w), f2(e0, e0), g23);
-                        g01 = __ffma2_rn(f2(P1.x, P1.y), f2(e1, e1), g01);
-                        g23 = __ffma2_rn(f2(P1.z, P1.w), f2(e1, e1), g23);
+                        gr = __ffma2_rn(f2(A.x, A.y), e, gr);
+                        gg = __ffma2_rn(f2(A.z, A.w), e, gg);
+                        gb = __ffma2_rn(f2(B.x, B.y), e, gb);
+                        gu = __ffma2_rn(f2(B.z, B.w), e, gu);
                         // dL/dq' per pixel: e * (P . cw)
-                        const float2 m0 = __ffma2_rn(f2(P0.z, P0.w), cw1, __fmul2_rn(f2(P0.x, P0.y), cw0));
-                        const float2 m1 = __ffma2_rn(f2(P1.z, P1.w), cw1, __fmul2_rn(f2(P1.x, P1.y), cw0));
-                        const float2 gq = __fmul2_rn(f2(e0, e1), f2(m0.x + m0.y, m1.x + m1.y));
+                        const float2 pc = __ffma2_rn(f2(B.z, B.w), cwu, __ffma2_rn(f2(B.x, B.y), cwb,
+                                                     __ffma2_rn(f2(A.z, A.w), cwg, __fmul2_rn(f2(A.x, A.y), cwr))));
+                        const float2 gq = __fmul2_rn(e, pc);
                         const float2 tr = __fmul2_rn(gq, rr), tx = __fmul2_rn(gq, dx);
                         srr = __ffma2_rn(tr, rr, srr);
                         srx = __ffma2_rn(tr, dx, srx);
@@ -528,7 +538,7 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 // the group's sums: record order sum gq r, sum gq dx, sum gq r^2, sum gq r dx, sum gq dx^2,
                 // d/d(u w), d/d(c u w)
                 float vals[9] = {sr.x + sr.y, sx.x + sx.y, srr.x + srr.y, srx.x + srx.y, sxx.x + sxx.y,
-                                 g23.y, g01.x, g01.y, g23.x};
+                                 gu.x + gu.y, gr.x + gr.y, gg.x + gg.y, gb.x + gb.y};
                 __syncwarp();
 #pragma unroll
                 for (int off = L / 2; off > 0; off >>= 1)
