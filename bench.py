@@ -971,9 +971,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", type=int, default=3)
-    # the defaults are the autotuner's choice for the 1M-Gaussian 1080p view on a GB300 (16x8 tiles,
-    # persistent schedule, 512 Gaussians per backward block; the deterministic mode 16x16 tiles);
-    # "auto" runs the tuner before the timed region
+    # the defaults are the autotuner's choice for the 1M-Gaussian 1080p view on a GB300 (16x16 tiles,
+    # persistent schedule, 512 Gaussians per backward block); "auto" runs the tuner before the timed region
     ap.add_argument("--tile", default=None, help="WxH (16x16, 8x8, 32x8, 16x8) or auto")
     ap.add_argument("--schedule", default="persistent", choices=["auto", "per-tile", "persistent"])
     ap.add_argument("--chunk", default="512", choices=["auto", "128", "64", "256", "512"],
@@ -1007,14 +1006,14 @@ def main():
         import torch
         torch.cuda.set_device(0)
         # the launch configuration as given; "auto" takes what the tuner picks for this view on a GB300
-        tile = (16, 8) if args.tile in (None, "auto") else tuple(int(v) for v in args.tile.split("x"))
+        tile = (16, 16) if args.tile in (None, "auto") else tuple(int(v) for v in args.tile.split("x"))
         persistent = args.schedule != "per-tile"
         chunk = 512 if args.chunk == "auto" else int(args.chunk)
         print(json.dumps(run_training(steps=args.steps, warmup=args.warmup, tile=tile, persistent=persistent,
                                       chunk=chunk)), flush=True)
         return
     if args.tile is None:
-        args.tile = "16x8"
+        args.tile = "16x16"
     if args.impl == "reference":
         run_reference(args)
     else:

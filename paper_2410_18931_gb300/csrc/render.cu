@@ -1,9 +1,10 @@
 // Per-pixel Weighted Sum Rendering, forward and backward (Eq. 7).
 //
 // One thread block per tile (or, with the persistent schedule, one per
-// resident slot taking tiles longest first).  The tile's Gaussian list (unordered: Eq. 7 is
-// a sum) is streamed through shared memory in chunks of one record per
-// thread; every thread owns a 2x2 block of pixels (two columns share each
+// resident slot taking tiles longest first).  Each warp of the block streams
+// the tile's Gaussian list (unordered: Eq. 7 is a sum) through shared memory
+// on its own, 32 records at a time, keeping those whose footprint reaches its
+// rows; every thread owns a 2x2 block of pixels (two columns share each
 // paired float2 FP32 instruction) and accumulates, in FP32 registers,
 //     N += (c u w) e,   D += (u w) e,   e = exp(-q/2) = 2^(-q'),   q <= 9
 // with q' = q log2(e)/2 evaluated from the record's sum of squares
@@ -14,10 +15,9 @@
 //
 // The backward recomputes every (pixel, Gaussian) term from the records and
 // the stored C and denominator (no per-pixel lists are kept).  It walks the
-// pixels inside each Gaussian's footprint (per-row spans) with the work split
-// evenly over the threads, so no lane idles on pixels outside a footprint and
-// no per-pair reduction across lanes is needed; per Gaussian it adds d/d(u w),
-// d/d(c u w) and moments of dL/dq' to a gradient record.
+// pixels of each Gaussian's footprint row by row (per-row spans), a group of
+// lanes per Gaussian, and per Gaussian adds d/d(u w), d/d(c u w) and moments
+// of dL/dq' to a gradient record.
 #include "wsr_launch.h"
 
 namespace wsr {
@@ -114,26 +114,25 @@ __device__ __forceinline__ void fwd_tile(const int tile, const float4* __restric
                                          const Views& vs, const float* __restrict__ wparams,
                                          float* __restrict__ out_rgb, float* __restrict__ out_den) {
     using S = FwdShape<TW, TH, PX>;
-    constexpr int NT = S::NT;
     constexpr int NW = S::NW;
-    __shared__ float4 s0[NT];   // mu_x, mu_y, qs, qw
-    __shared__ float4 s1[NT];   // qd, u w, c_r u w, c_g u w
-    __shared__ float2 s2[NT];   // c_b u w, u w
-    __shared__ float4 s3[NT];   // at the tile's first pixel centre: r, qd dx^2, 2 qd dx; and qd
-    // with several warps: bit w of smask[j] = Gaussian j reaches a pixel centre of warp w's rows,
-    // and each warp walks only the Gaussians of its own list
-    __shared__ unsigned smask[NT];
-    __shared__ unsigned char swl[NW][NT];
+    // per warp, the Gaussians of its current batch that reach its rows
+    __shared__ float4 s0[NW][32];   // mu_x, mu_y, qs, qw
+    __shared__ float4 s1[NW][32];   // qd, u w, c_r u w, c_g u w
+    __shared__ float2 s2[NW][32];   // c_b u w, u w
+    __shared__ float4 s3[NW][32];   // at the tile's first pixel centre: r, qd dx^2, 2 qd dx; and qd
 
     const TileCoord tc = tile_coord(vs, tile);
     const View& V = vs.v[tc.v];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int x0 = tc.tx * TW + (tid % S::BX) * PX;
     const int y0 = tc.ty * TH + (tid / S::BX) * S::PY;
     // offsets of the block's pixels from the tile's first pixel (PX == 1: the first column only, its two
     // rows paired instead)
     const float2 ox = f2((float)(x0 - tc.tx * TW), (float)(x0 - tc.tx * TW + 1));
     const float oy0 = (float)(y0 - tc.ty * TH), oy1 = oy0 + 1.0f;
+    // the warp's pixel-centre rectangle
+    const float xl = (float)(tc.tx * TW) + 0.5f, xh = xl + (float)(TW - 1);
+    const float yl = (float)(tc.ty * TH + S::row_lo(w)) + 0.5f, yh = (float)(tc.ty * TH + S::row_hi(w)) + 0.5f;
 
     // accumulators per pixel (column c, row r): (N_r, N_g) and (N_b, D)
     float2 rg[2][2], bd[2][2];
@@ -142,57 +141,40 @@ __device__ __forceinline__ void fwd_tile(const int tile, const float4* __restric
 #pragma unroll
         for (int c = 0; c < 2; ++c) rg[r][c] = bd[r][c] = f2(0.f, 0.f);
 
+    // Each warp takes the tile's list 32 Gaussians at a time on its own (no block barrier): a lane
+    // loads one record and, with several warps per tile, tests whether the footprint reaches a pixel
+    // centre of the warp's rows (exact ellipse-rectangle test); the hits are compacted and walked.
     const unsigned start = offsets[tile], end = offsets[tile + 1];
-    for (unsigned base = start; base < end; base += NT) {
-        const int cnt = (int)min((unsigned)NT, end - base);
-        __syncthreads();
-        if (tid < cnt) {
-            const unsigned r = list[base + tid];
-            const float4* p = rec + 3ull * r;
-            const float4 a = __ldg(p);
-            s0[tid] = a;
-            const float4 b = __ldg(p + 1);
-            s1[tid] = b;
-            s2[tid] = f2(__ldg(reinterpret_cast<const float*>(p + 2)), b.y);
-            {
-                const float gx = (float)(tc.tx * TW) + 0.5f - a.x, gy = (float)(tc.ty * TH) + 0.5f - a.y;
-                s3[tid] = make_float4(fmaf(a.z, gy, a.w * gx), b.x * gx * gx, 2.0f * b.x * gx, b.x);
-            }
-            if constexpr (NW > 1) {
-                const float xl = (float)(tc.tx * TW) + 0.5f, xh = xl + (float)(TW - 1);
-                unsigned m = 0;
-#pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    const float yl = (float)(tc.ty * TH + S::row_lo(w)) + 0.5f;
-                    const float yh = (float)(tc.ty * TH + S::row_hi(w)) + 0.5f;
-                    m |= footprint_hits(a.x, a.y, a.z, a.w, b.x, xl, xh, yl, yh) ? (1u << w) : 0u;
-                }
-                smask[tid] = m;
-            }
+    for (unsigned base = start; base < end; base += 32) {
+        const int cnt = (int)min(32u, end - base);
+        bool hit = false;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        float cb = 0.f;
+        if (lane < cnt) {
+            const float4* p = rec + 3ull * list[base + lane];
+            a = __ldg(p);
+            b = __ldg(p + 1);
+            cb = __ldg(reinterpret_cast<const float*>(p + 2));
+            hit = NW == 1 || footprint_hits(a.x, a.y, a.z, a.w, b.x, xl, xh, yl, yh);
         }
-        __syncthreads();
-        int nj = cnt;
-        if constexpr (NW > 1) {
-            // this warp's list: a ballot over the chunk, 32 Gaussians at a time
-            const int w = tid >> 5, lane = tid & 31;
-            nj = 0;
-            for (int j0 = 0; j0 < cnt; j0 += 32) {
-                const int jj = j0 + lane;
-                const bool hit = jj < cnt && ((smask[jj] >> w) & 1u);
-                const unsigned bal = __ballot_sync(0xffffffffu, hit);
-                if (hit) swl[w][nj + __popc(bal & ((1u << lane) - 1u))] = (unsigned char)jj;
-                nj += __popc(bal);
-            }
-            __syncwarp();
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        const int nj = __popc(bal);
+        __syncwarp();                                   // the previous batch's walk is done with the arrays
+        if (hit) {
+            const int k = __popc(bal & ((1u << lane) - 1u));
+            s0[w][k] = a;
+            s1[w][k] = b;
+            s2[w][k] = f2(cb, b.y);
+            const float gx = (float)(tc.tx * TW) + 0.5f - a.x, gy = (float)(tc.ty * TH) + 0.5f - a.y;
+            s3[w][k] = make_float4(fmaf(a.z, gy, a.w * gx), b.x * gx * gx, 2.0f * b.x * gx, b.x);
         }
+        __syncwarp();
 #pragma unroll 8
         for (int k = 0; k < nj; ++k) {
-            int j = k;
-            if constexpr (NW > 1) j = swl[threadIdx.x >> 5][k];
-            const float4 a = s0[j];
-            const float4 b = s1[j];
-            const float2 cbuw = s2[j];
-            const float4 t = s3[j];
+            const float4 a = s0[w][k];
+            const float4 b = s1[w][k];
+            const float2 cbuw = s2[w][k];
+            const float4 t = s3[w][k];
             const float2 crg = f2(b.z, b.w);
             // q' = r^2 + qd dx^2 with dx = g_x + o_x: qd dx^2 = qd g_x^2 + o_x (2 qd g_x + o_x qd) and
             // r = r_0 + qs o_y + qw o_x from the values at the tile's first pixel centre
