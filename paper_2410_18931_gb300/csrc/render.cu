@@ -43,6 +43,17 @@ struct BwdThreads {
     static constexpr int value = CH < 128 ? 2 * CH : 256;
 };
 
+// Asynchronous 16-byte global-to-shared copies (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // A lane count as a type, to instantiate one walk of the backward per group size.
 template <int N>
 struct Lanes {
@@ -120,6 +131,7 @@ __device__ __forceinline__ void fwd_tile(const int tile, const float4* __restric
     __shared__ float4 s1[NW][32];   // qd, u w, c_r u w, c_g u w
     __shared__ float2 s2[NW][32];   // c_b u w, u w
     __shared__ float4 s3[NW][32];   // at the tile's first pixel centre: r, qd dx^2, 2 qd dx; and qd
+    __shared__ float4 sraw[NW][2][32][3];   // per warp, two batches of records in flight (cp.async)
 
     const TileCoord tc = tile_coord(vs, tile);
     const View& V = vs.v[tc.v];
@@ -142,19 +154,34 @@ __device__ __forceinline__ void fwd_tile(const int tile, const float4* __restric
         for (int c = 0; c < 2; ++c) rg[r][c] = bd[r][c] = f2(0.f, 0.f);
 
     // Each warp takes the tile's list 32 Gaussians at a time on its own (no block barrier): a lane
-    // loads one record and, with several warps per tile, tests whether the footprint reaches a pixel
+    // takes one record and, with several warps per tile, tests whether the footprint reaches a pixel
     // centre of the warp's rows (exact ellipse-rectangle test); the hits are compacted and walked.
+    // The next batch's records are copied into shared memory (cp.async) while the warp walks this one.
     const unsigned start = offsets[tile], end = offsets[tile + 1];
-    for (unsigned base = start; base < end; base += 32) {
+    unsigned nidx = start + lane < end ? list[start + lane] : 0u;       // the next batch's record index
+    auto fetch = [&](unsigned b, int buf) {
+        if (b + lane < end) {
+            const float4* p = rec + 3ull * nidx;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) cp_async16(&sraw[w][buf][lane][q], p + q);
+        }
+        cp_async_commit();
+        nidx = b + 32 + lane < end ? list[b + 32 + lane] : 0u;
+    };
+    fetch(start, 0);
+    int buf = 0;
+    for (unsigned base = start; base < end; base += 32, buf ^= 1) {
         const int cnt = (int)min(32u, end - base);
+        fetch(base + 32, buf ^ 1);                      // an empty group past the end
+        cp_async_wait<1>();                             // this batch's copies have landed
+        __syncwarp();
         bool hit = false;
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
         float cb = 0.f;
         if (lane < cnt) {
-            const float4* p = rec + 3ull * list[base + lane];
-            a = __ldg(p);
-            b = __ldg(p + 1);
-            cb = __ldg(reinterpret_cast<const float*>(p + 2));
+            a = sraw[w][buf][lane][0];
+            b = sraw[w][buf][lane][1];
+            cb = sraw[w][buf][lane][2].x;
             hit = NW == 1 || footprint_hits(a.x, a.y, a.z, a.w, b.x, xl, xh, yl, yh);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, hit);
