@@ -654,7 +654,7 @@ def run_deterministic(S, scene, cam, weight, target, tile, persistent, chunk, fl
             "stage_ms": {k: round(float(v), 4) for k, v in zip(stage_names, st_ms)},
             "tile": "%dx%d" % tile, "schedule": "persistent" if persistent else "per-tile", "chunk": chunk,
             "longest_tile_list": longest, "bitwise_repeat": bool(same),
-            # + the backward's magnitude pass and the two ordered reductions (the list sort is in bin_kernels)
+            # + the largest-pixel-term kernel and the two ordered reductions (the list sort is in bin_kernels)
             "kernels_per_step": KERNELS_PER_STEP + bin_kernels + 3}
 
 

@@ -21,7 +21,7 @@ WSR_OPACITY_LOGIT, WSR_OPACITY_SH = 0, 1
 WSR_MAX_VIEWS = 32
 WSR_RECORD_FLOATS = 12
 WSR_GRAD_RECORD_FLOATS = 12
-WSR_GRAD_RECORD_FLOATS_DET = 32      # deterministic mode: 9 int64 sums and 9 magnitudes per record
+WSR_GRAD_RECORD_FLOATS_DET = 32      # deterministic mode: 9 int64 sums and their 9 bounds per record
 WSR_DET_MAX_SEGMENT = 8192
 WSR_SCAN_ONE_BLOCK_TILES = 32768     # wsr_bin scans (and orders) up to this many tiles in one kernel
 WSR_BIN_STATIC_MAX_TILES = 65536     # tiles over all views that wsr_bin_static handles

@@ -81,7 +81,7 @@ class GraphStep:
     @property
     def kernels_per_step(self) -> int:
         # project 1, bin (Renderer.bin_kernels), fwd 1, loss 1, bwd 1, project bwd 1;
-        # deterministic: + a second backward pass and two ordered reductions
+        # deterministic: + the largest-pixel-term kernel and two ordered reductions
         return 5 + self.r.bin_kernels + (3 if self.r.deterministic else 0)
 
 

@@ -401,15 +401,15 @@ wsr_status wsr_render_bwd_tiles(const float* records, int64_t n, const uint32_t*
     if (n > 0) WSR_CUDA(cudaMemsetAsync(grad_records, 0, sizeof(float) * rec_floats * (size_t)n * n_cams, s));
     if (!vs.det) {
         WSR_CUDA(launch_render_bwd(records, tile_offsets, tile_list, vs, wd, out_rgb, out_den, grad_rgb, grad_records,
-                                   hdr->gw, 0, nullptr, sched_of(vs, workspace, 1), s));
+                                   hdr->gw, 0, nullptr, nullptr, sched_of(vs, workspace, 1), s));
         return WSR_OK;
     }
-    // deterministic: the largest magnitude of every record term, then the terms as exact fixed-point sums;
-    // the background terms per tile, then summed in tile order
+    // deterministic: the largest pixel term over the image, then the record terms as exact fixed-point sums
+    // in units that a per-Gaussian bound fixes; the background terms per tile, then summed in tile order
     float* bg_tiles = (float*)((char*)workspace + ws_layout(vs).bg_tiles);
-    for (int pass = 1; pass <= 2; ++pass)
-        WSR_CUDA(launch_render_bwd(records, tile_offsets, tile_list, vs, wd, out_rgb, out_den, grad_rgb, grad_records,
-                                   hdr->gw, pass, bg_tiles, sched_of(vs, workspace, 1), s));
+    WSR_CUDA(launch_det_pmax(out_rgb, out_den, grad_rgb, vs.total_pix, &hdr->det_pmax, s));
+    WSR_CUDA(launch_render_bwd(records, tile_offsets, tile_list, vs, wd, out_rgb, out_den, grad_rgb, grad_records,
+                               hdr->gw, 1, bg_tiles, &hdr->det_pmax, sched_of(vs, workspace, 1), s));
     WSR_CUDA(launch_det_bg_reduce(bg_tiles, vs.total_tiles, hdr->gw, s));
     return WSR_OK;
 }

@@ -338,7 +338,8 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                                          const Views& vs, const float* __restrict__ wparams,
                                          const float* __restrict__ out_rgb, const float* __restrict__ out_den,
                                          const float* __restrict__ grad_rgb, float* __restrict__ grec,
-                                         float* __restrict__ gw, const int pass, float* __restrict__ bg_tiles) {
+                                         float* __restrict__ gw, const int pass, float* __restrict__ bg_tiles,
+                                         const unsigned* __restrict__ det_pmax) {
     constexpr int NT = BwdThreads<CH>::value;
     constexpr int NW = NT / 32;
     constexpr int PASSES = 2 * CH / NT;                // step A: (Gaussian, half) items per thread
@@ -373,6 +374,7 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
     const int y_lim = min(TH, V.H - y_org);
     const float wB = __ldg(wparams + 2);
     const float cB0 = __ldg(wparams + 3), cB1 = __ldg(wparams + 4), cB2 = __ldg(wparams + 5);
+    const float pmax = pass != 0 ? __int_as_float(*det_pmax) : 0.0f;    // deterministic mode
 
     float bg[4] = {0.f, 0.f, 0.f, 0.f};
     for (int p = tid; p < 2 * PP * TH; p += NT) {
@@ -560,25 +562,30 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                         atomicAdd(o + 1, make_float4(vals[4], vals[5], vals[6], vals[7]));
                         atomicAdd(reinterpret_cast<float*>(o + 2), vals[8]);
                     } else {
-                        // deterministic mode: a 128-byte record holds 9 int64 sums, then 9 magnitudes (float bits)
+                        // deterministic mode: a 128-byte record holds 9 int64 sums, then the 9 bounds (float
+                        // bits) that fix their units.  A term's bound caps the sum of its absolute pixel
+                        // terms over the whole footprint, the same in every tile of the Gaussian: at most
+                        // (2 hx + 2)(2 hy + 2) pixels (hx, hy its half-extents), each with e <= 1, every
+                        // pixel-table entry at most pmax, |r| <= sqrt(QM), |dx| <= hx inside the cutoff.
                         float* o = grec + (size_t)kDetRecordFloats * sidx[j];
                         int* mag = reinterpret_cast<int*>(o + 18);
-                        if (pass == 1) {
-                            // the largest |partial| of each term (non-negative floats order as their bit patterns)
+                        const float qd = b.x, hx = sqrtf(QM / qd);
+                        const float hy = sqrtf(QM * fmaf(a.w, a.w, qd) / (qd * a.z * a.z));
+                        const float npx = fminf((2.0f * hx + 2.0f) * (2.0f * hy + 2.0f), 1e12f);
+                        const float gqm = pmax * kLn2 * 1.0001f * (fabsf(b.z) + fabsf(b.w) + fabsf(c2.x) + fabsf(b.y));
+                        const float sq = sqrtf(QM);
+                        const float bound[9] = {npx * gqm * sq, npx * gqm * hx, npx * gqm * QM, npx * gqm * sq * hx,
+                                                npx * gqm * hx * hx, npx * pmax, npx * pmax, npx * pmax, npx * pmax};
+                        unsigned long long* sum = reinterpret_cast<unsigned long long*>(o);
 #pragma unroll
-                            for (int c = 0; c < 9; ++c) atomicMax(mag + c, __float_as_int(fabsf(vals[c])));
-                        } else {
-                            // each partial as fixed point with kDetBits bits below that magnitude: exact integer sums
-                            unsigned long long* sum = reinterpret_cast<unsigned long long*>(o);
-#pragma unroll
-                            for (int c = 0; c < 9; ++c) {
-                                const float m = __int_as_float(mag[c]);
-                                if (m > 0.0f) {
-                                    int e;
-                                    frexpf(m, &e);                  // m < 2^e
-                                    const long long q = __double2ll_rn(ldexp((double)vals[c], kDetBits - e));
-                                    atomicAdd(sum + c, (unsigned long long)q);
-                                }
+                        for (int c = 0; c < 9; ++c) {
+                            const float m = fminf(bound[c], 1e30f);
+                            mag[c] = __float_as_int(m);     // every tile of the Gaussian writes the same value
+                            if (m > 0.0f) {
+                                int e;
+                                frexpf(m, &e);              // m < 2^e
+                                const long long q = __double2ll_rn(ldexp((double)vals[c], kDetBits - e));
+                                atomicAdd(sum + c, (unsigned long long)q);
                             }
                         }
                     }
@@ -594,7 +601,7 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
         for (int w = 0; w < NW; ++w) t += sbg[tid][w];
         if (pass == 0) {
             if (t != 0.0f) atomicAdd(gw + 2 + tid, t);
-        } else if (pass == 2) {
+        } else {
             bg_tiles[4 * (size_t)tile + tid] = t;      // summed in tile order afterwards
         }
     }
@@ -606,12 +613,34 @@ __global__ void __launch_bounds__(BwdThreads<CH>::value, 1024 / BwdThreads<CH>::
                  const unsigned* __restrict__ list, const Views vs, const float* __restrict__ wparams,
                  const float* __restrict__ out_rgb, const float* __restrict__ out_den,
                  const float* __restrict__ grad_rgb, float* __restrict__ grec, float* __restrict__ gw,
-                 const int pass, float* __restrict__ bg_tiles, const unsigned* __restrict__ order,
+                 const int pass, float* __restrict__ bg_tiles, const unsigned* __restrict__ det_pmax,
+                 const unsigned* __restrict__ order,
                  unsigned* __restrict__ counter) {
     for_each_tile(order, counter, vs.total_tiles, [&](int tile) {
         bwd_tile<TW, TH, CH>(tile, rec, offsets, list, vs, wparams, out_rgb, out_den, grad_rgb, grec, gw, pass,
-                             bg_tiles);
+                             bg_tiles, det_pmax);
     });
+}
+
+// Deterministic mode: the largest magnitude of the backward's pixel terms, G / D per channel and
+// (G.C) / D, over all pixels (the same expressions as the backward's pixel table), as float bits
+// with an order-independent integer atomicMax.
+__global__ void __launch_bounds__(256) k_det_pmax(const float* __restrict__ out_rgb,
+                                                  const float* __restrict__ out_den,
+                                                  const float* __restrict__ grad_rgb, long long npix,
+                                                  unsigned* __restrict__ pmax) {
+    float m = 0.0f;
+    for (long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x; pix < npix;
+         pix += (long long)gridDim.x * blockDim.x) {
+        const float inv = 1.0f / out_den[pix];
+        const float G0 = grad_rgb[3 * pix], G1 = grad_rgb[3 * pix + 1], G2 = grad_rgb[3 * pix + 2];
+        const float C0 = out_rgb[3 * pix], C1 = out_rgb[3 * pix + 1], C2 = out_rgb[3 * pix + 2];
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(G0 * inv), fabsf(G1 * inv)),
+                           fmaxf(fabsf(G2 * inv), fabsf(-(G0 * C0 + G1 * C1 + G2 * C2) * inv))));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(pmax, __float_as_uint(m));
 }
 
 // Deterministic mode: the tiles' background terms summed in a fixed order.
@@ -661,7 +690,7 @@ cudaError_t fwd_t(const float* rec, const unsigned* off, const unsigned* list, c
 template <int TW, int TH, int CH>
 cudaError_t bwd_chunk(const float* rec, const unsigned* off, const unsigned* list, const Views& vs, WeightDev w,
                       const float* rgb, const float* den, const float* grgb, float* grec, float* gw, int pass,
-                      float* bg_tiles, Sched sched, cudaStream_t s) {
+                      float* bg_tiles, const unsigned* det_pmax, Sched sched, cudaStream_t s) {
     constexpr int NT = BwdThreads<CH>::value;
     const unsigned grid = grid_for(k_render_bwd<TW, TH, CH>, NT, vs, sched);
     if (sched.order) {
@@ -669,22 +698,19 @@ cudaError_t bwd_chunk(const float* rec, const unsigned* off, const unsigned* lis
         if (e != cudaSuccess) return e;
     }
     k_render_bwd<TW, TH, CH><<<grid, NT, 0, s>>>(reinterpret_cast<const float4*>(rec), off, list, vs, w.params,
-                                                     rgb, den, grgb, grec, gw, pass, bg_tiles, sched.order,
-                                                     sched.counter);
+                                                     rgb, den, grgb, grec, gw, pass, bg_tiles, det_pmax,
+                                                     sched.order, sched.counter);
     return cudaGetLastError();
 }
 
 template <int TW, int TH>
 cudaError_t bwd_t(const float* rec, const unsigned* off, const unsigned* list, const Views& vs, WeightDev w,
                   const float* rgb, const float* den, const float* grgb, float* grec, float* gw, int pass,
-                  float* bg_tiles, Sched sched, cudaStream_t s) {
-    if (vs.chunk == 64)
-        return bwd_chunk<TW, TH, 64>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sched, s);
-    if (vs.chunk == 256)
-        return bwd_chunk<TW, TH, 256>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sched, s);
-    if (vs.chunk == 512)
-        return bwd_chunk<TW, TH, 512>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sched, s);
-    return bwd_chunk<TW, TH, 128>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sched, s);
+                  float* bg_tiles, const unsigned* det_pmax, Sched sched, cudaStream_t s) {
+    const int ch = vs.chunk;
+    auto k = ch == 64 ? bwd_chunk<TW, TH, 64> : ch == 256 ? bwd_chunk<TW, TH, 256>
+                                              : ch == 512 ? bwd_chunk<TW, TH, 512> : bwd_chunk<TW, TH, 128>;
+    return k(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, det_pmax, sched, s);
 }
 
 // Diagnostic: the work of the render kernels, three counts added to count[0..2]:
@@ -831,17 +857,31 @@ cudaError_t launch_render_fwd(const float* rec, const unsigned* off, const unsig
 
 cudaError_t launch_render_bwd(const float* rec, const unsigned* off, const unsigned* list, const Views& vs,
                               WeightDev w, const float* rgb, const float* den, const float* grgb, float* grec,
-                              float* gw, int pass, float* bg_tiles, Sched sc, cudaStream_t s) {
+                              float* gw, int pass, float* bg_tiles, const unsigned* det_pmax, Sched sc,
+                              cudaStream_t s) {
     if (vs.total_tiles == 0) return cudaSuccess;
     if (vs.tile_w == 16 && vs.tile_h == 16)
-        return bwd_t<16, 16>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sc, s);
+        return bwd_t<16, 16>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, det_pmax, sc, s);
     if (vs.tile_w == 8 && vs.tile_h == 8)
-        return bwd_t<8, 8>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sc, s);
+        return bwd_t<8, 8>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, det_pmax, sc, s);
     if (vs.tile_w == 32 && vs.tile_h == 8)
-        return bwd_t<32, 8>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sc, s);
+        return bwd_t<32, 8>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, det_pmax, sc, s);
     if (vs.tile_w == 16 && vs.tile_h == 8)
-        return bwd_t<16, 8>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, sc, s);
+        return bwd_t<16, 8>(rec, off, list, vs, w, rgb, den, grgb, grec, gw, pass, bg_tiles, det_pmax, sc, s);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_det_pmax(const float* out_rgb, const float* out_den, const float* grad_rgb, long long npix,
+                            unsigned* pmax, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(pmax, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess || npix == 0) return e;
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const long long blocks = min((npix + 255) / 256, (long long)sms * 8);
+    k_det_pmax<<<(unsigned)blocks, 256, 0, s>>>(out_rgb, out_den, grad_rgb, npix, pmax);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_det_bg_reduce(const float* bg_tiles, int n_tiles, float* gw, cudaStream_t s) {

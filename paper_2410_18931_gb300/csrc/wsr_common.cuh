@@ -56,15 +56,17 @@ struct WsHeader {
     float gw[8];               // gradient accumulators of sigma, beta, w_B, c_B (6 used)
     unsigned long long total;  // tile instances counted by the last binning
     unsigned int work[4];      // persistent-schedule counters: [0] forward, [1] backward
+    unsigned int det_pmax;     // deterministic mode: the largest |pixel term| G/D, (G.C)/D (float bits)
 };
 
 constexpr size_t kWsHeader = 8192;
 constexpr size_t kWsDetSB = 256;       // deterministic mode: sigma/beta per projection-backward block
 constexpr int kDetSBBlocks = (int)((kWsHeader - kWsDetSB) / (2 * sizeof(float)));   // 992
-// Deterministic mode: a record term is added as 64-bit fixed point with kDetBits
-// bits below the largest magnitude of its partials, so up to 2^(62 - kDetBits)
-// partials per record sum without overflow.
-constexpr int kDetBits = 37;
+// Deterministic mode: a record term is added as 64-bit fixed point in units of
+// 2^(e - kDetBits), 2^e above an a-priori bound on the sum of the absolute
+// values of all its partials (over every tile of the Gaussian), so the exact
+// integer sum stays below 2^kDetBits < 2^63.
+constexpr int kDetBits = 60;
 constexpr int kDetRecordFloats = WSR_GRAD_RECORD_FLOATS_DET;
 constexpr int kDetMaxSegment = WSR_DET_MAX_SEGMENT;
 constexpr int kScanBlock = 1024;       // threads of a scan block

@@ -59,14 +59,17 @@ cudaError_t launch_render_fwd(const float* records, const unsigned* tile_offsets
                               const unsigned* tile_list, const Views& vs, WeightDev w,
                               float* out_rgb, float* out_den, Sched sched, cudaStream_t s);
 // pass 0: float atomics into WSR_GRAD_RECORD_FLOATS records and grad_wparams.  Deterministic mode
-// (WSR_GRAD_RECORD_FLOATS_DET records): pass 1 takes each record term's largest magnitude, pass 2
-// adds the terms as fixed point and stores each tile's background terms in bg_tiles[4 tile + c].
+// (pass 1, WSR_GRAD_RECORD_FLOATS_DET records): the record terms added as fixed point in units set by
+// a per-Gaussian bound from *det_pmax (launch_det_pmax first), each tile's background terms stored in
+// bg_tiles[4 tile + c].
 cudaError_t launch_render_bwd(const float* records, const unsigned* tile_offsets,
                               const unsigned* tile_list, const Views& vs, WeightDev w,
                               const float* out_rgb, const float* out_den, const float* grad_rgb,
-                              float* grad_records, float* grad_wparams, int pass, float* bg_tiles, Sched sched,
-                              cudaStream_t s);
+                              float* grad_records, float* grad_wparams, int pass, float* bg_tiles,
+                              const unsigned* det_pmax, Sched sched, cudaStream_t s);
 // deterministic mode: grad_wparams[2..5] = the tiles' background terms summed in tile order
+cudaError_t launch_det_pmax(const float* out_rgb, const float* out_den, const float* grad_rgb, long long npix,
+                            unsigned* pmax, cudaStream_t s);
 cudaError_t launch_det_bg_reduce(const float* bg_tiles, int n_tiles, float* grad_wparams, cudaStream_t s);
 
 cudaError_t launch_count_pairs(const float* records, const unsigned* tile_offsets, const unsigned* tile_list,

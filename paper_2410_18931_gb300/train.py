@@ -199,7 +199,7 @@ class TrainStep:
     @property
     def kernels_per_step(self) -> int:
         # project 1, bin (Renderer.bin_kernels), fwd 1, loss 1, bwd 1, project bwd 1, Adam 2;
-        # deterministic: + a second backward pass and two ordered reductions
+        # deterministic: + the largest-pixel-term kernel and two ordered reductions
         return 7 + self.r.bin_kernels + (3 if self.deterministic else 0)
 
     def train(self, steps: int, check_every: int = 10) -> torch.Tensor:

@@ -117,3 +117,43 @@ def test_deterministic_mode_reports_a_tile_beyond_its_sort_bound():
     with pytest.raises(A.WSRError) as err:
         r.forward(g, w.kind, wpar)
     assert err.value.status == A.WSR_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
+def test_deterministic_fixed_point_sums_stay_inside_their_bounds(tile):
+    """The deterministic backward adds each record term as 64-bit fixed point
+    in units of 2^(e - 60), 2^e above a per-Gaussian bound on the sum of the
+    term's absolute pixel terms over the whole footprint (stored beside the
+    sums).  Every integer sum stays below 2^60 in magnitude (three bits of
+    headroom in an int64), and every decoded sum lies within its bound, on a
+    scene of small, large and needle-shaped footprints under a random pixel
+    gradient."""
+    import torch
+    from paper_2410_18931_gb300 import Gaussians, Renderer
+    from paper_2410_18931_gb300 import _abi as A
+    rng = np.random.default_rng(91)
+    base = ws.random_scene(8000, 92, sh_degree=2, vd_opacity=True, clusters=8, box=1.2, log_scale_mu=-3.3)
+    base.log_scales[:200, 0] = rng.uniform(np.log(0.2), np.log(0.8), 200).astype(np.float32)    # needles
+    base.log_scales[:200, 1:] = np.float32(np.log(3e-3))
+    base.log_scales[200:220] = np.float32(np.log(0.4))                                          # large
+    cam = ws.look_at((0.3, -0.2, -3.4), width=160, height=120).rounded()
+    w = ws.default_weight(ws.LC)
+    g = Gaussians.from_scene(base)
+    wpar = torch.tensor(w.as_array(), device="cuda")
+    r = Renderer([cam], tile=tile, persistent=True, deterministic=True)
+    st = r.forward(g, w.kind, wpar)
+    G = torch.tensor(rng.normal(size=(cam.height * cam.width, 3)).astype(np.float32), device="cuda")
+    grec = torch.empty(g.n * A.WSR_GRAD_RECORD_FLOATS_DET, dtype=torch.float32, device="cuda")
+    r.wsr_render_bwd_tiles(st.records, g.n, st.tile_offsets, st.tile_list, w.kind, wpar, st.rgb, st.den, G, grec)
+    torch.cuda.synchronize()
+    recs = grec.cpu().numpy().reshape(g.n, A.WSR_GRAD_RECORD_FLOATS_DET)
+    sums = recs[:, :18].copy().view(np.int64)                 # [n, 9]
+    bounds = recs[:, 18:27]
+    assert np.all(bounds >= 0.0) and np.all(np.isfinite(bounds))
+    assert int(np.abs(sums).max()) < 2 ** 60
+    touched = bounds > 0
+    assert touched.sum() > 1000
+    e = np.frexp(bounds[touched])[1].astype(np.int64)         # bound < 2^e
+    val = np.ldexp(sums[touched].astype(np.float64), e - 60)
+    assert np.all(np.abs(val) <= bounds[touched].astype(np.float64) * (1 + 1e-6))
+    assert np.all(sums[~touched] == 0)
