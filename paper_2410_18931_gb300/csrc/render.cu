@@ -363,7 +363,6 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
     __shared__ unsigned short sord[CH];         // the chunk's Gaussians: wide ones first, most rows first
     __shared__ unsigned shist[NK];
     __shared__ unsigned snext[2];               // per class: the next position of the order a warp takes
-    __shared__ unsigned snwide;                 // wide Gaussians in the chunk
     __shared__ float sbg[4][NW];
 
     const TileCoord tc = tile_coord(vs, tile);
@@ -458,24 +457,33 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
         }
         if (tid < 2) snext[tid] = 0u;
         __syncthreads();
-        // ---- B: the chunk's order, wide first, most rows first (rank within the bucket from the count) ----
-        for (int gj = tid; gj < cnt; gj += NT) {
-            const int key = skey[gj];
-            unsigned at = srank[gj];
+        // ---- B: the chunk's order, wide first, most rows first: each warp forms the buckets' starts (the
+        // counts of all larger keys, a suffix scan over the NK <= 64 keys held two per lane), and a
+        // Gaussian's position is its bucket's start plus its rank in the bucket ----
+        const unsigned h0 = lane < NK ? shist[lane] : 0u, h1 = lane + 32 < NK ? shist[lane + 32] : 0u;
+        unsigned s0i = h0, s1i = h1;                    // inclusive suffix sums of keys lane and lane + 32
 #pragma unroll
-            for (int c = NK - 1; c > 0; --c) at += c > key ? shist[c] : 0u;
-            sord[at] = (unsigned short)gj;
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned y0 = __shfl_down_sync(0xffffffffu, s0i, off), y1 = __shfl_down_sync(0xffffffffu, s1i, off);
+            if (lane + off < 32) {
+                s0i += y0;
+                s1i += y1;
+            }
         }
-        if (tid == 0) {
-            unsigned nw = 0;
-#pragma unroll
-            for (int c = NB; c < NK; ++c) nw += shist[c];
-            snwide = nw;
+        s0i += __shfl_sync(0xffffffffu, s1i, 0);        // keys 32.. lie above every key of the first half
+        const unsigned start0 = s0i - h0, start1 = s1i - h1;
+        const int nwide = (int)__shfl_sync(0xffffffffu, s0i, NB);   // Gaussians with keys NB and up: the wide
+        static_assert(NB < 32, "the wide class starts in the first half of the keys");
+        for (int g0 = warp * 32; g0 < cnt; g0 += NT) {
+            const int gj = g0 + lane;
+            const int key = gj < cnt ? (int)skey[gj] : 0;
+            const unsigned a0 = __shfl_sync(0xffffffffu, start0, key & 31);
+            const unsigned a1 = __shfl_sync(0xffffffffu, start1, key & 31);
+            if (gj < cnt) sord[(key < 32 ? a0 : a1) + srank[gj]] = (unsigned short)gj;
         }
         __syncthreads();
         if (tid < NK) shist[tid] = 0u;                  // for the next chunk (step C does not read it)
         // ---- C: a group per Gaussian; each warp takes the next 32 / L Gaussians of a class ----
-        const int nwide = (int)snwide;
         auto walk = [&](auto lanes, const int lo, const int hi, unsigned* next) {
             constexpr int L = decltype(lanes)::value;
             constexpr int GW = 32 / L;                  // groups per warp
