@@ -66,11 +66,12 @@ template <bool SCATTER>
 __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ rec, long long n, const Views vs,
                                              unsigned* __restrict__ cursor, unsigned* __restrict__ list,
                                              unsigned long long capacity, WsHeader* hdr) {
-    __shared__ int s_end[8][32];        // inclusive prefix of segment counts
+    __shared__ int s_start[8][32];      // each Gaussian's first segment (exclusive prefix of segment counts)
+    __shared__ int s_gown[8][32];       // the lanes of the Gaussians with segments, in order
     __shared__ int4 s_rect[8][32];      // pixel rectangle: jx0, jx1, jy0, jy1
     __shared__ float4 s_geo[8][32][2];  // mu_x, mu_y, B'/A', A' QM | det', 1/A', dy*, margin
-    __shared__ int s_wend[8][32];       // inclusive prefix of the batch's tile counts
-    __shared__ int2 s_run[8][32];       // first tile (global index) and owning lane of each segment
+    __shared__ int2 s_run[8][32];       // per segment with tiles, in order: its first tile's counter, less
+                                        // its first position in the batch, and the owning lane
     const int v = blockIdx.y;
     const View& V = vs.v[v];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -100,24 +101,27 @@ __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ rec, lon
         const int y = __shfl_up_sync(0xffffffffu, inc, off);
         if (lane >= off) inc += y;
     }
-    s_end[warp][lane] = inc;
+    const int gex = inc - nseg;                          // this Gaussian's first segment
+    // the Gaussians with segments, in lane order: a segment's owner is found by counting starts (below)
+    const unsigned gmask = __ballot_sync(0xffffffffu, nseg > 0);
+    if (nseg > 0) s_gown[warp][__popc(gmask & ((1u << lane) - 1u))] = lane;
+    s_start[warp][lane] = gex;
     s_rect[warp][lane] = make_int4(jx0, jx1, jy0, jy1);
     s_geo[warp][lane][0] = g0;
     s_geo[warp][lane][1] = g1;
     __syncwarp();
     const int total = __shfl_sync(0xffffffffu, inc, 31);
     for (int c0 = 0; c0 < total; c0 += 32) {
-        // ---- this lane's segment: its range of tiles [ta, tb] ----
+        // ---- this lane's segment c0 + lane: its owner is the last Gaussian with segments whose first
+        // segment is at or before it (those starting before c0, plus the starts in the batch up to it) ----
+        const unsigned gst = __reduce_or_sync(0xffffffffu, nseg > 0 && gex >= c0 && gex < c0 + 32 ? 1u << (gex - c0)
+                                                                                               : 0u);
+        const int gbefore = __popc(__ballot_sync(0xffffffffu, nseg > 0 && gex < c0));
         const int c = c0 + lane;
         int ta = 0, tb = -1, lo = 0, row = 0;
         if (c < total) {
-            int hi = 31;            // owner: first lane whose inclusive end exceeds c
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (s_end[warp][mid] > c) hi = mid;
-                else lo = mid + 1;
-            }
-            const int k = c - (lo ? s_end[warp][lo - 1] : 0);   // segment index within the owner
+            lo = s_gown[warp][gbefore + __popc(gst & ((2u << lane) - 1u)) - 1];
+            const int k = c - s_start[warp][lo];                // segment index within the owner
             const int4 rc = s_rect[warp][lo];
             const float4 a = s_geo[warp][lo][0], b = s_geo[warp][lo][1];
             const int np = ((rc.y >> lw) - (rc.x >> lw) + kPiece) / kPiece;
@@ -141,7 +145,8 @@ __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ rec, lon
                 row = V.tile_base + ty * V.tiles_x;
             }
         }
-        // ---- the batch's tiles end to end, consecutive tiles to consecutive lanes ----
+        // ---- the batch's tiles end to end, consecutive tiles to consecutive lanes; a tile's segment is
+        // found the same way, by counting the segments that start at or before it ----
         const int wdt = max(tb - ta + 1, 0);   // a piece the band does not reach has none
         int winc = wdt;
 #pragma unroll
@@ -150,25 +155,26 @@ __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ rec, lon
             if (lane >= off) winc += y;
         }
         const int nt = __shfl_sync(0xffffffffu, winc, 31);
-        s_wend[warp][lane] = winc;
-        s_run[warp][lane] = make_int2(row + ta, lo);
+        const int wex = winc - wdt;                      // this segment's first position in the batch
+        const unsigned smask = __ballot_sync(0xffffffffu, wdt > 0);
+        if (wdt > 0) s_run[warp][__popc(smask & ((1u << lane) - 1u))] = make_int2(row + ta - wex, lo);
         __syncwarp();
-        for (int j = lane; j < nt; j += 32) {
-            int sl = 0, sh = 31;    // segment: first lane whose inclusive end exceeds j
-            while (sl < sh) {
-                const int mid = (sl + sh) >> 1;
-                if (s_wend[warp][mid] > j) sh = mid;
-                else sl = mid + 1;
-            }
-            const int2 run = s_run[warp][sl];
-            unsigned* cur = cursor + run.x + (j - (sl ? s_wend[warp][sl - 1] : 0));
-            if constexpr (SCATTER) {
-                const unsigned slot = atomicAdd(cur, 1u);
-                const long long rid = (long long)v * n + (long long)blockIdx.x * blockDim.x + warp * 32 + run.y;
-                if (slot < capacity) list[slot] = (unsigned)rid;
-                else set_error(hdr, WSR_ERR_CAPACITY);
-            } else {
-                atomicAdd(cur, 1u);
+        for (int j0 = 0; j0 < nt; j0 += 32) {
+            const unsigned sst = __reduce_or_sync(0xffffffffu, wdt > 0 && wex >= j0 && wex < j0 + 32 ? 1u << (wex - j0)
+                                                                                                  : 0u);
+            const int sbefore = __popc(__ballot_sync(0xffffffffu, wdt > 0 && wex < j0));
+            const int j = j0 + lane;
+            if (j < nt) {
+                const int2 run = s_run[warp][sbefore + __popc(sst & ((2u << lane) - 1u)) - 1];
+                unsigned* cur = cursor + run.x + j;
+                if constexpr (SCATTER) {
+                    const unsigned slot = atomicAdd(cur, 1u);
+                    const long long rid = (long long)v * n + (long long)blockIdx.x * blockDim.x + warp * 32 + run.y;
+                    if (slot < capacity) list[slot] = (unsigned)rid;
+                    else set_error(hdr, WSR_ERR_CAPACITY);
+                } else {
+                    atomicAdd(cur, 1u);
+                }
             }
         }
         __syncwarp();
