@@ -69,12 +69,14 @@ struct Lanes {
 // that even column that hold the span (a padding pixel at either end lies
 // outside the footprint or in the tile's zero column).
 struct RowSpans {
-    float Ap, hb, det, ia, ext;
+    float Ap, hb, det, ia, ext, apqm, hbia;
     __device__ __forceinline__ RowSpans(const float4 a, const float qd, const float QM) {
         Ap = fmaf(a.w, a.w, qd);
         hb = a.z * a.w;
         det = qd * a.z * a.z;
         ia = rcp_approx(Ap);
+        apqm = Ap * QM;
+        hbia = hb * ia;
         // rows the footprint can reach: |dy| <= sqrt(A' QM / det'), with a pixel of slack
         ext = fminf(sqrt_approx(fmaxf(Ap * QM * rcp_approx(det), 0.0f)), 1e6f) + 1.0f;
     }
@@ -95,6 +97,27 @@ struct RowSpans {
         if (!(fx0 <= fx1)) return 0;
         const int xs = (int)fx0 - x_org, len = (int)fx1 - (int)fx0 + 1, xe = xs & ~1;
         return (unsigned short)(xe | (((xs - xe + len + 1) >> 1) << 8));    // even start, column pairs
+    }
+    // the spans of local rows ly and ly + 1 (low and high half), two rows per paired FP32 op
+    __device__ __forceinline__ unsigned row2(const float4 a, int x_org, int y_org, int x_lim, int ly) const {
+        const float dy0 = (float)(y_org + ly) + 0.5f - a.y;
+        const float2 dy = f2(dy0, dy0 + 1.0f);
+        const float2 d4 = __ffma2_rn(__fmul2_rn(f2(-det, -det), dy), dy, f2(apqm, apqm));
+        const float2 h = __fmul2_rn(f2(sqrt_approx(fmaxf(d4.x, 0.0f)), sqrt_approx(fmaxf(d4.y, 0.0f))), f2(ia, ia));
+        const float2 cx = __ffma2_rn(f2(-hbia, -hbia), dy, f2(a.x, a.x));
+        const float2 l = __fadd2_rn(__ffma2_rn(h, f2(-1.0f, -1.0f), cx), f2(-0.52f, -0.52f));
+        const float2 r = __fadd2_rn(__fadd2_rn(cx, h), f2(-0.48f, -0.48f));
+        const float xlo = (float)x_org, xhi = (float)(x_org + x_lim - 1);
+        unsigned out = 0;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float fx0 = fmaxf(ceilf(k ? l.y : l.x), xlo), fx1 = fminf(floorf(k ? r.y : r.x), xhi);
+            if ((k ? d4.y : d4.x) >= 0.0f && fx0 <= fx1) {
+                const int xs = (int)fx0 - x_org, len = (int)fx1 - (int)fx0 + 1, xe = xs & ~1;
+                out |= (unsigned)(xe | (((xs - xe + len + 1) >> 1) << 8)) << (16 * k);
+            }
+        }
+        return out;
     }
 };
 
@@ -127,8 +150,7 @@ __device__ __forceinline__ void fwd_tile(const int tile, const float4* __restric
     using S = FwdShape<TW, TH, PX>;
     constexpr int NW = S::NW;
     // per warp, the Gaussians of its current batch that reach its rows
-    __shared__ float4 s0[NW][32];   // mu_x, mu_y, qs, qw
-    __shared__ float4 s1[NW][32];   // qd, u w, c_r u w, c_g u w
+    __shared__ float4 s0[NW][32];   // qs, qw, c_r u w, c_g u w
     __shared__ float2 s2[NW][32];   // c_b u w, u w
     __shared__ float4 s3[NW][32];   // at the tile's first pixel centre: r, qd dx^2, 2 qd dx; and qd
     __shared__ float4 sraw[NW][2][32][3];   // per warp, two batches of records in flight (cp.async)
@@ -189,8 +211,7 @@ __device__ __forceinline__ void fwd_tile(const int tile, const float4* __restric
         __syncwarp();                                   // the previous batch's walk is done with the arrays
         if (hit) {
             const int k = __popc(bal & ((1u << lane) - 1u));
-            s0[w][k] = a;
-            s1[w][k] = b;
+            s0[w][k] = make_float4(a.z, a.w, b.z, b.w);
             s2[w][k] = f2(cb, b.y);
             const float gx = (float)(tc.tx * TW) + 0.5f - a.x, gy = (float)(tc.ty * TH) + 0.5f - a.y;
             s3[w][k] = make_float4(fmaf(a.z, gy, a.w * gx), b.x * gx * gx, 2.0f * b.x * gx, b.x);
@@ -198,18 +219,18 @@ __device__ __forceinline__ void fwd_tile(const int tile, const float4* __restric
         __syncwarp();
 #pragma unroll 8
         for (int k = 0; k < nj; ++k) {
-            const float4 a = s0[w][k];
-            const float4 b = s1[w][k];
+            const float4 g = s0[w][k];
             const float2 cbuw = s2[w][k];
             const float4 t = s3[w][k];
-            const float2 crg = f2(b.z, b.w);
+            const float qs = g.x, qw = g.y;
+            const float2 crg = f2(g.z, g.w);
             // q' = r^2 + qd dx^2 with dx = g_x + o_x: qd dx^2 = qd g_x^2 + o_x (2 qd g_x + o_x qd) and
             // r = r_0 + qs o_y + qw o_x from the values at the tile's first pixel centre
             if constexpr (PX == 1) {
                 // one column, its two rows paired: the same dx, so the same qd dx^2
                 const float P1 = fmaf(ox.x, fmaf(ox.x, t.w, t.z), t.y);
-                const float base = fmaf(a.w, ox.x, t.x);
-                const float2 rr = __ffma2_rn(f2(a.z, a.z), f2(oy0, oy1), f2(base, base));
+                const float base = fmaf(qw, ox.x, t.x);
+                const float2 rr = __ffma2_rn(f2(qs, qs), f2(oy0, oy1), f2(base, base));
                 const float2 q = __ffma2_rn(rr, rr, f2(P1, P1));
                 if (q.x <= kQMax) {
                     const float e = ex2_approx(-q.x);
@@ -224,10 +245,10 @@ __device__ __forceinline__ void fwd_tile(const int tile, const float4* __restric
                 continue;
             }
             const float2 P = __ffma2_rn(ox, __ffma2_rn(ox, f2(t.w, t.w), f2(t.z, t.z)), f2(t.y, t.y));
-            const float rys[2] = {fmaf(a.z, oy0, t.x), fmaf(a.z, oy1, t.x)};
+            const float rys[2] = {fmaf(qs, oy0, t.x), fmaf(qs, oy1, t.x)};
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
-                const float2 rr = __ffma2_rn(f2(a.w, a.w), ox, f2(rys[r], rys[r]));
+                const float2 rr = __ffma2_rn(f2(qw, qw), ox, f2(rys[r], rys[r]));
                 const float2 q = __ffma2_rn(rr, rr, P);
                 if (q.x <= kQMax) {
                     const float e = ex2_approx(-q.x);
@@ -347,7 +368,7 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
     constexpr int HR = TH / 2;                          // rows per thread in step A
     constexpr int NB = TH + 1;                          // row counts 0 .. TH
     constexpr int NK = 2 * NB;                          // sort keys: narrow 0 .. TH, wide NB .. NB + TH
-    static_assert(PASSES * NT == 2 * CH && TH % 2 == 0 && TW % 8 == 0 && TW <= 64 && CH <= 512 && NK <= NT, "layout");
+    static_assert(PASSES * NT == 2 * CH && TH % 4 == 0 && TW % 8 == 0 && TW <= 64 && CH <= 512 && NK <= NT, "layout");
     // per pixel: G/D (3), -(G.C)/D, stored per column pair as (x0, x1, y0, y1) and (z0, z1, w0, w1)
     __shared__ float4 spA[PP * TH];
     __shared__ float4 spB[PP * TH];
@@ -431,15 +452,21 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 int ly_lo, ly_hi;
                 rs.rows(a, y_org, half * HR, min(HR, y_lim - half * HR), ly_lo, ly_hi);
 #pragma unroll
-                for (int k = 0; k < HR; ++k) {
+                for (int k = 0; k < HR; k += 2) {
                     const int ly = half * HR + k;
-                    unsigned short sp = 0;
-                    if (ly >= ly_lo && ly <= ly_hi) sp = rs.row(a, QM, x_org, y_org, x_lim, ly);
-                    sspan[gj][ly] = sp;
-                    if (sp >> 8) {
-                        row_lo = min(row_lo, ly);
-                        row_hi = max(row_hi, ly);
-                        umax = max(umax, sp >> 8);
+                    unsigned sp2 = 0;
+                    if (ly + 1 >= ly_lo && ly <= ly_hi) sp2 = rs.row2(a, x_org, y_org, x_lim, ly);
+                    if (ly < ly_lo) sp2 &= 0xffff0000u;            // rows outside the footprint's reach
+                    if (ly + 1 > ly_hi) sp2 &= 0x0000ffffu;
+                    *reinterpret_cast<unsigned*>(&sspan[gj][ly]) = sp2;
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        const unsigned sp = (sp2 >> (16 * t)) & 0xffffu;
+                        if (sp >> 8) {
+                            row_lo = min(row_lo, ly + t);
+                            row_hi = max(row_hi, ly + t);
+                            umax = max(umax, (int)(sp >> 8));
+                        }
                     }
                 }
             }
