@@ -321,31 +321,34 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 // Backward, one block per tile, a group of lanes per Gaussian.
 //
-// The tile's pixel terms P = (G/D, -(G.C)/D) sit in shared memory with one
-// zero column past the tile's right edge.  For each chunk of CH Gaussians of
+// The tile's pixel terms P = (G/D, -(G.C)/D) sit in shared memory by column
+// pairs, two float4 planes (x0, x1, y0, y1) and (z0, z1, w0, w1), with one
+// zero pair past the tile's right edge.  For each chunk of CH Gaussians of
 // the tile:
-//   A. two threads per Gaussian compute, for their half of the tile's rows,
-//      the span of pixels whose centre can lie inside the footprint (the roots
-//      of q(dx) = 9 on each row, widened slightly, padded to an even length:
-//      a padding pixel lies in the zero column or outside the footprint), and
-//      the first and last rows with a span;
+//   A. two threads per Gaussian compute, for their half of the tile's rows
+//      (two rows per paired op), the span of pixels whose centre can lie
+//      inside the footprint (the roots of q(dx) = 9 on each row, widened
+//      slightly), kept as its first column rounded down to even and a number
+//      of column pairs, and the first and last rows with a span, and take
+//      the Gaussian's rank in its bucket of the sort below;
 //   B. the chunk's Gaussians are ordered wide ones first (a row span longer
 //      than TW / 2 pixels), each class by its number of rows, longest first
-//      (a counting sort); each warp takes the next Gaussians of a class
-//      whenever it is free (a shared counter per class), so that the groups
-//      of a warp walk for the same number of steps and the warps stay busy;
+//      (a counting sort: the buckets' starts from one warp suffix scan); each
+//      warp takes the next Gaussians of a class whenever it is free (a shared
+//      counter per class), so that the groups of a warp walk for the same
+//      number of steps and the warps stay busy;
 //   C. a group of L consecutive lanes takes one Gaussian at a time and walks
 //      its rows one per step, L = TW / 4 for the wide class and TW / 8 for
 //      the narrow one (whose spans all fit in 4 L columns); lane k takes
-//      columns start + k + m L (m = 0..3) of the row, so the lanes of a group
-//      read consecutive pixels of the table (no bank conflicts), four pixels
-//      per step from one decode of the row's span, one paired FP32 op per
-//      quantity and two pixels.  The nine record terms stay in registers
-//      until the Gaussian's last row; then log2(L) shuffle steps sum them
-//      over the group and its first lane adds them to the Gaussian's global
-//      record (in the deterministic mode: its magnitude, then its fixed-point
-//      value).  A Gaussian's sums over a tile are thus formed in one fixed
-//      order, whichever group takes it.
+//      column pairs start / 2 + k + m L (m = 0, 1) of the row, so the lanes of
+//      a group read consecutive entries of each plane, four pixels per step
+//      from one decode of the row's span, every quantity of a column pair in
+//      one paired FP32 op.  The nine record terms stay in registers until
+//      the Gaussian's last row; then log2(L) shuffle steps sum them over the
+//      group and its first lane adds them to the Gaussian's global record (in
+//      the deterministic mode: as fixed point, in units that a per-Gaussian
+//      bound fixes).  A Gaussian's sums over a tile are thus formed in one
+//      fixed order, whichever group takes it.
 // Every pair is tested against the forward's cutoff (q' <= kQMax, FP32, from
 // the same record values).  The forward forms q' from values at the tile's
 // first pixel centre, the walk from each pixel's own offsets, so a pair
