@@ -77,6 +77,22 @@ __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_
 
 __device__ __forceinline__ void set_error(WsHeader* h, int code) { atomicCAS(&h->err, 0, code); }
 
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// Hardware square root and reciprocal (relative error ~2^-22): the backward's
+// per-row spans (widened by 0.02 pixel, far above that), the footprint test's
+// minimising points and the SSIM map's two quotients.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Does the footprint q' <= kQMax reach a pixel centre of the rectangle
 // [x0, x1] x [y0, y1] (pixel-centre coordinates)?  The record holds the
 // quadratic as a sum of squares, q' = (qs dy + qw dx)^2 + qd dx^2.  Its
@@ -93,40 +109,28 @@ __device__ __forceinline__ bool footprint_hits(float mx, float my, float qs, flo
         return fmaf(r, r, qd * dx * dx);
     };
     float best = 3.4e38f;
+    // The minimising points below come from hardware reciprocals (relative error ~2^-22): q is
+    // evaluated exactly at a point of the edge either way, and a point that far from the minimiser
+    // raises q by a relative ~1e-13 against the threshold's 1e-4 margin.
     // vertical edges x = x0, x1: the minimum over dy is at qs dy = -qw dx
     const float ex[2] = {x0 - mx, x1 - mx};
+    const float kx = -qw * rcp_approx(qs);
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const float dx = ex[k];
-        const float dy = fminf(fmaxf(-qw * dx / qs, y0 - my), y1 - my);
+        const float dy = fminf(fmaxf(kx * dx, y0 - my), y1 - my);
         best = fminf(best, q(dx, dy));
     }
     // horizontal edges y = y0, y1: the minimum over dx is at dx = -qw qs dy / (qw^2 + qd)
     const float ey[2] = {y0 - my, y1 - my};
-    const float den = fmaf(qw, qw, qd);
+    const float ky = -qw * qs * rcp_approx(fmaf(qw, qw, qd));
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const float dy = ey[k];
-        const float dx = fminf(fmaxf(-qw * qs * dy / den, x0 - mx), x1 - mx);
+        const float dx = fminf(fmaxf(ky * dy, x0 - mx), x1 - mx);
         best = fminf(best, q(dx, dy));
     }
     return best <= thr;
-}
-
-__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-
-// Hardware square root and reciprocal (relative error ~2^-22): the backward's
-// per-row spans (widened by 0.02 pixel, far above that) and the SSIM map's
-// two quotients.
-__device__ __forceinline__ float sqrt_approx(float x) {
-    float y;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float rcp_approx(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {
