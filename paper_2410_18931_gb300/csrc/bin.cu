@@ -87,10 +87,11 @@ __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ rec, lon
         const float4 r2 = __ldg(rec + 3 * r + 2);
         if (pixel_rect(r0, r2, V, jx0, jx1, jy0, jy1)) {
             const float qs = r0.z, qw = r0.w;
-            const float A = fmaf(qw, qw, qd), ia = 1.0f / A;
-            const float dxm = sqrtf(QM / qd);                   // half-width of the ellipse
+            // hardware reciprocal and square root (relative error ~2^-22, far below the margin below)
+            const float A = fmaf(qw, qw, qd), ia = rcp_approx(A);
+            const float dxm = sqrt_approx(QM * rcp_approx(qd));  // half-width of the ellipse
             g0 = make_float4(r0.x, r0.y, qs * qw * ia, A * QM);
-            g1 = make_float4(qd * qs * qs, ia, -(qw / qs) * dxm, fminf(2e-3f * dxm, 1e6f) + 0.01f);
+            g1 = make_float4(qd * qs * qs, ia, -(qw * rcp_approx(qs)) * dxm, fminf(2e-3f * dxm, 1e6f) + 0.01f);
             const int pcs = ((jx1 >> lw) - (jx0 >> lw) + kPiece) / kPiece;
             nseg = ((jy1 >> lh) - (jy0 >> lh) + 1) * pcs;
         }
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ rec, lon
             const float dya = (float)max(ty << lh, rc.z) + 0.5f - a.y;
             const float dyb = (float)min(((ty + 1) << lh) - 1, rc.w) + 0.5f - a.y;
             auto edge = [&](float dy, float side) {
-                return fmaf(-a.z, dy, side * sqrtf(fmaxf(fmaf(-b.x * dy, dy, a.w), 0.0f)) * b.y);
+                return fmaf(-a.z, dy, side * sqrt_approx(fmaxf(fmaf(-b.x * dy, dy, a.w), 0.0f)) * b.y);
             };
             const float xr = edge(fminf(fmaxf(b.z, dya), dyb), 1.0f);
             const float xl = edge(fminf(fmaxf(-b.z, dya), dyb), -1.0f);
