@@ -612,7 +612,7 @@ def run_ours(args):
 
 def run_deterministic(S, scene, cam, weight, target, tile, persistent, chunk, flush, reps: int = 5) -> dict:
     """The same step in the deterministic mode (tile lists sorted by record
-    index, fixed-point gradient sums in two backward passes): its time, and
+    index, fixed-point gradient sums in one backward walk): its time, and
     whether two runs give the same bits.  The sort holds a bounded number of
     instances per tile; when a tile holds more, the leg takes 8x8 tiles."""
     import numpy as np

@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(128, ONE ? 3 : 1) k_project_bwd(const GaussPtr
                     any |= (g9[e] != 0.0f);
                 }
             } else {
-                // 9 int64 sums with kDetBits bits below the magnitude 2^e of their largest partial
+                // 9 int64 sums in units of 2^(e - kDetBits), 2^e above the term's bound (stored beside them)
                 const float* gr = grec + kDetRecordFloats * ((long long)v * g.n + i);
                 const long long* sums = reinterpret_cast<const long long*>(gr);
                 const int* mag = reinterpret_cast<const int*>(gr + 18);
