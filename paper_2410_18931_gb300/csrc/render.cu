@@ -338,12 +338,13 @@ __device__ __forceinline__ float warp_sum(float v) {
 //      counter per class), so that the groups of a warp walk for the same
 //      number of steps and the warps stay busy;
 //   C. a group of L consecutive lanes takes one Gaussian at a time and walks
-//      its rows one per step, L = TW / 4 for the wide class and TW / 8 for
-//      the narrow one (whose spans all fit in 4 L columns); lane k takes
-//      column pairs start / 2 + k + m L (m = 0, 1) of the row, so the lanes of
-//      a group read consecutive entries of each plane, four pixels per step
-//      from one decode of the row's span, every quantity of a column pair in
-//      one paired FP32 op.  The nine record terms stay in registers until
+//      its rows one per step, L = TW / (2 M) for the wide class and TW / (4 M)
+//      for the narrow one (whose spans all fit in 2 M L columns), M = 4 column
+//      pairs per lane and row (2 for 8-pixel-wide tiles); lane k takes column
+//      pairs start / 2 + k + m L (m < M) of the row, so the lanes of a group
+//      read consecutive entries of each plane, 2 M pixels per step from one
+//      decode of the row's span, every quantity of a column pair in one
+//      paired FP32 op.  The nine record terms stay in registers until
 //      the Gaussian's last row; then log2(L) shuffle steps sum them over the
 //      group and its first lane adds them to the Gaussian's global record (in
 //      the deterministic mode: as fixed point, in units that a per-Gaussian
@@ -372,6 +373,7 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
     constexpr int NB = TH + 1;                          // row counts 0 .. TH
     constexpr int NK = 2 * NB;                          // sort keys: narrow 0 .. TH, wide NB .. NB + TH
     static_assert(PASSES * NT == 2 * CH && TH % 4 == 0 && TW % 8 == 0 && TW <= 64 && CH <= 512 && NK <= NT, "layout");
+    constexpr int M = TW >= 16 ? 4 : 2;                 // column pairs per lane and row in step C
     // per pixel: G/D (3), -(G.C)/D, stored per column pair as (x0, x1, y0, y1) and (z0, z1, w0, w1)
     __shared__ float4 spA[PP * TH];
     __shared__ float4 spB[PP * TH];
@@ -545,8 +547,7 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 float2 srr = f2(0.f, 0.f), srx = srr, sxx = srr, sr = srr, sx = srr;
                 // dx of this lane's two column pairs (2 (k + m L), +1) from the row's even first column, less
                 // that column
-                const float2 gxo[2] = {__fadd2_rn(f2((float)(2 * gk), (float)(2 * gk + 1)), gx2),
-                                       __fadd2_rn(f2((float)(2 * (gk + L)), (float)(2 * (gk + L) + 1)), gx2)};
+                const float2 gxb = __fadd2_rn(f2((float)(2 * gk), (float)(2 * gk + 1)), gx2);
                 for (int st = 0; st < steps; ++st) {
                     const int ly = r0 + st;
                     const unsigned sp = sspan[j][ly];
@@ -554,15 +555,16 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                     const int rowb = ly * PP, pb = rowb + (xe >> 1), pe = rowb + TW / 2;
                     const float xsf = (float)xe;
                     const float rb = qs * ((float)ly + gy0);                     // qs dy
+                    const float2 xb = __fadd2_rn(f2(xsf, xsf), gxb);             // dx of the lane's first pair
                     const float2 rb2 = f2(rb, rb);
 #pragma unroll
-                    for (int m = 0; m < 2; ++m) {
+                    for (int m = 0; m < M; ++m) {
                         // Columns outside the span evaluate q > 9 (the span holds every pixel centre of the row
                         // with q' <= kQMax, with a margin), so the cutoff test zeroes them; pairs past the tile
                         // read the zero pair.  No per-pixel validity mask is needed.
                         const int pi = min(pb + gk + m * L, pe);
                         const float4 A = spA[pi], B = spB[pi];          // (x0, x1, y0, y1), (z0, z1, w0, w1)
-                        const float2 dx = __fadd2_rn(f2(xsf, xsf), gxo[m]);
+                        const float2 dx = m == 0 ? xb : __fadd2_rn(xb, f2((float)(2 * m * L), (float)(2 * m * L)));
                         const float2 rr = __ffma2_rn(qw2, dx, rb2);
                         const float2 q = __ffma2_rn(rr, rr, __fmul2_rn(__fmul2_rn(qd2, dx), dx));
                         const float2 e = f2(ex2_approx(q.x <= kQMax ? -q.x : -256.0f),      // 2^-256 flushes to 0
@@ -630,8 +632,8 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 }
             }
         };
-        walk(Lanes<TW / 4>(), 0, nwide, &snext[0]);        // the wide class
-        walk(Lanes<TW / 8>(), nwide, cnt, &snext[1]);      // the narrow class
+        walk(Lanes<TW / (2 * M)>(), 0, nwide, &snext[0]);        // the wide class
+        walk(Lanes<TW / (4 * M)>(), nwide, cnt, &snext[1]);      // the narrow class
     }
     __syncthreads();
     if (tid < 4) {
