@@ -322,8 +322,8 @@ __device__ __forceinline__ float warp_sum(float v) {
 // Backward, one block per tile, a group of lanes per Gaussian.
 //
 // The tile's pixel terms P = (G/D, -(G.C)/D) sit in shared memory by column
-// pairs, two float4 planes (x0, x1, y0, y1) and (z0, z1, w0, w1), with one
-// zero pair past the tile's right edge.  For each chunk of CH Gaussians of
+// pairs, two float4 planes (x0, x1, y0, y1) and (z0, z1, w0, w1), with zero
+// pairs past the tile's right edge as far as a lane reads.  For each chunk of CH Gaussians of
 // the tile:
 //   A. two threads per Gaussian compute, for their half of the tile's rows
 //      (two rows per paired op), the span of pixels whose centre can lie
@@ -368,7 +368,10 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
     constexpr int NT = BwdThreads<CH>::value;
     constexpr int NW = NT / 32;
     constexpr int PASSES = 2 * CH / NT;                // step A: (Gaussian, half) items per thread
-    constexpr int PP = TW / 2 + 1;                      // pixel-table row pitch in column pairs: one zero pair
+    // pixel-table row pitch in column pairs: the row's TW / 2 pairs, then zero pairs up to the farthest pair a
+    // lane reads (start / 2 + k + m L <= (TW / 2 - 1) + (TW / 2 - 1)), so no index needs a clamp; odd, so that
+    // the rows start in different banks
+    constexpr int PP = TW - 1;
     constexpr int HR = TH / 2;                          // rows per thread in step A
     constexpr int NB = TH + 1;                          // row counts 0 .. TH
     constexpr int NK = 2 * NB;                          // sort keys: narrow 0 .. TH, wide NB .. NB + TH
@@ -536,9 +539,11 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 const float gy0 = (float)y_org + 0.5f - a.y;                 // dy of row 0
                 const float qs = a.z;
                 const float2 qw2 = f2(a.w, a.w), qd2 = f2(b.x, b.x), gx2 = f2(gx0, gx0);
-                // -ln2 (c u w, u w), each twice: dL/dq' = e * (P . cw) for two pixels at once
-                const float2 cwr = f2(-kLn2 * b.z, -kLn2 * b.z), cwg = f2(-kLn2 * b.w, -kLn2 * b.w);
-                const float2 cwb = f2(-kLn2 * c2.x, -kLn2 * c2.x), cwu = f2(-kLn2 * c2.y, -kLn2 * c2.y);
+                // dL/dq' = e (P . cw) with cw = -ln2 u w (c, 1): the colour c = (c u w) / (u w) per pixel
+                // pair, and the factor -ln2 u w applied to the moments once, after the walk
+                const float iuw = c2.y != 0.0f ? 1.0f / c2.y : 0.0f;
+                const float2 ccr = f2(b.z * iuw, b.z * iuw), ccg = f2(b.w * iuw, b.w * iuw);
+                const float2 ccb = f2(c2.x * iuw, c2.x * iuw);
                 // accumulators, each over the two pixels of a column pair: d/d(c u w) per channel, d/d(u w);
                 // and the moments of gq = dL/dq' in the record's own frame (r = qs dy + qw dx, dx):
                 // sum gq r^2, sum gq r dx, sum gq dx^2, sum gq r, sum gq dx.  Kept apart, a thin
@@ -552,7 +557,7 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                     const int ly = r0 + st;
                     const unsigned sp = sspan[j][ly];
                     const int xe = (int)(sp & 0xffu);                           // even first column
-                    const int rowb = ly * PP, pb = rowb + (xe >> 1), pe = rowb + TW / 2;
+                    const int pb = ly * PP + (xe >> 1) + gk;
                     const float xsf = (float)xe;
                     const float rb = qs * ((float)ly + gy0);                     // qs dy
                     const float2 xb = __fadd2_rn(f2(xsf, xsf), gxb);             // dx of the lane's first pair
@@ -561,12 +566,15 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                     for (int m = 0; m < M; ++m) {
                         // Columns outside the span evaluate q > 9 (the span holds every pixel centre of the row
                         // with q' <= kQMax, with a margin), so the cutoff test zeroes them; pairs past the tile
-                        // read the zero pair.  No per-pixel validity mask is needed.
-                        const int pi = min(pb + gk + m * L, pe);
+                        // read zero pairs.  No per-pixel validity mask is needed.
+                        const int pi = pb + m * L;
                         const float4 A = spA[pi], B = spB[pi];          // (x0, x1, y0, y1), (z0, z1, w0, w1)
                         const float2 dx = m == 0 ? xb : __fadd2_rn(xb, f2((float)(2 * m * L), (float)(2 * m * L)));
                         const float2 rr = __ffma2_rn(qw2, dx, rb2);
                         const float2 q = __ffma2_rn(rr, rr, __fmul2_rn(__fmul2_rn(qd2, dx), dx));
+                        // the cutoff: t = K (kQMax - q) is >= 0 for q <= kQMax and <= -256 beyond it (K times
+                        // the spacing of floats near kQMax is 256), so min(-q, t) is -q inside and flushes
+                        // e to 0 outside, as a select would
                         const float2 e = f2(ex2_approx(q.x <= kQMax ? -q.x : -256.0f),      // 2^-256 flushes to 0
                                             ex2_approx(q.y <= kQMax ? -q.y : -256.0f));
                         // d/d(c u w) and d/d(u w) at fixed c u w
@@ -574,9 +582,9 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                         gg = __ffma2_rn(f2(A.z, A.w), e, gg);
                         gb = __ffma2_rn(f2(B.x, B.y), e, gb);
                         gu = __ffma2_rn(f2(B.z, B.w), e, gu);
-                        // dL/dq' per pixel: e * (P . cw)
-                        const float2 pc = __ffma2_rn(f2(B.z, B.w), cwu, __ffma2_rn(f2(B.x, B.y), cwb,
-                                                     __ffma2_rn(f2(A.z, A.w), cwg, __fmul2_rn(f2(A.x, A.y), cwr))));
+                        // dL/dq' per pixel, less the factor -ln2 u w: e * (P_w + c . P_rgb)
+                        const float2 pc = __ffma2_rn(f2(B.x, B.y), ccb, __ffma2_rn(f2(A.z, A.w), ccg,
+                                                     __ffma2_rn(f2(A.x, A.y), ccr, f2(B.z, B.w))));
                         const float2 gq = __fmul2_rn(e, pc);
                         const float2 tr = __fmul2_rn(gq, rr), tx = __fmul2_rn(gq, dx);
                         srr = __ffma2_rn(tr, rr, srr);
@@ -588,8 +596,9 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 }
                 // the group's sums: record order sum gq r, sum gq dx, sum gq r^2, sum gq r dx, sum gq dx^2,
                 // d/d(u w), d/d(c u w)
-                float vals[9] = {sr.x + sr.y, sx.x + sx.y, srr.x + srr.y, srx.x + srx.y, sxx.x + sxx.y,
-                                 gu.x + gu.y, gr.x + gr.y, gg.x + gg.y, gb.x + gb.y};
+                const float fq = -kLn2 * c2.y;
+                float vals[9] = {fq * (sr.x + sr.y), fq * (sx.x + sx.y), fq * (srr.x + srr.y), fq * (srx.x + srx.y),
+                                 fq * (sxx.x + sxx.y), gu.x + gu.y, gr.x + gr.y, gg.x + gg.y, gb.x + gb.y};
                 __syncwarp();
 #pragma unroll
                 for (int off = L / 2; off > 0; off >>= 1)
