@@ -572,9 +572,6 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                         const float2 dx = m == 0 ? xb : __fadd2_rn(xb, f2((float)(2 * m * L), (float)(2 * m * L)));
                         const float2 rr = __ffma2_rn(qw2, dx, rb2);
                         const float2 q = __ffma2_rn(rr, rr, __fmul2_rn(__fmul2_rn(qd2, dx), dx));
-                        // the cutoff: t = K (kQMax - q) is >= 0 for q <= kQMax and <= -256 beyond it (K times
-                        // the spacing of floats near kQMax is 256), so min(-q, t) is -q inside and flushes
-                        // e to 0 outside, as a select would
                         const float2 e = f2(ex2_approx(q.x <= kQMax ? -q.x : -256.0f),      // 2^-256 flushes to 0
                                             ex2_approx(q.y <= kQMax ? -q.y : -256.0f));
                         // d/d(c u w) and d/d(u w) at fixed c u w
