@@ -527,7 +527,7 @@ def run_ours(args):
             roof["frac_at_measured_clock"] = round(ach / (peak * float(clk["sm_mhz"]) / SM_MAX_MHZ), 4)
         if kern == "k_render_bwd":
             # what bounds it (from the kernel's ncu capture): not FP32 throughput
-            roof["note"] = ("bound by issue (~62% active) and the FMA pipe (~59% busy) at 32 resident warps per SM "
+            roof["note"] = ("bound by the FMA pipe (~58% busy) and issue (~61% active) at 32 resident warps per SM "
                             "(64 registers), then by the two barriers of each chunk; it evaluates 1.36 pixel slots "
                             "per pair (a lane covers eight columns from each row's first column), and the row "
                             "spans and the per-chunk sort take about a quarter of its time")
