@@ -443,7 +443,8 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
         for (int ps = 0; ps < PASSES; ++ps) {
             const int u = tid + ps * NT;
             const int gj = u >> 1, half = u & 1;
-            int row_lo = TH, row_hi = -1, umax = 0;
+            unsigned rows = 0u;                         // bit ly: row ly has a span
+            unsigned umax = 0u;                         // the most column pairs of a row's span
             if (gj < cnt) {
                 const unsigned r = list[base + gj];
                 const float4* pr = rec + 3ull * r;
@@ -457,33 +458,25 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                     sidx[gj] = r;
                 }
                 const RowSpans rs(a, b.x, QM);
-                int ly_lo, ly_hi;
-                rs.rows(a, y_org, half * HR, min(HR, y_lim - half * HR), ly_lo, ly_hi);
 #pragma unroll
                 for (int k = 0; k < HR; k += 2) {
                     const int ly = half * HR + k;
-                    unsigned sp2 = 0;
-                    if (ly + 1 >= ly_lo && ly <= ly_hi) sp2 = rs.row2(a, x_org, y_org, x_lim, ly);
-                    if (ly < ly_lo) sp2 &= 0xffff0000u;            // rows outside the footprint's reach
-                    if (ly + 1 > ly_hi) sp2 &= 0x0000ffffu;
+                    // rows the footprint does not reach have no span (no root: the square root's argument is
+                    // negative); rows past the image's last have none either
+                    unsigned sp2 = rs.row2(a, x_org, y_org, x_lim, ly);
+                    if (ly + 1 >= y_lim) sp2 = ly < y_lim ? sp2 & 0x0000ffffu : 0u;
                     *reinterpret_cast<unsigned*>(&sspan[gj][ly]) = sp2;
-#pragma unroll
-                    for (int t = 0; t < 2; ++t) {
-                        const unsigned sp = (sp2 >> (16 * t)) & 0xffffu;
-                        if (sp >> 8) {
-                            row_lo = min(row_lo, ly + t);
-                            row_hi = max(row_hi, ly + t);
-                            umax = max(umax, (int)(sp >> 8));
-                        }
-                    }
+                    rows |= ((sp2 & 0x0000ff00u) ? 1u : 0u) << ly;
+                    rows |= ((sp2 & 0xff000000u) ? 2u : 0u) << ly;
+                    umax = max(umax, max((sp2 >> 8) & 0xffu, sp2 >> 24));
                 }
             }
-            row_lo = min(row_lo, __shfl_xor_sync(0xffffffffu, row_lo, 1));      // the two halves of a Gaussian
-            row_hi = max(row_hi, __shfl_xor_sync(0xffffffffu, row_hi, 1));
+            rows |= __shfl_xor_sync(0xffffffffu, rows, 1);           // the two halves of a Gaussian
             umax = max(umax, __shfl_xor_sync(0xffffffffu, umax, 1));
+            const int row_lo = rows ? __ffs((int)rows) - 1 : TH, row_hi = rows ? 31 - __clz((int)rows) : -1;
             if (gj < cnt && half == 0) {
                 const int nst = row_hi >= row_lo ? row_hi - row_lo + 1 : 0;
-                const int key = nst + (2 * umax > TW / 2 ? NB : 0);     // wide: a span longer than TW / 2 pixels
+                const int key = nst + (2 * (int)umax > TW / 2 ? NB : 0);    // wide: a span longer than TW / 2 pixels
                 sfirst[gj] = (unsigned char)max(row_lo, 0);
                 snst[gj] = (unsigned char)nst;
                 skey[gj] = (unsigned char)key;
