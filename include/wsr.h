@@ -132,7 +132,8 @@ enum {
  * the render schedule and the backward's Gaussians per block.  With
  * WSR_SCHEDULE_PERSISTENT, wsr_bin also orders the tiles by decreasing
  * instance count (a bucketed longest-first order kept in the workspace) and
- * the render calls launch one block per resident slot that takes tiles from
+ * the render calls launch one block per resident slot (wsr_render_fwd: at
+ * most 16 warps per SM, the forward's fastest grid) that takes tiles from
  * that order through a counter in the workspace; the same workspace and tiles
  * must then be passed to wsr_bin and the renderers.  `chunk` is how many of a
  * tile's Gaussians one block of wsr_render_bwd takes at a time: 0 for the
