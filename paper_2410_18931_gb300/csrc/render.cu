@@ -323,8 +323,8 @@ __device__ __forceinline__ float warp_sum(float v) {
 //
 // The tile's pixel terms P = (G/D, -(G.C)/D) sit in shared memory by column
 // pairs, two float4 planes (x0, x1, y0, y1) and (z0, z1, w0, w1), with zero
-// pairs past the tile's right edge as far as a lane reads.  For each chunk of CH Gaussians of
-// the tile:
+// pairs past the tile's right edge as far as a lane reads.  For each chunk of
+// CH Gaussians of the tile:
 //   A. two threads per Gaussian compute, for their half of the tile's rows
 //      (two rows per paired op), the span of pixels whose centre can lie
 //      inside the footprint (the roots of q(dx) = 9 on each row, widened
@@ -532,8 +532,8 @@ __device__ __forceinline__ void bwd_tile(const int tile, const float4* __restric
                 const float gy0 = (float)y_org + 0.5f - a.y;                 // dy of row 0
                 const float qs = a.z;
                 const float2 qw2 = f2(a.w, a.w), qd2 = f2(b.x, b.x), gx2 = f2(gx0, gx0);
-                // dL/dq' = e (P . cw) with cw = -ln2 u w (c, 1): the colour c = (c u w) / (u w) per pixel
-                // pair, and the factor -ln2 u w applied to the moments once, after the walk
+                // dL/dq' = e (P . cw) with cw = -ln2 u w (c, 1): the walk uses the colour c = (c u w) / (u w)
+                // (in both halves of a pair) and applies the factor -ln2 u w to the moments once, after it
                 const float iuw = c2.y != 0.0f ? 1.0f / c2.y : 0.0f;
                 const float2 ccr = f2(b.z * iuw, b.z * iuw), ccg = f2(b.w * iuw, b.w * iuw);
                 const float2 ccb = f2(c2.x * iuw, c2.x * iuw);
